@@ -1,0 +1,584 @@
+// Scene state, incremental potential and the Newton / PN / PPN time step, FP64.
+//
+// TEST INFRASTRUCTURE (oracle).  One call of ora_scene_step is one backward
+// Euler step, solved as the minimisation of the incremental potential by
+// Newton's method (Sec. 3) in one of three modes:
+//   ORA_NEWTON  no element is projected (Sec. 1; Newton-CG fallback on ind)
+//   ORA_PN      every element Hessian is clamped before assembly (Sec. 3)
+//   ORA_PPN     Algorithm 1: start unprojected; while the solver reports
+//               indefiniteness, project the elements with ||S^e g||_inf > delta
+//               in place and solve again, tightening delta by alpha; relax it by
+//               beta after a successful solve (Sec. 4).
+// The step then takes a backtracking line search (Sec. 5.1) and updates x.
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "ppn_oracle.h"
+
+namespace ora {
+double det3x3(const double* M);
+void edge_matrix(const double* c, double* D);
+void bsr_spmv(int64_t n_rows, const int64_t* row_ptr, const int32_t* col, const double* vals,
+              const double* x, double* y);
+bool spd_inverse3(const double* D, double* Dinv);
+void pcg(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* vals,
+         const double* b, double rel_tol, int max_iter, double* x_out, int* info);
+}  // namespace ora
+
+static thread_local std::string g_err;
+
+struct ora_scene {
+  int64_t nv = 0, nt = 0;
+  std::vector<double> X;
+  std::vector<int32_t> tets;
+  double mu = 0, lam = 0, rho = 0, dt = 0, grav[3] = {0, 0, 0};
+  std::vector<double> mass;
+  std::vector<uint8_t> fixed;
+  std::vector<int32_t> fixed_list;
+  std::vector<double> targets;
+  std::vector<double> x, v;
+  std::vector<int64_t> row_ptr;
+  std::vector<int32_t> col;
+  ora_params p;
+  ora_solve_hook hook = nullptr;
+  void* hook_user = nullptr;
+  std::vector<ora_iter_stats> iters;
+  std::vector<ora_attempt> attempts;
+};
+
+namespace {
+
+const double kInf = std::numeric_limits<double>::infinity();
+
+void corners(const ora_scene* s, int64_t e, const double* x, double* c) {
+  for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 3; ++k) c[3 * a + k] = x[3 * (int64_t)s->tets[4 * e + a] + k];
+}
+
+void element(const ora_scene* s, int64_t e, const double* x, double* psi, double* g, double* H) {
+  double Xc[12], xc[12];
+  corners(s, e, s->X.data(), Xc);
+  corners(s, e, x, xc);
+  ora_tet_eval(Xc, xc, s->mu, s->lam, psi, g, H);
+}
+
+double energy(const ora_scene* s, const double* x, const double* xhat) {
+  double E = 0.0;
+  const double w = 0.5 / (s->dt * s->dt);
+  for (int64_t v = 0; v < s->nv; ++v) {
+    if (s->fixed[v]) continue;
+    double d2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const double d = x[3 * v + k] - xhat[3 * v + k];
+      d2 += d * d;
+    }
+    E += w * s->mass[v] * d2;
+  }
+  for (int64_t e = 0; e < s->nt; ++e) {
+    double psi;
+    element(s, e, x, &psi, nullptr, nullptr);
+    E += psi;
+  }
+  return E;
+}
+
+// g = M (x - xhat) / dt^2 + sum_e S^eT g^e, zero on Dirichlet vertices
+void gradient_from(const ora_scene* s, const double* x, const double* xhat,
+                   const std::vector<double>& ge, double* g) {
+  const double w = 1.0 / (s->dt * s->dt);
+  for (int64_t v = 0; v < s->nv; ++v)
+    for (int k = 0; k < 3; ++k) g[3 * v + k] = w * s->mass[v] * (x[3 * v + k] - xhat[3 * v + k]);
+  for (int64_t e = 0; e < s->nt; ++e)
+    for (int a = 0; a < 4; ++a)
+      for (int k = 0; k < 3; ++k) g[3 * (int64_t)s->tets[4 * e + a] + k] += ge[12 * e + 3 * a + k];
+  for (int64_t v = 0; v < s->nv; ++v)
+    if (s->fixed[v])
+      for (int k = 0; k < 3; ++k) g[3 * v + k] = 0.0;
+}
+
+int64_t find_block(const ora_scene* s, int32_t i, int32_t j) {
+  for (int64_t k = s->row_ptr[i]; k < s->row_ptr[i + 1]; ++k)
+    if (s->col[k] == j) return k;
+  return -1;
+}
+
+// vals += S^eT M12 S^e restricted to free rows and columns
+void scatter_element(const ora_scene* s, int64_t e, const double* M12, double* vals) {
+  for (int a = 0; a < 4; ++a) {
+    const int32_t i = s->tets[4 * e + a];
+    if (s->fixed[i]) continue;
+    for (int b = 0; b < 4; ++b) {
+      const int32_t j = s->tets[4 * e + b];
+      if (s->fixed[j]) continue;
+      double* blk = vals + 9 * find_block(s, i, j);
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) blk[3 * r + c] += M12[12 * (3 * a + r) + 3 * b + c];
+    }
+  }
+}
+
+// unprojected H = M / dt^2 + sum_e S^eT H^e S^e with Dirichlet rows eliminated
+void assemble(const ora_scene* s, const std::vector<double>& He, std::vector<double>& vals) {
+  vals.assign(9 * s->col.size(), 0.0);
+  for (int64_t e = 0; e < s->nt; ++e) scatter_element(s, e, &He[144 * e], vals.data());
+  const double w = 1.0 / (s->dt * s->dt);
+  for (int64_t v = 0; v < s->nv; ++v) {
+    double* blk = vals.data() + 9 * find_block(s, (int32_t)v, (int32_t)v);
+    for (int r = 0; r < 3; ++r) {
+      if (s->fixed[v])
+        blk[3 * r + r] = 1.0;
+      else
+        blk[3 * r + r] += w * s->mass[v];
+    }
+  }
+}
+
+// r_e = ||S^e g||_inf : largest assembled gradient entry over the element's DOFs
+double element_residual(const ora_scene* s, int64_t e, const double* g) {
+  double r = 0.0;
+  for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 3; ++k) r = std::fmax(r, std::fabs(g[3 * (int64_t)s->tets[4 * e + a] + k]));
+  return r;
+}
+
+int64_t select(const ora_scene* s, const double* g, double delta, const uint8_t* already,
+               uint8_t* out_new) {
+  int64_t n = 0;
+  for (int64_t e = 0; e < s->nt; ++e) {
+    out_new[e] = 0;
+    if (already && already[e]) continue;
+    if (element_residual(s, e, g) > delta || delta <= s->p.eps_delta) {
+      out_new[e] = 1;
+      ++n;
+    }
+  }
+  return n;
+}
+
+int pcg_max(const ora_scene* s) {
+  if (s->p.pcg_max_iter > 0) return s->p.pcg_max_iter;
+  return (int)std::max<int64_t>(1000, 3 * s->nv);
+}
+
+// preconditioned (or mass-scaled) negative gradient, used when a solve gives no usable iterate
+int fallback_direction(const ora_scene* s, const std::vector<double>& vals, const double* g,
+                       double* dx) {
+  std::vector<double> Pinv(9 * (size_t)s->nv);
+  bool spd = true;
+  for (int64_t v = 0; v < s->nv && spd; ++v)
+    spd = ora::spd_inverse3(vals.data() + 9 * find_block(s, (int32_t)v, (int32_t)v), &Pinv[9 * v]);
+  if (spd) {
+    for (int64_t v = 0; v < s->nv; ++v)
+      for (int a = 0; a < 3; ++a) {
+        double t = 0.0;
+        for (int c = 0; c < 3; ++c) t += Pinv[9 * v + 3 * a + c] * g[3 * v + c];
+        dx[3 * v + a] = -t;
+      }
+    return 2;
+  }
+  for (int64_t v = 0; v < s->nv; ++v)
+    for (int a = 0; a < 3; ++a)
+      dx[3 * v + a] = s->fixed[v] ? 0.0 : -(s->dt * s->dt / s->mass[v]) * g[3 * v + a];
+  return 3;
+}
+
+}  // namespace
+
+extern "C" {
+
+ora_params ora_default_params(void) {
+  ora_params p;
+  p.alpha = 0.5;
+  p.beta = 2.0;
+  p.eps_delta = 1e-12;
+  p.eig_eps = 1e-8;
+  p.pcg_rel_tol = 1e-4;
+  p.armijo_c = 1e-4;
+  p.pcg_max_iter = 0;
+  p.newton_max_iter = 100;
+  p.ls_max_halvings = 30;
+  p.tol_kind = 0;
+  p.init_guess = 0;
+  return p;
+}
+
+const char* ora_last_error(void) { return g_err.c_str(); }
+
+ora_scene* ora_scene_create(const double* rest, int64_t n_v, const int32_t* tets, int64_t n_t,
+                            double E, double nu, double rho, double dt, const double* gravity,
+                            const int32_t* fixed, int64_t n_fixed, const ora_params* params) {
+  if (n_v <= 0 || n_t <= 0 || !rest || !tets || !(dt > 0) || !(rho > 0) || !(E > 0) ||
+      !(nu > -1.0 && nu < 0.5)) {
+    g_err = "invalid argument";
+    return nullptr;
+  }
+  ora_scene* s = new ora_scene();
+  s->nv = n_v;
+  s->nt = n_t;
+  s->X.assign(rest, rest + 3 * n_v);
+  s->tets.assign(tets, tets + 4 * n_t);
+  ora_lame(E, nu, &s->mu, &s->lam);
+  s->rho = rho;
+  s->dt = dt;
+  for (int k = 0; k < 3; ++k) s->grav[k] = gravity ? gravity[k] : 0.0;
+  s->p = params ? *params : ora_default_params();
+
+  // orientation and degeneracy, lumped mass
+  s->mass.assign(n_v, 0.0);
+  for (int64_t e = 0; e < n_t; ++e) {
+    for (int a = 0; a < 4; ++a)
+      if (s->tets[4 * e + a] < 0 || s->tets[4 * e + a] >= n_v) {
+        g_err = "tet index out of range";
+        delete s;
+        return nullptr;
+      }
+    double Xc[12], D[9];
+    corners(s, e, s->X.data(), Xc);
+    ora::edge_matrix(Xc, D);
+    double det = ora::det3x3(D);
+    double hmax = 0.0;
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b) {
+        double l2 = 0.0;
+        for (int k = 0; k < 3; ++k) l2 += (Xc[3 * a + k] - Xc[3 * b + k]) * (Xc[3 * a + k] - Xc[3 * b + k]);
+        hmax = std::fmax(hmax, std::sqrt(l2));
+      }
+    if (std::fabs(det) <= 1e-14 * hmax * hmax * hmax) {
+      g_err = "degenerate tet " + std::to_string(e);
+      delete s;
+      return nullptr;
+    }
+    if (det < 0) {
+      std::swap(s->tets[4 * e + 2], s->tets[4 * e + 3]);
+      det = -det;
+    }
+    for (int a = 0; a < 4; ++a) s->mass[s->tets[4 * e + a]] += rho * (det / 6.0) / 4.0;
+  }
+  s->fixed.assign(n_v, 0);
+  for (int64_t f = 0; f < n_fixed; ++f) {
+    if (fixed[f] < 0 || fixed[f] >= n_v) {
+      g_err = "fixed index out of range";
+      delete s;
+      return nullptr;
+    }
+    s->fixed[fixed[f]] = 1;
+    s->fixed_list.push_back(fixed[f]);
+  }
+  for (int64_t v = 0; v < n_v; ++v)
+    if (!s->fixed[v] && !(s->mass[v] > 0)) {
+      g_err = "free vertex without incident tet";
+      delete s;
+      return nullptr;
+    }
+  s->targets.resize(3 * s->fixed_list.size());
+  for (size_t f = 0; f < s->fixed_list.size(); ++f)
+    for (int k = 0; k < 3; ++k) s->targets[3 * f + k] = s->X[3 * (int64_t)s->fixed_list[f] + k];
+  s->x = s->X;
+  s->v.assign(3 * n_v, 0.0);
+
+  // full symmetric block pattern: row i holds every j sharing a tet with i (and i)
+  std::vector<std::vector<int32_t>> nb(n_v);
+  for (int64_t e = 0; e < n_t; ++e)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) nb[s->tets[4 * e + a]].push_back(s->tets[4 * e + b]);
+  s->row_ptr.assign(n_v + 1, 0);
+  for (int64_t v = 0; v < n_v; ++v) {
+    nb[v].push_back((int32_t)v);
+    std::vector<int32_t>& r = nb[v];
+    // insertion sort + unique (plain)
+    for (size_t i = 1; i < r.size(); ++i)
+      for (size_t j = i; j > 0 && r[j - 1] > r[j]; --j) std::swap(r[j - 1], r[j]);
+    std::vector<int32_t> u;
+    for (int32_t c : r)
+      if (u.empty() || u.back() != c) u.push_back(c);
+    r.swap(u);
+    s->row_ptr[v + 1] = s->row_ptr[v] + (int64_t)r.size();
+    s->col.insert(s->col.end(), r.begin(), r.end());
+  }
+  return s;
+}
+
+void ora_scene_destroy(ora_scene* s) { delete s; }
+
+int64_t ora_scene_nnzb(const ora_scene* s) { return (int64_t)s->col.size(); }
+
+void ora_scene_pattern(const ora_scene* s, int64_t* row_ptr, int32_t* col) {
+  std::memcpy(row_ptr, s->row_ptr.data(), sizeof(int64_t) * s->row_ptr.size());
+  std::memcpy(col, s->col.data(), sizeof(int32_t) * s->col.size());
+}
+
+void ora_scene_tets(const ora_scene* s, int32_t* tets) {
+  std::memcpy(tets, s->tets.data(), sizeof(int32_t) * s->tets.size());
+}
+
+void ora_scene_lumped_mass(const ora_scene* s, double* m) {
+  std::memcpy(m, s->mass.data(), sizeof(double) * s->nv);
+}
+
+void ora_scene_set_params(ora_scene* s, const ora_params* p) { s->p = *p; }
+
+int ora_scene_set_targets(ora_scene* s, const double* xyz) {
+  std::memcpy(s->targets.data(), xyz, sizeof(double) * s->targets.size());
+  return ORA_OK;
+}
+
+void ora_scene_get_state(const ora_scene* s, double* x, double* v) {
+  if (x) std::memcpy(x, s->x.data(), sizeof(double) * 3 * s->nv);
+  if (v) std::memcpy(v, s->v.data(), sizeof(double) * 3 * s->nv);
+}
+
+void ora_scene_set_state(ora_scene* s, const double* x, const double* v) {
+  if (x) std::memcpy(s->x.data(), x, sizeof(double) * 3 * s->nv);
+  if (v) std::memcpy(s->v.data(), v, sizeof(double) * 3 * s->nv);
+}
+
+void ora_scene_xhat(const ora_scene* s, double* xhat) {
+  for (int64_t v = 0; v < s->nv; ++v)
+    for (int k = 0; k < 3; ++k)
+      xhat[3 * v + k] = s->x[3 * v + k] + s->dt * s->v[3 * v + k] + s->dt * s->dt * s->grav[k];
+}
+
+void ora_scene_set_solve_hook(ora_scene* s, ora_solve_hook hook, void* user) {
+  s->hook = hook;
+  s->hook_user = user;
+}
+
+double ora_scene_energy(const ora_scene* s, const double* x, const double* xhat) {
+  return energy(s, x, xhat);
+}
+
+void ora_scene_gradient(const ora_scene* s, const double* x, const double* xhat, double* g) {
+  std::vector<double> ge(12 * s->nt);
+  for (int64_t e = 0; e < s->nt; ++e) element(s, e, x, nullptr, &ge[12 * e], nullptr);
+  gradient_from(s, x, xhat, ge, g);
+}
+
+void ora_scene_element_eval(const ora_scene* s, const double* x, double* psi_e, double* ge,
+                            double* He) {
+  for (int64_t e = 0; e < s->nt; ++e)
+    element(s, e, x, psi_e ? psi_e + e : nullptr, ge ? ge + 12 * e : nullptr,
+            He ? He + 144 * e : nullptr);
+}
+
+void ora_scene_assemble(const ora_scene* s, const double* x, const uint8_t* proj, double* out) {
+  std::vector<double> He(144 * s->nt), vals;
+  for (int64_t e = 0; e < s->nt; ++e) element(s, e, x, nullptr, nullptr, &He[144 * e]);
+  assemble(s, He, vals);
+  if (proj) {
+    std::vector<double> dH(144);
+    for (int64_t e = 0; e < s->nt; ++e)
+      if (proj[e]) {
+        ora_clamp(12, &He[144 * e], s->p.eig_eps, nullptr, dH.data());
+        scatter_element(s, e, dH.data(), vals.data());
+      }
+  }
+  std::memcpy(out, vals.data(), sizeof(double) * vals.size());
+}
+
+int64_t ora_scene_select(const ora_scene* s, const double* g, double delta, const uint8_t* already,
+                         uint8_t* out_new) {
+  return select(s, g, delta, already, out_new);
+}
+
+void ora_scene_project(const ora_scene* s, const double* x, const int32_t* sel, int64_t n_sel,
+                       double* dH) {
+  double H[144];
+  for (int64_t i = 0; i < n_sel; ++i) {
+    element(s, sel[i], x, nullptr, nullptr, H);
+    ora_clamp(12, H, s->p.eig_eps, nullptr, dH + 144 * i);
+  }
+}
+
+int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_stats* out) {
+  if (mode < ORA_NEWTON || mode > ORA_PPN) return ORA_ERR_INVALID;
+  const int64_t nv = s->nv, nt = s->nt, N = 3 * nv;
+  const ora_params& p = s->p;
+  std::vector<double> xn = s->x, vn = s->v, xhat(N), g(N), dx(N), xt(N);
+  std::vector<double> He(144 * nt), ge(12 * nt), vals, dH(144);
+  std::vector<uint8_t> proj(nt), fresh(nt);
+  ora_scene_xhat(s, xhat.data());
+  std::vector<double>& x = s->x;
+  if (p.init_guess == 1)
+    for (int64_t v = 0; v < nv; ++v)
+      for (int k = 0; k < 3; ++k) x[3 * v + k] = xn[3 * v + k] + s->dt * vn[3 * v + k];
+  for (size_t f = 0; f < s->fixed_list.size(); ++f)
+    for (int k = 0; k < 3; ++k) x[3 * (int64_t)s->fixed_list[f] + k] = s->targets[3 * f + k];
+
+  s->iters.clear();
+  s->attempts.clear();
+  double delta = kInf;  // Algorithm 1, before the Newton loop
+  double g0 = -1.0;
+  int status = ORA_ERR_NEWTON_MAXITER;
+  int total_proj = 0, total_cg = 0, total_att = 0;
+
+  for (int k = 0; k < p.newton_max_iter; ++k) {
+    for (int64_t e = 0; e < nt; ++e) element(s, e, x.data(), nullptr, &ge[12 * e], &He[144 * e]);
+    gradient_from(s, x.data(), xhat.data(), ge, g.data());
+    double gn2 = 0.0, gninf = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+      gn2 += g[i] * g[i];
+      gninf = std::fmax(gninf, std::fabs(g[i]));
+    }
+    gn2 = std::sqrt(gn2);
+    if (!std::isfinite(gn2)) {
+      status = ORA_ERR_NONFINITE;
+      break;
+    }
+    if (k == 0) g0 = gn2;
+    if (p.tol_kind == 0 && gn2 <= tol * g0) {
+      status = ORA_OK;
+      break;
+    }
+
+    ora_iter_stats st;
+    std::memset(&st, 0, sizeof(st));
+    st.newton_iter = k;
+    st.grad_norm2 = gn2;
+    st.grad_norminf = gninf;
+
+    // unprojected H (PN: every element clamped before assembly)
+    assemble(s, He, vals);
+    std::fill(proj.begin(), proj.end(), 0);
+    int n_proj = 0;
+    if (mode == ORA_PN) {
+      for (int64_t e = 0; e < nt; ++e) {
+        ora_clamp(12, &He[144 * e], p.eig_eps, nullptr, dH.data());
+        scatter_element(s, e, dH.data(), vals.data());
+        proj[e] = 1;
+      }
+      n_proj = (int)nt;
+    }
+    std::vector<double> b(N);
+    for (int64_t i = 0; i < N; ++i) b[i] = -g[i];
+
+    int info[4];
+    int attempt = 0;
+    auto solve = [&](int n_new, double delta_used) {
+      ora::pcg(nv, s->row_ptr.data(), s->col.data(), vals.data(), b.data(), p.pcg_rel_tol,
+               pcg_max(s), dx.data(), info);
+      if (s->hook) {
+        const int o = s->hook(k, attempt, n_proj, s->hook_user);
+        if (o >= 0) info[1] = o;
+      }
+      ora_attempt a;
+      a.newton_iter = k;
+      a.attempt = attempt;
+      a.n_new_projected = n_new;
+      a.ind = info[1];
+      a.cg_iters = info[0];
+      a.delta = delta_used;
+      s->attempts.push_back(a);
+      st.pcg_attempts += 1;
+      st.cg_iters += info[0];
+      st.precond_fail = info[2];
+      ++attempt;
+      return info[1] != 0;
+    };
+
+    bool ind = solve(mode == ORA_PN ? (int)nt : 0, kInf);
+    bool fallback = ind && mode != ORA_PPN;
+    if (mode == ORA_PPN) {
+      while (ind) {
+        if (delta == kInf) delta = p.alpha * gninf;
+        const int64_t n_new = select(s, g.data(), delta, proj.data(), fresh.data());
+        for (int64_t e = 0; e < nt; ++e)
+          if (fresh[e]) {
+            ora_clamp(12, &He[144 * e], p.eig_eps, nullptr, dH.data());
+            scatter_element(s, e, dH.data(), vals.data());  // in-place update
+            proj[e] = 1;
+          }
+        n_proj += (int)n_new;
+        st.n_new_projected += (int)n_new;
+        if (n_new > 0) ind = solve((int)n_new, delta);  // unchanged matrix: same verdict
+        if (ind) {
+          if (n_proj == nt) {  // fully projected and still indefinite (rounding)
+            fallback = true;
+            break;
+          }
+          delta *= p.alpha;  // tighten
+        }
+      }
+      delta *= p.beta;  // relax
+    }
+    st.n_projected_total = n_proj;
+    st.delta = delta;
+    total_proj += n_proj;
+    total_cg += st.cg_iters;
+    total_att += st.pcg_attempts;
+
+    if (fallback) {
+      bool zero = true;
+      for (int64_t i = 0; i < N && zero; ++i) zero = (dx[i] == 0.0);
+      st.fallback = zero ? fallback_direction(s, vals, g.data(), dx.data()) : 1;
+    }
+    double dd = 0.0;
+    for (int64_t i = 0; i < N; ++i) dd += g[i] * dx[i];
+    if (!(dd < 0.0)) {
+      st.fallback = fallback_direction(s, vals, g.data(), dx.data());
+      dd = 0.0;
+      for (int64_t i = 0; i < N; ++i) dd += g[i] * dx[i];
+    }
+    st.dir_deriv = dd;
+
+    // backtracking line search for sufficient decrease (Armijo)
+    const double E0 = energy(s, x.data(), xhat.data());
+    st.energy = E0;
+    double gamma = 1.0, Et = 0.0;
+    bool ok = false;
+    for (int h = 0; h <= p.ls_max_halvings; ++h) {
+      for (int64_t i = 0; i < N; ++i) xt[i] = x[i] + gamma * dx[i];
+      Et = energy(s, xt.data(), xhat.data());
+      if (Et <= E0 + p.armijo_c * gamma * dd) {
+        ok = true;
+        st.ls_halvings = h;
+        break;
+      }
+      gamma *= 0.5;
+    }
+    if (!ok) {
+      st.ls_halvings = p.ls_max_halvings;
+      s->iters.push_back(st);
+      status = ORA_ERR_LINESEARCH;
+      break;
+    }
+    x = xt;
+    st.gamma = gamma;
+    st.energy_new = Et;
+    s->iters.push_back(st);
+    if (p.tol_kind == 1) {
+      double m = 0.0;
+      for (int64_t i = 0; i < N; ++i) m = std::fmax(m, std::fabs(gamma * dx[i]));
+      if (m / s->dt < tol) {
+        status = ORA_OK;
+        break;
+      }
+    }
+  }
+  for (int64_t i = 0; i < N; ++i) s->v[i] = (x[i] - xn[i]) / s->dt;
+  if (out_x) std::memcpy(out_x, x.data(), sizeof(double) * N);
+  if (out) {
+    out->newton_iters = (int)s->iters.size();
+    out->total_projections = total_proj;
+    out->total_cg_iters = total_cg;
+    out->total_attempts = total_att;
+    out->status = status;
+  }
+  return status;
+}
+
+int ora_scene_iter_stats(const ora_scene* s, ora_iter_stats* buf, int cap) {
+  const int n = (int)s->iters.size();
+  for (int i = 0; i < n && i < cap; ++i) buf[i] = s->iters[i];
+  return n;
+}
+
+int ora_scene_attempts(const ora_scene* s, ora_attempt* buf, int cap) {
+  const int n = (int)s->attempts.size();
+  for (int i = 0; i < n && i < cap; ++i) buf[i] = s->attempts[i];
+  return n;
+}
+
+}  // extern "C"
