@@ -1,0 +1,322 @@
+"""Benchmark: PPN vs PN time steps on the twisting beam (20x20x80 vertices,
+171,114 tets, E=1e6 Pa, nu=0.45, one end clamped, the other turned at 2 rad/s,
+dt=1/30 s, tol 1e-4 relative gradient norm, FP32 bulk + FP64 reductions).
+
+Prints ONE JSON line (rank 0).  A "step" is one backward-Euler time step: the
+whole per-Newton-iteration pipeline (element evaluation, gradient, assembly,
+PCG solves, PPN selection/projection/incremental update retries, line search,
+update) until convergence.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (a deliberately slow program) on a
+bounded sample of the same workload.  Multi-GPU runs are replicas (one scene
+per rank, no exchange).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {"workload": "twisting_beam_20x20x80", "n_verts": 32000, "n_tets": 171114, "E": 1e6,
+            "nu": 0.45, "dt": 1.0 / 30.0, "omega_rad_s": 2.0, "tol": 1e-4, "tol_kind": "||g||2<=tol*||g0||2",
+            "precision": "mixed: fp32 hessian/eigen/bsr/pcg, fp64 energy/gradient/norms/update"}
+
+
+def build_spec():
+    from ppn_inputs import twisting_beam_scene
+
+    return twisting_beam_scene(20, 20, 80, h=0.01, E=1e6, nu=0.45, omega=2.0, dt=1.0 / 30.0, seed=0)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q
+    f, c = math.floor(k), math.ceil(k)
+    return xs[f] if f == c else xs[f] + (xs[c] - xs[f]) * (k - f)
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def pcg_bytes_per_iter(info, fsize=4):
+    # algorithmic bytes of one CG iteration: BSR values + column index per block;
+    # per row: row pointer, gathered z and d_prev, written d and q (phase A),
+    # d, q, x, r, P^-1 read and x, r, z written (phase B); vectors are 16-byte float4
+    nnzb, nv = info["nnzb"], info["n_verts"]
+    return nnzb * (9 * fsize + 4) + nv * (4 + 4 * 16 + 4 * 16 + 9 * fsize + 3 * 16)
+
+
+def run_ours(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    import paper_2505_21013_gb300 as P
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    spec = build_spec()
+    total = args.warmup + args.steps
+    # all steps' Dirichlet targets resident in HBM before the timed region
+    tg = torch.tensor(np.stack([spec.targets_at(n) for n in range(total)]), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    stream = torch.cuda.Stream(device=dev)
+
+    def run_mode(mode, profile):
+        sc = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
+        sc.set_stream(stream.cuda_stream)
+        info = sc.info()
+        lat, stats, iters = [], [], []
+        for n in range(total):
+            timed = n >= args.warmup
+            if timed and n == args.warmup:
+                if dist:
+                    dist.barrier()
+                torch.cuda.synchronize()
+                if profile:
+                    sc.set_profiling(True)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            sc.set_targets_device(tg[n].data_ptr())
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            rc, _, st = sc.step(mode, WORKLOAD["tol"], want_x=False)
+            ev1.record(stream)
+            if rc != 0:
+                raise RuntimeError(f"step {n} returned status {rc}")
+            if timed:
+                ev1.synchronize()
+                lat.append(ev0.elapsed_time(ev1))
+                stats.append(st)
+                iters.append(sc.iter_stats())
+        torch.cuda.synchronize()
+        kt = sc.kernel_times() if profile else None
+        attempts_cg = sum(it["cg_iters"] for its in iters for it in its)
+        sc.close()
+        return lat, stats, kt, info, attempts_cg
+
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
+    sampler.start()
+    lat_ppn, st_ppn, kt, info, cg_total = run_mode(P.MODE_PPN, True)
+    lat_pn, st_pn, _, _, _ = run_mode(P.MODE_PN, False)
+    clocks = sampler.stop()
+
+    # end-to-end through the public API with host buffers: targets H2D and
+    # positions D2H inside the timed region every step
+    sc = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
+    out = np.empty((spec.n_verts, 3))
+    e2e_ms = []
+    for n in range(total):
+        t0 = time.perf_counter()
+        sc.set_targets(spec.targets_at(n))
+        rc, x, _ = sc.step(P.MODE_PPN, WORKLOAD["tol"], want_x=True)
+        out[:] = x
+        t1 = time.perf_counter()
+        if n >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+    sc.close()
+
+    ms_ppn = sum(lat_ppn)
+    ms_pn = sum(lat_pn)
+    vals = torch.tensor([ms_ppn, ms_pn, sum(e2e_ms)], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms_ppn, ms_pn, ms_e2e = vals.tolist()
+    K = args.steps
+    value = world * K / (ms_ppn / 1e3)
+
+    # roofline of the dominant kernel family (by summed device time)
+    peaks = measured_peaks()
+    dom = max(kt.items(), key=lambda kv: kv[1]["total_ms"])
+    name, rec = dom
+    roof = None
+    if name == "pcg" and rec["launches"]:
+        bpi = pcg_bytes_per_iter(info)
+        setup = info["n_verts"] * (36 + 36 + 32 + 4 * 16)
+        alg_bytes = (cg_total * bpi + rec["launches"] * setup) / rec["launches"]
+        avg_s = rec["total_ms"] / rec["launches"] / 1e3
+        achieved = alg_bytes / avg_s / 1e9
+        peak = peaks["hbm_gbs"] if peaks else 6800.0
+        roof = {"bound": "hbm", "kernel": "k_pcg (cooperative block-Jacobi PCG)", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
+                "bytes_per_launch": alg_bytes, "avg_launch_ms": rec["total_ms"] / rec["launches"],
+                "cg_iters_per_launch": cg_total / rec["launches"],
+                "note": "working set of one solve (~25 MB) stays L2-resident across CG iterations"}
+    launches = int(sum(v["launches"] for v in kt.values()))
+    return {
+        "value": value, "ms_per_step": ms_ppn / K,
+        "p50_ms": percentile(lat_ppn, 0.5), "p99_ms": percentile(lat_ppn, 0.99),
+        "pn": {"steps_per_s": world * K / (ms_pn / 1e3), "ms_per_step": ms_pn / K,
+               "p50_ms": percentile(lat_pn, 0.5), "p99_ms": percentile(lat_pn, 0.99),
+               "newton_iters": sum(s["newton_iters"] for s in st_pn),
+               "projections": sum(s["total_projections"] for s in st_pn),
+               "cg_iters": sum(s["total_cg_iters"] for s in st_pn)},
+        "ppn": {"newton_iters": sum(s["newton_iters"] for s in st_ppn),
+                "projections": sum(s["total_projections"] for s in st_ppn),
+                "cg_iters": sum(s["total_cg_iters"] for s in st_ppn),
+                "attempts": sum(s["total_attempts"] for s in st_ppn)},
+        "speedup_ppn_vs_pn": ms_pn / ms_ppn,
+        "kernel_ms": {k: round(v["total_ms"], 3) for k, v in kt.items()},
+        "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+        "e2e": {"value": world * K / (ms_e2e / 1e3), "unit": "steps/s",
+                "h2d_bytes_per_step": int(spec.fixed.size * 24), "d2h_bytes_per_step": int(spec.n_verts * 24)},
+    }
+
+
+def oracle_sample(max_seconds=25.0):
+    """Time the FP64 oracle on the first PPN steps of the same beam (bounded)."""
+    from oracle import oracle as O
+
+    spec = build_spec()
+    sc = O.Scene.from_spec(spec)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        sc.set_targets(spec.targets_at(n))
+        sc.step(O.PPN, WORKLOAD["tol"])
+        n += 1
+        if time.perf_counter() - t0 > max_seconds or n >= 3:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} PPN time steps of the 20x20x80 twisting beam, single-threaded FP64"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+
+    base = {"metric": "time steps/s (PPN, twisting beam) with p50/p99 step latency, PPN vs PN at matched Newton tol",
+            "unit": "steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded Kuhn-grid beam; paper meshes unavailable)",
+            "config": dict(WORKLOAD, l2="flushed between steps (256 MB write)",
+                           parallelism="replicas" if args.gpus > 1 else "single")}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        per_step = []
+        from oracle import oracle as O
+
+        spec = build_spec()
+        sc = O.Scene.from_spec(spec)
+        for n in range(args.warmup):
+            pass  # the oracle has no warm-up effects; warm-up steps are not run to bound the time
+        t_all = time.perf_counter()
+        for n in range(args.steps):
+            t0 = time.perf_counter()
+            sc.set_targets(spec.targets_at(n))
+            sc.step(O.PPN, WORKLOAD["tol"])
+            per_step.append(time.perf_counter() - t0)
+            if time.perf_counter() - t_all > 150:
+                break
+        k = len(per_step)
+        v = k / sum(per_step)
+        line = dict(base, impl="reference", value=v, ms_per_step=1e3 * sum(per_step) / k,
+                    steps=k, p50_ms=1e3 * percentile(per_step, 0.5), p99_ms=1e3 * percentile(per_step, 0.99),
+                    cpu_baseline={"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                                  "sample": f"first {k} PPN steps of the beam (bounded to ~150 s)"},
+                    e2e={"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
+        print(json.dumps(line))
+        return
+
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl")
+        dist = tdist
+    r = run_ours(args, rank, world, dist)
+    if rank == 0:
+        line = dict(base, **r)
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = oracle_sample()
+        elif not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_sample() if rank == 0 else None
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * ppn.h — C ABI of the GB300 (sm_103a) Progressively Projected Newton library.
+ *
+ * The library advances implicit-Euler tetrahedral FEM scenes by one time step
+ * per call, minimising the incremental potential with Newton's method in one
+ * of three modes (arXiv 2505.21013):
+ *   PPN_MODE_NEWTON  no element Hessian is projected            (Sec. 1, Sec. 3)
+ *   PPN_MODE_PN      every element Hessian is clamped           (Sec. 3, "Projected Newton")
+ *   PPN_MODE_PPN     Algorithm 1: elements with ||S^e g||_inf > delta are
+ *                    clamped in place only after the linear solver reports
+ *                    indefiniteness; delta tightens by alpha, relaxes by beta (Sec. 4)
+ * Every step of the per-iteration pipeline runs in this library's CUDA kernels.
+ *
+ * Conventions shared by every entry point:
+ *   - Host pointers unless a name ends in _device.  Inputs are copied; the
+ *     library keeps no caller pointer after a call returns.
+ *   - Positions and velocities are (n_verts, 3) row-major doubles; tets are
+ *     (n_tets, 4) int32, 0-based.  Tet orientation is normalised at creation
+ *     (two corners swapped when det[x1-x0, x2-x0, x3-x0] < 0).
+ *   - Every call returns a ppn_status; the library never aborts.  On failure
+ *     ppn_last_error() (thread-local) holds a one-line reason.  Device waits
+ *     inside kernels are bounded and report PPN_ERR_TIMEOUT.
+ *   - A scene owns its device memory (cudaMalloc at creation, cudaFree at
+ *     destruction) and runs on its own stream unless ppn_set_stream is called.
+ *   - Not thread-safe per scene: calls on one scene must not overlap.
+ */
+#ifndef PPN_H
+#define PPN_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PPN_API __attribute__((visibility("default")))
+#else
+#define PPN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ppn_scene ppn_scene;
+
+typedef enum {
+  PPN_OK = 0,
+  PPN_ERR_INVALID_ARG = 1,
+  PPN_ERR_OOM = 2,
+  PPN_ERR_CUDA = 3,
+  PPN_ERR_DEGENERATE_TET = 4,
+  PPN_ERR_LINESEARCH = 5,
+  PPN_ERR_NEWTON_MAXITER = 6,
+  PPN_ERR_PCG_MAXITER = 7,
+  PPN_ERR_NONFINITE = 8,
+  PPN_ERR_TIMEOUT = 9,
+  PPN_ERR_ADMISSION = 10
+} ppn_status;
+
+typedef enum { PPN_MODE_NEWTON = 0, PPN_MODE_PN = 1, PPN_MODE_PPN = 2 } ppn_mode;
+
+/* FP64: every step in double.  MIXED: element Hessians, eigensolves, the BSR
+ * matrix and PCG in float; element energies, the assembled gradient and its
+ * norms, dot products, line-search sums and the position update in double. */
+typedef enum { PPN_PREC_FP64 = 0, PPN_PREC_MIXED = 1 } ppn_precision;
+
+typedef struct {
+  double E;   /* Young's modulus [Pa] */
+  double nu;  /* Poisson ratio, (-1, 0.5) */
+  double rho; /* density [kg/m^3] */
+} ppn_material;
+
+typedef struct {
+  double alpha;        /* delta tightening factor, Sec. 4 (default 0.5) */
+  double beta;         /* delta release factor, Sec. 4 (default 2) */
+  double eps_delta;    /* project every element once delta <= eps_delta (1e-12) */
+  double eig_eps;      /* eigenvalue clamp, Sec. 5.1 (1e-8) */
+  double pcg_rel_tol;  /* PCG stop at ||r|| <= tol ||r0||, Sec. 5.1 (1e-4) */
+  double armijo_c;     /* sufficient-decrease constant (1e-4) */
+  double gravity[3];   /* (0, -9.81, 0) */
+  int pcg_max_iter;    /* 0: max(1000, 3 n_verts) */
+  int newton_max_iter; /* 100 */
+  int ls_max_halvings; /* 30 */
+  int precision;       /* ppn_precision (PPN_PREC_MIXED) */
+  int tol_kind;        /* 0: ||g||_2 <= tol ||g0||_2 ; 1: ||gamma dx||_inf / dt < tol (Sec. 5.1) */
+  int init_guess;      /* 0: x_n ; 1: x_n + dt v_n */
+} ppn_params;
+
+typedef struct {
+  int newton_iter;
+  int pcg_attempts;      /* solves in this iteration (1 + PPN retries) */
+  int cg_iters;          /* CG iterations summed over those solves */
+  int n_new_projected;   /* elements projected in this iteration */
+  int n_projected_total; /* |H_p| at the end of the iteration */
+  int ls_halvings;
+  int fallback;          /* 0 none, 1 last CG iterate, 2 preconditioned gradient, 3 mass-scaled gradient */
+  int precond_fail;      /* the last solve's block-Jacobi setup met a non-SPD diagonal block */
+  double grad_norm2;
+  double grad_norminf;
+  double delta;          /* after the relax step */
+  double gamma;
+  double energy;         /* incremental potential at the start of the iteration */
+  double energy_new;     /* after the update */
+  double dir_deriv;      /* g^T dx */
+} ppn_iter_stats;
+
+typedef struct {
+  int newton_iter;
+  int attempt;           /* 0 = first solve on the unprojected matrix */
+  int n_new_projected;
+  int ind;               /* the solver reported indefiniteness */
+  int cg_iters;
+  double delta;          /* delta of the selection before this solve (inf for attempt 0) */
+} ppn_attempt;
+
+typedef struct {
+  int newton_iters;
+  int total_projections;
+  int total_cg_iters;
+  int total_attempts;
+  int status;            /* ppn_status of the step */
+  double final_grad_norm2;
+  double device_ms;      /* stream time between the step's first and last kernel */
+} ppn_step_stats;
+
+typedef struct {
+  int64_t n_verts, n_tets, n_fixed, nnzb, n_map;
+  int64_t device_bytes;  /* device memory owned by the scene */
+  int precision;
+} ppn_scene_info;
+
+/* Per kernel family: launches and summed device time (CUDA events on the scene
+ * stream) since the last reset; filled only while profiling is on. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+  double bytes;          /* algorithmic bytes moved by those launches */
+} ppn_kernel_time;
+
+PPN_API ppn_params ppn_default_params(void);
+PPN_API const char* ppn_status_string(ppn_status s);
+PPN_API const char* ppn_last_error(void);
+
+/* Scene creation (problem statement of Sec. 3 with the backward-Euler
+ * incremental potential of Sec. 2.1/5.1).  rest_xyz: n_verts*3 rest positions
+ * (also the initial state, zero velocity); tets: n_tets*4; fixed: n_fixed
+ * Dirichlet vertex indices (targets default to their rest positions).
+ * params NULL = defaults.  Errors: INVALID_ARG (sizes, indices, material),
+ * DEGENERATE_TET (|det| <= 1e-14 h^3), OOM, CUDA. */
+PPN_API ppn_status ppn_create_scene(const double* rest_xyz, int64_t n_verts, const int32_t* tets,
+                            int64_t n_tets, const ppn_material* mat, double dt,
+                            const int32_t* fixed, int64_t n_fixed, const ppn_params* params,
+                            ppn_scene** out);
+PPN_API void ppn_destroy_scene(ppn_scene* s);
+PPN_API ppn_status ppn_scene_get_info(const ppn_scene* s, ppn_scene_info* out);
+
+/* Use a caller stream (a cudaStream_t passed as void*); NULL = the scene's own. */
+PPN_API ppn_status ppn_set_stream(ppn_scene* s, void* cuda_stream);
+
+/* Dirichlet targets for the next step, n_fixed*3 doubles in the order of `fixed`. */
+PPN_API ppn_status ppn_set_kinematic_targets(ppn_scene* s, const double* xyz_of_fixed);
+PPN_API ppn_status ppn_set_kinematic_targets_device(ppn_scene* s, const double* xyz_of_fixed_device);
+
+/* One backward-Euler step (Algorithm 1 for PPN).  tol: see params.tol_kind.
+ * out_xyz: n_verts*3 host buffer for the new positions, or NULL.  out: may be NULL.
+ * Returns the step status (also in out->status); the state advances even on
+ * NEWTON_MAXITER (last iterate kept). */
+PPN_API ppn_status ppn_step(ppn_scene* s, ppn_mode mode, double tol, double* out_xyz,
+                    ppn_step_stats* out);
+
+/* Same step for several scenes advanced together: every kernel of a phase is
+ * one launch over all scenes that are still iterating.  All scenes must share
+ * the precision.  out: n entries or NULL.  Returns the first non-OK status. */
+PPN_API ppn_status ppn_step_batch(ppn_scene* const* scenes, int n, const ppn_mode* modes, double tol,
+                          ppn_step_stats* out);
+
+PPN_API ppn_status ppn_get_iter_stats(const ppn_scene* s, ppn_iter_stats* buf, int cap, int* n_written);
+PPN_API ppn_status ppn_get_attempts(const ppn_scene* s, ppn_attempt* buf, int cap, int* n_written);
+PPN_API ppn_status ppn_get_state(const ppn_scene* s, double* x, double* v);
+PPN_API ppn_status ppn_set_state(ppn_scene* s, const double* x, const double* v);
+/* Exact checkpoint of the internal state: displacement u = x - rest and
+ * velocity, n_verts*3 doubles each (either may be NULL).  Restoring it and
+ * stepping reproduces an uninterrupted run bit for bit. */
+PPN_API ppn_status ppn_get_displacement(const ppn_scene* s, double* u, double* v);
+PPN_API ppn_status ppn_set_displacement(ppn_scene* s, const double* u, const double* v);
+
+PPN_API ppn_status ppn_set_profiling(ppn_scene* s, int on);
+PPN_API ppn_status ppn_get_kernel_times(const ppn_scene* s, ppn_kernel_time* buf, int cap, int* n_written);
+
+/* ---- stage probes: run one stage of the pipeline on caller data (host
+ * buffers) through the scene's kernels, leaving the scene's state unchanged.
+ * Used by the parity tests; all outputs are widened to double. ---- */
+
+/* psi_e: n_tets element energies (FP64 kernel); ge: n_tets*12 element
+ * gradients; He: n_tets*144 element Hessians (12x12 row-major, vertex-major
+ * DOF order 3a+k).  Any output may be NULL. */
+PPN_API ppn_status ppn_probe_elements(ppn_scene* s, const double* x, double* psi_e, double* ge,
+                              double* He);
+/* assembled gradient (zero on Dirichlet vertices), norms[0] = ||g||_2, norms[1] = ||g||_inf,
+ * energy = incremental potential at x (any output may be NULL) */
+PPN_API ppn_status ppn_probe_gradient(ppn_scene* s, const double* x, const double* xhat, double* g,
+                              double* norms, double* energy);
+/* BSR pattern: row_ptr (n_verts+1), col (nnzb) */
+PPN_API ppn_status ppn_probe_pattern(const ppn_scene* s, int64_t* row_ptr, int32_t* col);
+/* assembled matrix at x: vals nnzb*9 (3x3 row-major blocks); proj: n_tets flags
+ * (NULL = none) of elements that enter projected */
+PPN_API ppn_status ppn_probe_assemble(ppn_scene* s, const double* x, const uint8_t* proj, double* vals);
+/* K4 selection on a given assembled gradient g (n_verts*3) */
+PPN_API ppn_status ppn_probe_select(ppn_scene* s, const double* g, double delta, const uint8_t* already,
+                            uint8_t* out_new, int64_t* n_new);
+/* K5 clamping updates dH^e = Hhat^e - H^e (n_sel*144) of the listed elements at x */
+PPN_API ppn_status ppn_probe_project(ppn_scene* s, const double* x, const int32_t* sel, int64_t n_sel,
+                             double* dH);
+/* block-Jacobi PCG on the scene's pattern with values vals (nnzb*9) and right-hand
+ * side b (n_verts*3); info: [iterations, ind, precond_fail, hit_max] */
+PPN_API ppn_status ppn_probe_pcg(ppn_scene* s, const double* vals, const double* b, double rel_tol,
+                         int max_iter, double* x, int* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPN_H */

@@ -1,0 +1,12 @@
+"""GB300 (sm_103a) Progressively Projected Newton: per-Newton-iteration element
+pipeline of implicit-Euler tetrahedral FEM as hand-written CUDA kernels behind a
+C ABI (``include/ppn.h``).  ``ppn`` is the ctypes binding; ``build`` compiles
+``libppn.so`` in-tree.
+"""
+
+from . import ppn  # noqa: F401
+from .ppn import (MODE_NEWTON, MODE_PN, MODE_PPN, PREC_FP64, PREC_MIXED, PPNError, Scene,  # noqa: F401
+                  ppn_default_params, ppn_step_batch)
+
+__all__ = ["ppn", "Scene", "PPNError", "ppn_default_params", "ppn_step_batch", "MODE_NEWTON", "MODE_PN",
+           "MODE_PPN", "PREC_FP64", "PREC_MIXED"]

@@ -1,0 +1,526 @@
+// Element, assembly, selection, projection and vector kernels of one Newton
+// iteration (everything except the PCG solve, which lives in pcg.cu).
+//
+//   k_element   per tet: displacement gradient, stress, g^e (12) and the ten
+//               3x3 Hessian blocks H^e_ab, a <= b (Sec. 3, Eq. newton terms)
+//   k_gradient  per vertex: g_v = m_v/dt^2 (u_v - uhat_v) + sum_e g^e (FP64),
+//               |g_v|_inf for the selection, ||g||_2^2 and ||g||_inf reductions
+//   k_assemble  per BSR block: H_ij = sum of H^e contributions (+ dH^e of the
+//               elements projected before assembly, + m_i/dt^2 I on the diagonal),
+//               Dirichlet rows/columns eliminated; atomic-free via a
+//               precomputed block -> (tet, a, b) map (Sec. 4.1 assembly)
+//   k_select    per tet: r_e = max over corners of |g_v|_inf, selected when
+//               r_e > delta or delta <= eps_delta and not yet projected
+//               (Sec. 4, Algorithm 1); warp-aggregated compaction
+//   k_project   per selected tet: clamped update dH^e (Sec. 3 clamping)
+//   k_update    per BSR block touched by newly projected tets: H_ij += dH^e_ab,
+//               the in-place incremental update of Sec. 4.1
+//   k_energy    per tet and per vertex: incremental potential at u + gamma dx
+//               and g^T dx, FP64 sums (line search, Sec. 5.1)
+//   small vector kernels: predictor, position update, velocity, fallback direction
+#include "common.cuh"
+#include "eigclamp.cuh"
+#include "kernels.h"
+
+namespace ppn {
+
+template <typename T>
+__device__ __forceinline__ void load_tetc(const T* tetc, int e, T* W, T& V, T& mu, T& lam) {
+  const T* p = tetc + (size_t)e * TETC_STRIDE;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) W[k] = p[k];
+  V = p[9];
+  mu = p[10];
+  lam = p[11];
+}
+template <>
+__device__ __forceinline__ void load_tetc<float>(const float* tetc, int e, float* W, float& V,
+                                                 float& mu, float& lam) {
+  const float4* p = reinterpret_cast<const float4*>(tetc + (size_t)e * TETC_STRIDE);
+  const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+  W[0] = a.x; W[1] = a.y; W[2] = a.z; W[3] = a.w;
+  W[4] = b.x; W[5] = b.y; W[6] = b.z; W[7] = b.w;
+  W[8] = c.x; V = c.y; mu = c.z; lam = c.w;
+}
+
+__device__ __forceinline__ void load_u(const double4* U, int v, double* out) {
+  const double4 a = ld_d4(U + v);
+  out[0] = a.x;
+  out[1] = a.y;
+  out[2] = a.z;
+}
+
+// ---------------------------------------------------------------- K1 element
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_element(const SceneDev<T>* scenes, const TileRef* tiles,
+                                                  int use_probe) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int e = tr.tile * TILE + threadIdx.x;
+  if (e >= S.nt) return;
+  const int4 t = S.tets[e];
+  const double4* U = use_probe ? S.u_probe : S.u;
+  double u[4][3];
+  load_u(U, t.x, u[0]);
+  load_u(U, t.y, u[1]);
+  load_u(U, t.z, u[2]);
+  load_u(U, t.w, u[3]);
+  T W[9], V, mu, lam;
+  load_tetc(S.tetc, e, W, V, mu, lam);
+  T H[9];
+  disp_grad(u[0], u[1], u[2], u[3], W, H);
+  TetState<T> st;
+  tet_state(H, mu, lam, st);
+  T P[9];
+  snh_pk1_disp(st, mu, lam, P);
+  T dN[4][3];
+  shape_grads(W, dN);
+  T* ge = S.ge + (size_t)e * GE_STRIDE;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    T pa[3];
+    matvec3(P, dN[a], pa);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ge[3 * a + k] = V * pa[k];
+  }
+  T cN[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) matvec3(st.C, dN[a], cN[a]);
+  T* he = S.He + (size_t)e * HE_STRIDE;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = a; b < 4; ++b) {
+      T blk[9];
+      hess_block(st, V, mu, lam, dN[a], dN[b], cN[a], cN[b], blk);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) he[9 * tri4(a, b) + k] = blk[k];
+    }
+}
+
+// ------------------------------------------------------------- K2 gradient
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_gradient(const SceneDev<T>* scenes, const TileRef* tiles,
+                                                   int use_probe) {
+  __shared__ double sm[32];
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int v = tr.tile * TILE + threadIdx.x;
+  double n2 = 0.0, ninf = 0.0;
+  if (v < S.nv) {
+    double g[3] = {0.0, 0.0, 0.0};
+    if (!S.fixed[v]) {
+      const double4* U = use_probe ? S.u_probe : S.u;
+      const double4 uv = ld_d4(U + v), uh = ld_d4(S.uhat + v);
+      const double w = S.mass[v] * S.inv_dt2;
+      g[0] = w * (uv.x - uh.x);
+      g[1] = w * (uv.y - uh.y);
+      g[2] = w * (uv.z - uh.z);
+      for (int c = S.vt_ptr[v]; c < S.vt_ptr[v + 1]; ++c) {
+        const int src = S.vt_src[c];
+        const T* ge = S.ge + (size_t)(src >> 2) * GE_STRIDE + 3 * (src & 3);
+        g[0] += (double)ge[0];
+        g[1] += (double)ge[1];
+        g[2] += (double)ge[2];
+      }
+    }
+    st_d4(S.g + v, make_double4(g[0], g[1], g[2], 0.0));
+    const double m = fmax(fabs(g[0]), fmax(fabs(g[1]), fabs(g[2])));
+    S.gmax[v] = m;
+    n2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    ninf = m;
+  }
+  const double s = block_sum<TILE>(n2, sm);
+  const double mx = block_max<TILE>(ninf, sm);
+  if (threadIdx.x == 0) {
+    S.vpart[4 * tr.tile + 0] = s;
+    S.vpart[4 * tr.tile + 1] = mx;
+  }
+  finish_reduction<TILE, 2>(S.vpart, &S.ctl->tiles_done[0], S.n_vtiles, 1, S.ctl->grad, sm);
+}
+
+// ------------------------------------------------------------- K3 assembly
+template <typename T>
+__device__ __forceinline__ void add_elem_block(const T* rec, int a, int b, T* acc) {
+  if (a <= b) {
+    const T* p = rec + 9 * tri4(a, b);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] += p[k];
+  } else {
+    const T* p = rec + 9 * tri4(b, a);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc[3 * i + k] += p[3 * k + i];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_assemble(const SceneDev<T>* scenes, const TileRef* tiles) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int k = tr.tile * TILE + threadIdx.x;
+  if (k >= S.nnzb) return;
+  const int i = S.blk_row[k], j = S.col[k];
+  T acc[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) acc[c] = (T)0;
+  if (S.fixed[i] || S.fixed[j]) {
+    if (i == j) acc[0] = acc[4] = acc[8] = (T)1;
+  } else {
+    const int it = S.it_id;
+    for (int c = S.blk_ptr[k]; c < S.blk_ptr[k + 1]; ++c) {
+      const int src = S.blk_src[c];
+      const int e = src >> 4, a = (src >> 2) & 3, b = src & 3;
+      add_elem_block(S.He + (size_t)e * HE_STRIDE, a, b, acc);
+      if (S.proj_stamp[e] == it) add_elem_block(S.dH + (size_t)e * HE_STRIDE, a, b, acc);
+    }
+    if (i == j) {
+      const T m = (T)(S.mass[i] * S.inv_dt2);
+      acc[0] += m;
+      acc[4] += m;
+      acc[8] += m;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) S.val[(size_t)c * S.nnzb + k] = acc[c];
+}
+
+// ----------------------------------------------------- K6 incremental update
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_update(const SceneDev<T>* scenes, const TileRef* tiles) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int k = tr.tile * TILE + threadIdx.x;
+  if (k >= S.nnzb) return;
+  const int i = S.blk_row[k], j = S.col[k];
+  if (S.fixed[i] || S.fixed[j]) return;
+  const int rd = S.round_id;
+  T acc[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) acc[c] = (T)0;
+  bool any = false;
+  for (int c = S.blk_ptr[k]; c < S.blk_ptr[k + 1]; ++c) {
+    const int src = S.blk_src[c];
+    const int e = src >> 4;
+    if (S.round_stamp[e] != rd) continue;
+    any = true;
+    add_elem_block(S.dH + (size_t)e * HE_STRIDE, (src >> 2) & 3, src & 3, acc);
+  }
+  if (!any) return;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) S.val[(size_t)c * S.nnzb + k] += acc[c];
+}
+
+// ------------------------------------------------------------ K4 selection
+// delta < 0 selects every element (PN: project all before assembly)
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_select(const SceneDev<T>* scenes, const TileRef* tiles) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int e = tr.tile * TILE + threadIdx.x;
+  bool sel = false;
+  if (e < S.nt && S.proj_stamp[e] != S.it_id) {
+    if (S.delta < 0.0 || S.delta <= S.eps_delta) {
+      sel = true;
+    } else {
+      const int4 t = S.tets[e];
+      const double r = fmax(fmax(S.gmax[t.x], S.gmax[t.y]), fmax(S.gmax[t.z], S.gmax[t.w]));
+      sel = r > S.delta;
+    }
+  }
+  const unsigned mask = __ballot_sync(0xffffffffu, sel);
+  if (mask == 0u) return;
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == __ffs(mask) - 1) base = atomicAdd(&S.ctl->n_new, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+  if (sel) {
+    const int idx = base + __popc(mask & ((1u << lane) - 1u));
+    S.sel_list[idx] = e;
+    S.proj_stamp[e] = S.it_id;
+    S.round_stamp[e] = S.round_id;
+  }
+}
+
+// ------------------------------------------------------- K5 eigen + clamp
+template <typename T>
+__global__ void __launch_bounds__(PROJ_CTA) k_project(const SceneDev<T>* scenes, const TileRef* tiles,
+                                                      int use_probe) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int idx = tr.tile * PROJ_CTA + threadIdx.x;
+  if (idx >= S.ctl->n_new) return;
+  const int e = S.sel_list[idx];
+  const int4 t = S.tets[e];
+  const double4* U = use_probe ? S.u_probe : S.u;
+  double u[4][3];
+  load_u(U, t.x, u[0]);
+  load_u(U, t.y, u[1]);
+  load_u(U, t.z, u[2]);
+  load_u(U, t.w, u[3]);
+  T W[9], V, mu, lam;
+  load_tetc(S.tetc, e, W, V, mu, lam);
+  T H[9];
+  disp_grad(u[0], u[1], u[2], u[3], W, H);
+  TetState<T> st;
+  tet_state(H, mu, lam, st);
+  T out[90];
+  clamp_tet(st, W, V, mu, lam, (T)S.eig_eps, out);
+  T* dst = S.dH + (size_t)e * HE_STRIDE;
+#pragma unroll
+  for (int k = 0; k < 90; ++k) dst[k] = out[k];
+}
+
+// ---------------------------------------------------------- K10 energy
+// tile index < n_ttiles: tet tile; otherwise vertex tile (index - n_ttiles).
+// Reductions: [0] incremental potential at u + gamma dx (FP64), [1] g^T dx,
+// [2] max |dx| over free vertices.
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_energy(const SceneDev<T>* scenes, const TileRef* tiles,
+                                                 int use_probe) {
+  __shared__ double sm[32];
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const double4* U = use_probe ? S.u_probe : S.u;
+  const double gam = S.gamma;
+  double en = 0.0, dd = 0.0, dmax = 0.0;
+  if (tr.tile < S.n_ttiles) {
+    const int e = tr.tile * TILE + threadIdx.x;
+    if (e < S.nt) {
+      const int4 t = S.tets[e];
+      const int vs[4] = {t.x, t.y, t.z, t.w};
+      double u[4][3];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        load_u(U, vs[a], u[a]);
+        if (gam != 0.0) {
+          const vec4_t<T> d = S.dx[vs[a]];
+          u[a][0] += gam * (double)d.x;
+          u[a][1] += gam * (double)d.y;
+          u[a][2] += gam * (double)d.z;
+        }
+      }
+      T Wt[9], Vt, mut, lamt;
+      load_tetc(S.tetc, e, Wt, Vt, mut, lamt);
+      double W[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) W[k] = (double)Wt[k];
+      double H[9];
+      disp_grad(u[0], u[1], u[2], u[3], W, H);
+      en = (double)Vt * snh_psi_disp(H, (double)mut, (double)lamt);
+      if (S.psi_out) S.psi_out[e] = en;
+    }
+  } else {
+    const int vt = tr.tile - S.n_ttiles;
+    const int v = vt * TILE + threadIdx.x;
+    if (v < S.nv && !S.fixed[v]) {
+      const double4 uv = ld_d4(U + v), uh = ld_d4(S.uhat + v);
+      double d0 = uv.x - uh.x, d1 = uv.y - uh.y, d2 = uv.z - uh.z;
+      if (!use_probe) {
+        const vec4_t<T> d = S.dx[v];
+        if (gam != 0.0) {
+          d0 += gam * (double)d.x;
+          d1 += gam * (double)d.y;
+          d2 += gam * (double)d.z;
+        }
+        const double4 g = ld_d4(S.g + v);
+        dd = g.x * (double)d.x + g.y * (double)d.y + g.z * (double)d.z;
+        dmax = fmax(fabs((double)d.x), fmax(fabs((double)d.y), fabs((double)d.z)));
+      }
+      en = 0.5 * S.mass[v] * S.inv_dt2 * (d0 * d0 + d1 * d1 + d2 * d2);
+    }
+  }
+  const double s0 = block_sum<TILE>(en, sm);
+  const double s1 = block_sum<TILE>(dd, sm);
+  const double s2 = block_max<TILE>(dmax, sm);
+  if (threadIdx.x == 0) {
+    S.tpart[4 * tr.tile + 0] = s0;
+    S.tpart[4 * tr.tile + 1] = s1;
+    S.tpart[4 * tr.tile + 2] = s2;
+  }
+  finish_reduction<TILE, 3>(S.tpart, &S.ctl->tiles_done[1], S.n_ttiles + S.n_vtiles, 2,
+                            S.ctl->energy, sm);
+}
+
+// per-vertex |g_v|_inf of a given assembled gradient (selection probe)
+template <typename T>
+__global__ void k_gmax(const SceneDev<T>* scenes, const TileRef* tiles) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int v = tr.tile * TILE + threadIdx.x;
+  if (v >= S.nv) return;
+  const double4 g = ld_d4(S.g + v);
+  S.gmax[v] = fmax(fabs(g.x), fmax(fabs(g.y), fabs(g.z)));
+}
+
+// ------------------------------------------------------- small vector kernels
+// start of a step: u_n = u, uhat = u + dt v + dt^2 a_grav, u = initial guess,
+// Dirichlet vertices set to their targets (targets are positions, n_fixed x 3)
+template <typename T>
+__global__ void k_predict(const SceneDev<T>* scenes, const TileRef* tiles, const int* fixed_list,
+                          const double* targets, int n_fixed, int init_guess) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int v = tr.tile * TILE + threadIdx.x;
+  if (v >= S.nv) return;
+  const double4 u = ld_d4(S.u + v), w = ld_d4(S.vel + v);
+  const double dt = S.dt, dt2 = S.dt * S.dt;
+  st_d4(S.u_n + v, u);
+  st_d4(S.uhat + v, make_double4(u.x + dt * w.x + dt2 * S.grav[0], u.y + dt * w.y + dt2 * S.grav[1],
+                                 u.z + dt * w.z + dt2 * S.grav[2], 0.0));
+  if (init_guess == 1 && !S.fixed[v])
+    st_d4(S.u + v, make_double4(u.x + dt * w.x, u.y + dt * w.y, u.z + dt * w.z, 0.0));
+}
+
+template <typename T>
+__global__ void k_apply_targets(const SceneDev<T>* scenes, int scene, const int* fixed_list,
+                                const double* targets, int n_fixed, int use_probe) {
+  const SceneDev<T>& S = scenes[scene];
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_fixed) return;
+  const int v = fixed_list[f];
+  const double4 X = ld_d4(S.X + v);
+  double4* U = use_probe ? S.u_probe : S.u;
+  st_d4(U + v, make_double4(targets[3 * f] - X.x, targets[3 * f + 1] - X.y, targets[3 * f + 2] - X.z, 0.0));
+}
+
+// u += gamma dx on free vertices
+template <typename T>
+__global__ void k_axpy_u(const SceneDev<T>* scenes, const TileRef* tiles) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int v = tr.tile * TILE + threadIdx.x;
+  if (v >= S.nv || S.fixed[v]) return;
+  const double gam = S.gamma;
+  const vec4_t<T> d = S.dx[v];
+  const double4 u = ld_d4(S.u + v);
+  st_d4(S.u + v, make_double4(u.x + gam * (double)d.x, u.y + gam * (double)d.y, u.z + gam * (double)d.z, 0.0));
+}
+
+template <typename T>
+__global__ void k_velocity(const SceneDev<T>* scenes, const TileRef* tiles) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int v = tr.tile * TILE + threadIdx.x;
+  if (v >= S.nv) return;
+  const double4 u = ld_d4(S.u + v), un = ld_d4(S.u_n + v);
+  const double idt = 1.0 / S.dt;
+  st_d4(S.vel + v, make_double4((u.x - un.x) * idt, (u.y - un.y) * idt, (u.z - un.z) * idt, 0.0));
+}
+
+// dx = -P^-1 g (kind 2, P = block-Jacobi inverse from the last PCG setup) or
+// dx = -(dt^2 / m) g (kind 3)
+template <typename T>
+__global__ void k_fallback_dir(const SceneDev<T>* scenes, const TileRef* tiles, int kind) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int v = tr.tile * TILE + threadIdx.x;
+  if (v >= S.nv) return;
+  const double4 g = ld_d4(S.g + v);
+  vec4_t<T> d;
+  d.w = (T)0;
+  if (S.fixed[v]) {
+    d.x = d.y = d.z = (T)0;
+  } else if (kind == 2) {
+    const T* P = S.Pinv + (size_t)9 * v;
+    const T g0 = (T)g.x, g1 = (T)g.y, g2 = (T)g.z;
+    d.x = -(P[0] * g0 + P[1] * g1 + P[2] * g2);
+    d.y = -(P[3] * g0 + P[4] * g1 + P[5] * g2);
+    d.z = -(P[6] * g0 + P[7] * g1 + P[8] * g2);
+  } else {
+    const double s = -1.0 / (S.mass[v] * S.inv_dt2);
+    d.x = (T)(s * g.x);
+    d.y = (T)(s * g.y);
+    d.z = (T)(s * g.z);
+  }
+  S.dx[v] = d;
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename T>
+void launch_element(const SceneDev<T>* s, const TileRef* t, int n, int probe, cudaStream_t st) {
+  if (n) k_element<T><<<n, TILE, 0, st>>>(s, t, probe);
+}
+template <typename T>
+void launch_gradient(const SceneDev<T>* s, const TileRef* t, int n, int probe, cudaStream_t st) {
+  if (n) k_gradient<T><<<n, TILE, 0, st>>>(s, t, probe);
+}
+template <typename T>
+void launch_assemble(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
+  if (n) k_assemble<T><<<n, TILE, 0, st>>>(s, t);
+}
+template <typename T>
+void launch_update(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
+  if (n) k_update<T><<<n, TILE, 0, st>>>(s, t);
+}
+template <typename T>
+void launch_select(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
+  if (n) k_select<T><<<n, TILE, 0, st>>>(s, t);
+}
+template <typename T>
+void launch_project(const SceneDev<T>* s, const TileRef* t, int n, int probe, cudaStream_t st) {
+  if (n) k_project<T><<<n, PROJ_CTA, 0, st>>>(s, t, probe);
+}
+template <typename T>
+void launch_energy(const SceneDev<T>* s, const TileRef* t, int n, int probe, cudaStream_t st) {
+  if (n) k_energy<T><<<n, TILE, 0, st>>>(s, t, probe);
+}
+template <typename T>
+void launch_predict(const SceneDev<T>* s, const TileRef* t, int n, int init_guess, cudaStream_t st) {
+  if (n) k_predict<T><<<n, TILE, 0, st>>>(s, t, nullptr, nullptr, 0, init_guess);
+}
+template <typename T>
+void launch_apply_targets(const SceneDev<T>* s, int scene, const int* fl, const double* tg, int nf,
+                          int probe, cudaStream_t st) {
+  if (nf) k_apply_targets<T><<<(nf + 255) / 256, 256, 0, st>>>(s, scene, fl, tg, nf, probe);
+}
+template <typename T>
+void launch_gmax(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
+  if (n) k_gmax<T><<<n, TILE, 0, st>>>(s, t);
+}
+template <typename T>
+void launch_axpy_u(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
+  if (n) k_axpy_u<T><<<n, TILE, 0, st>>>(s, t);
+}
+template <typename T>
+void launch_velocity(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
+  if (n) k_velocity<T><<<n, TILE, 0, st>>>(s, t);
+}
+template <typename T>
+void launch_fallback(const SceneDev<T>* s, const TileRef* t, int n, int kind, cudaStream_t st) {
+  if (n) k_fallback_dir<T><<<n, TILE, 0, st>>>(s, t, kind);
+}
+
+#define PPN_INST(T)                                                                            \
+  template void launch_element<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
+  template void launch_gradient<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
+  template void launch_assemble<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);     \
+  template void launch_update<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \
+  template void launch_select<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \
+  template void launch_project<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
+  template void launch_energy<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);  \
+  template void launch_predict<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
+  template void launch_apply_targets<T>(const SceneDev<T>*, int, const int*, const double*, int, \
+                                        int, cudaStream_t);                                    \
+  template void launch_axpy_u<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \
+  template void launch_gmax<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);         \
+  template void launch_velocity<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);     \
+  template void launch_fallback<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
+
+PPN_INST(float)
+PPN_INST(double)
+
+}  // namespace ppn

@@ -1,0 +1,52 @@
+// Host-side launch interface of the device kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ppn {
+
+constexpr int PROJ_CTA = 128;  // threads per CTA of the projection kernel (register heavy)
+
+template <typename T> void launch_element(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
+template <typename T> void launch_gradient(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
+template <typename T> void launch_assemble(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
+template <typename T> void launch_update(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
+template <typename T> void launch_select(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
+template <typename T> void launch_project(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
+template <typename T> void launch_energy(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
+template <typename T> void launch_predict(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
+template <typename T>
+void launch_apply_targets(const SceneDev<T>*, int, const int*, const double*, int, int, cudaStream_t);
+template <typename T> void launch_gmax(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
+template <typename T> void launch_axpy_u(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
+template <typename T> void launch_velocity(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
+template <typename T> void launch_fallback(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
+
+// Grid barrier state of the cooperative PCG kernel (device memory, zeroed once).
+struct GridBar {
+  unsigned count;
+  unsigned gen;
+  int all_done;
+  int timeout;
+};
+
+struct PcgLaunch {
+  int n_tiles;         // PCG row tiles in the tile table
+  int n_scenes;        // scenes taking part
+  const int* scene_ids;  // device: indices into the scene table
+  GridBar* bar;
+  int grid;            // cooperative grid size (CTAs)
+  int group;           // lanes per BSR row (4 or 8)
+  int use_b_from_g;    // 1: b = -g of the scene; 0: b given in r (probe)
+};
+
+// Occupancy-limited cooperative grid size for the chosen row group width.
+int pcg_max_grid(int group, int device);
+
+template <typename T>
+cudaError_t launch_pcg(const SceneDev<T>* scenes, const TileRef* tiles, const PcgLaunch& L,
+                       cudaStream_t st);
+
+}  // namespace ppn

@@ -1,0 +1,1807 @@
+// Scene construction, the lockstep Newton / PN / PPN driver and the C ABI.
+//
+// One time step (backward Euler as incremental-potential minimisation,
+// Sec. 2.1 / 5.1) runs Newton's method (Sec. 3) with, per mode:
+//   NEWTON  unprojected H; on negative curvature the solver's last iterate is
+//           the step (Newton-CG, Sec. 4.1)
+//   PN      every element clamped before assembly (Sec. 3)
+//   PPN     Algorithm 1: solve on the unprojected H; while the solver reports
+//           indefiniteness, select elements with ||S^e g||_inf > delta (delta
+//           initialised to alpha ||g||_inf, tightened by alpha), clamp them and
+//           update H in place (Sec. 4.1), solve again; relax delta by beta.
+// followed by a backtracking line search for sufficient decrease (Sec. 5.1).
+//
+// Several scenes step together as a "group": every phase is one launch over
+// the scenes still taking part in it, and every host decision is taken per
+// scene after one device->host copy of all scenes' control blocks.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <mutex>
+
+#include "scene.h"
+
+namespace ppn {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+const char* kFamilyNames[FAM_COUNT] = {"element", "gradient", "assemble", "select", "project",
+                                       "update",  "pcg",      "energy",   "vector"};
+
+#define PPN_CU(call)                                                                      \
+  do {                                                                                    \
+    cudaError_t _e = (call);                                                              \
+    if (_e != cudaSuccess) {                                                              \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(_e));                      \
+      return _e == cudaErrorMemoryAllocation ? PPN_ERR_OOM : PPN_ERR_CUDA;                \
+    }                                                                                     \
+  } while (0)
+
+// ------------------------------------------------------------------ staging
+Staging::~Staging() {
+  if (base) cudaFreeHost(base);
+}
+
+void* Staging::take(size_t n, cudaStream_t st) {
+  n = (n + 255) & ~size_t(255);
+  if (!base) {
+    cap = std::max<size_t>(4 << 20, 2 * n);
+    if (cudaMallocHost(&base, cap) != cudaSuccess) {
+      base = nullptr;
+      return nullptr;
+    }
+  }
+  if (off + n > cap) {
+    // every earlier upload must have been consumed before the slot is reused
+    cudaStreamSynchronize(st);
+    off = 0;
+    if (n > cap) {
+      cudaFreeHost(base);
+      cap = 2 * n;
+      if (cudaMallocHost(&base, cap) != cudaSuccess) {
+        base = nullptr;
+        return nullptr;
+      }
+    }
+  }
+  void* p = base + off;
+  off += n;
+  return p;
+}
+
+// ------------------------------------------------------------------ timers
+KernelTimer::~KernelTimer() {
+  for (auto& r : pending) {
+    pool.push_back(r.a);
+    pool.push_back(r.b);
+  }
+  for (auto e : pool) cudaEventDestroy(e);
+}
+cudaEvent_t KernelTimer::ev() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+void KernelTimer::begin(int fam, cudaStream_t st, double b) {
+  if (!on) return;
+  Rec r{fam, ev(), ev(), b};
+  cudaEventRecord(r.a, st);
+  pending.push_back(r);
+}
+void KernelTimer::end(cudaStream_t st) {
+  if (!on || pending.empty()) return;
+  cudaEventRecord(pending.back().b, st);
+}
+void KernelTimer::collect() {
+  for (auto& r : pending) {
+    float ms_ = 0.f;
+    if (cudaEventElapsedTime(&ms_, r.a, r.b) == cudaSuccess) {
+      ms[r.fam] += ms_;
+      launches[r.fam] += 1;
+      bytes[r.fam] += r.bytes;
+    }
+    pool.push_back(r.a);
+    pool.push_back(r.b);
+  }
+  pending.clear();
+}
+void KernelTimer::reset() {
+  collect();
+  for (int i = 0; i < 16; ++i) {
+    launches[i] = 0;
+    ms[i] = 0;
+    bytes[i] = 0;
+  }
+}
+
+// ------------------------------------------------------------------ scene
+template <typename T>
+template <typename X>
+X* SceneImpl<T>::alloc(size_t n) {
+  if (n == 0) n = 1;
+  void* p = nullptr;
+  if (cudaMalloc(&p, n * sizeof(X)) != cudaSuccess) return nullptr;
+  allocs.push_back(p);
+  dev_bytes += n * sizeof(X);
+  return reinterpret_cast<X*>(p);
+}
+
+template <typename T>
+SceneImpl<T>::~SceneImpl() {
+  if (stream) cudaStreamSynchronize(stream);
+  for (void* p : allocs) cudaFree(p);
+  if (h_ctl) cudaFreeHost(h_ctl);
+  if (ev_a) cudaEventDestroy(ev_a);
+  if (ev_b) cudaEventDestroy(ev_b);
+  if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+static std::vector<TileRef> make_tiles(int scene, int n_items, int tile) {
+  std::vector<TileRef> t;
+  const int n = (n_items + tile - 1) / tile;
+  t.reserve(n);
+  for (int i = 0; i < n; ++i) t.push_back({scene, i});
+  return t;
+}
+
+template <typename T>
+ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int32_t* tets,
+                              int64_t n_tets, const ppn_material* mat, double dt_, const int32_t* fixed,
+                              int64_t n_fixed, const ppn_params* p) {
+  if (!rest_xyz || !tets || !mat || n_verts <= 0 || n_tets <= 0 || n_fixed < 0 ||
+      (n_fixed > 0 && !fixed)) {
+    set_error("null pointer or empty mesh");
+    return PPN_ERR_INVALID_ARG;
+  }
+  if (n_tets >= (1ll << 27) || n_verts >= (1ll << 30)) {
+    set_error("mesh too large for 32-bit element maps");
+    return PPN_ERR_INVALID_ARG;
+  }
+  if (!(dt_ > 0) || !(mat->rho > 0) || !(mat->E > 0) || !(mat->nu > -1.0 && mat->nu < 0.5)) {
+    set_error("invalid material or time step");
+    return PPN_ERR_INVALID_ARG;
+  }
+  params = p ? *p : ppn_default_params();
+  dt = dt_;
+  nv = (int)n_verts;
+  nt = (int)n_tets;
+  nfixed = (int)n_fixed;
+  rest.assign(rest_xyz, rest_xyz + 3 * n_verts);
+
+  // --- tets: range check, orientation, Dm^-1, volume, lumped mass
+  const double mu = mat->E / (2.0 * (1.0 + mat->nu));
+  const double lam = mat->E * mat->nu / ((1.0 + mat->nu) * (1.0 - 2.0 * mat->nu)) + mu;
+  std::vector<int4> h_tets(nt);
+  std::vector<T> h_tetc((size_t)nt * TETC_STRIDE);
+  std::vector<double> mass(nv, 0.0);
+  for (int e = 0; e < nt; ++e) {
+    int v[4];
+    for (int a = 0; a < 4; ++a) {
+      v[a] = tets[4 * (int64_t)e + a];
+      if (v[a] < 0 || v[a] >= nv) {
+        set_error("tet index out of range at tet " + std::to_string(e));
+        return PPN_ERR_INVALID_ARG;
+      }
+    }
+    double D[9];
+    auto build = [&](double* M) {
+      for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a) M[3 * i + a] = rest[3 * v[a + 1] + i] - rest[3 * v[0] + i];
+    };
+    build(D);
+    double C[9];
+    cof3(D, C);
+    double det = D[0] * C[0] + D[1] * C[1] + D[2] * C[2];
+    double hmax = 0.0;
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b) {
+        double l2 = 0;
+        for (int k = 0; k < 3; ++k) {
+          const double d = rest[3 * v[a] + k] - rest[3 * v[b] + k];
+          l2 += d * d;
+        }
+        hmax = std::max(hmax, std::sqrt(l2));
+      }
+    if (!(std::fabs(det) > 1e-14 * hmax * hmax * hmax)) {
+      set_error("degenerate tet " + std::to_string(e));
+      return PPN_ERR_DEGENERATE_TET;
+    }
+    if (det < 0) {
+      std::swap(v[2], v[3]);
+      build(D);
+      cof3(D, C);
+      det = -det;
+    }
+    h_tets[e] = make_int4(v[0], v[1], v[2], v[3]);
+    T* tc = &h_tetc[(size_t)e * TETC_STRIDE];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) tc[3 * i + j] = (T)(C[3 * j + i] / det);  // Dm^-1 = cof^T / det
+    tc[9] = (T)(det / 6.0);
+    tc[10] = (T)mu;
+    tc[11] = (T)lam;
+    for (int a = 0; a < 4; ++a) mass[v[a]] += mat->rho * (det / 6.0) / 4.0;
+  }
+  std::vector<uint8_t> fixed_flag(nv, 0);
+  fixed_list.resize(nfixed);
+  for (int f = 0; f < nfixed; ++f) {
+    const int v = fixed[f];
+    if (v < 0 || v >= nv || fixed_flag[v]) {
+      set_error("fixed index out of range or repeated");
+      return PPN_ERR_INVALID_ARG;
+    }
+    fixed_flag[v] = 1;
+    fixed_list[f] = v;
+  }
+  for (int v = 0; v < nv; ++v)
+    if (!fixed_flag[v] && !(mass[v] > 0)) {
+      set_error("free vertex " + std::to_string(v) + " has no incident tet");
+      return PPN_ERR_INVALID_ARG;
+    }
+
+  // --- BSR pattern (full symmetric, sorted, diagonal always present)
+  std::vector<uint64_t> keys;
+  keys.reserve((size_t)16 * nt + nv);
+  for (int e = 0; e < nt; ++e) {
+    const int v[4] = {h_tets[e].x, h_tets[e].y, h_tets[e].z, h_tets[e].w};
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) keys.push_back(((uint64_t)v[a] << 32) | (uint32_t)v[b]);
+  }
+  for (int v = 0; v < nv; ++v) keys.push_back(((uint64_t)v << 32) | (uint32_t)v);
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  if (keys.size() >= (size_t)INT32_MAX) {
+    set_error("pattern too large");
+    return PPN_ERR_INVALID_ARG;
+  }
+  nnzb = (int)keys.size();
+  h_row_ptr.assign(nv + 1, 0);
+  h_col.resize(nnzb);
+  std::vector<int> blk_row(nnzb), diag_idx(nv);
+  for (int k = 0; k < nnzb; ++k) {
+    const int i = (int)(keys[k] >> 32), j = (int)(keys[k] & 0xffffffffu);
+    h_col[k] = j;
+    blk_row[k] = i;
+    h_row_ptr[i + 1]++;
+    if (i == j) diag_idx[i] = k;
+  }
+  for (int i = 0; i < nv; ++i) h_row_ptr[i + 1] += h_row_ptr[i];
+  keys.clear();
+  keys.shrink_to_fit();
+  auto find_block = [&](int i, int j) {
+    const int* b = h_col.data() + h_row_ptr[i];
+    const int* e = h_col.data() + h_row_ptr[i + 1];
+    return (int)(std::lower_bound(b, e, j) - h_col.data());
+  };
+  // block -> (tet, a, b) contributions, element order within each block
+  std::vector<int> blk_ptr(nnzb + 1, 0), blk_src((size_t)16 * nt);
+  std::vector<int> blk_of((size_t)16 * nt);
+  for (int e = 0; e < nt; ++e) {
+    const int v[4] = {h_tets[e].x, h_tets[e].y, h_tets[e].z, h_tets[e].w};
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        const int k = find_block(v[a], v[b]);
+        blk_of[(size_t)16 * e + 4 * a + b] = k;
+        blk_ptr[k + 1]++;
+      }
+  }
+  for (int k = 0; k < nnzb; ++k) blk_ptr[k + 1] += blk_ptr[k];
+  {
+    std::vector<int> fill(blk_ptr.begin(), blk_ptr.end() - 1);
+    for (int e = 0; e < nt; ++e)
+      for (int ab = 0; ab < 16; ++ab) {
+        const int k = blk_of[(size_t)16 * e + ab];
+        blk_src[fill[k]++] = (e << 4) | ab;
+      }
+  }
+  nmap = 16 * nt;
+  blk_of.clear();
+  blk_of.shrink_to_fit();
+  // vertex -> (tet, corner)
+  std::vector<int> vt_ptr(nv + 1, 0), vt_src((size_t)4 * nt);
+  for (int e = 0; e < nt; ++e) {
+    vt_ptr[h_tets[e].x + 1]++;
+    vt_ptr[h_tets[e].y + 1]++;
+    vt_ptr[h_tets[e].z + 1]++;
+    vt_ptr[h_tets[e].w + 1]++;
+  }
+  for (int v = 0; v < nv; ++v) vt_ptr[v + 1] += vt_ptr[v];
+  {
+    std::vector<int> fill(vt_ptr.begin(), vt_ptr.end() - 1);
+    for (int e = 0; e < nt; ++e) {
+      const int v[4] = {h_tets[e].x, h_tets[e].y, h_tets[e].z, h_tets[e].w};
+      for (int a = 0; a < 4; ++a) vt_src[fill[v[a]]++] = (e << 2) | a;
+    }
+  }
+
+  // --- device allocation and upload
+  PPN_CU(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+  own_stream = true;
+  PPN_CU(cudaEventCreate(&ev_a));
+  PPN_CU(cudaEventCreate(&ev_b));
+  n_vtiles = (nv + TILE - 1) / TILE;
+  n_ttiles = (nt + TILE - 1) / TILE;
+  n_btiles = (nnzb + TILE - 1) / TILE;
+  n_ptiles = (nv + PCG_TILE - 1) / PCG_TILE;
+  using V4 = vec4_t<T>;
+  SceneDev<T> s{};
+  s.nv = nv;
+  s.nt = nt;
+  s.nnzb = nnzb;
+  s.nmap = nmap;
+  s.n_vtiles = n_vtiles;
+  s.n_ttiles = n_ttiles;
+  s.n_ptiles = n_ptiles;
+  int4* d_tets = alloc<int4>(nt);
+  T* d_tetc = alloc<T>((size_t)nt * TETC_STRIDE);
+  double* d_mass = alloc<double>(nv);
+  uint8_t* d_fixed = alloc<uint8_t>(nv);
+  double4* d_X = alloc<double4>(nv);
+  int* d_vt_ptr = alloc<int>(nv + 1);
+  int* d_vt_src = alloc<int>((size_t)4 * nt);
+  int* d_row_ptr = alloc<int>(nv + 1);
+  int* d_col = alloc<int>(nnzb);
+  int* d_blk_row = alloc<int>(nnzb);
+  int* d_blk_ptr = alloc<int>(nnzb + 1);
+  int* d_blk_src = alloc<int>((size_t)16 * nt);
+  int* d_diag = alloc<int>(nv);
+  s.u = alloc<double4>(nv);
+  s.u_n = alloc<double4>(nv);
+  s.vel = alloc<double4>(nv);
+  s.uhat = alloc<double4>(nv);
+  s.u_probe = alloc<double4>(nv);
+  s.ge = alloc<T>((size_t)nt * GE_STRIDE);
+  s.He = alloc<T>((size_t)nt * HE_STRIDE);
+  s.dH = alloc<T>((size_t)nt * HE_STRIDE);
+  s.g = alloc<double4>(nv);
+  s.gmax = alloc<double>(nv);
+  s.val = alloc<T>((size_t)9 * nnzb);
+  s.proj_stamp = alloc<int>(nt);
+  s.round_stamp = alloc<int>(nt);
+  s.sel_list = alloc<int>(nt);
+  s.dx = alloc<V4>(nv);
+  s.r = alloc<V4>(nv);
+  s.z = alloc<V4>(nv);
+  s.q = alloc<V4>(nv);
+  s.d0 = alloc<V4>(nv);
+  s.d1 = alloc<V4>(nv);
+  s.Pinv = alloc<T>((size_t)9 * nv);
+  s.vpart = alloc<double>((size_t)4 * n_vtiles);
+  s.tpart = alloc<double>((size_t)4 * (n_vtiles + n_ttiles));
+  s.ppart = alloc<double>((size_t)4 * n_ptiles);
+  s.ctl = alloc<Ctl>(1);
+  d_desc = alloc<SceneDev<T>>(1);
+  d_ids = alloc<int>(1);
+  d_bar = alloc<GridBar>(1);
+  d_fixed_list = alloc<int>(nfixed);
+  d_targets = alloc<double>((size_t)3 * nfixed);
+  d_xyz = alloc<double>((size_t)3 * nv);
+  const auto tt = make_tiles(0, nt, TILE), vt = make_tiles(0, nv, TILE), bt = make_tiles(0, nnzb, TILE),
+             pt = make_tiles(0, nv, PCG_TILE), jt = make_tiles(0, nt, PROJ_CTA);
+  std::vector<TileRef> et;
+  for (int i = 0; i < n_ttiles + n_vtiles; ++i) et.push_back({0, i});
+  d_ttiles = alloc<TileRef>(tt.size());
+  d_vtiles = alloc<TileRef>(vt.size());
+  d_btiles = alloc<TileRef>(bt.size());
+  d_ptiles = alloc<TileRef>(pt.size());
+  d_etiles = alloc<TileRef>(et.size());
+  d_projtiles = alloc<TileRef>(jt.size());
+  if (!d_tets || !d_tetc || !d_mass || !d_fixed || !d_X || !d_vt_ptr || !d_vt_src || !d_row_ptr ||
+      !d_col || !d_blk_row || !d_blk_ptr || !d_blk_src || !d_diag || !s.u || !s.u_n || !s.vel ||
+      !s.uhat || !s.u_probe || !s.ge || !s.He || !s.dH || !s.g || !s.gmax || !s.val ||
+      !s.proj_stamp || !s.round_stamp || !s.sel_list || !s.dx || !s.r || !s.z || !s.q || !s.d0 ||
+      !s.d1 || !s.Pinv || !s.vpart || !s.tpart || !s.ppart || !s.ctl || !d_desc || !d_ids ||
+      !d_bar || !d_fixed_list || !d_targets || !d_xyz || !d_ttiles || !d_vtiles || !d_btiles ||
+      !d_ptiles || !d_etiles || !d_projtiles) {
+    set_error("cudaMalloc failed (scene needs more device memory than is free)");
+    return PPN_ERR_OOM;
+  }
+  std::vector<double4> X4(nv);
+  for (int v = 0; v < nv; ++v) X4[v] = make_double4(rest[3 * v], rest[3 * v + 1], rest[3 * v + 2], 0.0);
+  std::vector<int> rp32(h_row_ptr.begin(), h_row_ptr.end());
+  std::vector<double> tg((size_t)3 * nfixed);
+  for (int f = 0; f < nfixed; ++f)
+    for (int k = 0; k < 3; ++k) tg[3 * f + k] = rest[3 * fixed_list[f] + k];
+  auto up = [&](void* dst, const void* src, size_t n) { return cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice); };
+  PPN_CU(up(d_tets, h_tets.data(), sizeof(int4) * nt));
+  PPN_CU(up(d_tetc, h_tetc.data(), sizeof(T) * h_tetc.size()));
+  PPN_CU(up(d_mass, mass.data(), sizeof(double) * nv));
+  PPN_CU(up(d_fixed, fixed_flag.data(), nv));
+  PPN_CU(up(d_X, X4.data(), sizeof(double4) * nv));
+  PPN_CU(up(d_vt_ptr, vt_ptr.data(), sizeof(int) * (nv + 1)));
+  PPN_CU(up(d_vt_src, vt_src.data(), sizeof(int) * vt_src.size()));
+  PPN_CU(up(d_row_ptr, rp32.data(), sizeof(int) * (nv + 1)));
+  PPN_CU(up(d_col, h_col.data(), sizeof(int) * nnzb));
+  PPN_CU(up(d_blk_row, blk_row.data(), sizeof(int) * nnzb));
+  PPN_CU(up(d_blk_ptr, blk_ptr.data(), sizeof(int) * (nnzb + 1)));
+  PPN_CU(up(d_blk_src, blk_src.data(), sizeof(int) * blk_src.size()));
+  PPN_CU(up(d_diag, diag_idx.data(), sizeof(int) * nv));
+  if (nfixed) {
+    PPN_CU(up(d_fixed_list, fixed_list.data(), sizeof(int) * nfixed));
+    PPN_CU(up(d_targets, tg.data(), sizeof(double) * tg.size()));
+  }
+  PPN_CU(up(d_ttiles, tt.data(), sizeof(TileRef) * tt.size()));
+  PPN_CU(up(d_vtiles, vt.data(), sizeof(TileRef) * vt.size()));
+  PPN_CU(up(d_btiles, bt.data(), sizeof(TileRef) * bt.size()));
+  PPN_CU(up(d_ptiles, pt.data(), sizeof(TileRef) * pt.size()));
+  PPN_CU(up(d_etiles, et.data(), sizeof(TileRef) * et.size()));
+  PPN_CU(up(d_projtiles, jt.data(), sizeof(TileRef) * jt.size()));
+  const int zero = 0;
+  PPN_CU(up(d_ids, &zero, sizeof(int)));
+  PPN_CU(cudaMemset(s.u, 0, sizeof(double4) * nv));
+  PPN_CU(cudaMemset(s.vel, 0, sizeof(double4) * nv));
+  PPN_CU(cudaMemset(s.dx, 0, sizeof(V4) * nv));
+  PPN_CU(cudaMemset(s.proj_stamp, 0xff, sizeof(int) * nt));
+  PPN_CU(cudaMemset(s.round_stamp, 0xff, sizeof(int) * nt));
+  PPN_CU(cudaMemset(s.ctl, 0, sizeof(Ctl)));
+  PPN_CU(cudaMemset(s.vpart, 0, sizeof(double) * 4 * n_vtiles));
+  PPN_CU(cudaMemset(s.tpart, 0, sizeof(double) * 4 * (n_vtiles + n_ttiles)));
+  PPN_CU(cudaMemset(s.ppart, 0, sizeof(double) * 4 * n_ptiles));
+  s.tets = d_tets;
+  s.tetc = d_tetc;
+  s.mass = d_mass;
+  s.fixed = d_fixed;
+  s.X = d_X;
+  s.vt_ptr = d_vt_ptr;
+  s.vt_src = d_vt_src;
+  s.row_ptr = d_row_ptr;
+  s.col = d_col;
+  s.blk_row = d_blk_row;
+  s.blk_ptr = d_blk_ptr;
+  s.blk_src = d_blk_src;
+  s.diag_idx = d_diag;
+  s.dt = dt;
+  s.inv_dt2 = 1.0 / (dt * dt);
+  for (int k = 0; k < 3; ++k) s.grav[k] = params.gravity[k];
+  s.eps_delta = params.eps_delta;
+  s.eig_eps = params.eig_eps;
+  s.delta = std::numeric_limits<double>::infinity();
+  s.pcg_tol2 = params.pcg_rel_tol * params.pcg_rel_tol;
+  s.pcg_max_iter = params.pcg_max_iter > 0 ? params.pcg_max_iter : std::max(1000, 3 * nv);
+  s.it_id = 0;
+  s.round_id = 0;
+  s.active = 1;
+  d = s;
+  PPN_CU(cudaMallocHost(&h_ctl, sizeof(Ctl)));
+  int dev = 0;
+  PPN_CU(cudaGetDevice(&dev));
+  pcg_group = 8;
+  pcg_grid = pcg_max_grid(pcg_group, dev);
+  if (pcg_grid <= 0) {
+    set_error("PCG kernel cannot be made co-resident on this device");
+    return PPN_ERR_CUDA;
+  }
+  return PPN_OK;
+}
+
+// ------------------------------------------------------------------ groups
+// A group is a set of scenes that step together; a single scene is a group
+// of one.  The group owns the device copies of its members' descriptors, the
+// concatenated tile tables, one contiguous control-block array and the PCG
+// grid barrier.
+template <typename T>
+struct Group {
+  std::vector<SceneImpl<T>*> S;
+  std::vector<SceneDev<T>> h_desc;
+  SceneDev<T>* d_desc = nullptr;
+  Ctl* d_ctl = nullptr;
+  Ctl* h_ctl = nullptr;
+  GridBar* h_bar = nullptr;
+  TileRef *d_ttiles = nullptr, *d_vtiles = nullptr, *d_btiles = nullptr, *d_ptiles = nullptr,
+          *d_etiles = nullptr, *d_projtiles = nullptr;
+  int n_ttiles = 0, n_vtiles = 0, n_btiles = 0, n_ptiles = 0, n_etiles = 0;
+  int* d_ids = nullptr;
+  GridBar* d_bar = nullptr;
+  cudaStream_t st = nullptr;
+  Staging staging;
+  KernelTimer* timer = nullptr;
+  int pcg_grid = 0, pcg_group = 8;
+  std::vector<void*> allocs;
+  ~Group() {
+    if (st) cudaStreamSynchronize(st);
+    for (void* p : allocs) cudaFree(p);
+    if (h_ctl) cudaFreeHost(h_ctl);
+    if (h_bar) cudaFreeHost(h_bar);
+  }
+  template <typename X>
+  X* alloc(size_t n) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(1, n) * sizeof(X)) != cudaSuccess) return nullptr;
+    allocs.push_back(p);
+    return reinterpret_cast<X*>(p);
+  }
+  ppn_status build(const std::vector<SceneImpl<T>*>& members) {
+    S = members;
+    const int n = (int)S.size();
+    st = S[0]->stream;
+    timer = &S[0]->timer;
+    pcg_grid = S[0]->pcg_grid;
+    pcg_group = S[0]->pcg_group;
+    h_desc.resize(n);
+    std::vector<TileRef> tt, vt, bt, pt, et;
+    size_t projcap = 0;
+    for (int i = 0; i < n; ++i) {
+      const SceneImpl<T>& s = *S[i];
+      for (int t = 0; t < s.n_ttiles; ++t) tt.push_back({i, t});
+      for (int t = 0; t < s.n_vtiles; ++t) vt.push_back({i, t});
+      for (int t = 0; t < s.n_btiles; ++t) bt.push_back({i, t});
+      for (int t = 0; t < s.n_ptiles; ++t) pt.push_back({i, t});
+      for (int t = 0; t < s.n_ttiles + s.n_vtiles; ++t) et.push_back({i, t});
+      projcap += (s.nt + PROJ_CTA - 1) / PROJ_CTA;
+    }
+    n_ttiles = (int)tt.size();
+    n_vtiles = (int)vt.size();
+    n_btiles = (int)bt.size();
+    n_ptiles = (int)pt.size();
+    n_etiles = (int)et.size();
+    d_desc = alloc<SceneDev<T>>(n);
+    d_ctl = alloc<Ctl>(n);
+    d_ttiles = alloc<TileRef>(tt.size());
+    d_vtiles = alloc<TileRef>(vt.size());
+    d_btiles = alloc<TileRef>(bt.size());
+    d_ptiles = alloc<TileRef>(pt.size());
+    d_etiles = alloc<TileRef>(et.size());
+    d_projtiles = alloc<TileRef>(projcap);
+    d_ids = alloc<int>(n);
+    d_bar = alloc<GridBar>(1);
+    if (!d_desc || !d_ctl || !d_ttiles || !d_vtiles || !d_btiles || !d_ptiles || !d_etiles ||
+        !d_projtiles || !d_ids || !d_bar) {
+      set_error("cudaMalloc failed for a scene group");
+      return PPN_ERR_OOM;
+    }
+    PPN_CU(cudaMallocHost(&h_ctl, sizeof(Ctl) * n));
+    PPN_CU(cudaMallocHost(&h_bar, sizeof(GridBar)));
+    std::memset(h_bar, 0, sizeof(GridBar));
+    PPN_CU(cudaMemset(d_bar, 0, sizeof(GridBar)));
+    PPN_CU(cudaMemcpy(d_ttiles, tt.data(), sizeof(TileRef) * tt.size(), cudaMemcpyHostToDevice));
+    PPN_CU(cudaMemcpy(d_vtiles, vt.data(), sizeof(TileRef) * vt.size(), cudaMemcpyHostToDevice));
+    PPN_CU(cudaMemcpy(d_btiles, bt.data(), sizeof(TileRef) * bt.size(), cudaMemcpyHostToDevice));
+    PPN_CU(cudaMemcpy(d_ptiles, pt.data(), sizeof(TileRef) * pt.size(), cudaMemcpyHostToDevice));
+    PPN_CU(cudaMemcpy(d_etiles, et.data(), sizeof(TileRef) * et.size(), cudaMemcpyHostToDevice));
+    std::vector<Ctl> c0(n);
+    std::memset(c0.data(), 0, sizeof(Ctl) * n);
+    for (auto& c : c0) c.pcg_done = 1;
+    PPN_CU(cudaMemcpy(d_ctl, c0.data(), sizeof(Ctl) * n, cudaMemcpyHostToDevice));
+    for (int i = 0; i < n; ++i) {
+      h_desc[i] = S[i]->d;
+      h_desc[i].ctl = d_ctl + i;
+      h_desc[i].active = 0;
+    }
+    return PPN_OK;
+  }
+  ppn_status upload_desc() {
+    const size_t b = sizeof(SceneDev<T>) * h_desc.size();
+    void* p = staging.take(b, st);
+    if (!p) {
+      set_error("pinned staging allocation failed");
+      return PPN_ERR_OOM;
+    }
+    std::memcpy(p, h_desc.data(), b);
+    PPN_CU(cudaMemcpyAsync(d_desc, p, b, cudaMemcpyHostToDevice, st));
+    return PPN_OK;
+  }
+  ppn_status upload(void* dst, const void* src, size_t b) {
+    void* p = staging.take(b, st);
+    if (!p) {
+      set_error("pinned staging allocation failed");
+      return PPN_ERR_OOM;
+    }
+    std::memcpy(p, src, b);
+    PPN_CU(cudaMemcpyAsync(dst, p, b, cudaMemcpyHostToDevice, st));
+    return PPN_OK;
+  }
+  ppn_status sync_ctl() {
+    PPN_CU(cudaMemcpyAsync(h_ctl, d_ctl, sizeof(Ctl) * S.size(), cudaMemcpyDeviceToHost, st));
+    PPN_CU(cudaMemcpyAsync(h_bar, d_bar, sizeof(GridBar), cudaMemcpyDeviceToHost, st));
+    PPN_CU(cudaStreamSynchronize(st));
+    staging.reset();
+    if (timer) timer->collect();
+    return PPN_OK;
+  }
+  void set_active(const std::vector<char>& on) {
+    for (size_t i = 0; i < S.size(); ++i) h_desc[i].active = on[i] ? 1 : 0;
+  }
+};
+
+// Per-scene host state of the lockstep Newton loop.
+struct HostState {
+  int mode = 0;
+  int status = PPN_OK;
+  bool running = true;
+  int k = 0;
+  double delta = 0, g0 = -1, gn2 = 0, ginf = 0;
+  int n_proj = 0;
+  bool ind = false, fallback = false;
+  int precond_fail = 0, pcg_iters_last = 0;
+  double E0 = 0, dd = 0, dxmax = 0, gamma = 1;
+  int halvings = 0;
+  ppn_iter_stats cur{};
+  ppn_step_stats tot{};
+};
+
+template <typename T>
+struct Driver {
+  Group<T>& G;
+  std::vector<HostState> H;
+  const ppn_params& P;
+  explicit Driver(Group<T>& g) : G(g), P(g.S[0]->params) {}
+
+  double pcg_iter_bytes() const {
+    double b = 0;
+    for (auto* s : G.S) b += (double)s->nnzb * (9 * sizeof(T) + 4) + (double)s->nv * (4 + 12 * sizeof(T) + 9 * sizeof(T) + 12 * 4 * sizeof(T));
+    return b;
+  }
+
+  template <typename F>
+  void timed(int fam, double bytes, F&& f) {
+    G.timer->begin(fam, G.st, bytes);
+    f();
+    G.timer->end(G.st);
+  }
+
+  ppn_status check_launch() {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_error(std::string("kernel launch: ") + cudaGetErrorString(e));
+      return PPN_ERR_CUDA;
+    }
+    return PPN_OK;
+  }
+
+  // PCG over the scenes flagged in `on`; results land in each scene's Ctl
+  ppn_status solve(const std::vector<char>& on, int b_from_g) {
+    std::vector<int> ids;
+    for (size_t i = 0; i < on.size(); ++i)
+      if (on[i]) ids.push_back((int)i);
+    if (ids.empty()) return PPN_OK;
+    G.set_active(on);
+    ppn_status rc = G.upload_desc();
+    if (rc) return rc;
+    rc = G.upload(G.d_ids, ids.data(), sizeof(int) * ids.size());
+    if (rc) return rc;
+    PcgLaunch L;
+    L.n_tiles = G.n_ptiles;
+    L.n_scenes = (int)ids.size();
+    L.scene_ids = G.d_ids;
+    L.bar = G.d_bar;
+    L.grid = std::min(G.pcg_grid, G.n_ptiles);
+    L.group = G.pcg_group;
+    L.use_b_from_g = b_from_g;
+    cudaError_t e = cudaSuccess;
+    timed(FAM_PCG, 0.0, [&] { e = launch_pcg<T>(G.d_desc, G.d_ptiles, L, G.st); });
+    if (e != cudaSuccess) {
+      set_error(std::string("PCG launch: ") + cudaGetErrorString(e));
+      return PPN_ERR_CUDA;
+    }
+    return PPN_OK;
+  }
+
+  ppn_status step(const int* modes, double tol) {
+    const int n = (int)G.S.size();
+    H.assign(n, HostState());
+    std::vector<char> on(n, 1);
+    for (int i = 0; i < n; ++i) {
+      H[i].mode = modes[i];
+      H[i].delta = std::numeric_limits<double>::infinity();
+      G.S[i]->iters.clear();
+      G.S[i]->attempts.clear();
+    }
+    cudaEventRecord(G.S[0]->ev_a, G.st);
+    // predictor and Dirichlet targets
+    G.set_active(on);
+    ppn_status rc = G.upload_desc();
+    if (rc) return rc;
+    timed(FAM_VECTOR, 0, [&] { launch_predict<T>(G.d_desc, G.d_vtiles, G.n_vtiles, P.init_guess, G.st); });
+    for (int i = 0; i < n; ++i) {
+      SceneImpl<T>& s = *G.S[i];
+      const double* tg = s.ext_targets ? s.ext_targets : s.d_targets;
+      launch_apply_targets<T>(G.d_desc, i, s.d_fixed_list, tg, s.nfixed, 0, G.st);
+      s.ext_targets = nullptr;
+    }
+    if ((rc = check_launch())) return rc;
+
+    for (;;) {
+      std::vector<char> run(n, 0);
+      bool any = false;
+      for (int i = 0; i < n; ++i) {
+        run[i] = H[i].running;
+        any |= H[i].running;
+      }
+      if (!any) break;
+      // ---- element evaluation and gradient
+      for (int i = 0; i < n; ++i)
+        if (run[i]) {
+          G.h_desc[i].it_id = ++G.S[i]->it_counter;
+          G.h_desc[i].gamma = 0.0;
+        }
+      G.set_active(run);
+      if ((rc = G.upload_desc())) return rc;
+      timed(FAM_ELEMENT, 0, [&] { launch_element<T>(G.d_desc, G.d_ttiles, G.n_ttiles, 0, G.st); });
+      timed(FAM_GRADIENT, 0, [&] { launch_gradient<T>(G.d_desc, G.d_vtiles, G.n_vtiles, 0, G.st); });
+      if ((rc = check_launch())) return rc;
+      if ((rc = G.sync_ctl())) return rc;
+      std::vector<char> solve_on(n, 0), pn_on(n, 0);
+      bool any_solve = false, any_pn = false;
+      for (int i = 0; i < n; ++i) {
+        if (!run[i]) continue;
+        HostState& h = H[i];
+        const Ctl& c = G.h_ctl[i];
+        h.gn2 = std::sqrt(c.grad[0]);
+        h.ginf = c.grad[1];
+        h.tot.final_grad_norm2 = h.gn2;
+        if (!std::isfinite(h.gn2)) {
+          h.status = PPN_ERR_NONFINITE;
+          h.running = false;
+          continue;
+        }
+        if (h.k == 0) h.g0 = h.gn2;
+        if (P.tol_kind == 0 && h.gn2 <= tol * h.g0) {
+          h.status = PPN_OK;
+          h.running = false;
+          continue;
+        }
+        if (h.k >= P.newton_max_iter) {
+          h.status = PPN_ERR_NEWTON_MAXITER;
+          h.running = false;
+          continue;
+        }
+        h.cur = ppn_iter_stats{};
+        h.cur.newton_iter = h.k;
+        h.cur.grad_norm2 = h.gn2;
+        h.cur.grad_norminf = h.ginf;
+        h.n_proj = 0;
+        h.fallback = false;
+        solve_on[i] = 1;
+        any_solve = true;
+        if (h.mode == PPN_MODE_PN) {
+          pn_on[i] = 1;
+          any_pn = true;
+        }
+      }
+      if (!any_solve) continue;
+      // ---- PN: select every element and clamp before assembly
+      if (any_pn) {
+        for (int i = 0; i < n; ++i)
+          if (pn_on[i]) G.h_desc[i].delta = -1.0;
+        if ((rc = select_and_project(pn_on, true))) return rc;
+        for (int i = 0; i < n; ++i)
+          if (pn_on[i]) H[i].n_proj = G.S[i]->nt;
+      }
+      // ---- assembly and first solve
+      G.set_active(solve_on);
+      if ((rc = G.upload_desc())) return rc;
+      timed(FAM_ASSEMBLE, 0, [&] { launch_assemble<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st); });
+      if ((rc = check_launch())) return rc;
+      if ((rc = solve(solve_on, 1))) return rc;
+      if ((rc = G.sync_ctl())) return rc;
+      if ((rc = check_errors(solve_on))) return rc;
+      std::vector<char> retry(n, 0);
+      bool any_retry = false;
+      for (int i = 0; i < n; ++i) {
+        if (!solve_on[i]) continue;
+        record_attempt(i, 0, H[i].mode == PPN_MODE_PN ? G.S[i]->nt : 0,
+                       std::numeric_limits<double>::infinity());
+        if (H[i].ind && H[i].mode == PPN_MODE_PPN) {
+          retry[i] = 1;
+          any_retry = true;
+        } else if (H[i].ind) {
+          H[i].fallback = true;
+        }
+      }
+      // ---- PPN retries (Algorithm 1 inner loop)
+      int attempt = 1;
+      while (any_retry) {
+        for (int i = 0; i < n; ++i)
+          if (retry[i]) {
+            HostState& h = H[i];
+            if (std::isinf(h.delta)) h.delta = P.alpha * h.ginf;
+            G.h_desc[i].delta = h.delta;
+            G.h_desc[i].round_id = ++G.S[i]->round_counter;
+          }
+        if ((rc = select_and_project(retry, false))) return rc;
+        std::vector<char> resolve(n, 0);
+        bool any_resolve = false;
+        for (int i = 0; i < n; ++i)
+          if (retry[i] && G.h_ctl[i].n_new > 0) {
+            resolve[i] = 1;
+            any_resolve = true;
+          }
+        if (any_resolve) {
+          G.set_active(resolve);
+          if ((rc = G.upload_desc())) return rc;
+          timed(FAM_UPDATE, 0, [&] { launch_update<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st); });
+          if ((rc = check_launch())) return rc;
+          if ((rc = solve(resolve, 1))) return rc;
+          std::vector<int> n_new(n);
+          for (int i = 0; i < n; ++i) n_new[i] = G.h_ctl[i].n_new;
+          if ((rc = G.sync_ctl())) return rc;
+          if ((rc = check_errors(resolve))) return rc;
+          for (int i = 0; i < n; ++i)
+            if (resolve[i]) record_attempt(i, attempt, n_new[i], H[i].delta);
+        }
+        any_retry = false;
+        for (int i = 0; i < n; ++i) {
+          if (!retry[i]) continue;
+          HostState& h = H[i];
+          if (h.ind) {
+            if (h.n_proj >= G.S[i]->nt) {
+              h.fallback = true;  // fully projected and still indefinite (rounding)
+              retry[i] = 0;
+            } else {
+              h.delta *= P.alpha;  // tighten
+              any_retry = true;
+            }
+          } else {
+            retry[i] = 0;
+          }
+        }
+        ++attempt;
+      }
+      for (int i = 0; i < n; ++i)
+        if (solve_on[i] && H[i].mode == PPN_MODE_PPN) H[i].delta *= P.beta;  // relax
+      // ---- fallback directions when the solve gave no usable iterate
+      {
+        std::vector<char> fb2(n, 0), fb3(n, 0);
+        bool a2 = false, a3 = false;
+        for (int i = 0; i < n; ++i) {
+          if (!solve_on[i] || !H[i].fallback) continue;
+          if (H[i].pcg_iters_last == 0) {
+            if (H[i].precond_fail) {
+              fb3[i] = 1;
+              a3 = true;
+              H[i].cur.fallback = 3;
+            } else {
+              fb2[i] = 1;
+              a2 = true;
+              H[i].cur.fallback = 2;
+            }
+          } else {
+            H[i].cur.fallback = 1;
+          }
+        }
+        if (a2 && (rc = fallback_dir(fb2, 2))) return rc;
+        if (a3 && (rc = fallback_dir(fb3, 3))) return rc;
+      }
+      // ---- energy at gamma = 0 and directional derivative
+      if ((rc = energy(solve_on, true))) return rc;
+      {
+        std::vector<char> fb(n, 0);
+        bool afb = false;
+        int kind = 2;
+        for (int i = 0; i < n; ++i) {
+          if (!solve_on[i]) continue;
+          HostState& h = H[i];
+          if (!(h.dd < 0.0)) {
+            fb[i] = 1;
+            afb = true;
+            h.cur.fallback = h.precond_fail ? 3 : 2;
+            kind = h.cur.fallback;
+          }
+        }
+        if (afb) {
+          // rare: scenes needing the fallback are handled one kind at a time
+          for (int kd = 2; kd <= 3; ++kd) {
+            std::vector<char> sel(n, 0);
+            bool a = false;
+            for (int i = 0; i < n; ++i)
+              if (fb[i] && H[i].cur.fallback == kd) {
+                sel[i] = 1;
+                a = true;
+              }
+            if (a && (rc = fallback_dir(sel, kd))) return rc;
+          }
+          (void)kind;
+          if ((rc = energy(fb, true))) return rc;
+        }
+      }
+      // ---- backtracking line search (Armijo)
+      std::vector<char> ls(n, 0);
+      bool any_ls = false;
+      for (int i = 0; i < n; ++i)
+        if (solve_on[i]) {
+          ls[i] = 1;
+          any_ls = true;
+          H[i].gamma = 1.0;
+          H[i].halvings = 0;
+          H[i].cur.dir_deriv = H[i].dd;
+          H[i].cur.energy = H[i].E0;
+        }
+      std::vector<char> accept(n, 0);
+      while (any_ls) {
+        for (int i = 0; i < n; ++i)
+          if (ls[i]) G.h_desc[i].gamma = H[i].gamma;
+        if ((rc = energy(ls, false))) return rc;
+        any_ls = false;
+        for (int i = 0; i < n; ++i) {
+          if (!ls[i]) continue;
+          HostState& h = H[i];
+          const double Et = G.h_ctl[i].energy[0];
+          if (Et <= h.E0 + P.armijo_c * h.gamma * h.dd) {
+            ls[i] = 0;
+            accept[i] = 1;
+            h.cur.gamma = h.gamma;
+            h.cur.energy_new = Et;
+            h.cur.ls_halvings = h.halvings;
+          } else if (h.halvings >= P.ls_max_halvings) {
+            ls[i] = 0;
+            h.status = PPN_ERR_LINESEARCH;
+            h.running = false;
+            h.cur.ls_halvings = h.halvings;
+            finish_iter(i);
+          } else {
+            h.gamma *= 0.5;
+            h.halvings += 1;
+            any_ls = true;
+          }
+        }
+      }
+      // ---- position update
+      bool any_acc = false;
+      for (int i = 0; i < n; ++i) any_acc |= accept[i];
+      if (any_acc) {
+        for (int i = 0; i < n; ++i)
+          if (accept[i]) G.h_desc[i].gamma = H[i].gamma;
+        G.set_active(accept);
+        if ((rc = G.upload_desc())) return rc;
+        timed(FAM_VECTOR, 0, [&] { launch_axpy_u<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st); });
+        if ((rc = check_launch())) return rc;
+      }
+      for (int i = 0; i < n; ++i) {
+        if (!accept[i]) continue;
+        HostState& h = H[i];
+        finish_iter(i);
+        h.k += 1;
+        if (P.tol_kind == 1 && h.gamma * h.dxmax / G.S[i]->dt < tol) {
+          h.status = PPN_OK;
+          h.running = false;
+        }
+      }
+    }
+    // ---- velocities
+    G.set_active(std::vector<char>(n, 1));
+    if ((rc = G.upload_desc())) return rc;
+    timed(FAM_VECTOR, 0, [&] { launch_velocity<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st); });
+    cudaEventRecord(G.S[0]->ev_b, G.st);
+    if ((rc = check_launch())) return rc;
+    PPN_CU(cudaStreamSynchronize(G.st));
+    G.staging.reset();
+    G.timer->collect();
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, G.S[0]->ev_a, G.S[0]->ev_b);
+    for (int i = 0; i < n; ++i) {
+      H[i].tot.status = H[i].status;
+      H[i].tot.newton_iters = (int)G.S[i]->iters.size();
+      H[i].tot.device_ms = ms;
+      // keep the scene's own descriptor scalars in step with the group copy
+      G.S[i]->d.it_id = G.h_desc[i].it_id;
+      G.S[i]->d.round_id = G.h_desc[i].round_id;
+    }
+    return PPN_OK;
+  }
+
+  void finish_iter(int i) {
+    HostState& h = H[i];
+    h.cur.n_projected_total = h.n_proj;
+    h.cur.delta = h.delta;
+    h.cur.precond_fail = h.precond_fail;
+    G.S[i]->iters.push_back(h.cur);
+    h.tot.total_projections += h.n_proj;
+    h.tot.total_cg_iters += h.cur.cg_iters;
+    h.tot.total_attempts += h.cur.pcg_attempts;
+  }
+
+  void record_attempt(int i, int attempt, int n_new, double delta) {
+    HostState& h = H[i];
+    const Ctl& c = G.h_ctl[i];
+    h.ind = c.pcg_ind != 0;
+    h.precond_fail = c.pcg_precond_fail;
+    h.pcg_iters_last = c.pcg_iters;
+    h.cur.pcg_attempts += 1;
+    h.cur.cg_iters += c.pcg_iters;
+    ppn_attempt a;
+    a.newton_iter = h.k;
+    a.attempt = attempt;
+    a.n_new_projected = n_new;
+    a.ind = h.ind;
+    a.cg_iters = c.pcg_iters;
+    a.delta = delta;
+    G.S[i]->attempts.push_back(a);
+  }
+
+  ppn_status check_errors(const std::vector<char>& on) {
+    for (size_t i = 0; i < on.size(); ++i) {
+      if (!on[i]) continue;
+      if (G.h_ctl[i].error & kErrTimeout) {
+        set_error("PCG grid barrier timed out");
+        return PPN_ERR_TIMEOUT;
+      }
+    }
+    if (G.h_bar->timeout) {
+      set_error("PCG grid barrier timed out");
+      return PPN_ERR_TIMEOUT;
+    }
+    return PPN_OK;
+  }
+
+  // selection (delta in the descriptor; < 0 selects all) + clamping of the
+  // newly selected elements.  pn: no host sync needed for the count.
+  ppn_status select_and_project(const std::vector<char>& on, bool pn) {
+    const int n = (int)on.size();
+    G.set_active(on);
+    ppn_status rc = G.upload_desc();
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i)
+      if (on[i]) PPN_CU(cudaMemsetAsync(&G.d_ctl[i].n_new, 0, sizeof(int), G.st));
+    timed(FAM_SELECT, 0, [&] { launch_select<T>(G.d_desc, G.d_ttiles, G.n_ttiles, G.st); });
+    if ((rc = check_launch())) return rc;
+    std::vector<TileRef> jt;
+    if (pn) {
+      for (int i = 0; i < n; ++i)
+        if (on[i])
+          for (int t = 0; t < (G.S[i]->nt + PROJ_CTA - 1) / PROJ_CTA; ++t) jt.push_back({i, t});
+    } else {
+      if ((rc = G.sync_ctl())) return rc;
+      for (int i = 0; i < n; ++i)
+        if (on[i]) {
+          const int nn = G.h_ctl[i].n_new;
+          H[i].n_proj += nn;
+          H[i].cur.n_new_projected += nn;
+          for (int t = 0; t < (nn + PROJ_CTA - 1) / PROJ_CTA; ++t) jt.push_back({i, t});
+        }
+    }
+    if (jt.empty()) return PPN_OK;
+    if ((rc = G.upload(G.d_projtiles, jt.data(), sizeof(TileRef) * jt.size()))) return rc;
+    timed(FAM_PROJECT, 0, [&] { launch_project<T>(G.d_desc, G.d_projtiles, (int)jt.size(), 0, G.st); });
+    return check_launch();
+  }
+
+  ppn_status fallback_dir(const std::vector<char>& on, int kind) {
+    G.set_active(on);
+    ppn_status rc = G.upload_desc();
+    if (rc) return rc;
+    timed(FAM_VECTOR, 0, [&] { launch_fallback<T>(G.d_desc, G.d_vtiles, G.n_vtiles, kind, G.st); });
+    return check_launch();
+  }
+
+  // energy at u + gamma dx for the flagged scenes; at_zero also records E0, g^T dx, max|dx|
+  ppn_status energy(const std::vector<char>& on, bool at_zero) {
+    const int n = (int)on.size();
+    if (at_zero)
+      for (int i = 0; i < n; ++i)
+        if (on[i]) G.h_desc[i].gamma = 0.0;
+    G.set_active(on);
+    ppn_status rc = G.upload_desc();
+    if (rc) return rc;
+    timed(FAM_ENERGY, 0, [&] { launch_energy<T>(G.d_desc, G.d_etiles, G.n_etiles, 0, G.st); });
+    if ((rc = check_launch())) return rc;
+    if ((rc = G.sync_ctl())) return rc;
+    if (at_zero)
+      for (int i = 0; i < n; ++i)
+        if (on[i]) {
+          H[i].E0 = G.h_ctl[i].energy[0];
+          H[i].dd = G.h_ctl[i].energy[1];
+          H[i].dxmax = G.h_ctl[i].energy[2];
+        }
+    return PPN_OK;
+  }
+};
+
+// ------------------------------------------------------------------ group cache
+template <typename T>
+struct GroupCache {
+  std::map<std::vector<const void*>, std::unique_ptr<Group<T>>> groups;
+};
+
+template <typename T>
+static GroupCache<T>& group_cache() {
+  static GroupCache<T> c;
+  return c;
+}
+static std::mutex g_cache_mu;
+
+template <typename T>
+static Group<T>* get_group(const std::vector<SceneImpl<T>*>& members, ppn_status* rc) {
+  std::vector<const void*> key(members.begin(), members.end());
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto& c = group_cache<T>().groups;
+  auto it = c.find(key);
+  if (it != c.end()) {
+    // stream may have changed since the group was built
+    it->second->st = members[0]->stream;
+    *rc = PPN_OK;
+    return it->second.get();
+  }
+  auto g = std::make_unique<Group<T>>();
+  *rc = g->build(members);
+  if (*rc) return nullptr;
+  Group<T>* p = g.get();
+  c.emplace(key, std::move(g));
+  return p;
+}
+
+template <typename T>
+static void drop_groups_of(const SceneImpl<T>* s) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto& c = group_cache<T>().groups;
+  for (auto it = c.begin(); it != c.end();) {
+    if (std::find(it->first.begin(), it->first.end(), (const void*)s) != it->first.end())
+      it = c.erase(it);
+    else
+      ++it;
+  }
+}
+
+template <typename T>
+static ppn_status step_scenes(const std::vector<SceneImpl<T>*>& members, const int* modes, double tol,
+                              std::vector<ppn_step_stats>* out) {
+  ppn_status rc;
+  Group<T>* G = get_group<T>(members, &rc);
+  if (!G) return rc;
+  // sync descriptor scalars from the scenes (ids advance across groups)
+  for (size_t i = 0; i < members.size(); ++i) {
+    G->h_desc[i].it_id = members[i]->d.it_id;
+    G->h_desc[i].round_id = members[i]->d.round_id;
+    G->h_desc[i].delta = std::numeric_limits<double>::infinity();
+  }
+  Driver<T> D(*G);
+  rc = D.step(modes, tol);
+  if (out) {
+    out->resize(members.size());
+    for (size_t i = 0; i < members.size(); ++i) (*out)[i] = D.H[i].tot;
+  }
+  if (rc) return rc;
+  for (size_t i = 0; i < members.size(); ++i)
+    if (D.H[i].status != PPN_OK) return (ppn_status)D.H[i].status;
+  return PPN_OK;
+}
+
+// positions x = X + u into a host buffer
+template <typename T>
+__global__ void k_positions(const double4* X, const double4* u, double* xyz, int nv) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  const double4 a = ld_d4(X + v), b = ld_d4(u + v);
+  xyz[3 * v] = a.x + b.x;
+  xyz[3 * v + 1] = a.y + b.y;
+  xyz[3 * v + 2] = a.z + b.z;
+}
+
+template <typename T>
+__global__ void k_vel_out(const double4* w, double* xyz, int nv) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  const double4 a = ld_d4(w + v);
+  xyz[3 * v] = a.x;
+  xyz[3 * v + 1] = a.y;
+  xyz[3 * v + 2] = a.z;
+}
+
+template <typename T>
+static ppn_status read_positions(SceneImpl<T>& s, double* out) {
+  k_positions<T><<<(s.nv + 255) / 256, 256, 0, s.stream>>>(s.d.X, s.d.u, s.d_xyz, s.nv);
+  PPN_CU(cudaGetLastError());
+  PPN_CU(cudaMemcpyAsync(out, s.d_xyz, sizeof(double) * 3 * s.nv, cudaMemcpyDeviceToHost, s.stream));
+  PPN_CU(cudaStreamSynchronize(s.stream));
+  return PPN_OK;
+}
+
+// upload host positions as a displacement into `dst` (u = x - X)
+template <typename T>
+static ppn_status upload_positions(SceneImpl<T>& s, const double* x, double4* dst) {
+  std::vector<double4> u(s.nv);
+  for (int v = 0; v < s.nv; ++v)
+    u[v] = make_double4(x[3 * v] - s.rest[3 * v], x[3 * v + 1] - s.rest[3 * v + 1], x[3 * v + 2] - s.rest[3 * v + 2], 0.0);
+  PPN_CU(cudaMemcpyAsync(dst, u.data(), sizeof(double4) * s.nv, cudaMemcpyHostToDevice, s.stream));
+  PPN_CU(cudaStreamSynchronize(s.stream));
+  return PPN_OK;
+}
+
+// ------------------------------------------------------------------ probes
+template <typename T>
+struct Probe {
+  SceneImpl<T>& s;
+  Group<T>* G = nullptr;
+  explicit Probe(SceneImpl<T>& s_) : s(s_) {}
+  ppn_status begin() {
+    ppn_status rc;
+    G = get_group<T>({&s}, &rc);
+    if (!G) return rc;
+    G->h_desc[0].active = 1;
+    G->h_desc[0].it_id = ++s.it_counter;
+    G->h_desc[0].round_id = ++s.round_counter;
+    s.d.it_id = G->h_desc[0].it_id;
+    s.d.round_id = G->h_desc[0].round_id;
+    G->h_desc[0].gamma = 0.0;
+    return G->upload_desc();
+  }
+};
+
+template <typename T>
+static ppn_status probe_elements(SceneImpl<T>& s, const double* x, double* psi, double* ge, double* He) {
+  Probe<T> p(s);
+  ppn_status rc = p.begin();
+  if (rc) return rc;
+  if ((rc = upload_positions(s, x, s.d.u_probe))) return rc;
+  launch_element<T>(p.G->d_desc, p.G->d_ttiles, p.G->n_ttiles, 1, s.stream);
+  PPN_CU(cudaGetLastError());
+  PPN_CU(cudaStreamSynchronize(s.stream));
+  if (ge) {
+    std::vector<T> h((size_t)s.nt * GE_STRIDE);
+    PPN_CU(cudaMemcpy(h.data(), s.d.ge, sizeof(T) * h.size(), cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < h.size(); ++k) ge[k] = (double)h[k];
+  }
+  if (He) {
+    std::vector<T> h((size_t)s.nt * HE_STRIDE);
+    PPN_CU(cudaMemcpy(h.data(), s.d.He, sizeof(T) * h.size(), cudaMemcpyDeviceToHost));
+    for (int e = 0; e < s.nt; ++e)
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b)
+          for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) {
+              const T v = a <= b ? h[(size_t)e * HE_STRIDE + 9 * tri4(a, b) + 3 * i + k]
+                                 : h[(size_t)e * HE_STRIDE + 9 * tri4(b, a) + 3 * k + i];
+              He[(size_t)144 * e + 12 * (3 * a + i) + 3 * b + k] = (double)v;
+            }
+  }
+  if (psi) {
+    double* d_psi = nullptr;
+    PPN_CU(cudaMalloc(&d_psi, sizeof(double) * s.nt));
+    p.G->h_desc[0].psi_out = d_psi;
+    ppn_status rc2 = p.G->upload_desc();
+    if (rc2 == PPN_OK) {
+      launch_energy<T>(p.G->d_desc, p.G->d_etiles, p.G->n_etiles, 1, s.stream);
+      cudaMemcpyAsync(psi, d_psi, sizeof(double) * s.nt, cudaMemcpyDeviceToHost, s.stream);
+      cudaStreamSynchronize(s.stream);
+    }
+    p.G->h_desc[0].psi_out = nullptr;
+    cudaFree(d_psi);
+    if (rc2) return rc2;
+    PPN_CU(cudaGetLastError());
+  }
+  return PPN_OK;
+}
+
+template <typename T>
+static ppn_status probe_gradient(SceneImpl<T>& s, const double* x, const double* xhat, double* g,
+                                 double* norms, double* energy) {
+  Probe<T> p(s);
+  ppn_status rc = p.begin();
+  if (rc) return rc;
+  if ((rc = upload_positions(s, x, s.d.u_probe))) return rc;
+  if ((rc = upload_positions(s, xhat, s.d.uhat))) return rc;
+  launch_element<T>(p.G->d_desc, p.G->d_ttiles, p.G->n_ttiles, 1, s.stream);
+  launch_gradient<T>(p.G->d_desc, p.G->d_vtiles, p.G->n_vtiles, 1, s.stream);
+  if (energy) launch_energy<T>(p.G->d_desc, p.G->d_etiles, p.G->n_etiles, 1, s.stream);
+  PPN_CU(cudaGetLastError());
+  if ((rc = p.G->sync_ctl())) return rc;
+  if (norms) {
+    norms[0] = std::sqrt(p.G->h_ctl[0].grad[0]);
+    norms[1] = p.G->h_ctl[0].grad[1];
+  }
+  if (energy) *energy = p.G->h_ctl[0].energy[0];
+  if (g) {
+    std::vector<double4> h(s.nv);
+    PPN_CU(cudaMemcpy(h.data(), s.d.g, sizeof(double4) * s.nv, cudaMemcpyDeviceToHost));
+    for (int v = 0; v < s.nv; ++v) {
+      g[3 * v] = h[v].x;
+      g[3 * v + 1] = h[v].y;
+      g[3 * v + 2] = h[v].z;
+    }
+  }
+  return PPN_OK;
+}
+
+template <typename T>
+static ppn_status read_bsr(SceneImpl<T>& s, double* vals) {
+  std::vector<T> h((size_t)9 * s.nnzb);
+  PPN_CU(cudaMemcpy(h.data(), s.d.val, sizeof(T) * h.size(), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < s.nnzb; ++k)
+    for (int c = 0; c < 9; ++c) vals[(size_t)9 * k + c] = (double)h[(size_t)c * s.nnzb + k];
+  return PPN_OK;
+}
+
+// clamp the listed elements at the probe positions (fills dH, sets the count)
+template <typename T>
+static ppn_status probe_clamp_list(SceneImpl<T>& s, Probe<T>& p, const std::vector<int>& sel) {
+  if (sel.empty()) return PPN_OK;
+  PPN_CU(cudaMemcpy(s.d.sel_list, sel.data(), sizeof(int) * sel.size(), cudaMemcpyHostToDevice));
+  const int n = (int)sel.size();
+  PPN_CU(cudaMemcpy(&p.G->d_ctl[0].n_new, &n, sizeof(int), cudaMemcpyHostToDevice));
+  std::vector<TileRef> jt;
+  for (int t = 0; t < (n + PROJ_CTA - 1) / PROJ_CTA; ++t) jt.push_back({0, t});
+  ppn_status rc = p.G->upload(p.G->d_projtiles, jt.data(), sizeof(TileRef) * jt.size());
+  if (rc) return rc;
+  launch_project<T>(p.G->d_desc, p.G->d_projtiles, (int)jt.size(), 1, s.stream);
+  PPN_CU(cudaGetLastError());
+  PPN_CU(cudaStreamSynchronize(s.stream));
+  return PPN_OK;
+}
+
+template <typename T>
+static ppn_status probe_assemble(SceneImpl<T>& s, const double* x, const uint8_t* proj, double* vals) {
+  Probe<T> p(s);
+  ppn_status rc = p.begin();
+  if (rc) return rc;
+  if ((rc = upload_positions(s, x, s.d.u_probe))) return rc;
+  launch_element<T>(p.G->d_desc, p.G->d_ttiles, p.G->n_ttiles, 1, s.stream);
+  PPN_CU(cudaGetLastError());
+  std::vector<int> stamp(s.nt, -1), sel;
+  if (proj)
+    for (int e = 0; e < s.nt; ++e)
+      if (proj[e]) {
+        stamp[e] = p.G->h_desc[0].it_id;
+        sel.push_back(e);
+      }
+  PPN_CU(cudaMemcpyAsync(s.d.proj_stamp, stamp.data(), sizeof(int) * s.nt, cudaMemcpyHostToDevice, s.stream));
+  if ((rc = probe_clamp_list(s, p, sel))) return rc;
+  launch_assemble<T>(p.G->d_desc, p.G->d_btiles, p.G->n_btiles, s.stream);
+  PPN_CU(cudaGetLastError());
+  PPN_CU(cudaStreamSynchronize(s.stream));
+  return read_bsr(s, vals);
+}
+
+template <typename T>
+static ppn_status probe_select(SceneImpl<T>& s, const double* g, double delta, const uint8_t* already,
+                               uint8_t* out_new, int64_t* n_new) {
+  Probe<T> p(s);
+  ppn_status rc = p.begin();
+  if (rc) return rc;
+  std::vector<double4> g4(s.nv);
+  for (int v = 0; v < s.nv; ++v) g4[v] = make_double4(g[3 * v], g[3 * v + 1], g[3 * v + 2], 0.0);
+  PPN_CU(cudaMemcpy(s.d.g, g4.data(), sizeof(double4) * s.nv, cudaMemcpyHostToDevice));
+  std::vector<int> stamp(s.nt, -1);
+  if (already)
+    for (int e = 0; e < s.nt; ++e)
+      if (already[e]) stamp[e] = p.G->h_desc[0].it_id;
+  PPN_CU(cudaMemcpy(s.d.proj_stamp, stamp.data(), sizeof(int) * s.nt, cudaMemcpyHostToDevice));
+  p.G->h_desc[0].delta = delta;
+  if ((rc = p.G->upload_desc())) return rc;
+  PPN_CU(cudaMemsetAsync(&p.G->d_ctl[0].n_new, 0, sizeof(int), s.stream));
+  launch_gmax<T>(p.G->d_desc, p.G->d_vtiles, p.G->n_vtiles, s.stream);
+  launch_select<T>(p.G->d_desc, p.G->d_ttiles, p.G->n_ttiles, s.stream);
+  PPN_CU(cudaGetLastError());
+  if ((rc = p.G->sync_ctl())) return rc;
+  const int nn = p.G->h_ctl[0].n_new;
+  std::vector<int> list(nn);
+  if (nn) PPN_CU(cudaMemcpy(list.data(), s.d.sel_list, sizeof(int) * nn, cudaMemcpyDeviceToHost));
+  if (out_new) {
+    std::memset(out_new, 0, s.nt);
+    for (int e : list) out_new[e] = 1;
+  }
+  if (n_new) *n_new = nn;
+  return PPN_OK;
+}
+
+template <typename T>
+static ppn_status probe_project(SceneImpl<T>& s, const double* x, const int32_t* sel, int64_t n_sel,
+                                double* dH) {
+  Probe<T> p(s);
+  ppn_status rc = p.begin();
+  if (rc) return rc;
+  for (int64_t i = 0; i < n_sel; ++i)
+    if (sel[i] < 0 || sel[i] >= s.nt) {
+      set_error("element index out of range");
+      return PPN_ERR_INVALID_ARG;
+    }
+  if ((rc = upload_positions(s, x, s.d.u_probe))) return rc;
+  std::vector<int> list(sel, sel + n_sel);
+  // unique elements only (each owns one dH record)
+  std::vector<int> uniq(list);
+  std::sort(uniq.begin(), uniq.end());
+  uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+  if ((rc = probe_clamp_list(s, p, uniq))) return rc;
+  std::vector<T> rec(HE_STRIDE);
+  for (int64_t i = 0; i < n_sel; ++i) {
+    PPN_CU(cudaMemcpy(rec.data(), s.d.dH + (size_t)list[i] * HE_STRIDE, sizeof(T) * HE_STRIDE,
+                      cudaMemcpyDeviceToHost));
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b)
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c) {
+            const T v = a <= b ? rec[9 * tri4(a, b) + 3 * r + c] : rec[9 * tri4(b, a) + 3 * c + r];
+            dH[(size_t)144 * i + 12 * (3 * a + r) + 3 * b + c] = (double)v;
+          }
+  }
+  return PPN_OK;
+}
+
+template <typename T>
+static ppn_status probe_pcg(SceneImpl<T>& s, const double* vals, const double* b, double rel_tol,
+                            int max_iter, double* x, int* info) {
+  using V4 = vec4_t<T>;
+  Probe<T> p(s);
+  ppn_status rc = p.begin();
+  if (rc) return rc;
+  std::vector<T> h((size_t)9 * s.nnzb);
+  for (int k = 0; k < s.nnzb; ++k)
+    for (int c = 0; c < 9; ++c) h[(size_t)c * s.nnzb + k] = (T)vals[(size_t)9 * k + c];
+  PPN_CU(cudaMemcpy(s.d.val, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  std::vector<V4> r(s.nv);
+  for (int v = 0; v < s.nv; ++v) {
+    r[v].x = (T)b[3 * v];
+    r[v].y = (T)b[3 * v + 1];
+    r[v].z = (T)b[3 * v + 2];
+    r[v].w = (T)0;
+  }
+  PPN_CU(cudaMemcpy(s.d.r, r.data(), sizeof(V4) * s.nv, cudaMemcpyHostToDevice));
+  p.G->h_desc[0].pcg_tol2 = rel_tol * rel_tol;
+  p.G->h_desc[0].pcg_max_iter = max_iter > 0 ? max_iter : s.d.pcg_max_iter;
+  Driver<T> D(*p.G);
+  rc = D.solve(std::vector<char>{1}, 0);
+  p.G->h_desc[0].pcg_tol2 = s.d.pcg_tol2;
+  p.G->h_desc[0].pcg_max_iter = s.d.pcg_max_iter;
+  if (rc) return rc;
+  if ((rc = p.G->sync_ctl())) return rc;
+  if ((rc = D.check_errors(std::vector<char>{1}))) return rc;
+  const Ctl& c = p.G->h_ctl[0];
+  if (info) {
+    info[0] = c.pcg_iters;
+    info[1] = c.pcg_ind;
+    info[2] = c.pcg_precond_fail;
+    info[3] = c.pcg_hit_max;
+  }
+  std::vector<V4> xo(s.nv);
+  PPN_CU(cudaMemcpy(xo.data(), s.d.dx, sizeof(V4) * s.nv, cudaMemcpyDeviceToHost));
+  for (int v = 0; v < s.nv; ++v) {
+    x[3 * v] = (double)xo[v].x;
+    x[3 * v + 1] = (double)xo[v].y;
+    x[3 * v + 2] = (double)xo[v].z;
+  }
+  return PPN_OK;
+}
+
+}  // namespace ppn
+
+// ====================================================================== C ABI
+using namespace ppn;
+
+template <typename F>
+static ppn_status dispatch(ppn_scene* s, F&& f) {
+  if (!s) {
+    set_error("null scene");
+    return PPN_ERR_INVALID_ARG;
+  }
+  if (s->f) return f(*s->f);
+  return f(*s->d);
+}
+template <typename F>
+static ppn_status dispatch_c(const ppn_scene* s, F&& f) {
+  return dispatch(const_cast<ppn_scene*>(s), f);
+}
+
+extern "C" {
+
+ppn_params ppn_default_params(void) {
+  ppn_params p;
+  p.alpha = 0.5;
+  p.beta = 2.0;
+  p.eps_delta = 1e-12;
+  p.eig_eps = 1e-8;
+  p.pcg_rel_tol = 1e-4;
+  p.armijo_c = 1e-4;
+  p.gravity[0] = 0.0;
+  p.gravity[1] = -9.81;
+  p.gravity[2] = 0.0;
+  p.pcg_max_iter = 0;
+  p.newton_max_iter = 100;
+  p.ls_max_halvings = 30;
+  p.precision = PPN_PREC_MIXED;
+  p.tol_kind = 0;
+  p.init_guess = 0;
+  return p;
+}
+
+const char* ppn_status_string(ppn_status s) {
+  switch (s) {
+    case PPN_OK: return "ok";
+    case PPN_ERR_INVALID_ARG: return "invalid argument";
+    case PPN_ERR_OOM: return "out of device memory";
+    case PPN_ERR_CUDA: return "CUDA error";
+    case PPN_ERR_DEGENERATE_TET: return "degenerate tet";
+    case PPN_ERR_LINESEARCH: return "line search failed";
+    case PPN_ERR_NEWTON_MAXITER: return "Newton iteration cap reached";
+    case PPN_ERR_PCG_MAXITER: return "PCG iteration cap reached";
+    case PPN_ERR_NONFINITE: return "non-finite value";
+    case PPN_ERR_TIMEOUT: return "device wait timed out";
+    case PPN_ERR_ADMISSION: return "admission refused";
+  }
+  return "unknown status";
+}
+
+const char* ppn_last_error(void) { return g_last_error.c_str(); }
+
+ppn_status ppn_create_scene(const double* rest_xyz, int64_t n_verts, const int32_t* tets, int64_t n_tets,
+                            const ppn_material* mat, double dt, const int32_t* fixed, int64_t n_fixed,
+                            const ppn_params* params, ppn_scene** out) {
+  if (!out) {
+    set_error("null output pointer");
+    return PPN_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  const ppn_params p = params ? *params : ppn_default_params();
+  auto s = std::make_unique<ppn_scene>();
+  s->precision = p.precision;
+  ppn_status rc;
+  if (p.precision == PPN_PREC_FP64) {
+    s->d = std::make_unique<SceneImpl<double>>();
+    rc = s->d->init(rest_xyz, n_verts, tets, n_tets, mat, dt, fixed, n_fixed, &p);
+  } else if (p.precision == PPN_PREC_MIXED) {
+    s->f = std::make_unique<SceneImpl<float>>();
+    rc = s->f->init(rest_xyz, n_verts, tets, n_tets, mat, dt, fixed, n_fixed, &p);
+  } else {
+    set_error("unknown precision");
+    return PPN_ERR_INVALID_ARG;
+  }
+  if (rc != PPN_OK) return rc;
+  *out = s.release();
+  return PPN_OK;
+}
+
+void ppn_destroy_scene(ppn_scene* s) {
+  if (!s) return;
+  if (s->f) drop_groups_of(s->f.get());
+  if (s->d) drop_groups_of(s->d.get());
+  delete s;
+}
+
+ppn_status ppn_scene_get_info(const ppn_scene* s, ppn_scene_info* out) {
+  if (!out) return PPN_ERR_INVALID_ARG;
+  return dispatch_c(s, [&](auto& x) {
+    out->n_verts = x.nv;
+    out->n_tets = x.nt;
+    out->n_fixed = x.nfixed;
+    out->nnzb = x.nnzb;
+    out->n_map = x.nmap;
+    out->device_bytes = (int64_t)x.dev_bytes;
+    out->precision = s->precision;
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_set_stream(ppn_scene* s, void* cuda_stream) {
+  return dispatch(s, [&](auto& x) {
+    cudaStreamSynchronize(x.stream);
+    if (cuda_stream) {
+      if (x.own_stream) cudaStreamDestroy(x.stream);
+      x.own_stream = false;
+      x.stream = (cudaStream_t)cuda_stream;
+    } else if (!x.own_stream) {
+      PPN_CU(cudaStreamCreateWithFlags(&x.stream, cudaStreamNonBlocking));
+      x.own_stream = true;
+    }
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_set_kinematic_targets(ppn_scene* s, const double* xyz) {
+  return dispatch(s, [&](auto& x) {
+    if (x.nfixed == 0) return PPN_OK;
+    if (!xyz) {
+      set_error("null targets");
+      return PPN_ERR_INVALID_ARG;
+    }
+    PPN_CU(cudaMemcpyAsync(x.d_targets, xyz, sizeof(double) * 3 * x.nfixed, cudaMemcpyHostToDevice, x.stream));
+    PPN_CU(cudaStreamSynchronize(x.stream));
+    x.ext_targets = nullptr;
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_set_kinematic_targets_device(ppn_scene* s, const double* xyz) {
+  return dispatch(s, [&](auto& x) {
+    x.ext_targets = xyz;
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_step(ppn_scene* s, ppn_mode mode, double tol, double* out_xyz, ppn_step_stats* out) {
+  if (mode < PPN_MODE_NEWTON || mode > PPN_MODE_PPN || !(tol >= 0)) {
+    set_error("invalid mode or tolerance");
+    return PPN_ERR_INVALID_ARG;
+  }
+  return dispatch(s, [&](auto& x) {
+    std::vector<ppn_step_stats> st;
+    const int m = (int)mode;
+    using SI = std::remove_reference_t<decltype(x)>;
+    ppn_status rc = step_scenes(std::vector<SI*>{&x}, &m, tol, &st);
+    if (out && !st.empty()) *out = st[0];
+    if (rc != PPN_OK && rc != PPN_ERR_NEWTON_MAXITER && rc != PPN_ERR_LINESEARCH) return rc;
+    if (out_xyz) {
+      const ppn_status r2 = read_positions(x, out_xyz);
+      if (r2) return r2;
+    }
+    return rc;
+  });
+}
+
+ppn_status ppn_step_batch(ppn_scene* const* scenes, int n, const ppn_mode* modes, double tol,
+                          ppn_step_stats* out) {
+  if (!scenes || n <= 0 || !modes) {
+    set_error("invalid batch");
+    return PPN_ERR_INVALID_ARG;
+  }
+  const int prec = scenes[0] ? scenes[0]->precision : -1;
+  for (int i = 0; i < n; ++i)
+    if (!scenes[i] || scenes[i]->precision != prec) {
+      set_error("batch scenes must be non-null and share the precision");
+      return PPN_ERR_INVALID_ARG;
+    }
+  std::vector<int> m(modes, modes + n);
+  std::vector<ppn_step_stats> st;
+  ppn_status rc;
+  if (prec == PPN_PREC_FP64) {
+    std::vector<SceneImpl<double>*> v;
+    for (int i = 0; i < n; ++i) v.push_back(scenes[i]->d.get());
+    rc = step_scenes(v, m.data(), tol, &st);
+  } else {
+    std::vector<SceneImpl<float>*> v;
+    for (int i = 0; i < n; ++i) v.push_back(scenes[i]->f.get());
+    rc = step_scenes(v, m.data(), tol, &st);
+  }
+  if (out)
+    for (int i = 0; i < n && i < (int)st.size(); ++i) out[i] = st[i];
+  return rc;
+}
+
+ppn_status ppn_get_iter_stats(const ppn_scene* s, ppn_iter_stats* buf, int cap, int* n_written) {
+  return dispatch_c(s, [&](auto& x) {
+    const int n = (int)x.iters.size();
+    for (int i = 0; i < n && i < cap; ++i) buf[i] = x.iters[i];
+    if (n_written) *n_written = n;
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_get_attempts(const ppn_scene* s, ppn_attempt* buf, int cap, int* n_written) {
+  return dispatch_c(s, [&](auto& x) {
+    const int n = (int)x.attempts.size();
+    for (int i = 0; i < n && i < cap; ++i) buf[i] = x.attempts[i];
+    if (n_written) *n_written = n;
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_get_state(const ppn_scene* s, double* xo, double* vo) {
+  return dispatch_c(s, [&](auto& x) {
+    if (xo) {
+      ppn_status rc = read_positions(x, xo);
+      if (rc) return rc;
+    }
+    if (vo) {
+      using SI = std::remove_reference_t<decltype(x)>;
+      using TT = typename std::conditional<std::is_same<SI, SceneImpl<float>>::value, float, double>::type;
+      k_vel_out<TT><<<(x.nv + 255) / 256, 256, 0, x.stream>>>(x.d.vel, x.d_xyz, x.nv);
+      PPN_CU(cudaGetLastError());
+      PPN_CU(cudaMemcpyAsync(vo, x.d_xyz, sizeof(double) * 3 * x.nv, cudaMemcpyDeviceToHost, x.stream));
+      PPN_CU(cudaStreamSynchronize(x.stream));
+    }
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_set_state(ppn_scene* s, const double* xi, const double* vi) {
+  return dispatch(s, [&](auto& x) {
+    if (xi) {
+      ppn_status rc = upload_positions(x, xi, x.d.u);
+      if (rc) return rc;
+    }
+    if (vi) {
+      std::vector<double4> w(x.nv);
+      for (int v = 0; v < x.nv; ++v) w[v] = make_double4(vi[3 * v], vi[3 * v + 1], vi[3 * v + 2], 0.0);
+      PPN_CU(cudaMemcpy(x.d.vel, w.data(), sizeof(double4) * x.nv, cudaMemcpyHostToDevice));
+    }
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_get_displacement(const ppn_scene* s, double* uo, double* vo) {
+  return dispatch_c(s, [&](auto& x) {
+    std::vector<double4> h(x.nv);
+    double* outs[2] = {uo, vo};
+    double4* src[2] = {x.d.u, x.d.vel};
+    PPN_CU(cudaStreamSynchronize(x.stream));
+    for (int k = 0; k < 2; ++k) {
+      if (!outs[k]) continue;
+      PPN_CU(cudaMemcpy(h.data(), src[k], sizeof(double4) * x.nv, cudaMemcpyDeviceToHost));
+      for (int v = 0; v < x.nv; ++v) {
+        outs[k][3 * v] = h[v].x;
+        outs[k][3 * v + 1] = h[v].y;
+        outs[k][3 * v + 2] = h[v].z;
+      }
+    }
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_set_displacement(ppn_scene* s, const double* ui, const double* vi) {
+  return dispatch(s, [&](auto& x) {
+    std::vector<double4> h(x.nv);
+    const double* ins[2] = {ui, vi};
+    double4* dst[2] = {x.d.u, x.d.vel};
+    PPN_CU(cudaStreamSynchronize(x.stream));
+    for (int k = 0; k < 2; ++k) {
+      if (!ins[k]) continue;
+      for (int v = 0; v < x.nv; ++v) h[v] = make_double4(ins[k][3 * v], ins[k][3 * v + 1], ins[k][3 * v + 2], 0.0);
+      PPN_CU(cudaMemcpy(dst[k], h.data(), sizeof(double4) * x.nv, cudaMemcpyHostToDevice));
+    }
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_set_profiling(ppn_scene* s, int on) {
+  return dispatch(s, [&](auto& x) {
+    x.timer.on = on != 0;
+    x.timer.reset();
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_get_kernel_times(const ppn_scene* s, ppn_kernel_time* buf, int cap, int* n_written) {
+  return dispatch_c(s, [&](auto& x) {
+    int n = 0;
+    for (int f = 0; f < FAM_COUNT; ++f) {
+      if (n < cap && buf) {
+        std::memset(&buf[n], 0, sizeof(ppn_kernel_time));
+        std::snprintf(buf[n].name, sizeof(buf[n].name), "%s", kFamilyNames[f]);
+        buf[n].launches = x.timer.launches[f];
+        buf[n].total_ms = x.timer.ms[f];
+        buf[n].bytes = x.timer.bytes[f];
+      }
+      ++n;
+    }
+    if (n_written) *n_written = n;
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_probe_elements(ppn_scene* s, const double* x, double* psi_e, double* ge, double* He) {
+  if (!x) return PPN_ERR_INVALID_ARG;
+  return dispatch(s, [&](auto& sc) { return probe_elements(sc, x, psi_e, ge, He); });
+}
+
+ppn_status ppn_probe_pattern(const ppn_scene* s, int64_t* row_ptr, int32_t* col) {
+  return dispatch_c(s, [&](auto& x) {
+    if (row_ptr) std::memcpy(row_ptr, x.h_row_ptr.data(), sizeof(int64_t) * x.h_row_ptr.size());
+    if (col) std::memcpy(col, x.h_col.data(), sizeof(int32_t) * x.h_col.size());
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_probe_gradient(ppn_scene* s, const double* x, const double* xhat, double* g,
+                              double* norms, double* energy) {
+  if (!x || !xhat) return PPN_ERR_INVALID_ARG;
+  return dispatch(s, [&](auto& sc) { return probe_gradient(sc, x, xhat, g, norms, energy); });
+}
+
+ppn_status ppn_probe_assemble(ppn_scene* s, const double* x, const uint8_t* proj, double* vals) {
+  if (!x || !vals) return PPN_ERR_INVALID_ARG;
+  return dispatch(s, [&](auto& sc) { return probe_assemble(sc, x, proj, vals); });
+}
+
+ppn_status ppn_probe_select(ppn_scene* s, const double* g, double delta, const uint8_t* already,
+                            uint8_t* out_new, int64_t* n_new) {
+  if (!g) return PPN_ERR_INVALID_ARG;
+  return dispatch(s, [&](auto& sc) { return probe_select(sc, g, delta, already, out_new, n_new); });
+}
+
+ppn_status ppn_probe_project(ppn_scene* s, const double* x, const int32_t* sel, int64_t n_sel,
+                             double* dH) {
+  if (!x || (n_sel > 0 && (!sel || !dH)) || n_sel < 0) return PPN_ERR_INVALID_ARG;
+  return dispatch(s, [&](auto& sc) { return probe_project(sc, x, sel, n_sel, dH); });
+}
+
+ppn_status ppn_probe_pcg(ppn_scene* s, const double* vals, const double* b, double rel_tol,
+                         int max_iter, double* x, int* info) {
+  if (!vals || !b || !x) return PPN_ERR_INVALID_ARG;
+  return dispatch(s, [&](auto& sc) { return probe_pcg(sc, vals, b, rel_tol, max_iter, x, info); });
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Host-side scene objects and the lockstep Newton / PN / PPN driver.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/ppn.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ppn {
+
+void set_error(const std::string& msg);
+
+// Pinned staging arena for small host->device uploads (descriptor tables,
+// tile tables).  Slots are recycled after the owning stream has been synchronized.
+struct Staging {
+  char* base = nullptr;
+  size_t cap = 0, off = 0;
+  ~Staging();
+  void* take(size_t n, cudaStream_t st);
+  void reset() { off = 0; }
+};
+
+struct KernelTimer {
+  bool on = false;
+  struct Rec {
+    int fam;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  int64_t launches[16] = {0};
+  double ms[16] = {0};
+  double bytes[16] = {0};
+  ~KernelTimer();
+  cudaEvent_t ev();
+  void begin(int fam, cudaStream_t st, double b);
+  void end(cudaStream_t st);
+  void collect();  // after a stream sync
+  void reset();
+};
+
+enum KernelFamily {
+  FAM_ELEMENT = 0,
+  FAM_GRADIENT,
+  FAM_ASSEMBLE,
+  FAM_SELECT,
+  FAM_PROJECT,
+  FAM_UPDATE,
+  FAM_PCG,
+  FAM_ENERGY,
+  FAM_VECTOR,
+  FAM_COUNT
+};
+extern const char* kFamilyNames[FAM_COUNT];
+
+template <typename T>
+struct SceneImpl {
+  // sizes and parameters
+  int nv = 0, nt = 0, nnzb = 0, nmap = 0, nfixed = 0;
+  int n_vtiles = 0, n_ttiles = 0, n_btiles = 0, n_ptiles = 0;
+  ppn_params params;
+  double dt = 0;
+  std::vector<double> rest;       // host copy of rest positions (nv x 3)
+  std::vector<int> fixed_list;    // caller order
+  std::vector<int64_t> h_row_ptr; // pattern (host copy for probes)
+  std::vector<int> h_col;
+  // device memory
+  std::vector<void*> allocs;
+  size_t dev_bytes = 0;
+  SceneDev<T> d{};                // host mirror of the device descriptor
+  SceneDev<T>* d_desc = nullptr;  // device descriptor (single-scene launches)
+  TileRef *d_ttiles = nullptr, *d_vtiles = nullptr, *d_btiles = nullptr, *d_ptiles = nullptr,
+          *d_etiles = nullptr, *d_projtiles = nullptr;
+  int* d_ids = nullptr;
+  GridBar* d_bar = nullptr;
+  int* d_fixed_list = nullptr;
+  double* d_targets = nullptr;
+  const double* ext_targets = nullptr;  // device targets given by the caller for the next step
+  double* d_xyz = nullptr;              // nv x 3 output staging
+  Ctl* h_ctl = nullptr;                 // pinned
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Staging staging;
+  KernelTimer timer;
+  int pcg_group = 8, pcg_grid = 0;
+  // counters and per-step records
+  int it_counter = 0, round_counter = 0;
+  std::vector<ppn_iter_stats> iters;
+  std::vector<ppn_attempt> attempts;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+
+  ~SceneImpl();
+  ppn_status init(const double* rest_xyz, int64_t n_verts, const int32_t* tets, int64_t n_tets,
+                  const ppn_material* mat, double dt, const int32_t* fixed, int64_t n_fixed,
+                  const ppn_params* p);
+  template <typename X>
+  X* alloc(size_t n);
+};
+
+struct SceneBase;
+
+}  // namespace ppn
+
+struct ppn_scene {
+  int precision = PPN_PREC_MIXED;
+  std::unique_ptr<ppn::SceneImpl<float>> f;
+  std::unique_ptr<ppn::SceneImpl<double>> d;
+};

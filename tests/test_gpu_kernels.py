@@ -1,0 +1,194 @@
+"""GPU parity of each pipeline stage against the FP64 oracle, through the C ABI.
+
+Every test feeds the same seeded inputs to a CUDA stage (through a
+``ppn_probe_*`` entry point) and to the oracle, and compares element by
+element.  FP64 scenes must match to rounding (relative 1e-10 or tighter); the
+mixed-precision path (FP32 Hessians, eigensolves, BSR and PCG) to the bounds
+derived from FP32 rounding of O(1e2) operations (relative 2e-5 of the
+largest entry).
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2505_21013_gb300")
+from oracle import oracle as O  # noqa: E402
+from ppn_inputs import tiny_scene, twisting_beam_scene  # noqa: E402
+
+TOL = {P.PREC_FP64: 1e-10, P.PREC_MIXED: 2e-5}
+PRECS = [P.PREC_FP64, P.PREC_MIXED]
+
+
+def scene_pair(spec, prec):
+    return P.Scene.from_spec(spec, precision=prec), O.Scene.from_spec(spec)
+
+
+def deformed(spec, seed, amp=0.2):
+    rng = np.random.default_rng(seed)
+    x = spec.rest + amp * spec.meta["h"] * rng.standard_normal(spec.rest.shape)
+    x[spec.fixed] = spec.rest[spec.fixed]
+    return x
+
+
+def medium_spec(seed=0):
+    # several element/vertex tiles and PCG tiles with ragged tails
+    return twisting_beam_scene(7, 6, 13, h=0.02, E=1e5, nu=0.45, omega=5.0, dt=1 / 30, seed=seed)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_element_gradients_hessians_energies(prec):
+    spec = medium_spec(1)
+    g, o = scene_pair(spec, prec)
+    x = deformed(spec, 2, amp=0.4)
+    psi, ge, He = g.probe_elements(x)
+    psi_o, ge_o, He_o = o.element_eval(x)
+    # tet orientation normalisation must agree
+    assert np.array_equal(o.tets(), o.tets())
+    tol = TOL[prec]
+    assert np.abs(ge - ge_o).max() <= tol * np.abs(ge_o).max()
+    assert np.abs(He - He_o).max() <= tol * np.abs(He_o).max()
+    # element energies are FP64 in both precisions (Dm^-1 rounded to the storage type)
+    etol = 1e-9 if prec == P.PREC_FP64 else 2e-6
+    assert np.abs(psi - psi_o).max() <= etol * np.abs(psi_o).max()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_assembled_gradient_norms_and_energy(prec):
+    spec = medium_spec(3)
+    g, o = scene_pair(spec, prec)
+    x = deformed(spec, 4)
+    xhat = x + 0.001 * np.random.default_rng(5).standard_normal(x.shape)
+    gg, norms, en = g.probe_gradient(x, xhat)
+    go = o.gradient(x, xhat)
+    tol = TOL[prec]
+    assert np.abs(gg - go).max() <= tol * np.abs(go).max()
+    assert np.all(gg[spec.fixed] == 0)
+    assert abs(norms[0] - np.linalg.norm(go)) <= tol * np.linalg.norm(go)
+    assert abs(norms[1] - np.abs(go).max()) <= tol * np.abs(go).max()
+    eo = o.energy(x, xhat)
+    assert abs(en - eo) <= (1e-11 if prec == P.PREC_FP64 else 2e-6) * abs(eo)
+
+
+def test_bsr_pattern_is_identical():
+    spec = medium_spec(6)
+    g, o = scene_pair(spec, P.PREC_MIXED)
+    rp, col = g.probe_pattern()
+    rpo, colo = o.pattern()
+    assert np.array_equal(rp, rpo) and np.array_equal(col, colo)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_assembly_with_and_without_projection(prec):
+    spec = medium_spec(7)
+    g, o = scene_pair(spec, prec)
+    x = deformed(spec, 8, amp=0.6)
+    tol = TOL[prec]
+    v = g.probe_assemble(x)
+    vo = o.assemble(x)
+    assert np.abs(v - vo).max() <= tol * np.abs(vo).max()
+    proj = (np.random.default_rng(9).random(spec.n_tets) < 0.3).astype(np.uint8)
+    v = g.probe_assemble(x, proj)
+    vo = o.assemble(x, proj)
+    assert np.abs(v - vo).max() <= 4 * tol * np.abs(vo).max()
+
+
+def test_selection_is_exact_with_ties():
+    spec = medium_spec(10)
+    g, o = scene_pair(spec, P.PREC_MIXED)
+    rng = np.random.default_rng(11)
+    grad = rng.standard_normal((spec.n_verts, 3))
+    grad[spec.fixed] = 0
+    tets = o.tets()
+    r = np.abs(grad[tets]).max(axis=(1, 2))
+    for delta, frac in [(np.inf, 0.0), (2.0, 0.2), (float(r[5]), 0.1), (0.7, 0.5), (1e-13, 0.0), (-1.0, 0.0)]:
+        already = (rng.random(spec.n_tets) < frac).astype(np.uint8)
+        sel, n = g.probe_select(grad, delta, already)
+        if delta < 0:  # select-all request (PN)
+            assert np.array_equal(sel, ~already.astype(bool))
+            continue
+        sel_o, n_o = o.select(grad, delta, already)
+        assert np.array_equal(sel, sel_o) and n == n_o
+    # the exact tie r_e == delta is not selected on either side
+    sel, _ = g.probe_select(grad, float(r[5]))
+    assert not sel[5]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_projection_updates(prec):
+    spec = medium_spec(12)
+    g, o = scene_pair(spec, prec)
+    x = deformed(spec, 13, amp=1.0)
+    sel = np.arange(0, spec.n_tets, 7, dtype=np.int32)
+    dH = g.probe_project(x, sel)
+    dHo = o.project(x, sel)
+    _, _, He = o.element_eval(x)
+    scale = np.abs(He[sel]).max(axis=(1, 2))
+    err = np.abs(dH - dHo).max(axis=(1, 2)) / scale
+    assert err.max() <= (1e-9 if prec == P.PREC_FP64 else 2e-5)
+    # PSD after projection (independent LAPACK check)
+    w = np.linalg.eigvalsh(He[sel] + dH)
+    assert (w.min(axis=1) >= 1e-8 - (1e-9 if prec == P.PREC_FP64 else 2e-5) * scale).all()
+    # some element really had negative curvature
+    assert (np.linalg.eigvalsh(He[sel]).min(axis=1) < -1e-6 * scale).any()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_pcg_on_spd_and_indefinite_systems(prec):
+    spec = medium_spec(14)
+    g, o = scene_pair(spec, prec)
+    x = spec.rest  # rest state: K + M/dt^2 is SPD
+    vals = o.assemble(x)
+    rp, col = o.pattern()
+    b = np.random.default_rng(16).standard_normal((spec.n_verts, 3))
+    b[spec.fixed] = 0
+    xg, info = g.probe_pcg(vals, b, rel_tol=1e-4)
+    xo, info_o = O.pcg_bsr(rp, col, vals, b.reshape(-1), rel_tol=1e-4, max_iter=5000)
+    assert not info["ind"] and not info_o["ind"]
+    # same algorithm: the residual criterion holds and the iteration counts agree closely
+    A = lambda y: np.einsum("kij,kj->ki", vals, y.reshape(-1, 3)[col]).reshape(-1)
+    r = b.reshape(-1) - np.add.reduceat(np.einsum("kij,kj->ki", vals, xg[col]), rp[:-1]).reshape(-1)
+    assert np.linalg.norm(r) <= 1e-4 * np.linalg.norm(b) * (1.0 + (1e-6 if prec == P.PREC_FP64 else 5e-2))
+    if prec == P.PREC_FP64:
+        assert abs(info["iters"] - info_o["iters"]) <= 1
+        assert np.abs(xg.reshape(-1) - xo).max() <= 1e-6 * np.abs(xo).max()
+    else:
+        assert abs(info["iters"] - info_o["iters"]) <= max(3, info_o["iters"] // 10)
+    # indefinite: a strongly compressed state has negative-curvature directions
+    xi = deformed(spec, 17, amp=3.0)
+    vi = o.assemble(xi)
+    bi = b.copy()
+    xgi, infi = g.probe_pcg(vi, bi, rel_tol=1e-8)
+    xoi, infoi = O.pcg_bsr(rp, col, vi, bi.reshape(-1), rel_tol=1e-8, max_iter=5000)
+    assert infi["ind"] == infoi["ind"] == True  # noqa: E712
+    del A
+
+
+def test_pcg_zero_rhs_and_nonspd_diagonal():
+    spec = medium_spec(18)
+    g, o = scene_pair(spec, P.PREC_MIXED)
+    vals = o.assemble(spec.rest)
+    xg, info = g.probe_pcg(vals, np.zeros((spec.n_verts, 3)))
+    assert info["iters"] == 0 and not info["ind"] and np.all(xg == 0)
+    rp, col = o.pattern()
+    v2 = vals.copy()
+    free = np.setdiff1d(np.arange(spec.n_verts), spec.fixed)[0]
+    k = rp[free] + np.nonzero(col[rp[free]:rp[free + 1]] == free)[0][0]
+    v2[k] = np.diag([-9.0, 5.0, 1.0])  # the paper's Q = A + B + C in a diagonal block
+    b = np.ones((spec.n_verts, 3))
+    b[spec.fixed] = 0
+    xg, info = g.probe_pcg(v2, b)
+    assert info["ind"] and info["precond_fail"] and info["iters"] == 0
+
+
+def test_tiny_meshes_and_ragged_sizes():
+    for cells in [(1, 1, 1), (2, 1, 1), (3, 2, 1)]:
+        spec = tiny_scene(cells=cells, seed=sum(cells))
+        g, o = scene_pair(spec, P.PREC_FP64)
+        x = deformed(spec, 1, amp=0.3)
+        _, ge, He = g.probe_elements(x)
+        _, ge_o, He_o = o.element_eval(x)
+        assert np.abs(He - He_o).max() <= 1e-10 * np.abs(He_o).max()
+        v = g.probe_assemble(x)
+        assert np.abs(v - o.assemble(x)).max() <= 1e-10 * np.abs(v).max()
