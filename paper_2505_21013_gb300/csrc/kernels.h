@@ -24,29 +24,30 @@ template <typename T> void launch_axpy_u(const SceneDev<T>*, const TileRef*, int
 template <typename T> void launch_velocity(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
 template <typename T> void launch_fallback(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
 
-// Grid barrier state of the cooperative PCG kernel (device memory, zeroed once).
+// Grid barrier state of the cooperative PCG kernel (zeroed before each launch).
 struct GridBar {
-  unsigned count;
-  unsigned gen;
-  int all_done;
+  unsigned count;      // arrivals, monotonic within a launch
   int timeout;
+  int pad[2];
 };
 
+constexpr int PCG_MAX_SCENES = 256;  // scenes per PCG launch (per-CTA scalar state in shared memory)
+
 struct PcgLaunch {
-  int n_tiles;         // PCG row tiles in the tile table
-  int n_scenes;        // scenes taking part
-  const int* scene_ids;  // device: indices into the scene table
+  int n_tiles;           // PCG row tiles in the launch's tile table (TileRef.scene = slot)
+  const TileRef* tiles;  // device, grouped by slot, slot-major and tile-ascending
+  int n_scenes;          // slots taking part (<= PCG_MAX_SCENES)
+  const int* scene_ids;  // device: slot -> index into the scene table
   GridBar* bar;
-  int grid;            // cooperative grid size (CTAs)
-  int group;           // lanes per BSR row (4 or 8)
-  int use_b_from_g;    // 1: b = -g of the scene; 0: b given in r (probe)
+  int grid;              // cooperative grid size (CTAs)
+  int group;             // lanes per BSR row (4 or 8)
+  int use_b_from_g;      // 1: b = -g of the scene; 0: b given in r (probe)
 };
 
 // Occupancy-limited cooperative grid size for the chosen row group width.
 int pcg_max_grid(int group, int device);
 
 template <typename T>
-cudaError_t launch_pcg(const SceneDev<T>* scenes, const TileRef* tiles, const PcgLaunch& L,
-                       cudaStream_t st);
+cudaError_t launch_pcg(const SceneDev<T>* scenes, const PcgLaunch& L, cudaStream_t st);
 
 }  // namespace ppn

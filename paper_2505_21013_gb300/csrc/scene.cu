@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <map>
@@ -473,7 +474,8 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   PPN_CU(cudaMallocHost(&h_ctl, sizeof(Ctl)));
   int dev = 0;
   PPN_CU(cudaGetDevice(&dev));
-  pcg_group = 8;
+  pcg_group = 4;
+  if (const char* g = std::getenv("PPN_PCG_GROUP")) pcg_group = (std::atoi(g) == 8) ? 8 : 4;
   pcg_grid = pcg_max_grid(pcg_group, dev);
   if (pcg_grid <= 0) {
     set_error("PCG kernel cannot be made co-resident on this device");
@@ -499,6 +501,9 @@ struct Group {
           *d_etiles = nullptr, *d_projtiles = nullptr;
   int n_ttiles = 0, n_vtiles = 0, n_btiles = 0, n_ptiles = 0, n_etiles = 0;
   int* d_ids = nullptr;
+  TileRef* d_pcgtiles = nullptr;
+  std::vector<int> pcg_ids;  // slots of the tile table currently on the device
+  int pcg_ntiles = 0;
   GridBar* d_bar = nullptr;
   cudaStream_t st = nullptr;
   Staging staging;
@@ -551,9 +556,10 @@ struct Group {
     d_etiles = alloc<TileRef>(et.size());
     d_projtiles = alloc<TileRef>(projcap);
     d_ids = alloc<int>(n);
+    d_pcgtiles = alloc<TileRef>(pt.size());
     d_bar = alloc<GridBar>(1);
     if (!d_desc || !d_ctl || !d_ttiles || !d_vtiles || !d_btiles || !d_ptiles || !d_etiles ||
-        !d_projtiles || !d_ids || !d_bar) {
+        !d_projtiles || !d_ids || !d_bar || !d_pcgtiles) {
       set_error("cudaMalloc failed for a scene group");
       return PPN_ERR_OOM;
     }
@@ -665,21 +671,37 @@ struct Driver {
     G.set_active(on);
     ppn_status rc = G.upload_desc();
     if (rc) return rc;
-    rc = G.upload(G.d_ids, ids.data(), sizeof(int) * ids.size());
-    if (rc) return rc;
-    PcgLaunch L;
-    L.n_tiles = G.n_ptiles;
-    L.n_scenes = (int)ids.size();
-    L.scene_ids = G.d_ids;
-    L.bar = G.d_bar;
-    L.grid = std::min(G.pcg_grid, G.n_ptiles);
-    L.group = G.pcg_group;
-    L.use_b_from_g = b_from_g;
-    cudaError_t e = cudaSuccess;
-    timed(FAM_PCG, 0.0, [&] { e = launch_pcg<T>(G.d_desc, G.d_ptiles, L, G.st); });
-    if (e != cudaSuccess) {
-      set_error(std::string("PCG launch: ") + cudaGetErrorString(e));
-      return PPN_ERR_CUDA;
+    // slots of at most PCG_MAX_SCENES scenes per launch
+    for (size_t b = 0; b < ids.size(); b += PCG_MAX_SCENES) {
+      const size_t e = std::min(ids.size(), b + PCG_MAX_SCENES);
+      std::vector<int> sl(ids.begin() + b, ids.begin() + e);
+      int n_tiles = 0;
+      if (sl != G.pcg_ids) {
+        std::vector<TileRef> tt;
+        for (size_t k = 0; k < sl.size(); ++k)
+          for (int t = 0; t < G.S[sl[k]]->n_ptiles; ++t) tt.push_back({(int)k, t});
+        if ((rc = G.upload(G.d_ids, sl.data(), sizeof(int) * sl.size()))) return rc;
+        if ((rc = G.upload(G.d_pcgtiles, tt.data(), sizeof(TileRef) * tt.size()))) return rc;
+        G.pcg_ids = sl;
+        G.pcg_ntiles = (int)tt.size();
+      }
+      n_tiles = G.pcg_ntiles;
+      PcgLaunch L;
+      L.n_tiles = n_tiles;
+      L.tiles = G.d_pcgtiles;
+      L.n_scenes = (int)sl.size();
+      L.scene_ids = G.d_ids;
+      L.bar = G.d_bar;
+      L.grid = std::min(G.pcg_grid, n_tiles);
+      L.group = G.pcg_group;
+      L.use_b_from_g = b_from_g;
+      double bytes = 0.0;
+      cudaError_t err = cudaSuccess;
+      timed(FAM_PCG, bytes, [&] { err = launch_pcg<T>(G.d_desc, L, G.st); });
+      if (err != cudaSuccess) {
+        set_error(std::string("PCG launch: ") + cudaGetErrorString(err));
+        return PPN_ERR_CUDA;
+      }
     }
     return PPN_OK;
   }
