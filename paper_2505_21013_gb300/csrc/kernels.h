@@ -28,10 +28,11 @@ template <typename T> void launch_fallback(const SceneDev<T>*, const TileRef*, i
 struct GridBar {
   unsigned count;      // arrivals, monotonic within a launch
   int timeout;
-  int pad[2];
+  unsigned stamp;      // last exchange whose broadcast is complete
+  int pad;
 };
 
-constexpr int PCG_MAX_SCENES = 256;  // scenes per PCG launch (per-CTA scalar state in shared memory)
+constexpr int PCG_MAX_SCENES = 64;  // scenes per PCG launch (per-CTA scalar state in shared memory)
 
 struct PcgLaunch {
   int n_tiles;           // PCG row tiles in the launch's tile table (TileRef.scene = slot)
@@ -42,7 +43,19 @@ struct PcgLaunch {
   int grid;              // cooperative grid size (CTAs)
   int group;             // lanes per BSR row (4 or 8)
   int use_b_from_g;      // 1: b = -g of the scene; 0: b given in r (probe)
+  size_t smem_bytes;     // > 0: shared-memory-resident kernel with this dynamic size
+  int smem_blocks;       // block capacity of that layout (max blocks of one CTA)
+  void* bcast;           // device scratch of the resident kernel's exchange (PCG_XCH_BYTES)
+  unsigned launch_seq;   // distinct per launch on that scratch (stamps of older launches never match)
 };
+constexpr size_t PCG_XCH_BYTES = (512 + 128) * 1024 + 72 * 64;
+
+// dynamic shared memory of the resident PCG layout for ni rows and nb blocks
+size_t pcg_smem_bytes(int ni, int nb, int fsize);
+// co-resident grid of the resident PCG kernel with `smem` dynamic bytes (0: does not fit)
+int pcg_smem_max_grid(int group, int device, size_t smem, int fsize);
+template <typename T>
+cudaError_t launch_pcg_smem(const SceneDev<T>* scenes, const PcgLaunch& L, cudaStream_t st);
 
 // Occupancy-limited cooperative grid size for the chosen row group width.
 int pcg_max_grid(int group, int device);

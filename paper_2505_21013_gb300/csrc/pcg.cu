@@ -21,98 +21,12 @@
 // communication, and a scene's arithmetic does not depend on the grid size or
 // on the other scenes of a batch.  The barrier is one arrival counter that
 // only grows within a launch; its waits are bounded and report a timeout.
-#include "common.cuh"
-#include "kernels.h"
+#include "pcg_common.cuh"
 
 namespace ppn {
 
-namespace {
+using namespace pcgdev;
 
-constexpr unsigned kSpinLimit = 1u << 22;
-constexpr int NT = 1024;
-
-__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ float4 ldcg_v(const float4* p) { return __ldcg(p); }
-__device__ __forceinline__ double4 ldcg_v(const double4* p) {
-  const double2* q = reinterpret_cast<const double2*>(p);
-  const double2 a = __ldcg(q), b = __ldcg(q + 1);
-  return make_double4(a.x, a.y, b.x, b.y);
-}
-__device__ __forceinline__ void st_v(float4* p, float4 v) { *p = v; }
-__device__ __forceinline__ void st_v(double4* p, double4 v) { st_d4(p, v); }
-
-template <typename V4, typename T>
-__device__ __forceinline__ V4 mk(T x, T y, T z) {
-  V4 v;
-  v.x = x;
-  v.y = y;
-  v.z = z;
-  v.w = (T)0;
-  return v;
-}
-
-// Arrive and wait until `target` arrivals (all CTAs of barrier number target/gridDim.x).
-__device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned target, int* s_to) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(&bar->count, 1u);
-    unsigned spins = 0;
-    int to = 0;
-    while (ld_relaxed(&bar->count) < target) {
-      if (++spins > kSpinLimit) {
-        atomicExch(&bar->timeout, 1);
-        to = 1;
-        break;
-      }
-    }
-    __threadfence();
-    *s_to = to;
-  }
-  __syncthreads();
-  return *s_to == 0;
-}
-
-// sum of part[4 * t + k] over t in [0, n) by one warp, fixed order; valid in lane 0
-__device__ __forceinline__ double warp_tile_sum(const double* part, int n, int k) {
-  const int lane = threadIdx.x & 31;
-  double s = 0.0;
-#pragma unroll 4
-  for (int t = lane; t < n; t += 32) s += __ldcg(part + 4 * t + k);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  return s;
-}
-
-// reduction of one double per thread over aligned groups of PCG_TILE threads
-// (4 warps); result valid in the group's first thread
-__device__ __forceinline__ double subtile_sum(double v, double* sm) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) sm[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if ((threadIdx.x & (PCG_TILE - 1)) == 0) {
-    const int w0 = threadIdx.x >> 5;
-    s = ((sm[w0] + sm[w0 + 1]) + sm[w0 + 2]) + sm[w0 + 3];
-  }
-  __syncthreads();
-  return s;
-}
-
-// per-scene solver state, replicated identically in every CTA
-struct SState {
-  double rz, rr0, rr, alpha, beta, dq;
-  int iters, done, ind, pfail, hitmax, nonfinite;
-};
-
-}  // namespace
 
 template <typename T, int G>
 __global__ void __launch_bounds__(NT, 1)
@@ -148,31 +62,8 @@ __global__ void __launch_bounds__(NT, 1)
         const int kd = S.diag_idx[i];
 #pragma unroll
         for (int c = 0; c < 9; ++c) D[c] = S.val[(size_t)c * S.nnzb + kd];
-        // Cholesky of the lower triangle, then P = L^-T L^-1
-        bool ok = D[0] > (T)0;
-        const T l00 = ok ? sqrt(D[0]) : (T)1;
-        const T l10 = D[3] / l00, l20 = D[6] / l00;
-        const T d11 = D[4] - l10 * l10;
-        ok = ok && d11 > (T)0;
-        const T l11 = ok ? sqrt(d11) : (T)1;
-        const T l21 = (D[7] - l20 * l10) / l11;
-        const T d22 = D[8] - l20 * l20 - l21 * l21;
-        ok = ok && d22 > (T)0;
-        const T l22 = ok ? sqrt(d22) : (T)1;
-        const T i00 = (T)1 / l00, i11 = (T)1 / l11, i22 = (T)1 / l22;
-        const T i10 = -l10 * i00 * i11;
-        const T i21 = -l21 * i11 * i22;
-        const T i20 = -(l20 * i00 + l21 * i10) * i22;
         T Pm[9];
-        Pm[0] = i00 * i00 + i10 * i10 + i20 * i20;
-        Pm[1] = i10 * i11 + i20 * i21;
-        Pm[2] = i20 * i22;
-        Pm[4] = i11 * i11 + i21 * i21;
-        Pm[5] = i21 * i22;
-        Pm[8] = i22 * i22;
-        Pm[3] = Pm[1];
-        Pm[6] = Pm[2];
-        Pm[7] = Pm[5];
+        const bool ok = spd_inv3(D, Pm);
         T* P = S.Pinv + (size_t)9 * i;
 #pragma unroll
         for (int c = 0; c < 9; ++c) P[c] = Pm[c];
@@ -211,21 +102,7 @@ __global__ void __launch_bounds__(NT, 1)
     const double rz = warp_tile_sum(S.ppart, S.n_ptiles, 0);
     const double r2 = warp_tile_sum(S.ppart, S.n_ptiles, 1);
     const double f = warp_tile_sum(S.ppart, S.n_ptiles, 3);
-    if ((tid & 31) == 0) {
-      SState& s = st[si];
-      s.rz = rz;
-      s.rr0 = r2;
-      s.rr = r2;
-      s.alpha = 0.0;
-      s.beta = 0.0;
-      s.dq = 0.0;
-      s.iters = 0;
-      s.hitmax = 0;
-      s.nonfinite = !(r2 == r2) || !(rz == rz);
-      s.pfail = f > 0.0;
-      s.ind = f > 0.0;
-      s.done = (f > 0.0) || !(r2 > 0.0) || s.nonfinite;
-    }
+    if ((tid & 31) == 0) init_state(st[si], rz, r2, f);
   }
   __syncthreads();
 
@@ -309,19 +186,7 @@ __global__ void __launch_bounds__(NT, 1)
       if (st[si].done) continue;  // warp-uniform
       const SceneDev<T>& S = scenes[scene_ids[si]];
       const double dq = warp_tile_sum(S.ppart, S.n_ptiles, 2);
-      if ((tid & 31) == 0) {
-        SState& s = st[si];
-        s.dq = dq;
-        if (!(dq == dq)) {
-          s.nonfinite = 1;
-          s.done = 1;
-        } else if (!(dq > 0.0)) {
-          s.ind = 1;
-          s.done = 1;
-        } else {
-          s.alpha = s.rz / dq;
-        }
-      }
+      if ((tid & 31) == 0) after_dq(st[si], dq);
     }
     __syncthreads();
 
@@ -375,45 +240,14 @@ __global__ void __launch_bounds__(NT, 1)
       const SceneDev<T>& S = scenes[scene_ids[si]];
       const double rz = warp_tile_sum(S.ppart, S.n_ptiles, 0);
       const double r2 = warp_tile_sum(S.ppart, S.n_ptiles, 1);
-      if ((tid & 31) == 0) {
-        SState& s = st[si];
-        s.iters += 1;
-        s.rr = r2;
-        if (!(r2 == r2) || !(rz == rz)) {
-          s.nonfinite = 1;
-          s.done = 1;
-        } else if (r2 <= S.pcg_tol2 * s.rr0) {
-          s.done = 1;
-        } else if (s.iters >= S.pcg_max_iter) {
-          s.hitmax = 1;
-          s.done = 1;
-        } else {
-          s.beta = rz / s.rz;
-          s.rz = rz;
-        }
-      }
+      if ((tid & 31) == 0) after_rz(st[si], rz, r2, S.pcg_tol2, S.pcg_max_iter);
     }
     __syncthreads();
   }
 
   // every CTA holds the same final state; CTA 0 publishes it
   if (blockIdx.x == 0) {
-    for (int si = tid; si < n_scenes; si += NT) {
-      const SState& s = st[si];
-      Ctl* c = scenes[scene_ids[si]].ctl;
-      c->pcg_rr0 = s.rr0;
-      c->pcg_rr = s.rr;
-      c->pcg_rz = s.rz;
-      c->pcg_dq = s.dq;
-      c->pcg_alpha = s.alpha;
-      c->pcg_beta = s.beta;
-      c->pcg_iters = s.iters;
-      c->pcg_ind = s.ind;
-      c->pcg_precond_fail = s.pfail;
-      c->pcg_hit_max = s.hitmax;
-      c->pcg_done = 1;
-      if (s.nonfinite) c->error |= kErrNonFinite;
-    }
+    for (int si = tid; si < n_scenes; si += NT) publish(st[si], scenes[scene_ids[si]].ctl);
   }
 }
 

@@ -1,0 +1,374 @@
+// Helpers shared by the two cooperative PCG kernels (global-memory and
+// shared-memory-resident variants): bounded grid barrier, L2-only vector
+// loads, fixed-order reductions and the per-scene CG state.
+#pragma once
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ppn {
+namespace pcgdev {
+
+constexpr unsigned kSpinLimit = 1u << 22;
+constexpr int NT = 1024;
+
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ float4 ldcg_v(const float4* p) { return __ldcg(p); }
+__device__ __forceinline__ double4 ldcg_v(const double4* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = __ldcg(q), b = __ldcg(q + 1);
+  return make_double4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_v(float4* p, float4 v) { *p = v; }
+__device__ __forceinline__ void st_v(double4* p, double4 v) { st_d4(p, v); }
+
+template <typename V4, typename T>
+__device__ __forceinline__ V4 mk(T x, T y, T z) {
+  V4 v;
+  v.x = x;
+  v.y = y;
+  v.z = z;
+  v.w = (T)0;
+  return v;
+}
+
+// Arrive and wait until `target` arrivals (all CTAs of barrier number target/gridDim.x).
+// The wait is bounded; on timeout the barrier's flag is set and false returned.
+__device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned target, int* s_to) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&bar->count, 1u);
+    unsigned spins = 0;
+    int to = 0;
+    while (ld_relaxed(&bar->count) < target) {
+      if (++spins > kSpinLimit) {
+        atomicExch(&bar->timeout, 1);
+        to = 1;
+        break;
+      }
+    }
+    __threadfence();
+    *s_to = to;
+  }
+  __syncthreads();
+  return *s_to == 0;
+}
+
+// sum of part[4 * t + k] over t in [0, n) by one warp, fixed order; valid in lane 0
+__device__ __forceinline__ double warp_tile_sum(const double* part, int n, int k) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+#pragma unroll 4
+  for (int t = lane; t < n; t += 32) s += __ldcg(part + 4 * t + k);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// reduction of one double per thread over aligned groups of PCG_TILE threads
+// (4 warps); result valid in the group's first thread
+__device__ __forceinline__ double subtile_sum(double v, double* sm) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) sm[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if ((threadIdx.x & (PCG_TILE - 1)) == 0) {
+    const int w0 = threadIdx.x >> 5;
+    s = ((sm[w0] + sm[w0 + 1]) + sm[w0 + 2]) + sm[w0 + 3];
+  }
+  __syncthreads();
+  return s;
+}
+
+// ---- stamped partials: a tile partial and the phase that wrote it in one
+// 64-bit word (value rounded to a 48-bit double: sign, exponent, 36 mantissa
+// bits; low 16 bits = phase stamp).  64-bit aligned relaxed accesses are
+// single-copy atomic, so a reader that sees the stamp it waits for also sees
+// that phase's value; the writer's fence orders its vector stores before it.
+__device__ __forceinline__ unsigned long long pack_stamped(double v, unsigned stamp) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  b += 0x8000ull;  // round the magnitude at bit 16
+  return (b & ~0xFFFFull) | (unsigned long long)(stamp & 0xFFFFu);
+}
+__device__ __forceinline__ double stamped_value(unsigned long long w) {
+  return __longlong_as_double((long long)(w & ~0xFFFFull));
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Warp-wide wait-and-sum of slot k of n tile partials stamped `stamp` (fixed
+// order: lane-strided then a shuffle tree).  Valid in lane 0.  The wait is
+// bounded; *timeout is set when it gives up.
+__device__ __forceinline__ double warp_wait_sum(const double* part, int n, int k, unsigned stamp,
+                                                int* timeout) {
+  const unsigned long long* w = reinterpret_cast<const unsigned long long*>(part);
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int t0 = lane; t0 < n; t0 += 32 * 8) {
+    unsigned long long v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + 32 * u;
+      v[u] = t < n ? ld_relaxed_u64(w + 4 * t + k) : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + 32 * u;
+      if (t >= n) continue;
+      unsigned spins = 0;
+      while ((unsigned)(v[u] & 0xFFFFull) != (stamp & 0xFFFFu)) {
+        if (++spins > kSpinLimit) {
+          *timeout = 1;
+          break;
+        }
+        v[u] = ld_relaxed_u64(w + 4 * t + k);
+      }
+      s += stamped_value(v[u]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// the same for two slots of every tile, loaded together (one round trip)
+__device__ __forceinline__ void warp_wait_sum2(const double* part, int n, int k0, int k1, unsigned stamp,
+                                               int* timeout, double* out0, double* out1) {
+  const unsigned long long* w = reinterpret_cast<const unsigned long long*>(part);
+  const int lane = threadIdx.x & 31;
+  double s0 = 0.0, s1 = 0.0;
+  for (int t0 = lane; t0 < n; t0 += 32 * 4) {
+    unsigned long long a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + 32 * u;
+      a[u] = t < n ? ld_relaxed_u64(w + 4 * t + k0) : 0ull;
+      b[u] = t < n ? ld_relaxed_u64(w + 4 * t + k1) : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + 32 * u;
+      if (t >= n) continue;
+      unsigned spins = 0;
+      while ((unsigned)(a[u] & 0xFFFFull) != (stamp & 0xFFFFu) ||
+             (unsigned)(b[u] & 0xFFFFull) != (stamp & 0xFFFFu)) {
+        if (++spins > kSpinLimit) {
+          *timeout = 1;
+          break;
+        }
+        a[u] = ld_relaxed_u64(w + 4 * t + k0);
+        b[u] = ld_relaxed_u64(w + 4 * t + k1);
+      }
+      s0 += stamped_value(a[u]);
+      s1 += stamped_value(b[u]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+  }
+  *out0 = s0;
+  *out1 = s1;
+}
+
+// per-scene fields a PCG kernel needs, copied to shared memory once per solve
+// so that no phase chases descriptor pointers through global memory
+template <typename T>
+struct SceneLite {
+  using V4 = vec4_t<T>;
+  const int* row_ptr;
+  const int* col;
+  const T* val;
+  const int* diag_idx;
+  const double4* g;
+  V4* z;
+  V4* d0;
+  V4* d1;
+  V4* q;
+  V4* r;
+  V4* dx;
+  T* Pinv;
+  double* ppart;
+  Ctl* ctl;
+  double tol2;
+  int nv, nnzb, n_ptiles, max_iter;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_lite(SceneLite<T>& L, const SceneDev<T>& S) {
+  L.row_ptr = S.row_ptr;
+  L.col = S.col;
+  L.val = S.val;
+  L.diag_idx = S.diag_idx;
+  L.g = S.g;
+  L.z = S.z;
+  L.d0 = S.d0;
+  L.d1 = S.d1;
+  L.q = S.q;
+  L.r = S.r;
+  L.dx = S.dx;
+  L.Pinv = S.Pinv;
+  L.ppart = S.ppart;
+  L.ctl = S.ctl;
+  L.tol2 = S.pcg_tol2;
+  L.nv = S.nv;
+  L.nnzb = S.nnzb;
+  L.n_ptiles = S.n_ptiles;
+  L.max_iter = S.pcg_max_iter;
+}
+
+// per-scene solver state, replicated identically in every CTA
+struct SState {
+  double rz, rr0, rr, alpha, beta, dq;
+  int iters, done, ind, pfail, hitmax, nonfinite;
+};
+
+// 3x3 block-Jacobi inverse through the Cholesky factor of the lower triangle;
+// returns false when a pivot is not positive
+template <typename T>
+__device__ __forceinline__ bool spd_inv3(const T* D, T* Pm) {
+  bool ok = D[0] > (T)0;
+  const T l00 = ok ? sqrt(D[0]) : (T)1;
+  const T l10 = D[3] / l00, l20 = D[6] / l00;
+  const T d11 = D[4] - l10 * l10;
+  ok = ok && d11 > (T)0;
+  const T l11 = ok ? sqrt(d11) : (T)1;
+  const T l21 = (D[7] - l20 * l10) / l11;
+  const T d22 = D[8] - l20 * l20 - l21 * l21;
+  ok = ok && d22 > (T)0;
+  const T l22 = ok ? sqrt(d22) : (T)1;
+  const T i00 = (T)1 / l00, i11 = (T)1 / l11, i22 = (T)1 / l22;
+  const T i10 = -l10 * i00 * i11;
+  const T i21 = -l21 * i11 * i22;
+  const T i20 = -(l20 * i00 + l21 * i10) * i22;
+  Pm[0] = i00 * i00 + i10 * i10 + i20 * i20;
+  Pm[1] = i10 * i11 + i20 * i21;
+  Pm[2] = i20 * i22;
+  Pm[4] = i11 * i11 + i21 * i21;
+  Pm[5] = i21 * i22;
+  Pm[8] = i22 * i22;
+  Pm[3] = Pm[1];
+  Pm[6] = Pm[2];
+  Pm[7] = Pm[5];
+  return ok;
+}
+
+// scalar step after phase A: alpha, or the negative-curvature exit
+__device__ __forceinline__ void after_dq(SState& s, double dq) {
+  s.dq = dq;
+  if (!(dq == dq)) {
+    s.nonfinite = 1;
+    s.done = 1;
+  } else if (!(dq > 0.0)) {
+    s.ind = 1;
+    s.done = 1;
+  } else {
+    s.alpha = s.rz / dq;
+  }
+}
+
+// scalar step after phase B: convergence, iteration cap, beta
+__device__ __forceinline__ void after_rz(SState& s, double rz, double r2, double tol2, int max_iter) {
+  s.iters += 1;
+  s.rr = r2;
+  if (!(r2 == r2) || !(rz == rz)) {
+    s.nonfinite = 1;
+    s.done = 1;
+  } else if (r2 <= tol2 * s.rr0) {
+    s.done = 1;
+  } else if (s.iters >= max_iter) {
+    s.hitmax = 1;
+    s.done = 1;
+  } else {
+    s.beta = rz / s.rz;
+    s.rz = rz;
+  }
+}
+
+// Exchange area of the resident PCG kernel (byte offsets from the area base):
+//   records:   XCH_MAX_CTAS x XCH_REC_BYTES  {u64 stamp, u64 pad, double part[XCH_MAX_TILES][4]}
+//   mailboxes: XCH_MAX_CTAS x XCH_BOX_BYTES  {u64 stamp, u64 state[SSTATE_WORDS]}
+//   broadcast: PCG_MAX_SCENES x SSTATE_WORDS u64
+// Every word is accessed with explicit 64-bit relaxed loads/stores (no vector access).
+constexpr int XCH_MAX_CTAS = 1024;
+constexpr int XCH_MAX_TILES = 15;
+constexpr int XCH_REC_BYTES = 512;
+constexpr int XCH_BOX_BYTES = 128;
+constexpr int SSTATE_WORDS = 9;
+
+// SState <-> 9 words
+__device__ __forceinline__ unsigned long long sword(const SState& s, int w) {
+  switch (w) {
+    case 0: return (unsigned long long)__double_as_longlong(s.rz);
+    case 1: return (unsigned long long)__double_as_longlong(s.rr0);
+    case 2: return (unsigned long long)__double_as_longlong(s.rr);
+    case 3: return (unsigned long long)__double_as_longlong(s.alpha);
+    case 4: return (unsigned long long)__double_as_longlong(s.beta);
+    case 5: return (unsigned long long)__double_as_longlong(s.dq);
+    case 6: return (unsigned long long)(unsigned)s.iters | ((unsigned long long)(unsigned)s.done << 32);
+    case 7: return (unsigned long long)(unsigned)s.ind | ((unsigned long long)(unsigned)s.pfail << 32);
+    default: return (unsigned long long)(unsigned)s.hitmax | ((unsigned long long)(unsigned)s.nonfinite << 32);
+  }
+}
+__device__ __forceinline__ void set_sword(SState& s, int w, unsigned long long v) {
+  switch (w) {
+    case 0: s.rz = __longlong_as_double((long long)v); break;
+    case 1: s.rr0 = __longlong_as_double((long long)v); break;
+    case 2: s.rr = __longlong_as_double((long long)v); break;
+    case 3: s.alpha = __longlong_as_double((long long)v); break;
+    case 4: s.beta = __longlong_as_double((long long)v); break;
+    case 5: s.dq = __longlong_as_double((long long)v); break;
+    case 6: s.iters = (int)(v & 0xffffffffu); s.done = (int)(v >> 32); break;
+    case 7: s.ind = (int)(v & 0xffffffffu); s.pfail = (int)(v >> 32); break;
+    default: s.hitmax = (int)(v & 0xffffffffu); s.nonfinite = (int)(v >> 32); break;
+  }
+}
+
+__device__ __forceinline__ void init_state(SState& s, double rz, double r2, double f) {
+  s.rz = rz;
+  s.rr0 = r2;
+  s.rr = r2;
+  s.alpha = 0.0;
+  s.beta = 0.0;
+  s.dq = 0.0;
+  s.iters = 0;
+  s.hitmax = 0;
+  s.nonfinite = !(r2 == r2) || !(rz == rz);
+  s.pfail = f > 0.0;
+  s.ind = f > 0.0;
+  s.done = (f > 0.0) || !(r2 > 0.0) || s.nonfinite;
+}
+
+__device__ __forceinline__ void publish(const SState& s, Ctl* c) {
+  c->pcg_rr0 = s.rr0;
+  c->pcg_rr = s.rr;
+  c->pcg_rz = s.rz;
+  c->pcg_dq = s.dq;
+  c->pcg_alpha = s.alpha;
+  c->pcg_beta = s.beta;
+  c->pcg_iters = s.iters;
+  c->pcg_ind = s.ind;
+  c->pcg_precond_fail = s.pfail;
+  c->pcg_hit_max = s.hitmax;
+  c->pcg_done = 1;
+  if (s.nonfinite) c->error |= kErrNonFinite;
+}
+
+}  // namespace pcgdev
+}  // namespace ppn

@@ -502,8 +502,12 @@ struct Group {
   int n_ttiles = 0, n_vtiles = 0, n_btiles = 0, n_ptiles = 0, n_etiles = 0;
   int* d_ids = nullptr;
   TileRef* d_pcgtiles = nullptr;
+  void* d_bcast = nullptr;
+  unsigned pcg_launch_seq = 0;
   std::vector<int> pcg_ids;  // slots of the tile table currently on the device
   int pcg_ntiles = 0;
+  size_t pcg_smem_bytes = 0;  // > 0: resident PCG layout chosen for that table
+  int pcg_smem_blocks = 0, pcg_smem_grid = 0;
   GridBar* d_bar = nullptr;
   cudaStream_t st = nullptr;
   Staging staging;
@@ -557,9 +561,10 @@ struct Group {
     d_projtiles = alloc<TileRef>(projcap);
     d_ids = alloc<int>(n);
     d_pcgtiles = alloc<TileRef>(pt.size());
+    d_bcast = alloc<char>(PCG_XCH_BYTES);
     d_bar = alloc<GridBar>(1);
     if (!d_desc || !d_ctl || !d_ttiles || !d_vtiles || !d_btiles || !d_ptiles || !d_etiles ||
-        !d_projtiles || !d_ids || !d_bar || !d_pcgtiles) {
+        !d_projtiles || !d_ids || !d_bar || !d_pcgtiles || !d_bcast) {
       set_error("cudaMalloc failed for a scene group");
       return PPN_ERR_OOM;
     }
@@ -675,7 +680,6 @@ struct Driver {
     for (size_t b = 0; b < ids.size(); b += PCG_MAX_SCENES) {
       const size_t e = std::min(ids.size(), b + PCG_MAX_SCENES);
       std::vector<int> sl(ids.begin() + b, ids.begin() + e);
-      int n_tiles = 0;
       if (sl != G.pcg_ids) {
         std::vector<TileRef> tt;
         for (size_t k = 0; k < sl.size(); ++k)
@@ -684,26 +688,62 @@ struct Driver {
         if ((rc = G.upload(G.d_pcgtiles, tt.data(), sizeof(TileRef) * tt.size()))) return rc;
         G.pcg_ids = sl;
         G.pcg_ntiles = (int)tt.size();
+        plan_smem(sl, tt);
       }
-      n_tiles = G.pcg_ntiles;
+      const int n_tiles = G.pcg_ntiles;
       PcgLaunch L;
       L.n_tiles = n_tiles;
       L.tiles = G.d_pcgtiles;
       L.n_scenes = (int)sl.size();
       L.scene_ids = G.d_ids;
       L.bar = G.d_bar;
-      L.grid = std::min(G.pcg_grid, n_tiles);
+      L.grid = G.pcg_smem_bytes ? G.pcg_smem_grid : std::min(G.pcg_grid, n_tiles);
       L.group = G.pcg_group;
       L.use_b_from_g = b_from_g;
+      L.smem_bytes = G.pcg_smem_bytes;
+      L.smem_blocks = G.pcg_smem_blocks;
+      L.bcast = G.d_bcast;
+      L.launch_seq = ++G.pcg_launch_seq;
       double bytes = 0.0;
       cudaError_t err = cudaSuccess;
-      timed(FAM_PCG, bytes, [&] { err = launch_pcg<T>(G.d_desc, L, G.st); });
+      timed(FAM_PCG, bytes, [&] {
+        err = L.smem_bytes ? launch_pcg_smem<T>(G.d_desc, L, G.st) : launch_pcg<T>(G.d_desc, L, G.st);
+      });
       if (err != cudaSuccess) {
         set_error(std::string("PCG launch: ") + cudaGetErrorString(err));
         return PPN_ERR_CUDA;
       }
     }
     return PPN_OK;
+  }
+
+  // Choose the shared-memory-resident PCG when every CTA's rows fit.
+  void plan_smem(const std::vector<int>& sl, const std::vector<TileRef>& tt) {
+    G.pcg_smem_bytes = 0;
+    if (std::getenv("PPN_PCG_GLOBAL")) return;
+    const int n_tiles = (int)tt.size();
+    const int grid = std::min(G.pcg_grid, n_tiles);
+    int max_items = 0, max_blocks = 0;
+    for (int b = 0; b < grid; ++b) {
+      const int t0 = (int)(((long long)b * n_tiles) / grid), t1 = (int)(((long long)(b + 1) * n_tiles) / grid);
+      int blocks = 0;
+      for (int t = t0; t < t1; ++t) {
+        const SceneImpl<T>& sc = *G.S[sl[tt[t].scene]];
+        const int r0 = tt[t].tile * PCG_TILE, r1 = std::min(sc.nv, r0 + PCG_TILE);
+        if (r1 > r0) blocks += (int)(sc.h_row_ptr[r1] - sc.h_row_ptr[r0]);
+      }
+      max_items = std::max(max_items, (t1 - t0) * PCG_TILE);
+      max_blocks = std::max(max_blocks, blocks);
+    }
+    const size_t bytes = pcg_smem_bytes(max_items, max_blocks, (int)sizeof(T));
+    if (bytes > (size_t)196 * 1024 || max_items / PCG_TILE > 15 || grid > 1024) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int mg = pcg_smem_max_grid(G.pcg_group, dev, bytes, (int)sizeof(T));
+    if (mg < grid) return;
+    G.pcg_smem_bytes = bytes;
+    G.pcg_smem_blocks = max_blocks;
+    G.pcg_smem_grid = grid;
   }
 
   ppn_status step(const int* modes, double tol) {
