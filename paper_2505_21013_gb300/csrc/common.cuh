@@ -92,6 +92,7 @@ struct SceneDev {
   double* vpart;           // vertex tiles
   double* tpart;           // tet tiles
   double* ppart;           // PCG tiles
+  unsigned long long* pword;  // PCG tile partials as stamped hi/lo words, [4][n_ptiles][2]
   double* psi_out;         // optional per-element energies (probes)
   Ctl* ctl;
   // scalars of the current phase

@@ -205,6 +205,7 @@ struct SceneLite {
   V4* dx;
   T* Pinv;
   double* ppart;
+  unsigned long long* pword;
   Ctl* ctl;
   double tol2;
   int nv, nnzb, n_ptiles, max_iter;
@@ -225,6 +226,7 @@ __device__ __forceinline__ void load_lite(SceneLite<T>& L, const SceneDev<T>& S)
   L.dx = S.dx;
   L.Pinv = S.Pinv;
   L.ppart = S.ppart;
+  L.pword = S.pword;
   L.ctl = S.ctl;
   L.tol2 = S.pcg_tol2;
   L.nv = S.nv;
@@ -301,44 +303,7 @@ __device__ __forceinline__ void after_rz(SState& s, double rz, double r2, double
   }
 }
 
-// Exchange area of the resident PCG kernel (byte offsets from the area base):
-//   records:   XCH_MAX_CTAS x XCH_REC_BYTES  {u64 stamp, u64 pad, double part[XCH_MAX_TILES][4]}
-//   mailboxes: XCH_MAX_CTAS x XCH_BOX_BYTES  {u64 stamp, u64 state[SSTATE_WORDS]}
-//   broadcast: PCG_MAX_SCENES x SSTATE_WORDS u64
-// Every word is accessed with explicit 64-bit relaxed loads/stores (no vector access).
-constexpr int XCH_MAX_CTAS = 1024;
-constexpr int XCH_MAX_TILES = 15;
-constexpr int XCH_REC_BYTES = 512;
-constexpr int XCH_BOX_BYTES = 128;
-constexpr int SSTATE_WORDS = 9;
-
-// SState <-> 9 words
-__device__ __forceinline__ unsigned long long sword(const SState& s, int w) {
-  switch (w) {
-    case 0: return (unsigned long long)__double_as_longlong(s.rz);
-    case 1: return (unsigned long long)__double_as_longlong(s.rr0);
-    case 2: return (unsigned long long)__double_as_longlong(s.rr);
-    case 3: return (unsigned long long)__double_as_longlong(s.alpha);
-    case 4: return (unsigned long long)__double_as_longlong(s.beta);
-    case 5: return (unsigned long long)__double_as_longlong(s.dq);
-    case 6: return (unsigned long long)(unsigned)s.iters | ((unsigned long long)(unsigned)s.done << 32);
-    case 7: return (unsigned long long)(unsigned)s.ind | ((unsigned long long)(unsigned)s.pfail << 32);
-    default: return (unsigned long long)(unsigned)s.hitmax | ((unsigned long long)(unsigned)s.nonfinite << 32);
-  }
-}
-__device__ __forceinline__ void set_sword(SState& s, int w, unsigned long long v) {
-  switch (w) {
-    case 0: s.rz = __longlong_as_double((long long)v); break;
-    case 1: s.rr0 = __longlong_as_double((long long)v); break;
-    case 2: s.rr = __longlong_as_double((long long)v); break;
-    case 3: s.alpha = __longlong_as_double((long long)v); break;
-    case 4: s.beta = __longlong_as_double((long long)v); break;
-    case 5: s.dq = __longlong_as_double((long long)v); break;
-    case 6: s.iters = (int)(v & 0xffffffffu); s.done = (int)(v >> 32); break;
-    case 7: s.ind = (int)(v & 0xffffffffu); s.pfail = (int)(v >> 32); break;
-    default: s.hitmax = (int)(v & 0xffffffffu); s.nonfinite = (int)(v >> 32); break;
-  }
-}
+constexpr int XCH_MAX_CTAS = 1024;  // CTAs of one resident PCG launch (mailbox area)
 
 __device__ __forceinline__ void init_state(SState& s, double rz, double r2, double f) {
   s.rz = rz;

@@ -2,21 +2,29 @@
 // (SolveSPD of Algorithm 1; Sec. 4.1 "Linear Solvers", Sec. 5.1).
 //
 // Same iteration, scalars and reductions as the global-memory kernel in
-// pcg.cu; the difference is where the data of a CTA's rows lives.  When the
-// BSR rows of a CTA's contiguous tile range fit in shared memory, the setup
-// copies them there once per solve (column indices and 3x3 blocks, row-major
-// per block), together with the block-Jacobi inverse, each row's scene slot
-// and index, and the per-scene descriptors; the CTA then keeps its rows' x, r,
-// q, z and d vectors in shared memory for the whole solve.  Global memory only
-// carries what other CTAs need: z and the double-buffered d of every row
-// (gathered by neighbouring rows), the reduction partials and the final x.
-// Phase A issues all neighbour gathers of a lane before using any (up to U
-// blocks per lane per round).  There is no separate grid barrier: each tile
-// publishes its partials as stamped 64-bit words after a release fence, and a
-// CTA proceeds once it has read every tile's partial of the current phase,
-// which both completes the reduction and guarantees that every vector value
-// written before those partials is visible.  A CG iteration thus costs about
-// one L2 round trip for the gathers and one for each of the two reductions.
+// pcg.cu; the difference is where data lives and how CTAs exchange scalars.
+//
+// Data.  When the BSR rows of a CTA's contiguous tile range fit in shared
+// memory, the setup copies them there once per solve (column indices and 3x3
+// blocks, row-major per block) with the block-Jacobi inverse, each row's scene
+// slot and index, and the per-scene descriptors; the rows' x, r, q, z and d
+// vectors stay in shared memory for the whole solve.  Global memory carries
+// only what other CTAs need: z and the double-buffered d of every row
+// (gathered by neighbouring rows).  Phase A covers RPP rows per pass with G
+// lanes per row and issues all neighbour gathers of a lane before using any.
+//
+// Exchange.  A reduction value crosses the grid as two 64-bit words, hi and
+// lo (hi = the value with its 16 low mantissa bits cleared, lo = value - hi,
+// exact), each carrying the phase stamp in its 16 low bits.  Aligned 64-bit
+// accesses are single-copy atomic, so a word with the expected stamp carries
+// that phase's value and hi + lo restores the double exactly; no fence is
+// needed between a value and its flag.  Per phase: each CTA stores its vector
+// values, one fence per tile writer releases them, then the tile partials go
+// out as stamped words; CTA 0 reads every tile word (coalesced [k][tile]
+// layout, one round, re-polling only missing ones), sums each scene in tile
+// order and writes the sums as stamped words into one mailbox per CTA
+// (single-scene launches) or one broadcast area (batches); every CTA then
+// applies the same deterministic scalar update.  All waits are bounded.
 #include "pcg_common.cuh"
 
 namespace ppn {
@@ -27,19 +35,18 @@ namespace {
 
 template <typename T>
 struct SmemLayout {
-  double** lpart;  // [ntl] partial record of each local tile
-  double* lws;     // [ntl * 16 * 3] per-warp partial sums, summed per tile in fixed order
-  int* it_i;       // [ni] row index within its scene (-1: padding row)
-  int* it_slot;    // [ni] scene slot
-  int* lrp;        // [ni + 1] local row pointers into the block arrays
-  int* lcol;       // [nb] global column index
-  T* lval;         // [nb * 9] 3x3 blocks, row-major
-  T* lP;           // [ni * 9] block-Jacobi inverse
-  T* lx;           // [ni * 3]
+  double* lws;   // [ntl * 16 * 3] per-warp partial sums, summed per tile in fixed order
+  int* it_i;     // [ni] row index within its scene (-1: padding row)
+  int* it_slot;  // [ni] scene slot
+  int* lrp;      // [ni + 1] local row pointers into the block arrays
+  int* lcol;     // [nb] global column index
+  T* lval;       // [nb * 9] 3x3 blocks, row-major
+  T* lP;         // [ni * 9] block-Jacobi inverse
+  T* lx;         // [ni * 3]
   T* lr;
   T* lq;
   T* lz;
-  T* ld;           // own direction (in place; neighbours read the global copies)
+  T* ld;         // own direction (in place; neighbours read the global copies)
 };
 
 __host__ __device__ inline size_t rup16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -54,7 +61,6 @@ __device__ __forceinline__ SmemLayout<T> carve(char* base, int ni, int nb) {
     off += rup16(bytes);
     return p;
   };
-  L.lpart = (double**)take(sizeof(double*) * ntl);
   L.lws = (double*)take(sizeof(double) * ntl * 16 * 3);
   L.it_i = (int*)take(sizeof(int) * ni);
   L.it_slot = (int*)take(sizeof(int) * ni);
@@ -76,32 +82,68 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// ---- stamped hi/lo words (stamp 0 never used: the area is zeroed per launch)
+__device__ __forceinline__ unsigned stamp16(unsigned epoch) { return ((epoch - 1u) % 65535u) + 1u; }
+__device__ __forceinline__ void split_words(double v, unsigned s, unsigned long long* w) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long hb = b & ~0xFFFFull;
+  const double lo = v - __longlong_as_double((long long)hb);
+  const unsigned long long lb = (unsigned long long)__double_as_longlong(lo) & ~0xFFFFull;
+  w[0] = hb | s;
+  w[1] = lb | s;
+}
+__device__ __forceinline__ double join_words(unsigned long long h, unsigned long long l) {
+  return __longlong_as_double((long long)(h & ~0xFFFFull)) + __longlong_as_double((long long)(l & ~0xFFFFull));
+}
+__device__ __forceinline__ bool has_stamp(unsigned long long w, unsigned s) {
+  return (unsigned)(w & 0xFFFFull) == s;
+}
+// wait (bounded) for a word carrying stamp s; `w` is a first read of it.  Gives up
+// after kWaitSpins reads, or as soon as another thread of the CTA has given up.
+constexpr unsigned kWaitSpins = 1u << 20;
+__device__ __forceinline__ unsigned long long wait_word(const unsigned long long* p, unsigned long long w,
+                                                        unsigned s, volatile int* to) {
+  unsigned spins = 0;
+  while (!has_stamp(w, s)) {
+    if (++spins > kWaitSpins || *to) {
+      *to = 1;
+      break;
+    }
+    w = ld_relaxed_u64(p);
+  }
+  return w;
+}
+
 }  // namespace
 
 size_t pcg_smem_bytes(int ni, int nb, int fsize) {
   const size_t ntl = ni / PCG_TILE + 1;
-  return rup16(sizeof(double*) * ntl) + rup16(sizeof(double) * ntl * 16 * 3) + 2 * rup16(sizeof(int) * ni) +
-         rup16(sizeof(int) * (ni + 1)) + rup16(sizeof(int) * nb) + rup16((size_t)fsize * 9 * nb) +
-         rup16((size_t)fsize * 9 * ni) + 5 * rup16((size_t)fsize * 3 * ni);
+  return rup16(sizeof(double) * ntl * 16 * 3) + 2 * rup16(sizeof(int) * ni) + rup16(sizeof(int) * (ni + 1)) +
+         rup16(sizeof(int) * nb) + rup16((size_t)fsize * 9 * nb) + rup16((size_t)fsize * 9 * ni) +
+         5 * rup16((size_t)fsize * 3 * ni);
 }
 
-constexpr int NTS = 512;  // threads per CTA of the resident kernel (128-register budget, no spills)
+constexpr int NTS = 512;  // threads per CTA of the resident kernel (128-register budget)
+constexpr int MAXQ = 3;   // quantities exchanged per phase (setup: r.z, r.r, failed blocks)
 
 template <typename T, int G>
 __global__ void __launch_bounds__(NTS, 1)
     k_pcg_s(const SceneDev<T>* scenes, const TileRef* tiles, int n_tiles, const int* scene_ids,
-            int n_scenes, GridBar* bar, int b_from_g, int nb_cap, char* xch, unsigned launch_seq) {
+            int n_scenes, GridBar* bar, int b_from_g, int nb_cap, unsigned long long* xch) {
   using V4 = vec4_t<T>;
-  constexpr int RPP = NTS / G;  // rows per SpMV pass
-  constexpr int U = 4;          // blocks per lane per gather round
-  constexpr int NW = NTS / 32;  // warps
-  static_assert(RPP == PCG_TILE, "one SpMV pass covers exactly one reduction tile");
+  constexpr int RPP = NTS / G;            // rows per SpMV pass
+  constexpr int U = 16 / G;               // blocks per lane per gather round
+  constexpr int NW = NTS / 32;            // warps
+  constexpr int TPP = RPP / PCG_TILE;     // tiles per SpMV pass
+  constexpr int WPT = NW / TPP;           // warps per tile in an SpMV pass
+  static_assert(RPP % PCG_TILE == 0, "an SpMV pass covers whole reduction tiles");
   static_assert(NW <= 32, "one warp scans the warp totals");
   extern __shared__ __align__(16) char dyn[];
   __shared__ SState st[PCG_MAX_SCENES];
   __shared__ SceneLite<T> sl[PCG_MAX_SCENES];
+  __shared__ double s_sum[PCG_MAX_SCENES][MAXQ];
+  __shared__ unsigned long long s_w[2 * MAXQ];
   __shared__ int s_to, s_all_done;
-  __shared__ unsigned long long s_word[SSTATE_WORDS];
   __shared__ int s_scan[NW];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane32 = tid & 31;
@@ -113,27 +155,18 @@ __global__ void __launch_bounds__(NTS, 1)
   unsigned epoch = 0;
   if (tid == 0) s_to = 0;
 
-  // ---------------- per-scene descriptors and per-row (slot, index) into shared memory
-  for (int si = tid; si < n_scenes; si += NTS) load_lite(sl[si], scenes[scene_ids[si]]);
+  // ---------------- per-scene descriptors and per-row (slot, index) into shared memory;
+  // shared memory is not cleared between launches: the scalar state starts live
+  for (int si = tid; si < n_scenes; si += NTS) {
+    load_lite(sl[si], scenes[scene_ids[si]]);
+    st[si].done = 0;
+  }
   __syncthreads();
   for (int item = tid; item < n_items; item += NTS) {
     const TileRef tr = tiles[t0 + item / PCG_TILE];
     const int i = tr.tile * PCG_TILE + (item % PCG_TILE);
     L.it_slot[item] = tr.scene;
     L.it_i[item] = i < sl[tr.scene].nv ? i : -1;
-  }
-  for (int lt = tid; lt < ntl; lt += NTS) {
-    const TileRef tr = tiles[t0 + lt];
-    L.lpart[lt] = sl[tr.scene].ppart + 4 * tr.tile;
-  }
-  __shared__ int s_tb[PCG_MAX_SCENES + 1];  // first launch tile of each slot
-  if (tid == 0) {
-    int acc = 0;
-    for (int si = 0; si < n_scenes; ++si) {
-      s_tb[si] = acc;
-      acc += sl[si].n_ptiles;
-    }
-    s_tb[n_scenes] = acc;
   }
   __syncthreads();
 
@@ -193,92 +226,100 @@ __global__ void __launch_bounds__(NTS, 1)
   }
   __syncthreads();
 
-  // Exchange point (no hot line).  Every CTA posts its tiles' partials and a
-  // stamp in its own record; CTA 0 waits for all records, sums each scene's
-  // tile partials in tile order, updates the scalars with `update`, and
-  // writes a stamped mailbox per CTA (single scene: scalars inline); every
-  // other CTA polls only its own mailbox.  All waits are bounded.
-  const unsigned long long seq = (unsigned long long)launch_seq << 32;
-  auto rec_stamp = [&](int c) { return reinterpret_cast<unsigned long long*>(xch + (size_t)c * XCH_REC_BYTES); };
-  char* const boxes = xch + (size_t)XCH_MAX_CTAS * XCH_REC_BYTES;
-  auto box_word = [&](int c, int w) {  // w = 0: stamp, 1..9: state words
-    return reinterpret_cast<unsigned long long*>(boxes + (size_t)c * XCH_BOX_BYTES + 8 * w);
+  // ---------------- exchange
+  // tile partial k of tile t of a scene: pword[(k * n_ptiles + t) * 2 + h]
+  // mailbox of CTA c (single-scene launches): xch[c * 16 + 2q + h]
+  // broadcast (batches): xch[XCH_MAX_CTAS * 16 + (si * MAXQ + q) * 2 + h]
+  auto post_tile = [&](int lt, int k, double v, unsigned s) {
+    const TileRef tr = tiles[t0 + lt];
+    const SceneLite<T>& S = sl[tr.scene];
+    unsigned long long w[2];
+    split_words(v, s, w);
+    unsigned long long* p = S.pword + 2 * ((size_t)k * S.n_ptiles + tr.tile);
+    st_relaxed_u64(p, w[0]);
+    st_relaxed_u64(p + 1, w[1]);
   };
-  unsigned long long* const bcw =
-      reinterpret_cast<unsigned long long*>(xch + (size_t)XCH_MAX_CTAS * (XCH_REC_BYTES + XCH_BOX_BYTES));
-  auto exchange = [&](auto&& update) -> bool {
-    const unsigned long long S = seq | epoch;
-    __syncthreads();  // this CTA's record partials are written
-    if (tid == 0) {
-      __threadfence();
-      st_relaxed_u64(rec_stamp(blockIdx.x), S);
-    }
+  unsigned long long* const bcw = xch + (size_t)XCH_MAX_CTAS * 16;
+  // CTA 0 sums quantities ks[0..nq) of every live scene in tile order and publishes them;
+  // every other CTA waits for its words.  Then each CTA applies `update` to each live scene.
+  auto exchange = [&](const int* ks, int nq, auto&& update) -> bool {
+    const unsigned s = stamp16(epoch);
     if (blockIdx.x == 0) {
-      for (int c = tid; c < (int)gridDim.x; c += NTS) {
-        unsigned spins = 0;
-        while (ld_relaxed_u64(rec_stamp(c)) != S) {
-          if (++spins > kSpinLimit) {
-            s_to = 1;
-            break;
+      for (int si = warp; si < n_scenes; si += NW) {
+        if (st[si].done) continue;  // warp-uniform
+        const SceneLite<T>& S = sl[si];
+        const int n = S.n_ptiles;
+        for (int q = 0; q < nq; ++q) {
+          const unsigned long long* base = S.pword + 2 * (size_t)ks[q] * n;
+          double acc = 0.0;
+          for (int tw = lane32; tw < n; tw += 32 * 8) {
+            unsigned long long h[8], l[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int t = tw + 32 * u;
+              h[u] = t < n ? ld_relaxed_u64(base + 2 * t) : 0ull;
+              l[u] = t < n ? ld_relaxed_u64(base + 2 * t + 1) : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int t = tw + 32 * u;
+              if (t >= n) continue;
+              h[u] = wait_word(base + 2 * t, h[u], s, (volatile int*)&s_to);
+              l[u] = wait_word(base + 2 * t + 1, l[u], s, (volatile int*)&s_to);
+              acc += join_words(h[u], l[u]);
+            }
           }
+          acc = warp_sum(acc);
+          if (lane32 == 0) s_sum[si][q] = acc;
         }
       }
-      fence_acq_rel();
       __syncthreads();
-      if (!s_to) {
-        for (int si = warp; si < n_scenes; si += NW) update(si);
-        __syncthreads();
-        if (n_scenes > 1) {
-          for (int w = tid; w < n_scenes * SSTATE_WORDS; w += NTS)
-            st_relaxed_u64(bcw + w, sword(st[w / SSTATE_WORDS], w % SSTATE_WORDS));
-          __syncthreads();
-        }
-        for (int c = tid; c < (int)gridDim.x; c += NTS) {
-          if (n_scenes == 1)
-            for (int w = 0; w < SSTATE_WORDS; ++w) st_relaxed_u64(box_word(c, 1 + w), sword(st[0], w));
-          __threadfence();
-          st_relaxed_u64(box_word(c, 0), S);
+      if (n_scenes == 1) {
+        if (!st[0].done)
+          for (int c = tid; c < (int)gridDim.x; c += NTS)
+            for (int q = 0; q < nq; ++q) {
+              unsigned long long w[2];
+              split_words(s_sum[0][q], s, w);
+              st_relaxed_u64(xch + (size_t)c * 16 + 2 * q, w[0]);
+              st_relaxed_u64(xch + (size_t)c * 16 + 2 * q + 1, w[1]);
+            }
+      } else {
+        for (int x = tid; x < n_scenes * nq; x += NTS) {
+          const int si = x / nq, q = x % nq;
+          if (st[si].done) continue;
+          unsigned long long w[2];
+          split_words(s_sum[si][q], s, w);
+          st_relaxed_u64(bcw + 2 * (si * MAXQ + q), w[0]);
+          st_relaxed_u64(bcw + 2 * (si * MAXQ + q) + 1, w[1]);
         }
       }
+    } else if (n_scenes == 1) {
+      if (tid < 2 * nq && !st[0].done) {
+        const unsigned long long* p = xch + (size_t)blockIdx.x * 16 + tid;
+        s_w[tid] = wait_word(p, ld_relaxed_u64(p), s, (volatile int*)&s_to);
+      }
+      __syncthreads();
+      if (tid < nq && !st[0].done) s_sum[0][tid] = join_words(s_w[2 * tid], s_w[2 * tid + 1]);
     } else {
-      if (tid == 0) {
-        unsigned spins = 0;
-        while (ld_relaxed_u64(box_word(blockIdx.x, 0)) != S) {
-          if (++spins > kSpinLimit) {
-            s_to = 1;
-            break;
-          }
-        }
-        fence_acq_rel();
-      }
-      __syncthreads();
-      if (!s_to) {
-        if (n_scenes == 1) {
-          if (tid < SSTATE_WORDS) {
-            const unsigned long long v = ld_relaxed_u64(box_word(blockIdx.x, 1 + tid));
-            s_word[tid] = v;
-          }
-          __syncthreads();
-          if (tid == 0)
-            for (int w = 0; w < SSTATE_WORDS; ++w) set_sword(st[0], w, s_word[w]);
-        } else {
-          for (int si = tid; si < n_scenes; si += NTS)
-            for (int w = 0; w < SSTATE_WORDS; ++w) set_sword(st[si], w, ld_relaxed_u64(bcw + si * SSTATE_WORDS + w));
-        }
+      for (int x = tid; x < n_scenes * nq; x += NTS) {
+        const int si = x / nq, q = x % nq;
+        if (st[si].done) continue;
+        const unsigned long long* p = bcw + 2 * (si * MAXQ + q);
+        const unsigned long long h = wait_word(p, ld_relaxed_u64(p), s, (volatile int*)&s_to);
+        const unsigned long long l = wait_word(p + 1, ld_relaxed_u64(p + 1), s, (volatile int*)&s_to);
+        s_sum[si][q] = join_words(h, l);
       }
     }
+    fence_acq_rel();  // acquire: vector values released before the partials are visible
     __syncthreads();
-    if (s_to && tid == 0) atomicExch(&bar->timeout, 1);
-    return s_to == 0;
-  };
-  // fixed-order sum of slot k over a scene's tiles (one warp; valid in lane 0)
-  auto scene_sum = [&](int si, int k) {
-    const double* part = sl[si].ppart;
-    const int n = sl[si].n_ptiles;
-    double v = 0.0;
-#pragma unroll 4
-    for (int t = lane32; t < n; t += 32) v += __ldcg(part + 4 * t + k);
-    return warp_sum(v);
+    if (s_to) {
+      if (tid == 0) atomicExch(&bar->timeout, 1);
+      return false;
+    }
+    for (int si = tid; si < n_scenes; si += NTS)
+      if (!st[si].done) update(si);
+    __syncthreads();
+    return true;
   };
 
   // ---------------- setup: block-Jacobi inverse, r = b, z = P r, d = 0, x = 0
@@ -329,26 +370,26 @@ __global__ void __launch_bounds__(NTS, 1)
     r2 = warp_sum(r2);
     fail = warp_sum(fail);
     if (lane32 == 0) {
-      const int w = (base >> 5) + warp;  // 4 warps per tile
+      const int w = (base >> 5) + warp;  // 4 warps per tile (thread per row)
       L.lws[3 * w] = rz;
       L.lws[3 * w + 1] = r2;
       L.lws[3 * w + 2] = fail;
     }
   }
   __syncthreads();
+  ++epoch;
   for (int lt = tid; lt < ntl; lt += NTS) {
     const double* w = L.lws + 3 * 4 * lt;
-    double* p = L.lpart[lt];
-    p[0] = ((w[0] + w[3]) + w[6]) + w[9];
-    p[1] = ((w[1] + w[4]) + w[7]) + w[10];
-    p[3] = ((w[2] + w[5]) + w[8]) + w[11];
+    __threadfence();  // release this CTA's z and d stores before the partials
+    post_tile(lt, 0, ((w[0] + w[3]) + w[6]) + w[9], stamp16(epoch));
+    post_tile(lt, 1, ((w[1] + w[4]) + w[7]) + w[10], stamp16(epoch));
+    post_tile(lt, 3, ((w[2] + w[5]) + w[8]) + w[11], stamp16(epoch));
   }
-  ++epoch;
-  if (!exchange([&](int si) {
-        const double rz = scene_sum(si, 0), r2 = scene_sum(si, 1), f = scene_sum(si, 3);
-        if (lane32 == 0) init_state(st[si], rz, r2, f);
-      }))
-    return;
+  {
+    const int ks[3] = {0, 1, 3};
+    if (!exchange(ks, 3, [&](int si) { init_state(st[si], s_sum[si][0], s_sum[si][1], s_sum[si][2]); }))
+      return;
+  }
 
   for (;;) {
     if (tid == 0) {
@@ -435,21 +476,21 @@ __global__ void __launch_bounds__(NTS, 1)
       if (lane32 == 0) L.lws[3 * ((base / RPP) * NW + warp)] = dq;
     }
     __syncthreads();
+    ++epoch;
     for (int lt = tid; lt < ntl; lt += NTS) {
       if (st[L.it_slot[lt * PCG_TILE]].done) continue;
-      const double* w = L.lws + 3 * NW * lt;
+      // tile lt was covered by pass lt / TPP, warps [WPT * (lt % TPP), + WPT)
+      const double* w = L.lws + 3 * ((lt / TPP) * NW + WPT * (lt % TPP));
       double s = 0.0;
 #pragma unroll
-      for (int k = 0; k < NW; ++k) s += w[3 * k];
-      L.lpart[lt][2] = s;
+      for (int k = 0; k < WPT; ++k) s += w[3 * k];
+      __threadfence();  // release this CTA's d stores before the partial
+      post_tile(lt, 2, s, stamp16(epoch));
     }
-    ++epoch;
-    if (!exchange([&](int si) {
-          if (st[si].done) return;
-          const double dq = scene_sum(si, 2);
-          if (lane32 == 0) after_dq(st[si], dq);
-        }))
-      return;
+    {
+      const int ks[1] = {2};
+      if (!exchange(ks, 1, [&](int si) { after_dq(st[si], s_sum[si][0]); })) return;
+    }
 
     // ---------------- phase B: x += alpha d, r -= alpha q, z = P r (shared memory)
     for (int base = 0; base < n_items; base += NTS) {
@@ -492,20 +533,21 @@ __global__ void __launch_bounds__(NTS, 1)
       }
     }
     __syncthreads();
+    ++epoch;
     for (int lt = tid; lt < ntl; lt += NTS) {
       if (st[L.it_slot[lt * PCG_TILE]].done) continue;
       const double* w = L.lws + 3 * 4 * lt;
-      double* p = L.lpart[lt];
-      p[0] = ((w[0] + w[3]) + w[6]) + w[9];
-      p[1] = ((w[1] + w[4]) + w[7]) + w[10];
+      __threadfence();  // release this CTA's z stores before the partials
+      post_tile(lt, 0, ((w[0] + w[3]) + w[6]) + w[9], stamp16(epoch));
+      post_tile(lt, 1, ((w[1] + w[4]) + w[7]) + w[10], stamp16(epoch));
     }
-    ++epoch;
-    if (!exchange([&](int si) {
-          if (st[si].done) return;
-          const double rz = scene_sum(si, 0), r2 = scene_sum(si, 1);
-          if (lane32 == 0) after_rz(st[si], rz, r2, sl[si].tol2, sl[si].max_iter);
-        }))
-      return;
+    {
+      const int ks[2] = {0, 1};
+      if (!exchange(ks, 2, [&](int si) {
+            after_rz(st[si], s_sum[si][0], s_sum[si][1], sl[si].tol2, sl[si].max_iter);
+          }))
+        return;
+    }
   }
 
   // x of this CTA's rows to global memory; CTA 0 publishes the scalars
@@ -519,10 +561,10 @@ __global__ void __launch_bounds__(NTS, 1)
     for (int si = tid; si < n_scenes; si += NTS) publish(st[si], sl[si].ctl);
 }
 
-// rows are split over G = 4 lanes (512 threads cover one 128-row tile per pass)
+// G = 2 lanes per row: 512 threads cover two 128-row tiles per pass
 template <typename T>
 static const void* smem_kernel(int) {
-  return (const void*)k_pcg_s<T, 4>;
+  return (const void*)k_pcg_s<T, 2>;
 }
 
 int pcg_smem_max_grid(int group, int device, size_t smem, int fsize) {
@@ -543,9 +585,17 @@ int pcg_smem_max_grid(int group, int device, size_t smem, int fsize) {
 
 template <typename T>
 cudaError_t launch_pcg_smem(const SceneDev<T>* scenes, const PcgLaunch& L, cudaStream_t st) {
-  if (L.n_scenes <= 0 || L.n_scenes > PCG_MAX_SCENES || L.n_tiles <= 0) return cudaErrorInvalidValue;
+  if (L.n_scenes <= 0 || L.n_scenes > PCG_MAX_SCENES || L.n_tiles <= 0 || L.grid > XCH_MAX_CTAS)
+    return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(L.bar, 0, sizeof(GridBar), st);
   if (e != cudaSuccess) return e;
+  // no stamp of an earlier launch may survive in the exchange words
+  e = cudaMemsetAsync(L.bcast, 0, PCG_XCH_BYTES, st);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < L.n_pword; ++k) {
+    e = cudaMemsetAsync(L.pword[k], 0, L.pword_bytes[k], st);
+    if (e != cudaSuccess) return e;
+  }
   const TileRef* tiles = L.tiles;
   int n_tiles = L.n_tiles;
   const int* ids = L.scene_ids;
@@ -553,11 +603,9 @@ cudaError_t launch_pcg_smem(const SceneDev<T>* scenes, const PcgLaunch& L, cudaS
   GridBar* bar = L.bar;
   int bg = L.use_b_from_g;
   int nb_cap = L.smem_blocks;
-  char* xch = reinterpret_cast<char*>(L.bcast);
-  unsigned seq = L.launch_seq;
-  if (L.grid > XCH_MAX_CTAS) return cudaErrorInvalidValue;
+  unsigned long long* xch = reinterpret_cast<unsigned long long*>(L.bcast);
   void* args[] = {(void*)&scenes, (void*)&tiles, (void*)&n_tiles, (void*)&ids, (void*)&n_scenes,
-                  (void*)&bar, (void*)&bg, (void*)&nb_cap, (void*)&xch, (void*)&seq};
+                  (void*)&bar, (void*)&bg, (void*)&nb_cap, (void*)&xch};
   const void* k = smem_kernel<T>(L.group);
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
   if (e != cudaSuccess) return e;

@@ -378,6 +378,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   s.vpart = alloc<double>((size_t)4 * n_vtiles);
   s.tpart = alloc<double>((size_t)4 * (n_vtiles + n_ttiles));
   s.ppart = alloc<double>((size_t)4 * n_ptiles);
+  s.pword = alloc<unsigned long long>((size_t)8 * n_ptiles);
   s.ctl = alloc<Ctl>(1);
   d_desc = alloc<SceneDev<T>>(1);
   d_ids = alloc<int>(1);
@@ -399,7 +400,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
       !d_col || !d_blk_row || !d_blk_ptr || !d_blk_src || !d_diag || !s.u || !s.u_n || !s.vel ||
       !s.uhat || !s.u_probe || !s.ge || !s.He || !s.dH || !s.g || !s.gmax || !s.val ||
       !s.proj_stamp || !s.round_stamp || !s.sel_list || !s.dx || !s.r || !s.z || !s.q || !s.d0 ||
-      !s.d1 || !s.Pinv || !s.vpart || !s.tpart || !s.ppart || !s.ctl || !d_desc || !d_ids ||
+      !s.d1 || !s.Pinv || !s.vpart || !s.tpart || !s.ppart || !s.pword || !s.ctl || !d_desc || !d_ids ||
       !d_bar || !d_fixed_list || !d_targets || !d_xyz || !d_ttiles || !d_vtiles || !d_btiles ||
       !d_ptiles || !d_etiles || !d_projtiles) {
     set_error("cudaMalloc failed (scene needs more device memory than is free)");
@@ -704,6 +705,11 @@ struct Driver {
       L.smem_blocks = G.pcg_smem_blocks;
       L.bcast = G.d_bcast;
       L.launch_seq = ++G.pcg_launch_seq;
+      L.n_pword = (int)sl.size();
+      for (size_t k = 0; k < sl.size(); ++k) {
+        L.pword[k] = G.h_desc[sl[k]].pword;
+        L.pword_bytes[k] = sizeof(unsigned long long) * 8 * G.S[sl[k]]->n_ptiles;
+      }
       double bytes = 0.0;
       cudaError_t err = cudaSuccess;
       timed(FAM_PCG, bytes, [&] {
@@ -736,7 +742,7 @@ struct Driver {
       max_blocks = std::max(max_blocks, blocks);
     }
     const size_t bytes = pcg_smem_bytes(max_items, max_blocks, (int)sizeof(T));
-    if (bytes > (size_t)196 * 1024 || max_items / PCG_TILE > 15 || grid > 1024) return;
+    if (bytes > (size_t)196 * 1024 || grid > 1024) return;
     int dev = 0;
     cudaGetDevice(&dev);
     const int mg = pcg_smem_max_grid(G.pcg_group, dev, bytes, (int)sizeof(T));
