@@ -116,6 +116,40 @@ def pcg_bytes_per_iter(info, fsize=4):
     return nnzb * (9 * fsize + 4) + nv * (4 + 4 * 16 + 4 * 16 + 9 * fsize + 3 * 16)
 
 
+PCG_SOURCES = ("pcg_smem.cu", "pcg_common.cuh", "common.cuh", "kernels.h")
+PCG_PROFILE = os.path.join(ROOT, "profiles", "k_pcg_s_twisting_beam_20x20x80.md")
+
+
+def pcg_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in PCG_SOURCES:
+        with open(os.path.join(ROOT, "paper_2505_21013_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def pcg_profile_traffic():
+    """DRAM bytes per launch of the resident PCG kernel from the committed ncu
+    summary, or None when the kernel's sources changed since the capture."""
+    try:
+        txt = open(PCG_PROFILE).read()
+    except OSError:
+        return None
+    kv = {}
+    for ln in txt.splitlines():
+        if ln.startswith("- ") and ": " in ln:
+            k, v = ln[2:].split(": ", 1)
+            kv[k.strip("` ")] = v.strip("` ")
+    try:
+        if kv.get("source_sha256_16") != pcg_source_hash():
+            return None
+        return {"bytes": float(kv["dram_bytes_per_launch"]), "cg_iters": int(kv["cg_iters_per_launch"])}
+    except (KeyError, ValueError):
+        return None
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -132,6 +166,9 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.Stream(device=dev)
 
     def run_mode(mode, profile):
+        """W + K steps; per-step device time of the K timed steps.  With
+        `profile`, per-kernel-family CUDA events are recorded too (an untimed
+        run: the events add host work)."""
         sc = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
         sc.set_stream(stream.cuda_stream)
         info = sc.info()
@@ -160,16 +197,20 @@ def run_ours(args, rank, world, dist):
                 stats.append(st)
                 iters.append(sc.iter_stats())
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         kt = sc.kernel_times() if profile else None
-        attempts_cg = sum(it["cg_iters"] for its in iters for it in its)
+        cg = sum(it["cg_iters"] for its in iters for it in its)
         sc.close()
-        return lat, stats, kt, info, attempts_cg
+        return lat, stats, kt, info, cg
 
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
     sampler.start()
-    lat_ppn, st_ppn, kt, info, cg_total = run_mode(P.MODE_PPN, True)
-    lat_pn, st_pn, _, _, _ = run_mode(P.MODE_PN, False)
+    lat_ppn, st_ppn, _, info, _ = run_mode(P.MODE_PPN, False)
+    lat_pn, st_pn, _, _, _ = run_mode(P.MODE_PN, False) if not args.ppn_only else ([], [], None, None, 0)
     clocks = sampler.stop()
+    # kernel breakdown: the same PPN steps again with per-family events
+    _, _, kt, _, cg_total = run_mode(P.MODE_PPN, True)
 
     # end-to-end through the public API with host buffers: targets H2D and
     # positions D2H inside the timed region every step
@@ -182,6 +223,8 @@ def run_ours(args, rank, world, dist):
         rc, x, _ = sc.step(P.MODE_PPN, WORKLOAD["tol"], want_x=True)
         out[:] = x
         t1 = time.perf_counter()
+        if rc != 0:
+            raise RuntimeError(f"end-to-end step {n} returned status {rc}")
         if n >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
     sc.close()
@@ -203,35 +246,70 @@ def run_ours(args, rank, world, dist):
     if name == "pcg" and rec["launches"]:
         bpi = pcg_bytes_per_iter(info)
         setup = info["n_verts"] * (36 + 36 + 32 + 4 * 16)
-        alg_bytes = (cg_total * bpi + rec["launches"] * setup) / rec["launches"]
+        iters_per_launch = cg_total / rec["launches"]
+        alg_bytes = iters_per_launch * bpi + setup
         avg_s = rec["total_ms"] / rec["launches"] / 1e3
         achieved = alg_bytes / avg_s / 1e9
         peak = peaks["hbm_gbs"] if peaks else 6800.0
-        roof = {"bound": "hbm", "kernel": "k_pcg (cooperative block-Jacobi PCG)", "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+        prof = pcg_profile_traffic()
+        roof = {"bound": "hbm", "kernel": "k_pcg_s (resident cooperative block-Jacobi PCG)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": round(prof["bytes"]) if prof else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
                 "bytes_per_launch": alg_bytes, "avg_launch_ms": rec["total_ms"] / rec["launches"],
-                "cg_iters_per_launch": cg_total / rec["launches"],
-                "note": "working set of one solve (~25 MB) stays L2-resident across CG iterations"}
+                "cg_iters_per_launch": iters_per_launch,
+                "traffic_capture_cg_iters": prof["cg_iters"] if prof else None,
+                "note": "algorithmic bytes per launch = CG iterations x bytes per iteration + set-up; the working "
+                        "set of one solve (~25 MB) stays L2-resident across iterations, so DRAM traffic is far "
+                        "below the algorithmic bytes and the kernel is bound by grid-wide exchange latency"}
     launches = int(sum(v["launches"] for v in kt.values()))
-    return {
+    r = {
         "value": value, "ms_per_step": ms_ppn / K,
         "p50_ms": percentile(lat_ppn, 0.5), "p99_ms": percentile(lat_ppn, 0.99),
-        "pn": {"steps_per_s": world * K / (ms_pn / 1e3), "ms_per_step": ms_pn / K,
-               "p50_ms": percentile(lat_pn, 0.5), "p99_ms": percentile(lat_pn, 0.99),
-               "newton_iters": sum(s["newton_iters"] for s in st_pn),
-               "projections": sum(s["total_projections"] for s in st_pn),
-               "cg_iters": sum(s["total_cg_iters"] for s in st_pn)},
         "ppn": {"newton_iters": sum(s["newton_iters"] for s in st_ppn),
                 "projections": sum(s["total_projections"] for s in st_ppn),
                 "cg_iters": sum(s["total_cg_iters"] for s in st_ppn),
                 "attempts": sum(s["total_attempts"] for s in st_ppn)},
-        "speedup_ppn_vs_pn": ms_pn / ms_ppn,
         "kernel_ms": {k: round(v["total_ms"], 3) for k, v in kt.items()},
         "roofline": roof, "clocks": clocks, "gpu_launches": launches,
         "e2e": {"value": world * K / (ms_e2e / 1e3), "unit": "steps/s",
                 "h2d_bytes_per_step": int(spec.fixed.size * 24), "d2h_bytes_per_step": int(spec.n_verts * 24)},
     }
+    if lat_pn:
+        r["pn"] = {"steps_per_s": world * K / (ms_pn / 1e3), "ms_per_step": ms_pn / K,
+                   "p50_ms": percentile(lat_pn, 0.5), "p99_ms": percentile(lat_pn, 0.99),
+                   "newton_iters": sum(s["newton_iters"] for s in st_pn),
+                   "projections": sum(s["total_projections"] for s in st_pn),
+                   "cg_iters": sum(s["total_cg_iters"] for s in st_pn)}
+        r["speedup_ppn_vs_pn"] = ms_pn / ms_ppn
+    return r
+
+
+def profile_pcg(iters, repeats=4):
+    """Fixed-length PCG solves on the workload's assembled system (for ncu
+    captures of the resident PCG kernel): one PPN step, then `repeats` solves
+    of exactly `iters` CG iterations on the Hessian at that state."""
+    import numpy as np
+
+    import paper_2505_21013_gb300 as P
+
+    spec = build_spec()
+    sc = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
+    sc.set_targets(spec.targets_at(0))
+    rc, x, _ = sc.step(P.MODE_PPN, WORKLOAD["tol"], want_x=True)
+    if rc != 0:
+        raise RuntimeError(f"step returned status {rc}")
+    nnzb = sc.info()["nnzb"]
+    vals = sc.probe_assemble(x)
+    b = np.random.default_rng(0).standard_normal((spec.n_verts, 3))
+    b[spec.fixed] = 0
+    out = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        _, inf = sc.probe_pcg(vals, b, rel_tol=1e-30, max_iter=iters)
+        out.append({"iters": inf["iters"], "host_ms": (time.perf_counter() - t0) * 1e3})
+    sc.close()
+    print(json.dumps({"profile_pcg": out, "source_sha256_16": pcg_source_hash(), "nnzb": nnzb}))
 
 
 def oracle_sample(max_seconds=25.0):
@@ -260,7 +338,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ppn-only", action="store_true", help="skip the PN comparison run")
+    ap.add_argument("--profile-pcg", type=int, default=0, metavar="ITERS",
+                    help="run fixed-length PCG solves for an ncu capture instead of the benchmark")
     args = ap.parse_args()
+    if args.profile_pcg:
+        profile_pcg(args.profile_pcg)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
 
@@ -310,8 +394,6 @@ def main():
         line = dict(base, **r)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = oracle_sample()
-        elif not args.no_cpu_baseline:
-            line["cpu_baseline"] = oracle_sample() if rank == 0 else None
         print(json.dumps(line))
     if dist:
         dist.barrier()

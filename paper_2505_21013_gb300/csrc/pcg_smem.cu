@@ -245,33 +245,45 @@ __global__ void __launch_bounds__(NTS, 1)
   auto exchange = [&](const int* ks, int nq, auto&& update) -> bool {
     const unsigned s = stamp16(epoch);
     if (blockIdx.x == 0) {
-      for (int si = warp; si < n_scenes; si += NW) {
+      // one warp per (scene, quantity); each lane polls all of its pending words
+      // in one round per L2 round trip, then the warp sums in a fixed order
+      for (int x = warp; x < n_scenes * nq; x += NW) {
+        const int si = x / nq, q = x % nq;
         if (st[si].done) continue;  // warp-uniform
         const SceneLite<T>& S = sl[si];
         const int n = S.n_ptiles;
-        for (int q = 0; q < nq; ++q) {
-          const unsigned long long* base = S.pword + 2 * (size_t)ks[q] * n;
-          double acc = 0.0;
-          for (int tw = lane32; tw < n; tw += 32 * 8) {
-            unsigned long long h[8], l[8];
+        const unsigned long long* base = S.pword + 2 * (size_t)ks[q] * n;
+        double acc = 0.0;
+        for (int tw = lane32; tw < n; tw += 32 * 8) {
+          unsigned long long h[8], l[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int t = tw + 32 * u;
-              h[u] = t < n ? ld_relaxed_u64(base + 2 * t) : 0ull;
-              l[u] = t < n ? ld_relaxed_u64(base + 2 * t + 1) : 0ull;
+          for (int u = 0; u < 8; ++u) {
+            const int t = tw + 32 * u;
+            h[u] = t < n ? ld_relaxed_u64(base + 2 * t) : (unsigned long long)s;
+            l[u] = t < n ? ld_relaxed_u64(base + 2 * t + 1) : (unsigned long long)s;
+          }
+          for (unsigned spins = 0;; ++spins) {
+            bool ready = true;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) ready &= has_stamp(h[u], s) & has_stamp(l[u], s);
+            if (ready) break;
+            if (spins > kWaitSpins || *(volatile int*)&s_to) {
+              s_to = 1;
+              break;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
               const int t = tw + 32 * u;
-              if (t >= n) continue;
-              h[u] = wait_word(base + 2 * t, h[u], s, (volatile int*)&s_to);
-              l[u] = wait_word(base + 2 * t + 1, l[u], s, (volatile int*)&s_to);
-              acc += join_words(h[u], l[u]);
+              if (!has_stamp(h[u], s)) h[u] = ld_relaxed_u64(base + 2 * t);
+              if (!has_stamp(l[u], s)) l[u] = ld_relaxed_u64(base + 2 * t + 1);
             }
           }
-          acc = warp_sum(acc);
-          if (lane32 == 0) s_sum[si][q] = acc;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (tw + 32 * u < n) acc += join_words(h[u], l[u]);
         }
+        acc = warp_sum(acc);
+        if (lane32 == 0) s_sum[si][q] = acc;
       }
       __syncthreads();
       if (n_scenes == 1) {
@@ -310,7 +322,11 @@ __global__ void __launch_bounds__(NTS, 1)
         s_sum[si][q] = join_words(h, l);
       }
     }
-    fence_acq_rel();  // acquire: vector values released before the partials are visible
+    // acquire by the threads that observed stamped words (the barrier below
+    // orders the rest of the CTA after them): vector values released before
+    // the tile partials are visible to this CTA's gathers
+    const bool polled = blockIdx.x == 0 ? warp < n_scenes * nq : (n_scenes == 1 ? tid < 2 * nq : tid < n_scenes * nq);
+    if (polled) fence_acq_rel();
     __syncthreads();
     if (s_to) {
       if (tid == 0) atomicExch(&bar->timeout, 1);
