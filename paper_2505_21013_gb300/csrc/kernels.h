@@ -45,13 +45,11 @@ struct PcgLaunch {
   int use_b_from_g;      // 1: b = -g of the scene; 0: b given in r (probe)
   size_t smem_bytes;     // > 0: shared-memory-resident kernel with this dynamic size
   int smem_blocks;       // block capacity of that layout (max blocks of one CTA)
-  void* bcast;           // device scratch of the resident kernel's exchange (PCG_XCH_BYTES)
   unsigned launch_seq;
   int n_pword;           // stamped partial arrays to clear before the launch
   void* pword[PCG_MAX_SCENES];
   size_t pword_bytes[PCG_MAX_SCENES];
 };
-constexpr size_t PCG_XCH_BYTES = 1024 * 128 + PCG_MAX_SCENES * 3 * 2 * 8;
 
 // dynamic shared memory of the resident PCG layout for ni rows and nb blocks
 size_t pcg_smem_bytes(int ni, int nb, int fsize);

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(NT, 1)
   constexpr int RPP = NT / G;  // rows per SpMV pass
   __shared__ double sm[NT / 32];
   __shared__ double rowv[RPP];
-  __shared__ SState st[PCG_MAX_SCENES];
+  __shared__ SState<double> st[PCG_MAX_SCENES];
   __shared__ int s_to, s_all_done;
 
   const int tid = threadIdx.x;
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(NT, 1)
         i = tr.tile * PCG_TILE + (item % PCG_TILE);
         live = !st[slot].done && i < S.nv;
         if (live) {
-          const SState& s = st[slot];
+          const SState<double>& s = st[slot];
           const T beta = (T)s.beta;
           const V4* dprev = (s.iters & 1) ? S.d0 : S.d1;
           const int kb = S.row_ptr[i], ke = S.row_ptr[i + 1];
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(NT, 1)
       }
       double dq = 0.0;
       if (lane == 0 && live) {
-        const SState& s = st[slot];
+        const SState<double>& s = st[slot];
         const SceneDev<T>& S = scenes[scene_ids[slot]];
         const T beta = (T)s.beta;
         const V4* dprev = (s.iters & 1) ? S.d0 : S.d1;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(NT, 1)
         live = !st[tr.scene].done;
       }
       if (live) {
-        const SState& s = st[tr.scene];
+        const SState<double>& s = st[tr.scene];
         const SceneDev<T>& S = scenes[scene_ids[tr.scene]];
         const int i = tr.tile * PCG_TILE + (item % PCG_TILE);
         if (i < S.nv) {

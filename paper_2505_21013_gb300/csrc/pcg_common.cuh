@@ -88,19 +88,6 @@ __device__ __forceinline__ double subtile_sum(double v, double* sm) {
   return s;
 }
 
-// ---- stamped partials: a tile partial and the phase that wrote it in one
-// 64-bit word (value rounded to a 48-bit double: sign, exponent, 36 mantissa
-// bits; low 16 bits = phase stamp).  64-bit aligned relaxed accesses are
-// single-copy atomic, so a reader that sees the stamp it waits for also sees
-// that phase's value; the writer's fence orders its vector stores before it.
-__device__ __forceinline__ unsigned long long pack_stamped(double v, unsigned stamp) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  b += 0x8000ull;  // round the magnitude at bit 16
-  return (b & ~0xFFFFull) | (unsigned long long)(stamp & 0xFFFFu);
-}
-__device__ __forceinline__ double stamped_value(unsigned long long w) {
-  return __longlong_as_double((long long)(w & ~0xFFFFull));
-}
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -110,82 +97,6 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-
-// Warp-wide wait-and-sum of slot k of n tile partials stamped `stamp` (fixed
-// order: lane-strided then a shuffle tree).  Valid in lane 0.  The wait is
-// bounded; *timeout is set when it gives up.
-__device__ __forceinline__ double warp_wait_sum(const double* part, int n, int k, unsigned stamp,
-                                                int* timeout) {
-  const unsigned long long* w = reinterpret_cast<const unsigned long long*>(part);
-  const int lane = threadIdx.x & 31;
-  double s = 0.0;
-  for (int t0 = lane; t0 < n; t0 += 32 * 8) {
-    unsigned long long v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int t = t0 + 32 * u;
-      v[u] = t < n ? ld_relaxed_u64(w + 4 * t + k) : 0ull;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int t = t0 + 32 * u;
-      if (t >= n) continue;
-      unsigned spins = 0;
-      while ((unsigned)(v[u] & 0xFFFFull) != (stamp & 0xFFFFu)) {
-        if (++spins > kSpinLimit) {
-          *timeout = 1;
-          break;
-        }
-        v[u] = ld_relaxed_u64(w + 4 * t + k);
-      }
-      s += stamped_value(v[u]);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  return s;
-}
-
-// the same for two slots of every tile, loaded together (one round trip)
-__device__ __forceinline__ void warp_wait_sum2(const double* part, int n, int k0, int k1, unsigned stamp,
-                                               int* timeout, double* out0, double* out1) {
-  const unsigned long long* w = reinterpret_cast<const unsigned long long*>(part);
-  const int lane = threadIdx.x & 31;
-  double s0 = 0.0, s1 = 0.0;
-  for (int t0 = lane; t0 < n; t0 += 32 * 4) {
-    unsigned long long a[4], b[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int t = t0 + 32 * u;
-      a[u] = t < n ? ld_relaxed_u64(w + 4 * t + k0) : 0ull;
-      b[u] = t < n ? ld_relaxed_u64(w + 4 * t + k1) : 0ull;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int t = t0 + 32 * u;
-      if (t >= n) continue;
-      unsigned spins = 0;
-      while ((unsigned)(a[u] & 0xFFFFull) != (stamp & 0xFFFFu) ||
-             (unsigned)(b[u] & 0xFFFFull) != (stamp & 0xFFFFu)) {
-        if (++spins > kSpinLimit) {
-          *timeout = 1;
-          break;
-        }
-        a[u] = ld_relaxed_u64(w + 4 * t + k0);
-        b[u] = ld_relaxed_u64(w + 4 * t + k1);
-      }
-      s0 += stamped_value(a[u]);
-      s1 += stamped_value(b[u]);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 += __shfl_down_sync(0xffffffffu, s0, o);
-    s1 += __shfl_down_sync(0xffffffffu, s1, o);
-  }
-  *out0 = s0;
-  *out1 = s1;
-}
 
 // per-scene fields a PCG kernel needs, copied to shared memory once per solve
 // so that no phase chases descriptor pointers through global memory
@@ -235,9 +146,12 @@ __device__ __forceinline__ void load_lite(SceneLite<T>& L, const SceneDev<T>& S)
   L.max_iter = S.pcg_max_iter;
 }
 
-// per-scene solver state, replicated identically in every CTA
+// per-scene solver state, replicated identically in every CTA.  R is the
+// type of the CG scalars: double in the FP64 path, float in the mixed path
+// (its vectors are FP32, and FP64 issues at a small fraction of the FP32 rate).
+template <typename R>
 struct SState {
-  double rz, rr0, rr, alpha, beta, dq;
+  R rz, rr0, rr, alpha, beta, dq;
   int iters, done, ind, pfail, hitmax, nonfinite;
 };
 
@@ -272,12 +186,13 @@ __device__ __forceinline__ bool spd_inv3(const T* D, T* Pm) {
 }
 
 // scalar step after phase A: alpha, or the negative-curvature exit
-__device__ __forceinline__ void after_dq(SState& s, double dq) {
+template <typename R>
+__device__ __forceinline__ void after_dq(SState<R>& s, R dq) {
   s.dq = dq;
   if (!(dq == dq)) {
     s.nonfinite = 1;
     s.done = 1;
-  } else if (!(dq > 0.0)) {
+  } else if (!(dq > (R)0)) {
     s.ind = 1;
     s.done = 1;
   } else {
@@ -286,13 +201,14 @@ __device__ __forceinline__ void after_dq(SState& s, double dq) {
 }
 
 // scalar step after phase B: convergence, iteration cap, beta
-__device__ __forceinline__ void after_rz(SState& s, double rz, double r2, double tol2, int max_iter) {
+template <typename R>
+__device__ __forceinline__ void after_rz(SState<R>& s, R rz, R r2, double tol2, int max_iter) {
   s.iters += 1;
   s.rr = r2;
   if (!(r2 == r2) || !(rz == rz)) {
     s.nonfinite = 1;
     s.done = 1;
-  } else if (r2 <= tol2 * s.rr0) {
+  } else if (r2 <= (R)tol2 * s.rr0) {
     s.done = 1;
   } else if (s.iters >= max_iter) {
     s.hitmax = 1;
@@ -303,24 +219,26 @@ __device__ __forceinline__ void after_rz(SState& s, double rz, double r2, double
   }
 }
 
-constexpr int XCH_MAX_CTAS = 1024;  // CTAs of one resident PCG launch (mailbox area)
+constexpr int XCH_MAX_CTAS = 1024;  // CTAs of one resident PCG launch
 
-__device__ __forceinline__ void init_state(SState& s, double rz, double r2, double f) {
+template <typename R>
+__device__ __forceinline__ void init_state(SState<R>& s, R rz, R r2, R f) {
   s.rz = rz;
   s.rr0 = r2;
   s.rr = r2;
-  s.alpha = 0.0;
-  s.beta = 0.0;
-  s.dq = 0.0;
+  s.alpha = (R)0;
+  s.beta = (R)0;
+  s.dq = (R)0;
   s.iters = 0;
   s.hitmax = 0;
   s.nonfinite = !(r2 == r2) || !(rz == rz);
-  s.pfail = f > 0.0;
-  s.ind = f > 0.0;
-  s.done = (f > 0.0) || !(r2 > 0.0) || s.nonfinite;
+  s.pfail = f > (R)0;
+  s.ind = f > (R)0;
+  s.done = (f > (R)0) || !(r2 > (R)0) || s.nonfinite;
 }
 
-__device__ __forceinline__ void publish(const SState& s, Ctl* c) {
+template <typename R>
+__device__ __forceinline__ void publish(const SState<R>& s, Ctl* c) {
   c->pcg_rr0 = s.rr0;
   c->pcg_rr = s.rr;
   c->pcg_rz = s.rz;

@@ -13,18 +13,21 @@
 // (gathered by neighbouring rows).  Phase A covers RPP rows per pass with G
 // lanes per row and issues all neighbour gathers of a lane before using any.
 //
-// Exchange.  A reduction value crosses the grid as two 64-bit words, hi and
-// lo (hi = the value with its 16 low mantissa bits cleared, lo = value - hi,
-// exact), each carrying the phase stamp in its 16 low bits.  Aligned 64-bit
-// accesses are single-copy atomic, so a word with the expected stamp carries
-// that phase's value and hi + lo restores the double exactly; no fence is
-// needed between a value and its flag.  Per phase: each CTA stores its vector
-// values, one fence per tile writer releases them, then the tile partials go
-// out as stamped words; CTA 0 reads every tile word (coalesced [k][tile]
-// layout, one round, re-polling only missing ones), sums each scene in tile
-// order and writes the sums as stamped words into one mailbox per CTA
-// (single-scene launches) or one broadcast area (batches); every CTA then
-// applies the same deterministic scalar update.  All waits are bounded.
+// Exchange.  Each tile partial of a reduction crosses the grid as stamped
+// 64-bit words (one word for an FP32 partial, hi and lo words for an FP64
+// one).  Aligned 64-bit accesses are single-copy atomic, so a word with the
+// expected stamp carries that phase's value; no fence is needed between a
+// value and its flag.  Per phase: each CTA stores its vector values, then its
+// tile partials as stamped words ([quantity][tile] layout per scene); a fence
+// before the partials of phase B (and of the set-up) releases the z and d
+// values that the next phase A gathers.  Every CTA reads all tile words it
+// needs (one warp per scene and quantity, all pending words re-polled together
+// each round), sums them in tile order, which gives the same bits in every
+// CTA, and applies the same scalar update.  All waits are bounded.
+//
+// Precision.  The reductions and CG scalars use the vector type T: FP32 in the
+// mixed path (FP64 issues at a small fraction of the FP32 rate on this part),
+// FP64 in the FP64 path.
 #include "pcg_common.cuh"
 
 namespace ppn {
@@ -35,7 +38,7 @@ namespace {
 
 template <typename T>
 struct SmemLayout {
-  double* lws;   // [ntl * 16 * 3] per-warp partial sums, summed per tile in fixed order
+  T* lws;        // [ntl * 16 * 3] per-warp partial sums, summed per tile in fixed order
   int* it_i;     // [ni] row index within its scene (-1: padding row)
   int* it_slot;  // [ni] scene slot
   int* lrp;      // [ni + 1] local row pointers into the block arrays
@@ -61,7 +64,7 @@ __device__ __forceinline__ SmemLayout<T> carve(char* base, int ni, int nb) {
     off += rup16(bytes);
     return p;
   };
-  L.lws = (double*)take(sizeof(double) * ntl * 16 * 3);
+  L.lws = (T*)take(sizeof(double) * ntl * 16 * 3);
   L.it_i = (int*)take(sizeof(int) * ni);
   L.it_slot = (int*)take(sizeof(int) * ni);
   L.lrp = (int*)take(sizeof(int) * (ni + 1));
@@ -76,43 +79,53 @@ __device__ __forceinline__ SmemLayout<T> carve(char* base, int ni, int nb) {
   return L;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
 
-// ---- stamped hi/lo words (stamp 0 never used: the area is zeroed per launch)
-__device__ __forceinline__ unsigned stamp16(unsigned epoch) { return ((epoch - 1u) % 65535u) + 1u; }
-__device__ __forceinline__ void split_words(double v, unsigned s, unsigned long long* w) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const unsigned long long hb = b & ~0xFFFFull;
-  const double lo = v - __longlong_as_double((long long)hb);
-  const unsigned long long lb = (unsigned long long)__double_as_longlong(lo) & ~0xFFFFull;
-  w[0] = hb | s;
-  w[1] = lb | s;
-}
-__device__ __forceinline__ double join_words(unsigned long long h, unsigned long long l) {
-  return __longlong_as_double((long long)(h & ~0xFFFFull)) + __longlong_as_double((long long)(l & ~0xFFFFull));
-}
-__device__ __forceinline__ bool has_stamp(unsigned long long w, unsigned s) {
-  return (unsigned)(w & 0xFFFFull) == s;
-}
-// wait (bounded) for a word carrying stamp s; `w` is a first read of it.  Gives up
-// after kWaitSpins reads, or as soon as another thread of the CTA has given up.
-constexpr unsigned kWaitSpins = 1u << 20;
-__device__ __forceinline__ unsigned long long wait_word(const unsigned long long* p, unsigned long long w,
-                                                        unsigned s, volatile int* to) {
-  unsigned spins = 0;
-  while (!has_stamp(w, s)) {
-    if (++spins > kWaitSpins || *to) {
-      *to = 1;
-      break;
-    }
-    w = ld_relaxed_u64(p);
+// ---- stamped words.  A tile partial crosses the grid as N 64-bit words, each
+// carrying the phase stamp; stamp 0 is never used (the words are zeroed before
+// every launch).  FP32 partials: one word, stamp = the 32-bit phase counter in
+// the high half, the value's bits in the low half.  FP64 partials: hi and lo
+// words (hi = the value with its 16 low mantissa bits cleared, lo = value - hi,
+// exact), stamp in the 16 low bits of each.
+template <typename R>
+struct Words;
+template <>
+struct Words<float> {
+  static constexpr int N = 1;
+  __device__ static unsigned stamp(unsigned epoch) { return epoch; }
+  __device__ static unsigned long long filler(unsigned s) { return (unsigned long long)s << 32; }
+  __device__ static void split(float v, unsigned s, unsigned long long* w) {
+    w[0] = ((unsigned long long)s << 32) | __float_as_uint(v);
   }
-  return w;
-}
+  __device__ static bool has(unsigned long long w, unsigned s) { return (unsigned)(w >> 32) == s; }
+  __device__ static float join(const unsigned long long* w) { return __uint_as_float((unsigned)w[0]); }
+};
+template <>
+struct Words<double> {
+  static constexpr int N = 2;
+  __device__ static unsigned stamp(unsigned epoch) { return ((epoch - 1u) % 65535u) + 1u; }
+  __device__ static unsigned long long filler(unsigned s) { return s; }
+  __device__ static void split(double v, unsigned s, unsigned long long* w) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned long long hb = b & ~0xFFFFull;
+    const double lo = v - __longlong_as_double((long long)hb);
+    const unsigned long long lb = (unsigned long long)__double_as_longlong(lo) & ~0xFFFFull;
+    w[0] = hb | s;
+    w[1] = lb | s;
+  }
+  __device__ static bool has(unsigned long long w, unsigned s) { return (unsigned)(w & 0xFFFFull) == s; }
+  __device__ static double join(const unsigned long long* w) {
+    return __longlong_as_double((long long)(w[0] & ~0xFFFFull)) +
+           __longlong_as_double((long long)(w[1] & ~0xFFFFull));
+  }
+};
+// bound of one wait, in polling rounds; a CTA that gives up flags a timeout
+constexpr unsigned kWaitSpins = 1u << 20;
 
 }  // namespace
 
@@ -129,7 +142,7 @@ constexpr int MAXQ = 3;   // quantities exchanged per phase (setup: r.z, r.r, fa
 template <typename T, int G>
 __global__ void __launch_bounds__(NTS, 1)
     k_pcg_s(const SceneDev<T>* scenes, const TileRef* tiles, int n_tiles, const int* scene_ids,
-            int n_scenes, GridBar* bar, int b_from_g, int nb_cap, unsigned long long* xch) {
+            int n_scenes, GridBar* bar, int b_from_g, int nb_cap) {
   using V4 = vec4_t<T>;
   constexpr int RPP = NTS / G;            // rows per SpMV pass
   constexpr int U = 16 / G;               // blocks per lane per gather round
@@ -138,11 +151,12 @@ __global__ void __launch_bounds__(NTS, 1)
   constexpr int WPT = NW / TPP;           // warps per tile in an SpMV pass
   static_assert(RPP % PCG_TILE == 0, "an SpMV pass covers whole reduction tiles");
   static_assert(NW <= 32, "one warp scans the warp totals");
+  using W = Words<T>;
+  constexpr int NWD = W::N;               // words per exchanged value
   extern __shared__ __align__(16) char dyn[];
-  __shared__ SState st[PCG_MAX_SCENES];
+  __shared__ SState<T> st[PCG_MAX_SCENES];
   __shared__ SceneLite<T> sl[PCG_MAX_SCENES];
-  __shared__ double s_sum[PCG_MAX_SCENES][MAXQ];
-  __shared__ unsigned long long s_w[2 * MAXQ];
+  __shared__ T s_sum[PCG_MAX_SCENES][MAXQ];
   __shared__ int s_to, s_all_done;
   __shared__ int s_scan[NW];
 
@@ -228,105 +242,67 @@ __global__ void __launch_bounds__(NTS, 1)
 
   // ---------------- exchange
   // tile partial k of tile t of a scene: pword[(k * n_ptiles + t) * 2 + h]
-  // mailbox of CTA c (single-scene launches): xch[c * 16 + 2q + h]
-  // broadcast (batches): xch[XCH_MAX_CTAS * 16 + (si * MAXQ + q) * 2 + h]
-  auto post_tile = [&](int lt, int k, double v, unsigned s) {
+  auto post_tile = [&](int lt, int k, T v, unsigned s) {
     const TileRef tr = tiles[t0 + lt];
     const SceneLite<T>& S = sl[tr.scene];
-    unsigned long long w[2];
-    split_words(v, s, w);
-    unsigned long long* p = S.pword + 2 * ((size_t)k * S.n_ptiles + tr.tile);
-    st_relaxed_u64(p, w[0]);
-    st_relaxed_u64(p + 1, w[1]);
+    unsigned long long w[NWD];
+    W::split(v, s, w);
+    unsigned long long* p = S.pword + NWD * ((size_t)k * S.n_ptiles + tr.tile);
+#pragma unroll
+    for (int j = 0; j < NWD; ++j) st_relaxed_u64(p + j, w[j]);
   };
-  unsigned long long* const bcw = xch + (size_t)XCH_MAX_CTAS * 16;
-  // CTA 0 sums quantities ks[0..nq) of every live scene in tile order and publishes them;
-  // every other CTA waits for its words.  Then each CTA applies `update` to each live scene.
-  auto exchange = [&](const int* ks, int nq, auto&& update) -> bool {
-    const unsigned s = stamp16(epoch);
-    if (blockIdx.x == 0) {
-      // one warp per (scene, quantity); each lane polls all of its pending words
-      // in one round per L2 round trip, then the warp sums in a fixed order
-      for (int x = warp; x < n_scenes * nq; x += NW) {
-        const int si = x / nq, q = x % nq;
-        if (st[si].done) continue;  // warp-uniform
-        const SceneLite<T>& S = sl[si];
-        const int n = S.n_ptiles;
-        const unsigned long long* base = S.pword + 2 * (size_t)ks[q] * n;
-        double acc = 0.0;
-        for (int tw = lane32; tw < n; tw += 32 * 8) {
-          unsigned long long h[8], l[8];
+  // Every CTA sums quantities ks[0..nq) of every live scene from the tile words
+  // in the same fixed order (so all CTAs hold bitwise-equal scalars), then
+  // applies `update` to each live scene.  One warp per (scene, quantity); each
+  // lane polls all of its pending words in one round per L2 round trip.
+  // `acquire`: the phase that follows gathers vector values of other CTAs.
+  auto exchange = [&](const int* ks, int nq, bool acquire, auto&& update) -> bool {
+    const unsigned s = W::stamp(epoch);
+    for (int x = warp; x < n_scenes * nq; x += NW) {
+      const int si = x / nq, q = x % nq;
+      if (st[si].done) continue;  // warp-uniform
+      const SceneLite<T>& S = sl[si];
+      const int n = S.n_ptiles;
+      const unsigned long long* base = S.pword + NWD * (size_t)ks[q] * n;
+      T acc = (T)0;
+      for (int tw = lane32; tw < n; tw += 32 * 8) {
+        unsigned long long w[8][NWD];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int t = tw + 32 * u;
+#pragma unroll
+          for (int j = 0; j < NWD; ++j) w[u][j] = t < n ? ld_relaxed_u64(base + NWD * t + j) : W::filler(s);
+        }
+        for (unsigned spins = 0;; ++spins) {
+          bool ready = true;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int j = 0; j < NWD; ++j) ready &= W::has(w[u][j], s);
+          if (ready) break;
+          if (spins > kWaitSpins || *(volatile int*)&s_to) {
+            s_to = 1;
+            break;
+          }
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int t = tw + 32 * u;
-            h[u] = t < n ? ld_relaxed_u64(base + 2 * t) : (unsigned long long)s;
-            l[u] = t < n ? ld_relaxed_u64(base + 2 * t + 1) : (unsigned long long)s;
+#pragma unroll
+            for (int j = 0; j < NWD; ++j)
+              if (!W::has(w[u][j], s)) w[u][j] = ld_relaxed_u64(base + NWD * t + j);
           }
-          for (unsigned spins = 0;; ++spins) {
-            bool ready = true;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) ready &= has_stamp(h[u], s) & has_stamp(l[u], s);
-            if (ready) break;
-            if (spins > kWaitSpins || *(volatile int*)&s_to) {
-              s_to = 1;
-              break;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int t = tw + 32 * u;
-              if (!has_stamp(h[u], s)) h[u] = ld_relaxed_u64(base + 2 * t);
-              if (!has_stamp(l[u], s)) l[u] = ld_relaxed_u64(base + 2 * t + 1);
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (tw + 32 * u < n) acc += join_words(h[u], l[u]);
         }
-        acc = warp_sum(acc);
-        if (lane32 == 0) s_sum[si][q] = acc;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (tw + 32 * u < n) acc += W::join(w[u]);
       }
-      __syncthreads();
-      if (n_scenes == 1) {
-        if (!st[0].done)
-          for (int c = tid; c < (int)gridDim.x; c += NTS)
-            for (int q = 0; q < nq; ++q) {
-              unsigned long long w[2];
-              split_words(s_sum[0][q], s, w);
-              st_relaxed_u64(xch + (size_t)c * 16 + 2 * q, w[0]);
-              st_relaxed_u64(xch + (size_t)c * 16 + 2 * q + 1, w[1]);
-            }
-      } else {
-        for (int x = tid; x < n_scenes * nq; x += NTS) {
-          const int si = x / nq, q = x % nq;
-          if (st[si].done) continue;
-          unsigned long long w[2];
-          split_words(s_sum[si][q], s, w);
-          st_relaxed_u64(bcw + 2 * (si * MAXQ + q), w[0]);
-          st_relaxed_u64(bcw + 2 * (si * MAXQ + q) + 1, w[1]);
-        }
-      }
-    } else if (n_scenes == 1) {
-      if (tid < 2 * nq && !st[0].done) {
-        const unsigned long long* p = xch + (size_t)blockIdx.x * 16 + tid;
-        s_w[tid] = wait_word(p, ld_relaxed_u64(p), s, (volatile int*)&s_to);
-      }
-      __syncthreads();
-      if (tid < nq && !st[0].done) s_sum[0][tid] = join_words(s_w[2 * tid], s_w[2 * tid + 1]);
-    } else {
-      for (int x = tid; x < n_scenes * nq; x += NTS) {
-        const int si = x / nq, q = x % nq;
-        if (st[si].done) continue;
-        const unsigned long long* p = bcw + 2 * (si * MAXQ + q);
-        const unsigned long long h = wait_word(p, ld_relaxed_u64(p), s, (volatile int*)&s_to);
-        const unsigned long long l = wait_word(p + 1, ld_relaxed_u64(p + 1), s, (volatile int*)&s_to);
-        s_sum[si][q] = join_words(h, l);
-      }
+      acc = warp_sum(acc);
+      if (lane32 == 0) s_sum[si][q] = acc;
     }
-    // acquire by the threads that observed stamped words (the barrier below
+    // acquire by the warps that observed stamped words (the barrier below
     // orders the rest of the CTA after them): vector values released before
     // the tile partials are visible to this CTA's gathers
-    const bool polled = blockIdx.x == 0 ? warp < n_scenes * nq : (n_scenes == 1 ? tid < 2 * nq : tid < n_scenes * nq);
-    if (polled) fence_acq_rel();
+    if (acquire && warp < n_scenes * nq) fence_acq_rel();
     __syncthreads();
     if (s_to) {
       if (tid == 0) atomicExch(&bar->timeout, 1);
@@ -341,7 +317,7 @@ __global__ void __launch_bounds__(NTS, 1)
   // ---------------- setup: block-Jacobi inverse, r = b, z = P r, d = 0, x = 0
   for (int base = 0; base < n_items; base += NTS) {
     const int item = base + tid;
-    double rz = 0.0, r2 = 0.0, fail = 0.0;
+    T rz = (T)0, r2 = (T)0, fail = (T)0;
     const int i = item < n_items ? L.it_i[item] : -1;
     if (i >= 0) {
       const SceneLite<T>& S = sl[L.it_slot[item]];
@@ -378,9 +354,9 @@ __global__ void __launch_bounds__(NTS, 1)
       lz[2] = z2;
       lx[0] = lx[1] = lx[2] = (T)0;
       ld[0] = ld[1] = ld[2] = (T)0;
-      rz = (double)(r.x * z0 + r.y * z1 + r.z * z2);
-      r2 = (double)(r.x * r.x + r.y * r.y + r.z * r.z);
-      fail = ok ? 0.0 : 1.0;
+      rz = r.x * z0 + r.y * z1 + r.z * z2;
+      r2 = r.x * r.x + r.y * r.y + r.z * r.z;
+      fail = ok ? (T)0 : (T)1;
     }
     rz = warp_sum(rz);
     r2 = warp_sum(r2);
@@ -395,15 +371,15 @@ __global__ void __launch_bounds__(NTS, 1)
   __syncthreads();
   ++epoch;
   for (int lt = tid; lt < ntl; lt += NTS) {
-    const double* w = L.lws + 3 * 4 * lt;
+    const T* w = L.lws + 3 * 4 * lt;
     __threadfence();  // release this CTA's z and d stores before the partials
-    post_tile(lt, 0, ((w[0] + w[3]) + w[6]) + w[9], stamp16(epoch));
-    post_tile(lt, 1, ((w[1] + w[4]) + w[7]) + w[10], stamp16(epoch));
-    post_tile(lt, 3, ((w[2] + w[5]) + w[8]) + w[11], stamp16(epoch));
+    post_tile(lt, 0, ((w[0] + w[3]) + w[6]) + w[9], W::stamp(epoch));
+    post_tile(lt, 1, ((w[1] + w[4]) + w[7]) + w[10], W::stamp(epoch));
+    post_tile(lt, 3, ((w[2] + w[5]) + w[8]) + w[11], W::stamp(epoch));
   }
   {
     const int ks[3] = {0, 1, 3};
-    if (!exchange(ks, 3, [&](int si) { init_state(st[si], s_sum[si][0], s_sum[si][1], s_sum[si][2]); }))
+    if (!exchange(ks, 3, true, [&](int si) { init_state(st[si], s_sum[si][0], s_sum[si][1], s_sum[si][2]); }))
       return;
   }
 
@@ -429,8 +405,8 @@ __global__ void __launch_bounds__(NTS, 1)
         live = i >= 0 && !st[slot].done;
         if (live) {
           const SceneLite<T>& S = sl[slot];
-          const SState& s = st[slot];
-          const T beta = (T)s.beta;
+          const SState<T>& s = st[slot];
+          const T beta = s.beta;
           const V4* dprev = (s.iters & 1) ? S.d0 : S.d1;
           const int lb = L.lrp[item], le = L.lrp[item + 1];
           for (int b0 = lb + lane; b0 < le; b0 += G * U) {
@@ -469,11 +445,11 @@ __global__ void __launch_bounds__(NTS, 1)
         ay += __shfl_down_sync(0xffffffffu, ay, o, G);
         az += __shfl_down_sync(0xffffffffu, az, o, G);
       }
-      double dq = 0.0;
+      T dq = (T)0;
       if (lane == 0 && live) {
-        const SState& s = st[slot];
+        const SState<T>& s = st[slot];
         const SceneLite<T>& S = sl[slot];
-        const T beta = (T)s.beta;
+        const T beta = s.beta;
         V4* dcur = (s.iters & 1) ? S.d1 : S.d0;
         T* ld = L.ld + 3 * item;
         const T* lz = L.lz + 3 * item;
@@ -486,7 +462,7 @@ __global__ void __launch_bounds__(NTS, 1)
         lq[0] = ax;
         lq[1] = ay;
         lq[2] = az;
-        dq = (double)(d0 * ax + d1 * ay + d2 * az);
+        dq = d0 * ax + d1 * ay + d2 * az;
       }
       dq = warp_sum(dq);  // rows of this warp, fixed tree
       if (lane32 == 0) L.lws[3 * ((base / RPP) * NW + warp)] = dq;
@@ -496,27 +472,28 @@ __global__ void __launch_bounds__(NTS, 1)
     for (int lt = tid; lt < ntl; lt += NTS) {
       if (st[L.it_slot[lt * PCG_TILE]].done) continue;
       // tile lt was covered by pass lt / TPP, warps [WPT * (lt % TPP), + WPT)
-      const double* w = L.lws + 3 * ((lt / TPP) * NW + WPT * (lt % TPP));
-      double s = 0.0;
+      const T* w = L.lws + 3 * ((lt / TPP) * NW + WPT * (lt % TPP));
+      T s = (T)0;
 #pragma unroll
       for (int k = 0; k < WPT; ++k) s += w[3 * k];
-      __threadfence();  // release this CTA's d stores before the partial
-      post_tile(lt, 2, s, stamp16(epoch));
+      // no release here: phase B reads no other CTA's vectors, and the fence
+      // before the phase-B partials also releases this phase's d stores
+      post_tile(lt, 2, s, W::stamp(epoch));
     }
     {
       const int ks[1] = {2};
-      if (!exchange(ks, 1, [&](int si) { after_dq(st[si], s_sum[si][0]); })) return;
+      if (!exchange(ks, 1, false, [&](int si) { after_dq(st[si], s_sum[si][0]); })) return;
     }
 
     // ---------------- phase B: x += alpha d, r -= alpha q, z = P r (shared memory)
     for (int base = 0; base < n_items; base += NTS) {
       const int item = base + tid;
-      double rz = 0.0, r2 = 0.0;
+      T rz = (T)0, r2 = (T)0;
       const int i = item < n_items ? L.it_i[item] : -1;
       const int slot = item < n_items ? L.it_slot[item] : 0;
       if (i >= 0 && !st[slot].done) {
         const SceneLite<T>& S = sl[slot];
-        const T alpha = (T)st[slot].alpha;
+        const T alpha = st[slot].alpha;
         T* lx = L.lx + 3 * item;
         T* lr = L.lr + 3 * item;
         const T* ld = L.ld + 3 * item;
@@ -537,8 +514,8 @@ __global__ void __launch_bounds__(NTS, 1)
         lz[1] = z1;
         lz[2] = z2;
         st_v(S.z + i, mk<V4, T>(z0, z1, z2));
-        rz = (double)(r0 * z0 + r1 * z1 + rr2 * z2);
-        r2 = (double)(r0 * r0 + r1 * r1 + rr2 * rr2);
+        rz = r0 * z0 + r1 * z1 + rr2 * z2;
+        r2 = r0 * r0 + r1 * r1 + rr2 * rr2;
       }
       rz = warp_sum(rz);
       r2 = warp_sum(r2);
@@ -552,14 +529,14 @@ __global__ void __launch_bounds__(NTS, 1)
     ++epoch;
     for (int lt = tid; lt < ntl; lt += NTS) {
       if (st[L.it_slot[lt * PCG_TILE]].done) continue;
-      const double* w = L.lws + 3 * 4 * lt;
-      __threadfence();  // release this CTA's z stores before the partials
-      post_tile(lt, 0, ((w[0] + w[3]) + w[6]) + w[9], stamp16(epoch));
-      post_tile(lt, 1, ((w[1] + w[4]) + w[7]) + w[10], stamp16(epoch));
+      const T* w = L.lws + 3 * 4 * lt;
+      __threadfence();  // release this CTA's z and d stores before the partials
+      post_tile(lt, 0, ((w[0] + w[3]) + w[6]) + w[9], W::stamp(epoch));
+      post_tile(lt, 1, ((w[1] + w[4]) + w[7]) + w[10], W::stamp(epoch));
     }
     {
       const int ks[2] = {0, 1};
-      if (!exchange(ks, 2, [&](int si) {
+      if (!exchange(ks, 2, true, [&](int si) {
             after_rz(st[si], s_sum[si][0], s_sum[si][1], sl[si].tol2, sl[si].max_iter);
           }))
         return;
@@ -606,8 +583,6 @@ cudaError_t launch_pcg_smem(const SceneDev<T>* scenes, const PcgLaunch& L, cudaS
   cudaError_t e = cudaMemsetAsync(L.bar, 0, sizeof(GridBar), st);
   if (e != cudaSuccess) return e;
   // no stamp of an earlier launch may survive in the exchange words
-  e = cudaMemsetAsync(L.bcast, 0, PCG_XCH_BYTES, st);
-  if (e != cudaSuccess) return e;
   for (int k = 0; k < L.n_pword; ++k) {
     e = cudaMemsetAsync(L.pword[k], 0, L.pword_bytes[k], st);
     if (e != cudaSuccess) return e;
@@ -619,9 +594,8 @@ cudaError_t launch_pcg_smem(const SceneDev<T>* scenes, const PcgLaunch& L, cudaS
   GridBar* bar = L.bar;
   int bg = L.use_b_from_g;
   int nb_cap = L.smem_blocks;
-  unsigned long long* xch = reinterpret_cast<unsigned long long*>(L.bcast);
   void* args[] = {(void*)&scenes, (void*)&tiles, (void*)&n_tiles, (void*)&ids, (void*)&n_scenes,
-                  (void*)&bar, (void*)&bg, (void*)&nb_cap, (void*)&xch};
+                  (void*)&bar, (void*)&bg, (void*)&nb_cap};
   const void* k = smem_kernel<T>(L.group);
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
   if (e != cudaSuccess) return e;

@@ -503,7 +503,6 @@ struct Group {
   int n_ttiles = 0, n_vtiles = 0, n_btiles = 0, n_ptiles = 0, n_etiles = 0;
   int* d_ids = nullptr;
   TileRef* d_pcgtiles = nullptr;
-  void* d_bcast = nullptr;
   unsigned pcg_launch_seq = 0;
   std::vector<int> pcg_ids;  // slots of the tile table currently on the device
   int pcg_ntiles = 0;
@@ -562,10 +561,9 @@ struct Group {
     d_projtiles = alloc<TileRef>(projcap);
     d_ids = alloc<int>(n);
     d_pcgtiles = alloc<TileRef>(pt.size());
-    d_bcast = alloc<char>(PCG_XCH_BYTES);
     d_bar = alloc<GridBar>(1);
     if (!d_desc || !d_ctl || !d_ttiles || !d_vtiles || !d_btiles || !d_ptiles || !d_etiles ||
-        !d_projtiles || !d_ids || !d_bar || !d_pcgtiles || !d_bcast) {
+        !d_projtiles || !d_ids || !d_bar || !d_pcgtiles) {
       set_error("cudaMalloc failed for a scene group");
       return PPN_ERR_OOM;
     }
@@ -703,7 +701,6 @@ struct Driver {
       L.use_b_from_g = b_from_g;
       L.smem_bytes = G.pcg_smem_bytes;
       L.smem_blocks = G.pcg_smem_blocks;
-      L.bcast = G.d_bcast;
       L.launch_seq = ++G.pcg_launch_seq;
       L.n_pword = (int)sl.size();
       for (size_t k = 0; k < sl.size(); ++k) {
