@@ -92,7 +92,8 @@ struct SceneDev {
   double* vpart;           // vertex tiles
   double* tpart;           // tet tiles
   double* ppart;           // PCG tiles
-  unsigned long long* pword;  // PCG tile partials as stamped hi/lo words, [4][n_ptiles][2]
+  unsigned long long* pword;  // PCG tile partials as stamped words, [4][n_ptiles][<= 2]
+  T* zrec;                    // FP32 path: [2][nv] 32-byte records {z, 0, d_prev, 0} of the resident PCG
   double* psi_out;         // optional per-element energies (probes)
   Ctl* ctl;
   // scalars of the current phase

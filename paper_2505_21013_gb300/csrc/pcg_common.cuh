@@ -117,6 +117,7 @@ struct SceneLite {
   T* Pinv;
   double* ppart;
   unsigned long long* pword;
+  T* zrec;
   Ctl* ctl;
   double tol2;
   int nv, nnzb, n_ptiles, max_iter;
@@ -138,6 +139,7 @@ __device__ __forceinline__ void load_lite(SceneLite<T>& L, const SceneDev<T>& S)
   L.Pinv = S.Pinv;
   L.ppart = S.ppart;
   L.pword = S.pword;
+  L.zrec = S.zrec;
   L.ctl = S.ctl;
   L.tol2 = S.pcg_tol2;
   L.nv = S.nv;

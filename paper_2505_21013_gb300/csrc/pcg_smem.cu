@@ -124,6 +124,21 @@ struct Words<double> {
            __longlong_as_double((long long)(w[1] & ~0xFFFFull));
   }
 };
+// ---- FP32 z / d_prev records: one 32-byte record {z.xyz, 0, d.xyz, 0} per row
+// and parity buffer, so a neighbour gather is one 256-bit load.  Iteration k
+// reads buffer k & 1 (z_k, d_{k-1}) and writes d_k and z_{k+1} into the other.
+__device__ __forceinline__ void ld_rec(const float* p, float (&a)[8]) {
+  asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(a[0]), "=f"(a[1]), "=f"(a[2]), "=f"(a[3]), "=f"(a[4]), "=f"(a[5]), "=f"(a[6]), "=f"(a[7])
+               : "l"(p));
+}
+__device__ __forceinline__ void st_rec_half(float* p, float x, float y, float z) {
+  asm volatile("st.global.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(0.0f) : "memory");
+}
+__device__ __forceinline__ float* rec_ptr(float* base, int nv, int parity, int i) {
+  return base + ((size_t)parity * nv + i) * 8;
+}
+
 // bound of one wait, in polling rounds; a CTA that gives up flags a timeout
 constexpr unsigned kWaitSpins = 1u << 20;
 
@@ -152,6 +167,7 @@ __global__ void __launch_bounds__(NTS, 1)
   static_assert(RPP % PCG_TILE == 0, "an SpMV pass covers whole reduction tiles");
   static_assert(NW <= 32, "one warp scans the warp totals");
   using W = Words<T>;
+  constexpr bool REC = sizeof(T) == 4;    // FP32: z / d_prev records (one 256-bit gather per block)
   constexpr int NWD = W::N;               // words per exchanged value
   extern __shared__ __align__(16) char dyn[];
   __shared__ SState<T> st[PCG_MAX_SCENES];
@@ -340,8 +356,14 @@ __global__ void __launch_bounds__(NTS, 1)
       const T z0 = Pm[0] * r.x + Pm[1] * r.y + Pm[2] * r.z;
       const T z1 = Pm[3] * r.x + Pm[4] * r.y + Pm[5] * r.z;
       const T z2 = Pm[6] * r.x + Pm[7] * r.y + Pm[8] * r.z;
-      st_v(S.z + i, mk<V4, T>(z0, z1, z2));
-      st_v(S.d1 + i, mk<V4, T>((T)0, (T)0, (T)0));
+      if constexpr (REC) {
+        float* rp = rec_ptr(S.zrec, S.nv, 0, i);
+        st_rec_half(rp, z0, z1, z2);
+        st_rec_half(rp + 4, 0.0f, 0.0f, 0.0f);
+      } else {
+        st_v(S.z + i, mk<V4, T>(z0, z1, z2));
+        st_v(S.d1 + i, mk<V4, T>((T)0, (T)0, (T)0));
+      }
       T* lr = L.lr + 3 * item;
       T* lz = L.lz + 3 * item;
       T* lx = L.lx + 3 * item;
@@ -418,23 +440,41 @@ __global__ void __launch_bounds__(NTS, 1)
               ok[u] = b < le;
               j[u] = ok[u] ? L.lcol[b] : 0;
             }
-            V4 zj[U], pj[U];
+            if constexpr (REC) {
+              const float* rb = rec_ptr(S.zrec, S.nv, s.iters & 1, 0);
+              float a[U][8];
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-              if (ok[u]) {
-                zj[u] = ldcg_v(S.z + j[u]);
-                pj[u] = ldcg_v(dprev + j[u]);
-              }
+              for (int u = 0; u < U; ++u)
+                if (ok[u]) ld_rec(rb + (size_t)8 * j[u], a[u]);
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-              if (ok[u]) {
-                const T* v = L.lval + 9 * (b0 + G * u);
-                const T dj0 = zj[u].x + beta * pj[u].x, dj1 = zj[u].y + beta * pj[u].y,
-                        dj2 = zj[u].z + beta * pj[u].z;
-                ax += v[0] * dj0 + v[1] * dj1 + v[2] * dj2;
-                ay += v[3] * dj0 + v[4] * dj1 + v[5] * dj2;
-                az += v[6] * dj0 + v[7] * dj1 + v[8] * dj2;
-              }
+              for (int u = 0; u < U; ++u)
+                if (ok[u]) {
+                  const T* v = L.lval + 9 * (b0 + G * u);
+                  const T dj0 = a[u][0] + beta * a[u][4], dj1 = a[u][1] + beta * a[u][5],
+                          dj2 = a[u][2] + beta * a[u][6];
+                  ax += v[0] * dj0 + v[1] * dj1 + v[2] * dj2;
+                  ay += v[3] * dj0 + v[4] * dj1 + v[5] * dj2;
+                  az += v[6] * dj0 + v[7] * dj1 + v[8] * dj2;
+                }
+            } else {
+              V4 zj[U], pj[U];
+#pragma unroll
+              for (int u = 0; u < U; ++u)
+                if (ok[u]) {
+                  zj[u] = ldcg_v(S.z + j[u]);
+                  pj[u] = ldcg_v(dprev + j[u]);
+                }
+#pragma unroll
+              for (int u = 0; u < U; ++u)
+                if (ok[u]) {
+                  const T* v = L.lval + 9 * (b0 + G * u);
+                  const T dj0 = zj[u].x + beta * pj[u].x, dj1 = zj[u].y + beta * pj[u].y,
+                          dj2 = zj[u].z + beta * pj[u].z;
+                  ax += v[0] * dj0 + v[1] * dj1 + v[2] * dj2;
+                  ay += v[3] * dj0 + v[4] * dj1 + v[5] * dj2;
+                  az += v[6] * dj0 + v[7] * dj1 + v[8] * dj2;
+                }
+            }
           }
         }
       }
@@ -457,7 +497,10 @@ __global__ void __launch_bounds__(NTS, 1)
         ld[0] = d0;
         ld[1] = d1;
         ld[2] = d2;
-        st_v(dcur + i, mk<V4, T>(d0, d1, d2));
+        if constexpr (REC)
+          st_rec_half(rec_ptr(S.zrec, S.nv, (s.iters + 1) & 1, i) + 4, d0, d1, d2);
+        else
+          st_v(dcur + i, mk<V4, T>(d0, d1, d2));
         T* lq = L.lq + 3 * item;
         lq[0] = ax;
         lq[1] = ay;
@@ -513,7 +556,10 @@ __global__ void __launch_bounds__(NTS, 1)
         lz[0] = z0;
         lz[1] = z1;
         lz[2] = z2;
-        st_v(S.z + i, mk<V4, T>(z0, z1, z2));
+        if constexpr (REC)
+          st_rec_half(rec_ptr(S.zrec, S.nv, (st[slot].iters + 1) & 1, i), z0, z1, z2);
+        else
+          st_v(S.z + i, mk<V4, T>(z0, z1, z2));
         rz = r0 * z0 + r1 * z1 + rr2 * z2;
         r2 = r0 * r0 + r1 * r1 + rr2 * rr2;
       }

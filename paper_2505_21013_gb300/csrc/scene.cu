@@ -379,6 +379,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   s.tpart = alloc<double>((size_t)4 * (n_vtiles + n_ttiles));
   s.ppart = alloc<double>((size_t)4 * n_ptiles);
   s.pword = alloc<unsigned long long>((size_t)8 * n_ptiles);
+  s.zrec = sizeof(T) == 4 ? alloc<T>((size_t)16 * nv) : nullptr;
   s.ctl = alloc<Ctl>(1);
   d_desc = alloc<SceneDev<T>>(1);
   d_ids = alloc<int>(1);
@@ -400,7 +401,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
       !d_col || !d_blk_row || !d_blk_ptr || !d_blk_src || !d_diag || !s.u || !s.u_n || !s.vel ||
       !s.uhat || !s.u_probe || !s.ge || !s.He || !s.dH || !s.g || !s.gmax || !s.val ||
       !s.proj_stamp || !s.round_stamp || !s.sel_list || !s.dx || !s.r || !s.z || !s.q || !s.d0 ||
-      !s.d1 || !s.Pinv || !s.vpart || !s.tpart || !s.ppart || !s.pword || !s.ctl || !d_desc || !d_ids ||
+      !s.d1 || !s.Pinv || !s.vpart || !s.tpart || !s.ppart || !s.pword || (sizeof(T) == 4 && !s.zrec) || !s.ctl || !d_desc || !d_ids ||
       !d_bar || !d_fixed_list || !d_targets || !d_xyz || !d_ttiles || !d_vtiles || !d_btiles ||
       !d_ptiles || !d_etiles || !d_projtiles) {
     set_error("cudaMalloc failed (scene needs more device memory than is free)");
