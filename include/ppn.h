@@ -215,6 +215,40 @@ PPN_API ppn_status ppn_probe_project(ppn_scene* s, const double* x, const int32_
 PPN_API ppn_status ppn_probe_pcg(ppn_scene* s, const double* vals, const double* b, double rel_tol,
                          int max_iter, double* x, int* info);
 
+/* ---- PCG without per-call device allocation (the paper has no counterpart) ----
+ *
+ * Block-Jacobi PCG with the negative-curvature exit (the linear solve of Sec. 4.1,
+ * "Linear Solvers", and Sec. 5.1) on a caller's device-resident FP32 BSR system,
+ * using only a fixed scratch arena in device global memory (a file-scope
+ * __device__ array sized for PPN_PCG_STATIC_MAX_ROWS block rows, about 8 MB).
+ * It is for callers that must not allocate device memory per call, e.g. a
+ * serving loop running under a fixed HBM budget, where cudaMalloc may fail and
+ * cudaFree synchronises the device.
+ *
+ * All pointers except `info` are DEVICE pointers owned by the caller:
+ *   row_ptr  n_rows+1 int32, non-decreasing, row_ptr[0] = 0, row_ptr[n_rows] = nnzb
+ *   col      nnzb int32 block columns in [0, n_rows); every row holds its diagonal block
+ *   val      9*nnzb float, component-major: entry c (row-major in the 3x3 block) of
+ *            block k at val[c*nnzb + k]
+ *   b        n_rows 16-byte records {b_x, b_y, b_z, ignored} (16-byte aligned)
+ *   x        n_rows 16-byte records, written with the solution (16-byte aligned)
+ * rel_tol: stop at ||r|| <= rel_tol ||b||; max_iter <= 0: max(1000, 3 n_rows).
+ * info (host, may be NULL): [iterations, ind, precond_fail, hit_max].
+ * stream: a cudaStream_t or NULL; the call waits for it before returning.
+ *
+ * Errors: PPN_ERR_INVALID_ARG for null pointers, n_rows > PPN_PCG_STATIC_MAX_ROWS,
+ * or a malformed pattern (checked on the device before the solve);
+ * PPN_ERR_TIMEOUT when a grid-wide wait runs out; PPN_ERR_NONFINITE; PPN_ERR_CUDA.
+ * The first call on a device looks up the arena's address and the solver's
+ * occupancy; make it once at start-up.  The arena is shared per device: calls
+ * on the same device must not overlap, and the library serialises its host
+ * threads with a lock.  The barrier and status words that must start at zero
+ * are cleared by every call. */
+#define PPN_PCG_STATIC_MAX_ROWS 65536
+PPN_API ppn_status ppn_pcg_solve_static(const int32_t* row_ptr, const int32_t* col, const float* val,
+                                        int32_t n_rows, int32_t nnzb, const float* b, float* x,
+                                        double rel_tol, int32_t max_iter, int32_t* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -100,6 +100,8 @@ SIGNATURES = {
     "ppn_probe_select": (_st, [_P, _pd, C.c_double, _pu, _pu, _pl]),
     "ppn_probe_project": (_st, [_P, _pd, _pi, C.c_int64, _pd]),
     "ppn_probe_pcg": (_st, [_P, _pd, _pd, C.c_double, C.c_int, _pd, C.POINTER(C.c_int)]),
+    "ppn_pcg_solve_static": (_st, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                   C.c_void_p, C.c_double, C.c_int32, C.POINTER(C.c_int32), C.c_void_p]),
 }
 
 _lib = None
@@ -342,3 +344,15 @@ def ppn_step_batch(scenes, modes, tol):
     out = (ppn_step_stats * n)()
     rc = lib().ppn_step_batch(arr, n, m, float(tol), out)
     return rc, [struct_dict(out[i]) for i in range(n)]
+
+
+def pcg_solve_static(row_ptr: int, col: int, val: int, n_rows: int, nnzb: int, b: int, x: int,
+                     rel_tol: float = 1e-4, max_iter: int = 0, stream: int = 0) -> dict:
+    """``ppn_pcg_solve_static`` on device pointers (see ``include/ppn.h``): int32
+    row_ptr/col, component-major FP32 values, 16-byte {x, y, z, pad} FP32 records
+    for b and x.  Returns the solver's info; raises PPNError on failure."""
+    info = (C.c_int32 * 4)()
+    _check(lib().ppn_pcg_solve_static(C.c_void_p(row_ptr), C.c_void_p(col), C.c_void_p(val), int(n_rows),
+                                      int(nnzb), C.c_void_p(b), C.c_void_p(x), float(rel_tol), int(max_iter),
+                                      info, C.c_void_p(stream or None)), "ppn_pcg_solve_static")
+    return {"iters": info[0], "ind": bool(info[1]), "precond_fail": bool(info[2]), "hit_max": bool(info[3])}
