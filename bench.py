@@ -150,6 +150,22 @@ def pcg_profile_traffic():
         return None
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise max over ranks of this rank's timings (ms); identity at N=1."""
+    import torch
+
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def steps_per_s(world, steps, ms):
+    """Whole-job throughput: every rank advances its own scene `steps` times
+    (replicas, weak scaling) within the slowest rank's `ms`."""
+    return world * steps / (ms / 1e3)
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -229,14 +245,9 @@ def run_ours(args, rank, world, dist):
             e2e_ms.append((t1 - t0) * 1e3)
     sc.close()
 
-    ms_ppn = sum(lat_ppn)
-    ms_pn = sum(lat_pn)
-    vals = torch.tensor([ms_ppn, ms_pn, sum(e2e_ms)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms_ppn, ms_pn, ms_e2e = vals.tolist()
+    ms_ppn, ms_pn, ms_e2e = max_over_ranks([sum(lat_ppn), sum(lat_pn), sum(e2e_ms)], dist, dev)
     K = args.steps
-    value = world * K / (ms_ppn / 1e3)
+    value = steps_per_s(world, K, ms_ppn)
 
     # roofline of the dominant kernel family (by summed device time)
     peaks = measured_peaks()
@@ -272,11 +283,11 @@ def run_ours(args, rank, world, dist):
                 "attempts": sum(s["total_attempts"] for s in st_ppn)},
         "kernel_ms": {k: round(v["total_ms"], 3) for k, v in kt.items()},
         "roofline": roof, "clocks": clocks, "gpu_launches": launches,
-        "e2e": {"value": world * K / (ms_e2e / 1e3), "unit": "steps/s",
+        "e2e": {"value": steps_per_s(world, K, ms_e2e), "unit": "steps/s",
                 "h2d_bytes_per_step": int(spec.fixed.size * 24), "d2h_bytes_per_step": int(spec.n_verts * 24)},
     }
     if lat_pn:
-        r["pn"] = {"steps_per_s": world * K / (ms_pn / 1e3), "ms_per_step": ms_pn / K,
+        r["pn"] = {"steps_per_s": steps_per_s(world, K, ms_pn), "ms_per_step": ms_pn / K,
                    "p50_ms": percentile(lat_pn, 0.5), "p99_ms": percentile(lat_pn, 0.99),
                    "newton_iters": sum(s["newton_iters"] for s in st_pn),
                    "projections": sum(s["total_projections"] for s in st_pn),
