@@ -64,19 +64,27 @@ extern "C" int ora_eigh(int n, const double* A_in, double* w, double* Q) {
   return ORA_OK;
 }
 
-// Hhat = Q max(D, eps) Q^T and dH = Hhat - H (the in-place update of Sec. 4.1).
-extern "C" int ora_clamp(int n, const double* H, double eps, double* Hhat, double* dH) {
+// Hhat = Q f(D) Q^T and dH = Hhat - H (the in-place update of Sec. 4.1), with
+// f(lambda) = max(lambda, eps) (clamping, Sec. 3) or max(|lambda|, eps)
+// (eigenvalue mirroring, which the paper compares against clamping, Sec. 5.2).
+extern "C" int ora_project(int n, const double* H, double eps, int kind, double* Hhat, double* dH) {
+  if (kind != ORA_PROJ_CLAMP && kind != ORA_PROJ_MIRROR) return ORA_ERR_INVALID;
   std::vector<double> w(n), Q((size_t)n * n), Hh((size_t)n * n);
   int rc = ora_eigh(n, H, w.data(), Q.data());
   if (rc) return rc;
+  for (int k = 0; k < n; ++k) w[k] = std::fmax(kind == ORA_PROJ_MIRROR ? std::fabs(w[k]) : w[k], eps);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
       double s = 0.0;
-      for (int k = 0; k < n; ++k) s += Q[(size_t)i * n + k] * std::fmax(w[k], eps) * Q[(size_t)j * n + k];
+      for (int k = 0; k < n; ++k) s += Q[(size_t)i * n + k] * w[k] * Q[(size_t)j * n + k];
       Hh[(size_t)i * n + j] = s;
     }
   if (Hhat) std::memcpy(Hhat, Hh.data(), sizeof(double) * (size_t)n * n);
   if (dH)
     for (size_t k = 0; k < (size_t)n * n; ++k) dH[k] = Hh[k] - H[k];
   return ORA_OK;
+}
+
+extern "C" int ora_clamp(int n, const double* H, double eps, double* Hhat, double* dH) {
+  return ora_project(n, H, eps, ORA_PROJ_CLAMP, Hhat, dH);
 }

@@ -2,13 +2,18 @@
 //
 // TEST INFRASTRUCTURE (oracle).  One call of ora_scene_step is one backward
 // Euler step, solved as the minimisation of the incremental potential by
-// Newton's method (Sec. 3) in one of three modes:
+// Newton's method (Sec. 3) in one of four modes:
 //   ORA_NEWTON  no element is projected (Sec. 1; Newton-CG fallback on ind)
 //   ORA_PN      every element Hessian is clamped before assembly (Sec. 3)
 //   ORA_PPN     Algorithm 1: start unprojected; while the solver reports
 //               indefiniteness, project the elements with ||S^e g||_inf > delta
 //               in place and solve again, tightening delta by alpha; relax it by
 //               beta after a successful solve (Sec. 4).
+//   ORA_PDN     project-on-demand (Sec. 2.2, Sec. 5.1): solve unprojected; when
+//               the solver reports indefiniteness, project every element in
+//               place and solve again, then assemble projected for the next
+//               pdn_countdown iterations (countdown 4) before trying
+//               unprojected again.  The countdown starts at 0 every time step.
 // The step then takes a backtracking line search (Sec. 5.1) and updates x.
 #include <cmath>
 #include <cstring>
@@ -202,6 +207,8 @@ ora_params ora_default_params(void) {
   p.ls_max_halvings = 30;
   p.tol_kind = 0;
   p.init_guess = 0;
+  p.pdn_countdown = 4;
+  p.projection = ORA_PROJ_CLAMP;
   return p;
 }
 
@@ -371,7 +378,7 @@ void ora_scene_assemble(const ora_scene* s, const double* x, const uint8_t* proj
     std::vector<double> dH(144);
     for (int64_t e = 0; e < s->nt; ++e)
       if (proj[e]) {
-        ora_clamp(12, &He[144 * e], s->p.eig_eps, nullptr, dH.data());
+        ora_project(12, &He[144 * e], s->p.eig_eps, s->p.projection, nullptr, dH.data());
         scatter_element(s, e, dH.data(), vals.data());
       }
   }
@@ -388,12 +395,12 @@ void ora_scene_project(const ora_scene* s, const double* x, const int32_t* sel, 
   double H[144];
   for (int64_t i = 0; i < n_sel; ++i) {
     element(s, sel[i], x, nullptr, nullptr, H);
-    ora_clamp(12, H, s->p.eig_eps, nullptr, dH + 144 * i);
+    ora_project(12, H, s->p.eig_eps, s->p.projection, nullptr, dH + 144 * i);
   }
 }
 
 int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_stats* out) {
-  if (mode < ORA_NEWTON || mode > ORA_PPN) return ORA_ERR_INVALID;
+  if (mode < ORA_NEWTON || mode > ORA_PDN) return ORA_ERR_INVALID;
   const int64_t nv = s->nv, nt = s->nt, N = 3 * nv;
   const ora_params& p = s->p;
   std::vector<double> xn = s->x, vn = s->v, xhat(N), g(N), dx(N), xt(N);
@@ -413,6 +420,7 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
   double g0 = -1.0;
   int status = ORA_ERR_NEWTON_MAXITER;
   int total_proj = 0, total_cg = 0, total_att = 0;
+  int countdown = 0;  // PDN: iterations left that assemble projected
 
   for (int k = 0; k < p.newton_max_iter; ++k) {
     for (int64_t e = 0; e < nt; ++e) element(s, e, x.data(), nullptr, &ge[12 * e], &He[144 * e]);
@@ -439,17 +447,23 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
     st.grad_norm2 = gn2;
     st.grad_norminf = gninf;
 
-    // unprojected H (PN: every element clamped before assembly)
+    // unprojected H (PN, and PDN within its countdown: every element clamped before assembly)
     assemble(s, He, vals);
     std::fill(proj.begin(), proj.end(), 0);
     int n_proj = 0;
-    if (mode == ORA_PN) {
-      for (int64_t e = 0; e < nt; ++e) {
-        ora_clamp(12, &He[144 * e], p.eig_eps, nullptr, dH.data());
-        scatter_element(s, e, dH.data(), vals.data());
-        proj[e] = 1;
-      }
+    auto project_all = [&]() {
+      for (int64_t e = 0; e < nt; ++e)
+        if (!proj[e]) {
+          ora_project(12, &He[144 * e], p.eig_eps, p.projection, nullptr, dH.data());
+          scatter_element(s, e, dH.data(), vals.data());
+          proj[e] = 1;
+        }
       n_proj = (int)nt;
+    };
+    const bool pre = mode == ORA_PN || (mode == ORA_PDN && countdown > 0);
+    if (pre) {
+      project_all();
+      if (mode == ORA_PDN) --countdown;
     }
     std::vector<double> b(N);
     for (int64_t i = 0; i < N; ++i) b[i] = -g[i];
@@ -478,15 +492,22 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
       return info[1] != 0;
     };
 
-    bool ind = solve(mode == ORA_PN ? (int)nt : 0, kInf);
+    bool ind = solve(pre ? (int)nt : 0, kInf);
     bool fallback = ind && mode != ORA_PPN;
+    if (mode == ORA_PDN && ind && !pre) {  // indefinite: project everything, solve again
+      project_all();
+      st.n_new_projected = (int)nt;
+      ind = solve((int)nt, -1.0);
+      fallback = ind;
+      countdown = p.pdn_countdown;
+    }
     if (mode == ORA_PPN) {
       while (ind) {
         if (delta == kInf) delta = p.alpha * gninf;
         const int64_t n_new = select(s, g.data(), delta, proj.data(), fresh.data());
         for (int64_t e = 0; e < nt; ++e)
           if (fresh[e]) {
-            ora_clamp(12, &He[144 * e], p.eig_eps, nullptr, dH.data());
+            ora_project(12, &He[144 * e], p.eig_eps, p.projection, nullptr, dH.data());
             scatter_element(s, e, dH.data(), vals.data());  // in-place update
             proj[e] = 1;
           }

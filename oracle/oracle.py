@@ -14,14 +14,16 @@ import numpy as np
 
 from . import build as _build
 
-NEWTON, PN, PPN = 0, 1, 2
+NEWTON, PN, PPN, PDN = 0, 1, 2, 3
+PROJ_CLAMP, PROJ_MIRROR = 0, 1
 
 
 class Params(C.Structure):
     _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("eps_delta", C.c_double),
                 ("eig_eps", C.c_double), ("pcg_rel_tol", C.c_double), ("armijo_c", C.c_double),
                 ("pcg_max_iter", C.c_int), ("newton_max_iter", C.c_int),
-                ("ls_max_halvings", C.c_int), ("tol_kind", C.c_int), ("init_guess", C.c_int)]
+                ("ls_max_halvings", C.c_int), ("tol_kind", C.c_int), ("init_guess", C.c_int),
+                ("pdn_countdown", C.c_int), ("projection", C.c_int)]
 
 
 class IterStats(C.Structure):
@@ -81,6 +83,7 @@ def lib():
         "ora_tet_eval": (I, [pd, pd, D, D, pd, pd, pd]),
         "ora_eigh": (I, [I, pd, pd, pd]),
         "ora_clamp": (I, [I, pd, D, pd, pd]),
+        "ora_project": (I, [I, pd, D, I, pd, pd]),
         "ora_pcg_bsr": (I, [I64, pl, pi, pd, pd, D, I, pd, C.POINTER(C.c_int)]),
         "ora_scene_create": (P, [pd, I64, pi, I64, D, D, D, D, pd, pi, I64, C.POINTER(Params)]),
         "ora_scene_destroy": (None, [P]),
@@ -169,6 +172,19 @@ def clamp(H, eps=1e-8):
     Hh = np.zeros((n, n))
     dH = np.zeros((n, n))
     lib().ora_clamp(n, _dp(H), eps, _dp(Hh), _dp(dH))
+    return Hh, dH
+
+
+def project(H, eps=1e-8, kind=PROJ_CLAMP):
+    """Hhat = Q f(D) Q^T and dH = Hhat - H with f = max(lambda, eps) (clamp) or
+    max(|lambda|, eps) (mirror)."""
+    H = np.ascontiguousarray(np.asarray(H, np.float64))
+    n = H.shape[0]
+    Hh = np.zeros((n, n))
+    dH = np.zeros((n, n))
+    rc = lib().ora_project(n, _dp(H), eps, int(kind), _dp(Hh), _dp(dH))
+    if rc:
+        raise ValueError(f"ora_project failed ({rc})")
     return Hh, dH
 
 

@@ -48,7 +48,8 @@
 extern "C" {
 #endif
 
-enum { ORA_NEWTON = 0, ORA_PN = 1, ORA_PPN = 2 };
+enum { ORA_NEWTON = 0, ORA_PN = 1, ORA_PPN = 2, ORA_PDN = 3 };
+enum { ORA_PROJ_CLAMP = 0, ORA_PROJ_MIRROR = 1 };
 
 enum {
   ORA_OK = 0,
@@ -71,6 +72,8 @@ typedef struct {
   int ls_max_halvings; /* default 30 */
   int tol_kind;        /* 0: ||g||_2 <= tol ||g0||_2 ; 1: ||gamma dx||_inf / dt < tol */
   int init_guess;      /* 0: x_n ; 1: x_n + dt v_n (free vertices) */
+  int pdn_countdown;   /* PDN: iterations that stay projected after an indefinite solve, default 4 */
+  int projection;      /* ORA_PROJ_CLAMP: max(lambda, eps); ORA_PROJ_MIRROR: max(|lambda|, eps) */
 } ora_params;
 
 typedef struct {
@@ -131,6 +134,8 @@ int ora_tet_eval(const double* X, const double* x, double mu, double lam_s,
 /* ---- dense symmetric eigen (cyclic Jacobi) and clamping ---- */
 int ora_eigh(int n, const double* A, double* w, double* Q);
 int ora_clamp(int n, const double* H, double eps, double* Hhat, double* dH);
+/* the same with a projection kind: ORA_PROJ_CLAMP or ORA_PROJ_MIRROR */
+int ora_project(int n, const double* H, double eps, int kind, double* Hhat, double* dH);
 
 /* ---- BSR PCG on a caller matrix ---- */
 /* info[0] = iterations, info[1] = ind, info[2] = precond_fail, info[3] = hit max_iter */
