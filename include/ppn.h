@@ -55,7 +55,15 @@ typedef enum {
   PPN_ERR_ADMISSION = 10
 } ppn_status;
 
-typedef enum { PPN_MODE_NEWTON = 0, PPN_MODE_PN = 1, PPN_MODE_PPN = 2 } ppn_mode;
+/* NEWTON: project nothing; PN: clamp every element Hessian before assembly;
+ * PPN: Algorithm 1; PDN: project-on-demand, the comparison method of Sec. 2.2 /
+ * Sec. 5.1 (solve unprojected; on indefiniteness project every element and
+ * solve again, then stay projected for pdn_countdown iterations). */
+typedef enum { PPN_MODE_NEWTON = 0, PPN_MODE_PN = 1, PPN_MODE_PPN = 2, PPN_MODE_PDN = 3 } ppn_mode;
+
+/* element projection: CLAMP max(lambda, eps) (Sec. 3, the paper's default);
+ * MIRROR max(|lambda|, eps) (eigenvalue mirroring, compared in Sec. 5.2) */
+typedef enum { PPN_PROJ_CLAMP = 0, PPN_PROJ_MIRROR = 1 } ppn_projection;
 
 /* FP64: every step in double.  MIXED: element Hessians, eigensolves, the BSR
  * matrix and PCG in float; element energies, the assembled gradient and its
@@ -82,6 +90,8 @@ typedef struct {
   int precision;       /* ppn_precision (PPN_PREC_MIXED) */
   int tol_kind;        /* 0: ||g||_2 <= tol ||g0||_2 ; 1: ||gamma dx||_inf / dt < tol (Sec. 5.1) */
   int init_guess;      /* 0: x_n ; 1: x_n + dt v_n */
+  int pdn_countdown;   /* PDN: iterations that stay projected after an indefinite solve (4, Sec. 5.1) */
+  int projection;      /* ppn_projection (PPN_PROJ_CLAMP) */
 } ppn_params;
 
 typedef struct {

@@ -105,6 +105,8 @@ struct SceneDev {
   int pcg_max_iter;
   int it_id, round_id;
   int mode;
+  int proj_kind;           // ppn_projection: 0 clamp, 1 mirror
+  int init_guess;          // 0: x_n ; 1: x_n + dt v_n
   int active;              // the scene takes part in the current launch
 };
 

@@ -3,7 +3,9 @@
 //
 // The projection is the clamping of Sec. 3: H^e = Q D Q^T is replaced by
 // Q max(D, eps) Q^T, added to the assembled matrix as the difference
-// dH^e = sum_{lambda_i < eps} (eps - lambda_i) q_i q_i^T (Sec. 4.1).
+// dH^e = sum_{lambda_i < eps} (eps - lambda_i) q_i q_i^T (Sec. 4.1).  With
+// `mirror` the target of such an eigenvalue is max(|lambda_i|, eps) instead
+// (eigenvalue mirroring, which the paper compares against clamping, Sec. 5.2).
 //
 // Reduction.  A linear tet's Hessian is H^e = V B^T A B with B the 9x12 map
 // x_e -> vec F built from the shape gradients dN_a (rows of the 4x3 matrix D),
@@ -123,7 +125,7 @@ PPN_HD int jacobi9(T* A, T* V) {
 // W = Dm^-1 (row a-1 = dN_a), V = rest volume.  Returns the number of clamped
 // eigenvalues of M (the three translation modes are always clamped as well).
 template <typename T>
-PPN_HD int clamp_tet(const TetState<T>& st, const T* W, T Vol, T mu, T lam, T eps, T* out) {
+PPN_HD int clamp_tet(const TetState<T>& st, const T* W, T Vol, T mu, T lam, T eps, bool mirror, T* out) {
   T dN[4][3];
   shape_grads(W, dN);
   // G = sum_a dN_a dN_a^T and its Cholesky factor L
@@ -182,7 +184,7 @@ PPN_HD int clamp_tet(const TetState<T>& st, const T* W, T Vol, T mu, T lam, T ep
     const T lp = A[s9(p, p)];
     if (lp < eps) {
       ++n_clamped;
-      const T w = eps - lp;
+      const T w = (mirror ? (-lp > eps ? -lp : eps) : eps) - lp;
       T q[4][3];
 #pragma unroll
       for (int a = 0; a < 4; ++a)

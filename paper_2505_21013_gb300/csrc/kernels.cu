@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(PROJ_CTA) k_project(const SceneDev<T>* scenes,
   TetState<T> st;
   tet_state(H, mu, lam, st);
   T out[90];
-  clamp_tet(st, W, V, mu, lam, (T)S.eig_eps, out);
+  clamp_tet(st, W, V, mu, lam, (T)S.eig_eps, S.proj_kind == 1, out);
   T* dst = S.dH + (size_t)e * HE_STRIDE;
 #pragma unroll
   for (int k = 0; k < 90; ++k) dst[k] = out[k];
@@ -367,7 +367,7 @@ __global__ void k_gmax(const SceneDev<T>* scenes, const TileRef* tiles) {
 // Dirichlet vertices set to their targets (targets are positions, n_fixed x 3)
 template <typename T>
 __global__ void k_predict(const SceneDev<T>* scenes, const TileRef* tiles, const int* fixed_list,
-                          const double* targets, int n_fixed, int init_guess) {
+                          const double* targets, int n_fixed) {
   const TileRef tr = tiles[blockIdx.x];
   const SceneDev<T>& S = scenes[tr.scene];
   if (!S.active) return;
@@ -378,7 +378,7 @@ __global__ void k_predict(const SceneDev<T>* scenes, const TileRef* tiles, const
   st_d4(S.u_n + v, u);
   st_d4(S.uhat + v, make_double4(u.x + dt * w.x + dt2 * S.grav[0], u.y + dt * w.y + dt2 * S.grav[1],
                                  u.z + dt * w.z + dt2 * S.grav[2], 0.0));
-  if (init_guess == 1 && !S.fixed[v])
+  if (S.init_guess == 1 && !S.fixed[v])
     st_d4(S.u + v, make_double4(u.x + dt * w.x, u.y + dt * w.y, u.z + dt * w.z, 0.0));
 }
 
@@ -479,8 +479,8 @@ void launch_energy(const SceneDev<T>* s, const TileRef* t, int n, int probe, cud
   if (n) k_energy<T><<<n, TILE, 0, st>>>(s, t, probe);
 }
 template <typename T>
-void launch_predict(const SceneDev<T>* s, const TileRef* t, int n, int init_guess, cudaStream_t st) {
-  if (n) k_predict<T><<<n, TILE, 0, st>>>(s, t, nullptr, nullptr, 0, init_guess);
+void launch_predict(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
+  if (n) k_predict<T><<<n, TILE, 0, st>>>(s, t, nullptr, nullptr, 0);
 }
 template <typename T>
 void launch_apply_targets(const SceneDev<T>* s, int scene, const int* fl, const double* tg, int nf,
@@ -512,7 +512,7 @@ void launch_fallback(const SceneDev<T>* s, const TileRef* t, int n, int kind, cu
   template void launch_select<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \
   template void launch_project<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
   template void launch_energy<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);  \
-  template void launch_predict<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
+  template void launch_predict<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \
   template void launch_apply_targets<T>(const SceneDev<T>*, int, const int*, const double*, int, \
                                         int, cudaStream_t);                                    \
   template void launch_axpy_u<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \

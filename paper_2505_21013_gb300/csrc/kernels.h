@@ -16,7 +16,7 @@ template <typename T> void launch_update(const SceneDev<T>*, const TileRef*, int
 template <typename T> void launch_select(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
 template <typename T> void launch_project(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
 template <typename T> void launch_energy(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
-template <typename T> void launch_predict(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
+template <typename T> void launch_predict(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
 template <typename T>
 void launch_apply_targets(const SceneDev<T>*, int, const int*, const double*, int, int, cudaStream_t);
 template <typename T> void launch_gmax(const SceneDev<T>*, const TileRef*, int, cudaStream_t);

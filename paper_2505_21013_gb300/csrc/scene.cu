@@ -172,6 +172,11 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
     return PPN_ERR_INVALID_ARG;
   }
   params = p ? *p : ppn_default_params();
+  if ((params.projection != PPN_PROJ_CLAMP && params.projection != PPN_PROJ_MIRROR) || params.pdn_countdown < 0 ||
+      !(params.alpha > 0 && params.alpha < 1) || !(params.beta >= 1) || !(params.eig_eps >= 0)) {
+    set_error("invalid parameters (projection kind, pdn_countdown, alpha in (0,1), beta >= 1, eig_eps >= 0)");
+    return PPN_ERR_INVALID_ARG;
+  }
   dt = dt_;
   nv = (int)n_verts;
   nt = (int)n_tets;
@@ -466,6 +471,8 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   for (int k = 0; k < 3; ++k) s.grav[k] = params.gravity[k];
   s.eps_delta = params.eps_delta;
   s.eig_eps = params.eig_eps;
+  s.proj_kind = params.projection;
+  s.init_guess = params.init_guess;
   s.delta = std::numeric_limits<double>::infinity();
   s.pcg_tol2 = params.pcg_rel_tol * params.pcg_rel_tol;
   s.pcg_max_iter = params.pcg_max_iter > 0 ? params.pcg_max_iter : std::max(1000, 3 * nv);
@@ -634,6 +641,8 @@ struct HostState {
   int precond_fail = 0, pcg_iters_last = 0;
   double E0 = 0, dd = 0, dxmax = 0, gamma = 1;
   int halvings = 0;
+  int countdown = 0;  // PDN: iterations left that assemble projected
+  bool pre = false;   // this iteration projects every element before assembly
   ppn_iter_stats cur{};
   ppn_step_stats tot{};
 };
@@ -642,8 +651,9 @@ template <typename T>
 struct Driver {
   Group<T>& G;
   std::vector<HostState> H;
-  const ppn_params& P;
-  explicit Driver(Group<T>& g) : G(g), P(g.S[0]->params) {}
+  explicit Driver(Group<T>& g) : G(g) {}
+  // parameters of scene i (scenes of one batch may differ)
+  const ppn_params& Pi(int i) const { return G.S[i]->params; }
 
   double pcg_iter_bytes() const {
     double b = 0;
@@ -765,7 +775,7 @@ struct Driver {
     G.set_active(on);
     ppn_status rc = G.upload_desc();
     if (rc) return rc;
-    timed(FAM_VECTOR, 0, [&] { launch_predict<T>(G.d_desc, G.d_vtiles, G.n_vtiles, P.init_guess, G.st); });
+    timed(FAM_VECTOR, 0, [&] { launch_predict<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st); });
     for (int i = 0; i < n; ++i) {
       SceneImpl<T>& s = *G.S[i];
       const double* tg = s.ext_targets ? s.ext_targets : s.d_targets;
@@ -809,12 +819,12 @@ struct Driver {
           continue;
         }
         if (h.k == 0) h.g0 = h.gn2;
-        if (P.tol_kind == 0 && h.gn2 <= tol * h.g0) {
+        if (Pi(i).tol_kind == 0 && h.gn2 <= tol * h.g0) {
           h.status = PPN_OK;
           h.running = false;
           continue;
         }
-        if (h.k >= P.newton_max_iter) {
+        if (h.k >= Pi(i).newton_max_iter) {
           h.status = PPN_ERR_NEWTON_MAXITER;
           h.running = false;
           continue;
@@ -827,9 +837,11 @@ struct Driver {
         h.fallback = false;
         solve_on[i] = 1;
         any_solve = true;
-        if (h.mode == PPN_MODE_PN) {
+        h.pre = h.mode == PPN_MODE_PN || (h.mode == PPN_MODE_PDN && h.countdown > 0);
+        if (h.pre) {
           pn_on[i] = 1;
           any_pn = true;
+          if (h.mode == PPN_MODE_PDN) --h.countdown;
         }
       }
       if (!any_solve) continue;
@@ -849,18 +861,42 @@ struct Driver {
       if ((rc = solve(solve_on, 1))) return rc;
       if ((rc = G.sync_ctl())) return rc;
       if ((rc = check_errors(solve_on))) return rc;
-      std::vector<char> retry(n, 0);
-      bool any_retry = false;
+      std::vector<char> retry(n, 0), pdn(n, 0);
+      bool any_retry = false, any_pdn = false;
       for (int i = 0; i < n; ++i) {
         if (!solve_on[i]) continue;
-        record_attempt(i, 0, H[i].mode == PPN_MODE_PN ? G.S[i]->nt : 0,
-                       std::numeric_limits<double>::infinity());
+        record_attempt(i, 0, H[i].pre ? G.S[i]->nt : 0, std::numeric_limits<double>::infinity());
         if (H[i].ind && H[i].mode == PPN_MODE_PPN) {
           retry[i] = 1;
           any_retry = true;
+        } else if (H[i].ind && H[i].mode == PPN_MODE_PDN && !H[i].pre) {
+          pdn[i] = 1;
+          any_pdn = true;
         } else if (H[i].ind) {
           H[i].fallback = true;
         }
+      }
+      // ---- PDN: indefinite, so project every element in place and solve again
+      if (any_pdn) {
+        for (int i = 0; i < n; ++i)
+          if (pdn[i]) {
+            G.h_desc[i].delta = -1.0;  // select every element not yet projected
+            G.h_desc[i].round_id = ++G.S[i]->round_counter;
+          }
+        if ((rc = select_and_project(pdn, false))) return rc;
+        G.set_active(pdn);
+        if ((rc = G.upload_desc())) return rc;
+        timed(FAM_UPDATE, 0, [&] { launch_update<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st); });
+        if ((rc = check_launch())) return rc;
+        if ((rc = solve(pdn, 1))) return rc;
+        if ((rc = G.sync_ctl())) return rc;
+        if ((rc = check_errors(pdn))) return rc;
+        for (int i = 0; i < n; ++i)
+          if (pdn[i]) {
+            record_attempt(i, 1, G.S[i]->nt, -1.0);
+            H[i].countdown = Pi(i).pdn_countdown;
+            if (H[i].ind) H[i].fallback = true;  // fully projected and still indefinite (rounding)
+          }
       }
       // ---- PPN retries (Algorithm 1 inner loop)
       int attempt = 1;
@@ -868,7 +904,7 @@ struct Driver {
         for (int i = 0; i < n; ++i)
           if (retry[i]) {
             HostState& h = H[i];
-            if (std::isinf(h.delta)) h.delta = P.alpha * h.ginf;
+            if (std::isinf(h.delta)) h.delta = Pi(i).alpha * h.ginf;
             G.h_desc[i].delta = h.delta;
             G.h_desc[i].round_id = ++G.S[i]->round_counter;
           }
@@ -902,7 +938,7 @@ struct Driver {
               h.fallback = true;  // fully projected and still indefinite (rounding)
               retry[i] = 0;
             } else {
-              h.delta *= P.alpha;  // tighten
+              h.delta *= Pi(i).alpha;  // tighten
               any_retry = true;
             }
           } else {
@@ -912,7 +948,7 @@ struct Driver {
         ++attempt;
       }
       for (int i = 0; i < n; ++i)
-        if (solve_on[i] && H[i].mode == PPN_MODE_PPN) H[i].delta *= P.beta;  // relax
+        if (solve_on[i] && H[i].mode == PPN_MODE_PPN) H[i].delta *= Pi(i).beta;  // relax
       // ---- fallback directions when the solve gave no usable iterate
       {
         std::vector<char> fb2(n, 0), fb3(n, 0);
@@ -990,13 +1026,13 @@ struct Driver {
           if (!ls[i]) continue;
           HostState& h = H[i];
           const double Et = G.h_ctl[i].energy[0];
-          if (Et <= h.E0 + P.armijo_c * h.gamma * h.dd) {
+          if (Et <= h.E0 + Pi(i).armijo_c * h.gamma * h.dd) {
             ls[i] = 0;
             accept[i] = 1;
             h.cur.gamma = h.gamma;
             h.cur.energy_new = Et;
             h.cur.ls_halvings = h.halvings;
-          } else if (h.halvings >= P.ls_max_halvings) {
+          } else if (h.halvings >= Pi(i).ls_max_halvings) {
             ls[i] = 0;
             h.status = PPN_ERR_LINESEARCH;
             h.running = false;
@@ -1025,7 +1061,7 @@ struct Driver {
         HostState& h = H[i];
         finish_iter(i);
         h.k += 1;
-        if (P.tol_kind == 1 && h.gamma * h.dxmax / G.S[i]->dt < tol) {
+        if (Pi(i).tol_kind == 1 && h.gamma * h.dxmax / G.S[i]->dt < tol) {
           h.status = PPN_OK;
           h.running = false;
         }
@@ -1551,6 +1587,8 @@ ppn_params ppn_default_params(void) {
   p.beta = 2.0;
   p.eps_delta = 1e-12;
   p.eig_eps = 1e-8;
+  p.pdn_countdown = 4;
+  p.projection = PPN_PROJ_CLAMP;
   p.pcg_rel_tol = 1e-4;
   p.armijo_c = 1e-4;
   p.gravity[0] = 0.0;
@@ -1669,7 +1707,7 @@ ppn_status ppn_set_kinematic_targets_device(ppn_scene* s, const double* xyz) {
 }
 
 ppn_status ppn_step(ppn_scene* s, ppn_mode mode, double tol, double* out_xyz, ppn_step_stats* out) {
-  if (mode < PPN_MODE_NEWTON || mode > PPN_MODE_PPN || !(tol >= 0)) {
+  if (mode < PPN_MODE_NEWTON || mode > PPN_MODE_PDN || !(tol >= 0)) {
     set_error("invalid mode or tolerance");
     return PPN_ERR_INVALID_ARG;
   }
@@ -1701,6 +1739,15 @@ ppn_status ppn_step_batch(ppn_scene* const* scenes, int n, const ppn_mode* modes
       return PPN_ERR_INVALID_ARG;
     }
   std::vector<int> m(modes, modes + n);
+  for (int i = 0; i < n; ++i)
+    if (m[i] < PPN_MODE_NEWTON || m[i] > PPN_MODE_PDN) {
+      set_error("invalid mode in batch");
+      return PPN_ERR_INVALID_ARG;
+    }
+  if (!(tol >= 0)) {
+    set_error("invalid tolerance");
+    return PPN_ERR_INVALID_ARG;
+  }
   std::vector<ppn_step_stats> st;
   ppn_status rc;
   if (prec == PPN_PREC_FP64) {

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libppn.so")
 PPN_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "DEGENERATE_TET", 5: "LINESEARCH",
                 6: "NEWTON_MAXITER", 7: "PCG_MAXITER", 8: "NONFINITE", 9: "TIMEOUT", 10: "ADMISSION"}
-MODE_NEWTON, MODE_PN, MODE_PPN = 0, 1, 2
+MODE_NEWTON, MODE_PN, MODE_PPN, MODE_PDN = 0, 1, 2, 3
+PROJ_CLAMP, PROJ_MIRROR = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 
 
@@ -31,7 +32,7 @@ class ppn_params(C.Structure):
                 ("eig_eps", C.c_double), ("pcg_rel_tol", C.c_double), ("armijo_c", C.c_double),
                 ("gravity", C.c_double * 3), ("pcg_max_iter", C.c_int), ("newton_max_iter", C.c_int),
                 ("ls_max_halvings", C.c_int), ("precision", C.c_int), ("tol_kind", C.c_int),
-                ("init_guess", C.c_int)]
+                ("init_guess", C.c_int), ("pdn_countdown", C.c_int), ("projection", C.c_int)]
 
 
 class ppn_iter_stats(C.Structure):

@@ -21,8 +21,11 @@ TOL = {P.PREC_FP64: 1e-10, P.PREC_MIXED: 2e-5}
 PRECS = [P.PREC_FP64, P.PREC_MIXED]
 
 
-def scene_pair(spec, prec):
-    return P.Scene.from_spec(spec, precision=prec), O.Scene.from_spec(spec)
+def scene_pair(spec, prec, mirror=False):
+    pg, po = P.ppn_default_params(), O.default_params()
+    if mirror:
+        pg.projection, po.projection = P.PROJ_MIRROR, O.PROJ_MIRROR
+    return P.Scene.from_spec(spec, params=pg, precision=prec), O.Scene.from_spec(spec, po)
 
 
 def deformed(spec, seed, amp=0.2):
@@ -115,10 +118,11 @@ def test_selection_is_exact_with_ties():
     assert not sel[5]
 
 
+@pytest.mark.parametrize("mirror", [False, True])
 @pytest.mark.parametrize("prec", PRECS)
-def test_projection_updates(prec):
+def test_projection_updates(prec, mirror):
     spec = medium_spec(12)
-    g, o = scene_pair(spec, prec)
+    g, o = scene_pair(spec, prec, mirror)
     x = deformed(spec, 13, amp=1.0)
     sel = np.arange(0, spec.n_tets, 7, dtype=np.int32)
     dH = g.probe_project(x, sel)

@@ -16,12 +16,12 @@ P = pytest.importorskip("paper_2505_21013_gb300")
 from oracle import oracle as O  # noqa: E402
 from ppn_inputs import cube_scene, twisting_beam_scene  # noqa: E402
 
-MODES = [(P.MODE_NEWTON, O.NEWTON), (P.MODE_PN, O.PN), (P.MODE_PPN, O.PPN)]
+MODES = [(P.MODE_NEWTON, O.NEWTON), (P.MODE_PN, O.PN), (P.MODE_PPN, O.PPN), (P.MODE_PDN, O.PDN)]
 
 
-def run_pair(spec, mode_g, mode_o, steps, tol, prec, params=None):
+def run_pair(spec, mode_g, mode_o, steps, tol, prec, params=None, oparams=None):
     g = P.Scene.from_spec(spec, params=params, precision=prec)
-    o = O.Scene.from_spec(spec)
+    o = O.Scene.from_spec(spec, oparams)
     out = []
     for n in range(steps):
         tg = spec.targets_at(n)
@@ -62,6 +62,9 @@ def test_violent_beam_fp64_matches_oracle(mode_g, mode_o):
             assert abs(st["newton_iters"] - sto["newton_iters"]) <= 1
         if mode_g == P.MODE_PN:
             assert st["total_projections"] == st["newton_iters"] * spec.n_tets
+        if mode_g == P.MODE_PDN:  # all or nothing per iteration
+            assert all(it["n_projected_total"] in (0, spec.n_tets) for it in its)
+            assert st["total_projections"] % spec.n_tets == 0
 
 
 @pytest.mark.parametrize("mode_g,mode_o", MODES)
@@ -153,3 +156,18 @@ def test_free_fall_exact_on_gpu():
     _, x1, _ = sc.step(P.MODE_PPN, 1e-12)
     g = np.array(spec.gravity)
     assert np.allclose(x1, spec.rest + spec.dt ** 2 * g, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("mode_g,mode_o", [(P.MODE_PN, O.PN), (P.MODE_PPN, O.PPN), (P.MODE_PDN, O.PDN)])
+def test_mirroring_fp64_matches_oracle(mode_g, mode_o):
+    spec = twisting_beam_scene(4, 4, 10, h=0.02, E=1e5, nu=0.45, omega=10.0, dt=0.1, seed=2)
+    pg = P.ppn_default_params()
+    pg.projection = P.PROJ_MIRROR
+    po = O.default_params()
+    po.projection = O.PROJ_MIRROR
+    _, _, out = run_pair(spec, mode_g, mode_o, 3, 1e-6, P.PREC_FP64, params=pg, oparams=po)
+    for rc, x, st, its, rco, xo, sto, itso in out:
+        assert rc == rco == 0
+        disp = np.abs(xo - spec.rest).max()
+        assert np.abs(x - xo).max() <= 1e-5 * disp
+        assert abs(st["newton_iters"] - sto["newton_iters"]) <= 1
