@@ -225,6 +225,73 @@ PPN_API ppn_status ppn_probe_project(ppn_scene* s, const double* x, const int32_
 PPN_API ppn_status ppn_probe_pcg(ppn_scene* s, const double* vals, const double* b, double rel_tol,
                          int max_iter, double* x, int* info);
 
+/* ---- Serving: time-step requests over resident scenes (continuous batching) ----
+ *
+ * The paper has no serving layer; this is the request loop around the same
+ * time step (Sec. 3 with Algorithm 1).  A server owns a CUDA stream, a worker
+ * thread and its scenes, which stay resident on the device (mesh, BSR pattern,
+ * state) between requests.
+ *   - Admission by HBM footprint: ppn_server_add_scene admits a scene only when
+ *     the device memory of all resident scenes stays within hbm_fraction of the
+ *     device's memory; otherwise PPN_ERR_ADMISSION (nothing is kept).  Removing
+ *     a scene frees its memory for later admissions.
+ *   - A request is one time step of one scene (mode, tolerance, optional new
+ *     kinematic targets).  Requests of one scene run in submission order.
+ *   - Continuous batching: up to max_batch scenes step together, one launch per
+ *     phase over all of them.  At every Newton-iteration boundary the finished
+ *     scenes leave the batch (their results become available) and queued
+ *     requests join in the free slots, so requests that arrive while others
+ *     run are admitted as slots free up and their work overlaps on the device.
+ *     A scene's result does not depend on the other scenes of the batch
+ *     (every reduction is per scene and in a fixed order).
+ * Every call returns a status; waits on the worker are bounded only by the
+ * requests themselves (each time step has its own iteration caps). */
+typedef struct ppn_server ppn_server;
+
+typedef struct {
+  double hbm_fraction; /* admission cap: resident scenes' device memory <= this x device memory (0.8) */
+  int max_batch;       /* scenes that step together (64) */
+  int precision;       /* ppn_precision of every scene of the server (PPN_PREC_MIXED) */
+} ppn_server_config;
+
+typedef struct {
+  double t_submit_ms; /* times since the server was created */
+  double t_start_ms;  /* the request joined the batch */
+  double t_done_ms;   /* its result was available */
+  int batch_max;      /* largest batch the request was part of */
+} ppn_request_times;
+
+typedef struct {
+  int64_t submitted, completed, rejected_scenes;
+  int resident_scenes;
+  double resident_bytes, budget_bytes;
+  double p50_ms, p99_ms; /* latency (done - submit) percentiles over completed requests */
+  double steps_per_s;    /* completed requests / (last completion - first submission) */
+} ppn_server_stats;
+
+PPN_API ppn_server_config ppn_server_default_config(void);
+PPN_API ppn_status ppn_server_create(const ppn_server_config* cfg, ppn_server** out);
+/* Finishes the requests already submitted, then frees the server and its scenes. */
+PPN_API void ppn_server_destroy(ppn_server* srv);
+/* Same arguments as ppn_create_scene (params->precision must equal the server's);
+ * scene_id receives the server's handle of the scene. */
+PPN_API ppn_status ppn_server_add_scene(ppn_server* srv, const double* rest_xyz, int64_t n_verts,
+                                        const int32_t* tets, int64_t n_tets, const ppn_material* mat, double dt,
+                                        const int32_t* fixed, int64_t n_fixed, const ppn_params* params,
+                                        int32_t* scene_id);
+/* PPN_ERR_INVALID_ARG while the scene has unfinished requests. */
+PPN_API ppn_status ppn_server_remove_scene(ppn_server* srv, int32_t scene_id);
+/* targets: NULL (keep the scene's current kinematic targets) or n_fixed*3 positions,
+ * copied before the call returns.  ticket receives the request's handle. */
+PPN_API ppn_status ppn_server_submit(ppn_server* srv, int32_t scene_id, ppn_mode mode, double tol,
+                                     const double* targets, int64_t* ticket);
+/* wait != 0 blocks until the request is done.  *done = 1 when it is; then out_xyz
+ * (n_verts*3, may be NULL), stats and times (may be NULL) are filled, the ticket
+ * is released, and the request's own status is returned. */
+PPN_API ppn_status ppn_server_poll(ppn_server* srv, int64_t ticket, int wait, int* done, double* out_xyz,
+                                   ppn_step_stats* stats, ppn_request_times* times);
+PPN_API ppn_status ppn_server_get_stats(ppn_server* srv, ppn_server_stats* out);
+
 /* ---- PCG without per-call device allocation (the paper has no counterpart) ----
  *
  * Block-Jacobi PCG with the negative-curvature exit (the linear solve of Sec. 4.1,

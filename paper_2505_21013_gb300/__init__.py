@@ -6,7 +6,7 @@ C ABI (``include/ppn.h``).  ``ppn`` is the ctypes binding; ``build`` compiles
 
 from . import ppn  # noqa: F401
 from .ppn import (MODE_NEWTON, MODE_PDN, MODE_PN, MODE_PPN, PREC_FP64, PREC_MIXED, PROJ_CLAMP,  # noqa: F401
-                  PROJ_MIRROR, PPNError, Scene, ppn_default_params, ppn_step_batch)
+                  PROJ_MIRROR, PPNError, Scene, Server, ppn_default_params, ppn_step_batch)
 
-__all__ = ["ppn", "Scene", "PPNError", "ppn_default_params", "ppn_step_batch", "MODE_NEWTON", "MODE_PN",
+__all__ = ["ppn", "Scene", "Server", "PPNError", "ppn_default_params", "ppn_step_batch", "MODE_NEWTON", "MODE_PN",
            "MODE_PPN", "MODE_PDN", "PROJ_CLAMP", "PROJ_MIRROR", "PREC_FP64", "PREC_MIXED"]

@@ -1,0 +1,840 @@
+// Scene groups and the lockstep Newton / PN / PPN / PDN driver.
+//
+// A Group holds the device tables of a set of scenes that step together: one
+// descriptor per scene, tile tables for every kernel family, control blocks.
+// The Driver runs Newton iterations over a group: every phase is one launch
+// over the scenes still taking part in it, and every host decision is taken
+// per scene after one device->host copy of all scenes' control blocks.  A time
+// step is begin() for the scenes that start it, tick() (one Newton iteration
+// of every running scene) until they stop, and finish().  Scenes may join a
+// group at an iteration boundary, which is how the serving loop batches
+// requests continuously.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "scene.h"
+
+namespace ppn {
+
+#define PPN_CU(call)                                                                      \
+  do {                                                                                    \
+    cudaError_t _e = (call);                                                              \
+    if (_e != cudaSuccess) {                                                              \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(_e));                      \
+      return _e == cudaErrorMemoryAllocation ? PPN_ERR_OOM : PPN_ERR_CUDA;                \
+    }                                                                                     \
+  } while (0)
+
+template <typename T>
+struct Group {
+  std::vector<SceneImpl<T>*> S;
+  std::vector<SceneDev<T>> h_desc;
+  SceneDev<T>* d_desc = nullptr;
+  Ctl* d_ctl = nullptr;
+  Ctl* h_ctl = nullptr;
+  GridBar* h_bar = nullptr;
+  TileRef *d_ttiles = nullptr, *d_vtiles = nullptr, *d_btiles = nullptr, *d_ptiles = nullptr,
+          *d_etiles = nullptr, *d_projtiles = nullptr;
+  int n_ttiles = 0, n_vtiles = 0, n_btiles = 0, n_ptiles = 0, n_etiles = 0;
+  int* d_ids = nullptr;
+  TileRef* d_pcgtiles = nullptr;
+  unsigned pcg_launch_seq = 0;
+  std::vector<int> pcg_ids;  // slots of the tile table currently on the device
+  int pcg_ntiles = 0;
+  size_t pcg_smem_bytes = 0;  // > 0: resident PCG layout chosen for that table
+  int pcg_smem_blocks = 0, pcg_smem_grid = 0;
+  GridBar* d_bar = nullptr;
+  cudaStream_t st = nullptr;
+  Staging staging;
+  KernelTimer* timer = nullptr;
+  int pcg_grid = 0, pcg_group = 8;
+  std::vector<void*> allocs;
+  // capacities of the device tables (a group can be rebuilt for new members)
+  size_t cap_n = 0, cap_tt = 0, cap_vt = 0, cap_bt = 0, cap_pt = 0, cap_et = 0, cap_proj = 0;
+  ~Group() { release(); }
+  void release() {
+    if (st) cudaStreamSynchronize(st);
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    if (h_ctl) cudaFreeHost(h_ctl);
+    if (h_bar) cudaFreeHost(h_bar);
+    h_ctl = nullptr;
+    h_bar = nullptr;
+    cap_n = cap_tt = cap_vt = cap_bt = cap_pt = cap_et = cap_proj = 0;
+  }
+  template <typename X>
+  X* alloc(size_t n) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(1, n) * sizeof(X)) != cudaSuccess) return nullptr;
+    allocs.push_back(p);
+    return reinterpret_cast<X*>(p);
+  }
+  // (Re)build the group's tables for `members`.  Device tables are reused when
+  // they are large enough and regrown (with headroom) otherwise.
+  ppn_status build(const std::vector<SceneImpl<T>*>& members) {
+    if (st) cudaStreamSynchronize(st);
+    S = members;
+    const int n = (int)S.size();
+    st = S[0]->stream;
+    timer = &S[0]->timer;
+    pcg_grid = S[0]->pcg_grid;
+    pcg_group = S[0]->pcg_group;
+    h_desc.resize(n);
+    std::vector<TileRef> tt, vt, bt, pt, et;
+    size_t projcap = 0;
+    for (int i = 0; i < n; ++i) {
+      const SceneImpl<T>& s = *S[i];
+      for (int t = 0; t < s.n_ttiles; ++t) tt.push_back({i, t});
+      for (int t = 0; t < s.n_vtiles; ++t) vt.push_back({i, t});
+      for (int t = 0; t < s.n_btiles; ++t) bt.push_back({i, t});
+      for (int t = 0; t < s.n_ptiles; ++t) pt.push_back({i, t});
+      for (int t = 0; t < s.n_ttiles + s.n_vtiles; ++t) et.push_back({i, t});
+      projcap += (s.nt + PROJ_CTA - 1) / PROJ_CTA;
+    }
+    n_ttiles = (int)tt.size();
+    n_vtiles = (int)vt.size();
+    n_btiles = (int)bt.size();
+    n_ptiles = (int)pt.size();
+    n_etiles = (int)et.size();
+    if (n > (int)cap_n || tt.size() > cap_tt || vt.size() > cap_vt || bt.size() > cap_bt || pt.size() > cap_pt ||
+        et.size() > cap_et || projcap > cap_proj) {
+      const bool grow = !allocs.empty();
+      release();
+      auto room = [&](size_t x) { return grow ? x + x / 2 : x; };
+      cap_n = room(n);
+      cap_tt = room(tt.size());
+      cap_vt = room(vt.size());
+      cap_bt = room(bt.size());
+      cap_pt = room(pt.size());
+      cap_et = room(et.size());
+      cap_proj = room(projcap);
+      d_desc = alloc<SceneDev<T>>(cap_n);
+      d_ctl = alloc<Ctl>(cap_n);
+      d_ttiles = alloc<TileRef>(cap_tt);
+      d_vtiles = alloc<TileRef>(cap_vt);
+      d_btiles = alloc<TileRef>(cap_bt);
+      d_ptiles = alloc<TileRef>(cap_pt);
+      d_etiles = alloc<TileRef>(cap_et);
+      d_projtiles = alloc<TileRef>(cap_proj);
+      d_ids = alloc<int>(cap_n);
+      d_pcgtiles = alloc<TileRef>(cap_pt);
+      d_bar = alloc<GridBar>(1);
+      if (!d_desc || !d_ctl || !d_ttiles || !d_vtiles || !d_btiles || !d_ptiles || !d_etiles ||
+          !d_projtiles || !d_ids || !d_bar || !d_pcgtiles) {
+        set_error("cudaMalloc failed for a scene group");
+        return PPN_ERR_OOM;
+      }
+      PPN_CU(cudaMallocHost(&h_ctl, sizeof(Ctl) * cap_n));
+      PPN_CU(cudaMallocHost(&h_bar, sizeof(GridBar)));
+    }
+    pcg_ids.clear();
+    pcg_ntiles = 0;
+    pcg_smem_bytes = 0;
+    std::memset(h_bar, 0, sizeof(GridBar));
+    PPN_CU(cudaMemset(d_bar, 0, sizeof(GridBar)));
+    PPN_CU(cudaMemcpy(d_ttiles, tt.data(), sizeof(TileRef) * tt.size(), cudaMemcpyHostToDevice));
+    PPN_CU(cudaMemcpy(d_vtiles, vt.data(), sizeof(TileRef) * vt.size(), cudaMemcpyHostToDevice));
+    PPN_CU(cudaMemcpy(d_btiles, bt.data(), sizeof(TileRef) * bt.size(), cudaMemcpyHostToDevice));
+    PPN_CU(cudaMemcpy(d_ptiles, pt.data(), sizeof(TileRef) * pt.size(), cudaMemcpyHostToDevice));
+    PPN_CU(cudaMemcpy(d_etiles, et.data(), sizeof(TileRef) * et.size(), cudaMemcpyHostToDevice));
+    std::vector<Ctl> c0(n);
+    std::memset(c0.data(), 0, sizeof(Ctl) * n);
+    for (auto& c : c0) c.pcg_done = 1;
+    PPN_CU(cudaMemcpy(d_ctl, c0.data(), sizeof(Ctl) * n, cudaMemcpyHostToDevice));
+    for (int i = 0; i < n; ++i) {
+      h_desc[i] = S[i]->d;
+      h_desc[i].ctl = d_ctl + i;
+      h_desc[i].active = 0;
+    }
+    return PPN_OK;
+  }
+  // write the per-step descriptor scalars of the members back to their scenes
+  // (before the group is rebuilt for other members)
+  void stash() {
+    for (size_t i = 0; i < S.size() && i < h_desc.size(); ++i) {
+      S[i]->d.it_id = h_desc[i].it_id;
+      S[i]->d.round_id = h_desc[i].round_id;
+      S[i]->d.delta = h_desc[i].delta;
+      S[i]->d.gamma = h_desc[i].gamma;
+    }
+  }
+  ppn_status upload_desc() {
+    const size_t b = sizeof(SceneDev<T>) * h_desc.size();
+    void* p = staging.take(b, st);
+    if (!p) {
+      set_error("pinned staging allocation failed");
+      return PPN_ERR_OOM;
+    }
+    std::memcpy(p, h_desc.data(), b);
+    PPN_CU(cudaMemcpyAsync(d_desc, p, b, cudaMemcpyHostToDevice, st));
+    return PPN_OK;
+  }
+  ppn_status upload(void* dst, const void* src, size_t b) {
+    void* p = staging.take(b, st);
+    if (!p) {
+      set_error("pinned staging allocation failed");
+      return PPN_ERR_OOM;
+    }
+    std::memcpy(p, src, b);
+    PPN_CU(cudaMemcpyAsync(dst, p, b, cudaMemcpyHostToDevice, st));
+    return PPN_OK;
+  }
+  ppn_status sync_ctl() {
+    PPN_CU(cudaMemcpyAsync(h_ctl, d_ctl, sizeof(Ctl) * S.size(), cudaMemcpyDeviceToHost, st));
+    PPN_CU(cudaMemcpyAsync(h_bar, d_bar, sizeof(GridBar), cudaMemcpyDeviceToHost, st));
+    PPN_CU(cudaStreamSynchronize(st));
+    staging.reset();
+    if (timer) timer->collect();
+    return PPN_OK;
+  }
+  void set_active(const std::vector<char>& on) {
+    for (size_t i = 0; i < S.size(); ++i) h_desc[i].active = on[i] ? 1 : 0;
+  }
+};
+
+// Per-scene host state of the lockstep Newton loop.
+struct HostState {
+  int mode = 0;
+  int status = PPN_OK;
+  bool running = true;
+  int k = 0;
+  double delta = 0, g0 = -1, gn2 = 0, ginf = 0;
+  int n_proj = 0;
+  bool ind = false, fallback = false;
+  int precond_fail = 0, pcg_iters_last = 0;
+  double E0 = 0, dd = 0, dxmax = 0, gamma = 1;
+  int halvings = 0;
+  int countdown = 0;  // PDN: iterations left that assemble projected
+  bool pre = false;   // this iteration projects every element before assembly
+  double tol = 0;     // Newton tolerance of the current step
+  ppn_iter_stats cur{};
+  ppn_step_stats tot{};
+};
+
+template <typename T>
+struct Driver {
+  Group<T>& G;
+  std::vector<HostState> H;
+  explicit Driver(Group<T>& g) : G(g) {}
+  // parameters of scene i (scenes of one batch may differ)
+  const ppn_params& Pi(int i) const { return G.S[i]->params; }
+
+  double pcg_iter_bytes() const {
+    double b = 0;
+    for (auto* s : G.S) b += (double)s->nnzb * (9 * sizeof(T) + 4) + (double)s->nv * (4 + 12 * sizeof(T) + 9 * sizeof(T) + 12 * 4 * sizeof(T));
+    return b;
+  }
+
+  template <typename F>
+  void timed(int fam, double bytes, F&& f) {
+    G.timer->begin(fam, G.st, bytes);
+    f();
+    G.timer->end(G.st);
+  }
+
+  ppn_status check_launch() {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_error(std::string("kernel launch: ") + cudaGetErrorString(e));
+      return PPN_ERR_CUDA;
+    }
+    return PPN_OK;
+  }
+
+  // PCG over the scenes flagged in `on`; results land in each scene's Ctl
+  ppn_status solve(const std::vector<char>& on, int b_from_g) {
+    std::vector<int> ids;
+    for (size_t i = 0; i < on.size(); ++i)
+      if (on[i]) ids.push_back((int)i);
+    if (ids.empty()) return PPN_OK;
+    G.set_active(on);
+    ppn_status rc = G.upload_desc();
+    if (rc) return rc;
+    // slots of at most PCG_MAX_SCENES scenes per launch
+    for (size_t b = 0; b < ids.size(); b += PCG_MAX_SCENES) {
+      const size_t e = std::min(ids.size(), b + PCG_MAX_SCENES);
+      std::vector<int> sl(ids.begin() + b, ids.begin() + e);
+      if (sl != G.pcg_ids) {
+        std::vector<TileRef> tt;
+        for (size_t k = 0; k < sl.size(); ++k)
+          for (int t = 0; t < G.S[sl[k]]->n_ptiles; ++t) tt.push_back({(int)k, t});
+        if ((rc = G.upload(G.d_ids, sl.data(), sizeof(int) * sl.size()))) return rc;
+        if ((rc = G.upload(G.d_pcgtiles, tt.data(), sizeof(TileRef) * tt.size()))) return rc;
+        G.pcg_ids = sl;
+        G.pcg_ntiles = (int)tt.size();
+        plan_smem(sl, tt);
+      }
+      const int n_tiles = G.pcg_ntiles;
+      PcgLaunch L;
+      L.n_tiles = n_tiles;
+      L.tiles = G.d_pcgtiles;
+      L.n_scenes = (int)sl.size();
+      L.scene_ids = G.d_ids;
+      L.bar = G.d_bar;
+      L.grid = G.pcg_smem_bytes ? G.pcg_smem_grid : std::min(G.pcg_grid, n_tiles);
+      L.group = G.pcg_group;
+      L.use_b_from_g = b_from_g;
+      L.smem_bytes = G.pcg_smem_bytes;
+      L.smem_blocks = G.pcg_smem_blocks;
+      L.launch_seq = ++G.pcg_launch_seq;
+      L.n_pword = (int)sl.size();
+      for (size_t k = 0; k < sl.size(); ++k) {
+        L.pword[k] = G.h_desc[sl[k]].pword;
+        L.pword_bytes[k] = sizeof(unsigned long long) * 8 * G.S[sl[k]]->n_ptiles;
+      }
+      double bytes = 0.0;
+      cudaError_t err = cudaSuccess;
+      timed(FAM_PCG, bytes, [&] {
+        err = L.smem_bytes ? launch_pcg_smem<T>(G.d_desc, L, G.st) : launch_pcg<T>(G.d_desc, L, G.st);
+      });
+      if (err != cudaSuccess) {
+        set_error(std::string("PCG launch: ") + cudaGetErrorString(err));
+        return PPN_ERR_CUDA;
+      }
+    }
+    return PPN_OK;
+  }
+
+  // Choose the shared-memory-resident PCG when every CTA's rows fit.
+  void plan_smem(const std::vector<int>& sl, const std::vector<TileRef>& tt) {
+    G.pcg_smem_bytes = 0;
+    if (std::getenv("PPN_PCG_GLOBAL")) return;
+    const int n_tiles = (int)tt.size();
+    const int grid = std::min(G.pcg_grid, n_tiles);
+    int max_items = 0, max_blocks = 0;
+    for (int b = 0; b < grid; ++b) {
+      const int t0 = (int)(((long long)b * n_tiles) / grid), t1 = (int)(((long long)(b + 1) * n_tiles) / grid);
+      int blocks = 0;
+      for (int t = t0; t < t1; ++t) {
+        const SceneImpl<T>& sc = *G.S[sl[tt[t].scene]];
+        const int r0 = tt[t].tile * PCG_TILE, r1 = std::min(sc.nv, r0 + PCG_TILE);
+        if (r1 > r0) blocks += (int)(sc.h_row_ptr[r1] - sc.h_row_ptr[r0]);
+      }
+      max_items = std::max(max_items, (t1 - t0) * PCG_TILE);
+      max_blocks = std::max(max_blocks, blocks);
+    }
+    const size_t bytes = pcg_smem_bytes(max_items, max_blocks, (int)sizeof(T));
+    if (bytes > (size_t)196 * 1024 || grid > 1024) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int mg = pcg_smem_max_grid(G.pcg_group, dev, bytes, (int)sizeof(T));
+    if (mg < grid) return;
+    G.pcg_smem_bytes = bytes;
+    G.pcg_smem_blocks = max_blocks;
+    G.pcg_smem_grid = grid;
+  }
+
+  // Start a time step for the flagged slots (their H[i].mode and H[i].tol set):
+  // predictor, Dirichlet targets, delta = infinity (Algorithm 1, before the Newton loop).
+  ppn_status begin(const std::vector<char>& on) {
+    const int n = (int)G.S.size();
+    for (int i = 0; i < n; ++i) {
+      if (!on[i]) continue;
+      const int mode = H[i].mode;
+      const double tol = H[i].tol;
+      H[i] = HostState();
+      H[i].mode = mode;
+      H[i].tol = tol;
+      H[i].delta = std::numeric_limits<double>::infinity();
+      G.h_desc[i].delta = H[i].delta;
+      G.S[i]->iters.clear();
+      G.S[i]->attempts.clear();
+    }
+    G.set_active(on);
+    ppn_status rc = G.upload_desc();
+    if (rc) return rc;
+    timed(FAM_VECTOR, 0, [&] { launch_predict<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st); });
+    for (int i = 0; i < n; ++i) {
+      if (!on[i]) continue;
+      SceneImpl<T>& s = *G.S[i];
+      const double* tg = s.ext_targets ? s.ext_targets : s.d_targets;
+      launch_apply_targets<T>(G.d_desc, i, s.d_fixed_list, tg, s.nfixed, 0, G.st);
+      s.ext_targets = nullptr;
+    }
+    return check_launch();
+  }
+
+  bool any_running() const {
+    for (const HostState& h : H)
+      if (h.running) return true;
+    return false;
+  }
+
+  // One Newton iteration of every running slot (lockstep over the group).
+  ppn_status tick() {
+    const int n = (int)G.S.size();
+    ppn_status rc = PPN_OK;
+    std::vector<char> run(n, 0);
+    bool any = false;
+    for (int i = 0; i < n; ++i) {
+      run[i] = H[i].running;
+      any |= H[i].running;
+    }
+    if (!any) return PPN_OK;
+    // ---- element evaluation and gradient
+    for (int i = 0; i < n; ++i)
+      if (run[i]) {
+        G.h_desc[i].it_id = ++G.S[i]->it_counter;
+        G.h_desc[i].gamma = 0.0;
+      }
+    G.set_active(run);
+    if ((rc = G.upload_desc())) return rc;
+    timed(FAM_ELEMENT, 0, [&] { launch_element<T>(G.d_desc, G.d_ttiles, G.n_ttiles, 0, G.st); });
+    timed(FAM_GRADIENT, 0, [&] { launch_gradient<T>(G.d_desc, G.d_vtiles, G.n_vtiles, 0, G.st); });
+    if ((rc = check_launch())) return rc;
+    if ((rc = G.sync_ctl())) return rc;
+    std::vector<char> solve_on(n, 0), pn_on(n, 0);
+    bool any_solve = false, any_pn = false;
+    for (int i = 0; i < n; ++i) {
+      if (!run[i]) continue;
+      HostState& h = H[i];
+      const Ctl& c = G.h_ctl[i];
+      h.gn2 = std::sqrt(c.grad[0]);
+      h.ginf = c.grad[1];
+      h.tot.final_grad_norm2 = h.gn2;
+      if (!std::isfinite(h.gn2)) {
+        h.status = PPN_ERR_NONFINITE;
+        h.running = false;
+        continue;
+      }
+      if (h.k == 0) h.g0 = h.gn2;
+      if (Pi(i).tol_kind == 0 && h.gn2 <= h.tol * h.g0) {
+        h.status = PPN_OK;
+        h.running = false;
+        continue;
+      }
+      if (h.k >= Pi(i).newton_max_iter) {
+        h.status = PPN_ERR_NEWTON_MAXITER;
+        h.running = false;
+        continue;
+      }
+      h.cur = ppn_iter_stats{};
+      h.cur.newton_iter = h.k;
+      h.cur.grad_norm2 = h.gn2;
+      h.cur.grad_norminf = h.ginf;
+      h.n_proj = 0;
+      h.fallback = false;
+      solve_on[i] = 1;
+      any_solve = true;
+      h.pre = h.mode == PPN_MODE_PN || (h.mode == PPN_MODE_PDN && h.countdown > 0);
+      if (h.pre) {
+        pn_on[i] = 1;
+        any_pn = true;
+        if (h.mode == PPN_MODE_PDN) --h.countdown;
+      }
+    }
+    if (!any_solve) return PPN_OK;
+    // ---- PN: select every element and clamp before assembly
+    if (any_pn) {
+      for (int i = 0; i < n; ++i)
+        if (pn_on[i]) G.h_desc[i].delta = -1.0;
+      if ((rc = select_and_project(pn_on, true))) return rc;
+      for (int i = 0; i < n; ++i)
+        if (pn_on[i]) H[i].n_proj = G.S[i]->nt;
+    }
+    // ---- assembly and first solve
+    G.set_active(solve_on);
+    if ((rc = G.upload_desc())) return rc;
+    timed(FAM_ASSEMBLE, 0, [&] { launch_assemble<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st); });
+    if ((rc = check_launch())) return rc;
+    if ((rc = solve(solve_on, 1))) return rc;
+    if ((rc = G.sync_ctl())) return rc;
+    if ((rc = check_errors(solve_on))) return rc;
+    std::vector<char> retry(n, 0), pdn(n, 0);
+    bool any_retry = false, any_pdn = false;
+    for (int i = 0; i < n; ++i) {
+      if (!solve_on[i]) continue;
+      record_attempt(i, 0, H[i].pre ? G.S[i]->nt : 0, std::numeric_limits<double>::infinity());
+      if (H[i].ind && H[i].mode == PPN_MODE_PPN) {
+        retry[i] = 1;
+        any_retry = true;
+      } else if (H[i].ind && H[i].mode == PPN_MODE_PDN && !H[i].pre) {
+        pdn[i] = 1;
+        any_pdn = true;
+      } else if (H[i].ind) {
+        H[i].fallback = true;
+      }
+    }
+    // ---- PDN: indefinite, so project every element in place and solve again
+    if (any_pdn) {
+      for (int i = 0; i < n; ++i)
+        if (pdn[i]) {
+          G.h_desc[i].delta = -1.0;  // select every element not yet projected
+          G.h_desc[i].round_id = ++G.S[i]->round_counter;
+        }
+      if ((rc = select_and_project(pdn, false))) return rc;
+      G.set_active(pdn);
+      if ((rc = G.upload_desc())) return rc;
+      timed(FAM_UPDATE, 0, [&] { launch_update<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st); });
+      if ((rc = check_launch())) return rc;
+      if ((rc = solve(pdn, 1))) return rc;
+      if ((rc = G.sync_ctl())) return rc;
+      if ((rc = check_errors(pdn))) return rc;
+      for (int i = 0; i < n; ++i)
+        if (pdn[i]) {
+          record_attempt(i, 1, G.S[i]->nt, -1.0);
+          H[i].countdown = Pi(i).pdn_countdown;
+          if (H[i].ind) H[i].fallback = true;  // fully projected and still indefinite (rounding)
+        }
+    }
+    // ---- PPN retries (Algorithm 1 inner loop)
+    int attempt = 1;
+    while (any_retry) {
+      for (int i = 0; i < n; ++i)
+        if (retry[i]) {
+          HostState& h = H[i];
+          if (std::isinf(h.delta)) h.delta = Pi(i).alpha * h.ginf;
+          G.h_desc[i].delta = h.delta;
+          G.h_desc[i].round_id = ++G.S[i]->round_counter;
+        }
+      if ((rc = select_and_project(retry, false))) return rc;
+      std::vector<char> resolve(n, 0);
+      bool any_resolve = false;
+      for (int i = 0; i < n; ++i)
+        if (retry[i] && G.h_ctl[i].n_new > 0) {
+          resolve[i] = 1;
+          any_resolve = true;
+        }
+      if (any_resolve) {
+        G.set_active(resolve);
+        if ((rc = G.upload_desc())) return rc;
+        timed(FAM_UPDATE, 0, [&] { launch_update<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st); });
+        if ((rc = check_launch())) return rc;
+        if ((rc = solve(resolve, 1))) return rc;
+        std::vector<int> n_new(n);
+        for (int i = 0; i < n; ++i) n_new[i] = G.h_ctl[i].n_new;
+        if ((rc = G.sync_ctl())) return rc;
+        if ((rc = check_errors(resolve))) return rc;
+        for (int i = 0; i < n; ++i)
+          if (resolve[i]) record_attempt(i, attempt, n_new[i], H[i].delta);
+      }
+      any_retry = false;
+      for (int i = 0; i < n; ++i) {
+        if (!retry[i]) continue;
+        HostState& h = H[i];
+        if (h.ind) {
+          if (h.n_proj >= G.S[i]->nt) {
+            h.fallback = true;  // fully projected and still indefinite (rounding)
+            retry[i] = 0;
+          } else {
+            h.delta *= Pi(i).alpha;  // tighten
+            any_retry = true;
+          }
+        } else {
+          retry[i] = 0;
+        }
+      }
+      ++attempt;
+    }
+    for (int i = 0; i < n; ++i)
+      if (solve_on[i] && H[i].mode == PPN_MODE_PPN) H[i].delta *= Pi(i).beta;  // relax
+    // ---- fallback directions when the solve gave no usable iterate
+    {
+      std::vector<char> fb2(n, 0), fb3(n, 0);
+      bool a2 = false, a3 = false;
+      for (int i = 0; i < n; ++i) {
+        if (!solve_on[i] || !H[i].fallback) continue;
+        if (H[i].pcg_iters_last == 0) {
+          if (H[i].precond_fail) {
+            fb3[i] = 1;
+            a3 = true;
+            H[i].cur.fallback = 3;
+          } else {
+            fb2[i] = 1;
+            a2 = true;
+            H[i].cur.fallback = 2;
+          }
+        } else {
+          H[i].cur.fallback = 1;
+        }
+      }
+      if (a2 && (rc = fallback_dir(fb2, 2))) return rc;
+      if (a3 && (rc = fallback_dir(fb3, 3))) return rc;
+    }
+    // ---- energy at gamma = 0 and directional derivative
+    if ((rc = energy(solve_on, true))) return rc;
+    {
+      std::vector<char> fb(n, 0);
+      bool afb = false;
+      int kind = 2;
+      for (int i = 0; i < n; ++i) {
+        if (!solve_on[i]) continue;
+        HostState& h = H[i];
+        if (!(h.dd < 0.0)) {
+          fb[i] = 1;
+          afb = true;
+          h.cur.fallback = h.precond_fail ? 3 : 2;
+          kind = h.cur.fallback;
+        }
+      }
+      if (afb) {
+        // rare: scenes needing the fallback are handled one kind at a time
+        for (int kd = 2; kd <= 3; ++kd) {
+          std::vector<char> sel(n, 0);
+          bool a = false;
+          for (int i = 0; i < n; ++i)
+            if (fb[i] && H[i].cur.fallback == kd) {
+              sel[i] = 1;
+              a = true;
+            }
+          if (a && (rc = fallback_dir(sel, kd))) return rc;
+        }
+        (void)kind;
+        if ((rc = energy(fb, true))) return rc;
+      }
+    }
+    // ---- backtracking line search (Armijo)
+    std::vector<char> ls(n, 0);
+    bool any_ls = false;
+    for (int i = 0; i < n; ++i)
+      if (solve_on[i]) {
+        ls[i] = 1;
+        any_ls = true;
+        H[i].gamma = 1.0;
+        H[i].halvings = 0;
+        H[i].cur.dir_deriv = H[i].dd;
+        H[i].cur.energy = H[i].E0;
+      }
+    std::vector<char> accept(n, 0);
+    while (any_ls) {
+      for (int i = 0; i < n; ++i)
+        if (ls[i]) G.h_desc[i].gamma = H[i].gamma;
+      if ((rc = energy(ls, false))) return rc;
+      any_ls = false;
+      for (int i = 0; i < n; ++i) {
+        if (!ls[i]) continue;
+        HostState& h = H[i];
+        const double Et = G.h_ctl[i].energy[0];
+        if (Et <= h.E0 + Pi(i).armijo_c * h.gamma * h.dd) {
+          ls[i] = 0;
+          accept[i] = 1;
+          h.cur.gamma = h.gamma;
+          h.cur.energy_new = Et;
+          h.cur.ls_halvings = h.halvings;
+        } else if (h.halvings >= Pi(i).ls_max_halvings) {
+          ls[i] = 0;
+          h.status = PPN_ERR_LINESEARCH;
+          h.running = false;
+          h.cur.ls_halvings = h.halvings;
+          finish_iter(i);
+        } else {
+          h.gamma *= 0.5;
+          h.halvings += 1;
+          any_ls = true;
+        }
+      }
+    }
+    // ---- position update
+    bool any_acc = false;
+    for (int i = 0; i < n; ++i) any_acc |= accept[i];
+    if (any_acc) {
+      for (int i = 0; i < n; ++i)
+        if (accept[i]) G.h_desc[i].gamma = H[i].gamma;
+      G.set_active(accept);
+      if ((rc = G.upload_desc())) return rc;
+      timed(FAM_VECTOR, 0, [&] { launch_axpy_u<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st); });
+      if ((rc = check_launch())) return rc;
+    }
+    for (int i = 0; i < n; ++i) {
+      if (!accept[i]) continue;
+      HostState& h = H[i];
+      finish_iter(i);
+      h.k += 1;
+      if (Pi(i).tol_kind == 1 && h.gamma * h.dxmax / G.S[i]->dt < h.tol) {
+        h.status = PPN_OK;
+        h.running = false;
+      }
+    }
+    return PPN_OK;
+  }
+
+  // End the time step of the flagged slots: velocities and step statistics.
+  ppn_status finish(const std::vector<char>& on) {
+    const int n = (int)G.S.size();
+    G.set_active(on);
+    ppn_status rc = G.upload_desc();
+    if (rc) return rc;
+    timed(FAM_VECTOR, 0, [&] { launch_velocity<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st); });
+    if ((rc = check_launch())) return rc;
+    for (int i = 0; i < n; ++i) {
+      if (!on[i]) continue;
+      H[i].tot.status = H[i].status;
+      H[i].tot.newton_iters = (int)G.S[i]->iters.size();
+      // keep the scene's own descriptor scalars in step with the group copy
+      G.S[i]->d.it_id = G.h_desc[i].it_id;
+      G.S[i]->d.round_id = G.h_desc[i].round_id;
+    }
+    return PPN_OK;
+  }
+
+  // One time step of every scene of the group (all start and end together).
+  ppn_status step(const int* modes, double tol) {
+    const int n = (int)G.S.size();
+    H.assign(n, HostState());
+    std::vector<char> on(n, 1);
+    for (int i = 0; i < n; ++i) {
+      H[i].mode = modes[i];
+      H[i].tol = tol;
+    }
+    cudaEventRecord(G.S[0]->ev_a, G.st);
+    ppn_status rc = begin(on);
+    if (rc) return rc;
+    while (any_running())
+      if ((rc = tick())) return rc;
+    if ((rc = finish(on))) return rc;
+    cudaEventRecord(G.S[0]->ev_b, G.st);
+    PPN_CU(cudaStreamSynchronize(G.st));
+    G.staging.reset();
+    G.timer->collect();
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, G.S[0]->ev_a, G.S[0]->ev_b);
+    for (int i = 0; i < n; ++i) H[i].tot.device_ms = ms;
+    return PPN_OK;
+  }
+
+  void finish_iter(int i) {
+    HostState& h = H[i];
+    h.cur.n_projected_total = h.n_proj;
+    h.cur.delta = h.delta;
+    h.cur.precond_fail = h.precond_fail;
+    G.S[i]->iters.push_back(h.cur);
+    h.tot.total_projections += h.n_proj;
+    h.tot.total_cg_iters += h.cur.cg_iters;
+    h.tot.total_attempts += h.cur.pcg_attempts;
+  }
+
+  void record_attempt(int i, int attempt, int n_new, double delta) {
+    HostState& h = H[i];
+    const Ctl& c = G.h_ctl[i];
+    h.ind = c.pcg_ind != 0;
+    h.precond_fail = c.pcg_precond_fail;
+    h.pcg_iters_last = c.pcg_iters;
+    h.cur.pcg_attempts += 1;
+    h.cur.cg_iters += c.pcg_iters;
+    ppn_attempt a;
+    a.newton_iter = h.k;
+    a.attempt = attempt;
+    a.n_new_projected = n_new;
+    a.ind = h.ind;
+    a.cg_iters = c.pcg_iters;
+    a.delta = delta;
+    G.S[i]->attempts.push_back(a);
+  }
+
+  ppn_status check_errors(const std::vector<char>& on) {
+    for (size_t i = 0; i < on.size(); ++i) {
+      if (!on[i]) continue;
+      if (G.h_ctl[i].error & kErrTimeout) {
+        set_error("PCG grid barrier timed out");
+        return PPN_ERR_TIMEOUT;
+      }
+    }
+    if (G.h_bar->timeout) {
+      set_error("PCG grid barrier timed out");
+      return PPN_ERR_TIMEOUT;
+    }
+    return PPN_OK;
+  }
+
+  // selection (delta in the descriptor; < 0 selects all) + clamping of the
+  // newly selected elements.  pn: no host sync needed for the count.
+  ppn_status select_and_project(const std::vector<char>& on, bool pn) {
+    const int n = (int)on.size();
+    G.set_active(on);
+    ppn_status rc = G.upload_desc();
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i)
+      if (on[i]) PPN_CU(cudaMemsetAsync(&G.d_ctl[i].n_new, 0, sizeof(int), G.st));
+    timed(FAM_SELECT, 0, [&] { launch_select<T>(G.d_desc, G.d_ttiles, G.n_ttiles, G.st); });
+    if ((rc = check_launch())) return rc;
+    std::vector<TileRef> jt;
+    if (pn) {
+      for (int i = 0; i < n; ++i)
+        if (on[i])
+          for (int t = 0; t < (G.S[i]->nt + PROJ_CTA - 1) / PROJ_CTA; ++t) jt.push_back({i, t});
+    } else {
+      if ((rc = G.sync_ctl())) return rc;
+      for (int i = 0; i < n; ++i)
+        if (on[i]) {
+          const int nn = G.h_ctl[i].n_new;
+          H[i].n_proj += nn;
+          H[i].cur.n_new_projected += nn;
+          for (int t = 0; t < (nn + PROJ_CTA - 1) / PROJ_CTA; ++t) jt.push_back({i, t});
+        }
+    }
+    if (jt.empty()) return PPN_OK;
+    if ((rc = G.upload(G.d_projtiles, jt.data(), sizeof(TileRef) * jt.size()))) return rc;
+    timed(FAM_PROJECT, 0, [&] { launch_project<T>(G.d_desc, G.d_projtiles, (int)jt.size(), 0, G.st); });
+    return check_launch();
+  }
+
+  ppn_status fallback_dir(const std::vector<char>& on, int kind) {
+    G.set_active(on);
+    ppn_status rc = G.upload_desc();
+    if (rc) return rc;
+    timed(FAM_VECTOR, 0, [&] { launch_fallback<T>(G.d_desc, G.d_vtiles, G.n_vtiles, kind, G.st); });
+    return check_launch();
+  }
+
+  // energy at u + gamma dx for the flagged scenes; at_zero also records E0, g^T dx, max|dx|
+  ppn_status energy(const std::vector<char>& on, bool at_zero) {
+    const int n = (int)on.size();
+    if (at_zero)
+      for (int i = 0; i < n; ++i)
+        if (on[i]) G.h_desc[i].gamma = 0.0;
+    G.set_active(on);
+    ppn_status rc = G.upload_desc();
+    if (rc) return rc;
+    timed(FAM_ENERGY, 0, [&] { launch_energy<T>(G.d_desc, G.d_etiles, G.n_etiles, 0, G.st); });
+    if ((rc = check_launch())) return rc;
+    if ((rc = G.sync_ctl())) return rc;
+    if (at_zero)
+      for (int i = 0; i < n; ++i)
+        if (on[i]) {
+          H[i].E0 = G.h_ctl[i].energy[0];
+          H[i].dd = G.h_ctl[i].energy[1];
+          H[i].dxmax = G.h_ctl[i].energy[2];
+        }
+    return PPN_OK;
+  }
+};
+
+// ------------------------------------------------------------------ group cache
+
+// positions x = X + u into a host buffer
+template <typename T>
+__global__ void k_positions(const double4* X, const double4* u, double* xyz, int nv) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  const double4 a = ld_d4(X + v), b = ld_d4(u + v);
+  xyz[3 * v] = a.x + b.x;
+  xyz[3 * v + 1] = a.y + b.y;
+  xyz[3 * v + 2] = a.z + b.z;
+}
+
+template <typename T>
+__global__ void k_vel_out(const double4* w, double* xyz, int nv) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  const double4 a = ld_d4(w + v);
+  xyz[3 * v] = a.x;
+  xyz[3 * v + 1] = a.y;
+  xyz[3 * v + 2] = a.z;
+}
+
+template <typename T>
+inline ppn_status read_positions(SceneImpl<T>& s, double* out) {
+  k_positions<T><<<(s.nv + 255) / 256, 256, 0, s.stream>>>(s.d.X, s.d.u, s.d_xyz, s.nv);
+  PPN_CU(cudaGetLastError());
+  PPN_CU(cudaMemcpyAsync(out, s.d_xyz, sizeof(double) * 3 * s.nv, cudaMemcpyDeviceToHost, s.stream));
+  PPN_CU(cudaStreamSynchronize(s.stream));
+  return PPN_OK;
+}
+
+}  // namespace ppn

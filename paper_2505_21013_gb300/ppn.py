@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libppn.so")
 
 PPN_OK = 0
+PPN_ERR_ADMISSION = 10
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "DEGENERATE_TET", 5: "LINESEARCH",
                 6: "NEWTON_MAXITER", 7: "PCG_MAXITER", 8: "NONFINITE", 9: "TIMEOUT", 10: "ADMISSION"}
 MODE_NEWTON, MODE_PN, MODE_PPN, MODE_PDN = 0, 1, 2, 3
@@ -52,6 +53,21 @@ class ppn_step_stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("total_projections", C.c_int), ("total_cg_iters", C.c_int),
                 ("total_attempts", C.c_int), ("status", C.c_int), ("final_grad_norm2", C.c_double),
                 ("device_ms", C.c_double)]
+
+
+class ppn_server_config(C.Structure):
+    _fields_ = [("hbm_fraction", C.c_double), ("max_batch", C.c_int), ("precision", C.c_int)]
+
+
+class ppn_request_times(C.Structure):
+    _fields_ = [("t_submit_ms", C.c_double), ("t_start_ms", C.c_double), ("t_done_ms", C.c_double),
+                ("batch_max", C.c_int)]
+
+
+class ppn_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected_scenes", C.c_int64),
+                ("resident_scenes", C.c_int), ("resident_bytes", C.c_double), ("budget_bytes", C.c_double),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("steps_per_s", C.c_double)]
 
 
 class ppn_scene_info(C.Structure):
@@ -101,6 +117,16 @@ SIGNATURES = {
     "ppn_probe_select": (_st, [_P, _pd, C.c_double, _pu, _pu, _pl]),
     "ppn_probe_project": (_st, [_P, _pd, _pi, C.c_int64, _pd]),
     "ppn_probe_pcg": (_st, [_P, _pd, _pd, C.c_double, C.c_int, _pd, C.POINTER(C.c_int)]),
+    "ppn_server_default_config": (ppn_server_config, []),
+    "ppn_server_create": (_st, [C.POINTER(ppn_server_config), C.POINTER(_P)]),
+    "ppn_server_destroy": (None, [_P]),
+    "ppn_server_add_scene": (_st, [_P, _pd, C.c_int64, _pi, C.c_int64, C.POINTER(ppn_material), C.c_double, _pi,
+                                   C.c_int64, C.POINTER(ppn_params), _pi]),
+    "ppn_server_remove_scene": (_st, [_P, C.c_int32]),
+    "ppn_server_submit": (_st, [_P, C.c_int32, C.c_int, C.c_double, _pd, _pl]),
+    "ppn_server_poll": (_st, [_P, C.c_int64, C.c_int, C.POINTER(C.c_int), _pd, C.POINTER(ppn_step_stats),
+                              C.POINTER(ppn_request_times)]),
+    "ppn_server_get_stats": (_st, [_P, C.POINTER(ppn_server_stats)]),
     "ppn_pcg_solve_static": (_st, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                    C.c_void_p, C.c_double, C.c_int32, C.POINTER(C.c_int32), C.c_void_p]),
 }
@@ -357,3 +383,77 @@ def pcg_solve_static(row_ptr: int, col: int, val: int, n_rows: int, nnzb: int, b
                                       int(nnzb), C.c_void_p(b), C.c_void_p(x), float(rel_tol), int(max_iter),
                                       info, C.c_void_p(stream or None)), "ppn_pcg_solve_static")
     return {"iters": info[0], "ind": bool(info[1]), "precond_fail": bool(info[2]), "hit_max": bool(info[3])}
+
+
+class Server:
+    """Serving loop over resident scenes (``ppn_server_*`` in include/ppn.h):
+    scenes admitted by HBM footprint, one request = one time step, continuous
+    batching of the running requests on the device."""
+
+    def __init__(self, hbm_fraction=0.8, max_batch=64, precision=PREC_MIXED):
+        cfg = lib().ppn_server_default_config()
+        cfg.hbm_fraction = hbm_fraction
+        cfg.max_batch = max_batch
+        cfg.precision = precision
+        h = _P()
+        _check(lib().ppn_server_create(C.byref(cfg), C.byref(h)), "ppn_server_create")
+        self._h = h
+        self.precision = precision
+        self.n_verts = {}
+        self.n_fixed = {}
+
+    def add_scene(self, spec, params: ppn_params | None = None) -> int:
+        p = params if params is not None else ppn_default_params()
+        p.precision = self.precision
+        p.gravity[0], p.gravity[1], p.gravity[2] = spec.gravity
+        rest = _arr(spec.rest, np.float64)
+        tets = _arr(spec.tets, np.int32)
+        fixed = _arr(spec.fixed, np.int32)
+        mat = ppn_material(spec.E, spec.nu, spec.rho)
+        sid = C.c_int32()
+        _check(lib().ppn_server_add_scene(self._h, _d(rest), rest.shape[0], tets.ctypes.data_as(_pi), tets.shape[0],
+                                          C.byref(mat), spec.dt, fixed.ctypes.data_as(_pi), fixed.shape[0],
+                                          C.byref(p), C.byref(sid)), "ppn_server_add_scene")
+        self.n_verts[sid.value] = rest.shape[0]
+        self.n_fixed[sid.value] = fixed.shape[0]
+        return sid.value
+
+    def remove_scene(self, sid: int):
+        _check(lib().ppn_server_remove_scene(self._h, int(sid)), "ppn_server_remove_scene")
+        self.n_verts.pop(sid, None)
+
+    def submit(self, sid: int, mode: int, tol: float, targets=None) -> int:
+        t = C.c_int64()
+        tg = None if targets is None else _arr(targets, np.float64)
+        _check(lib().ppn_server_submit(self._h, int(sid), int(mode), float(tol), _d(tg) if tg is not None else None,
+                                       C.byref(t)), "ppn_server_submit")
+        return t.value
+
+    def poll(self, ticket: int, sid: int, wait: bool = True):
+        """(done, status, positions, stats, times); positions/stats/times are None until done."""
+        done = C.c_int()
+        x = np.zeros((self.n_verts[sid], 3))
+        st = ppn_step_stats()
+        tm = ppn_request_times()
+        rc = lib().ppn_server_poll(self._h, int(ticket), 1 if wait else 0, C.byref(done), _d(x), C.byref(st),
+                                   C.byref(tm))
+        if not done.value:
+            _check(rc, "ppn_server_poll")
+            return False, rc, None, None, None
+        return True, rc, x, struct_dict(st), struct_dict(tm)
+
+    def stats(self) -> dict:
+        s = ppn_server_stats()
+        _check(lib().ppn_server_get_stats(self._h, C.byref(s)), "ppn_server_get_stats")
+        return struct_dict(s)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ppn_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
