@@ -104,6 +104,25 @@ void gradient_from(const ora_scene* s, const double* x, const double* xhat,
       for (int k = 0; k < 3; ++k) g[3 * v + k] = 0.0;
 }
 
+// ||s||_2 with s_v = m_v |x_v - xhat_v| / dt^2 + sum_e |g^e_v| (component-wise, free
+// vertices): the size of the terms whose sum is the residual g.  Rounding in that
+// sum is a few ulps of s, so the relative test ||g|| <= tol ||g0|| cannot be met
+// once ||g0|| itself is at that level (a scene already at rest).
+double residual_scale(const ora_scene* s, const double* x, const double* xhat, const std::vector<double>& ge) {
+  const double w = 1.0 / (s->dt * s->dt);
+  std::vector<double> a((size_t)3 * s->nv);
+  for (int64_t v = 0; v < s->nv; ++v)
+    for (int k = 0; k < 3; ++k) a[3 * v + k] = w * s->mass[v] * std::fabs(x[3 * v + k] - xhat[3 * v + k]);
+  for (int64_t e = 0; e < s->nt; ++e)
+    for (int i = 0; i < 4; ++i)
+      for (int k = 0; k < 3; ++k) a[3 * (int64_t)s->tets[4 * e + i] + k] += std::fabs(ge[12 * e + 3 * i + k]);
+  double n2 = 0.0;
+  for (int64_t v = 0; v < s->nv; ++v)
+    if (!s->fixed[v])
+      for (int k = 0; k < 3; ++k) n2 += a[3 * v + k] * a[3 * v + k];
+  return std::sqrt(n2);
+}
+
 int64_t find_block(const ora_scene* s, int32_t i, int32_t j) {
   for (int64_t k = s->row_ptr[i]; k < s->row_ptr[i + 1]; ++k)
     if (s->col[k] == j) return k;
@@ -209,6 +228,8 @@ ora_params ora_default_params(void) {
   p.init_guess = 0;
   p.pdn_countdown = 4;
   p.projection = ORA_PROJ_CLAMP;
+  p.grad_floor = 1e-12;
+  p.ls_slack = 1e-12;
   return p;
 }
 
@@ -436,7 +457,8 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
       break;
     }
     if (k == 0) g0 = gn2;
-    if (p.tol_kind == 0 && gn2 <= tol * g0) {
+    const double floor = p.grad_floor * residual_scale(s, x.data(), xhat.data(), ge);
+    if (p.tol_kind == 0 && (gn2 <= tol * g0 || gn2 <= floor)) {
       status = ORA_OK;
       break;
     }
@@ -552,7 +574,9 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
     for (int h = 0; h <= p.ls_max_halvings; ++h) {
       for (int64_t i = 0; i < N; ++i) xt[i] = x[i] + gamma * dx[i];
       Et = energy(s, xt.data(), xhat.data());
-      if (Et <= E0 + p.armijo_c * gamma * dd) {
+      // the FP64 sums resolve E only to a few ulps: a slack of ls_slack |E0| keeps a
+      // step whose predicted decrease is below that resolution from being rejected
+      if (Et <= E0 + p.armijo_c * gamma * dd + p.ls_slack * std::fabs(E0)) {
         ok = true;
         st.ls_halvings = h;
         break;

@@ -23,7 +23,8 @@ class Params(C.Structure):
                 ("eig_eps", C.c_double), ("pcg_rel_tol", C.c_double), ("armijo_c", C.c_double),
                 ("pcg_max_iter", C.c_int), ("newton_max_iter", C.c_int),
                 ("ls_max_halvings", C.c_int), ("tol_kind", C.c_int), ("init_guess", C.c_int),
-                ("pdn_countdown", C.c_int), ("projection", C.c_int)]
+                ("pdn_countdown", C.c_int), ("projection", C.c_int), ("grad_floor", C.c_double),
+                ("ls_slack", C.c_double)]
 
 
 class IterStats(C.Structure):

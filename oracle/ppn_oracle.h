@@ -74,6 +74,8 @@ typedef struct {
   int init_guess;      /* 0: x_n ; 1: x_n + dt v_n (free vertices) */
   int pdn_countdown;   /* PDN: iterations that stay projected after an indefinite solve, default 4 */
   int projection;      /* ORA_PROJ_CLAMP: max(lambda, eps); ORA_PROJ_MIRROR: max(|lambda|, eps) */
+  double grad_floor;   /* tol_kind 0 also stops at ||g||_2 <= grad_floor ||s||_2 (rounding floor), default 1e-12 */
+  double ls_slack;     /* Armijo test allows ls_slack |E0| of energy rounding, default 1e-12 */
 } ora_params;
 
 typedef struct {

@@ -240,3 +240,35 @@ def test_checkpoint_resume_is_bitwise():
     _, xa, _ = sc.step(O.PPN, 1e-6)
     _, xb, _ = sc2.step(O.PPN, 1e-6)
     assert np.array_equal(xa, xb)
+
+
+def test_scene_at_rest_stops_at_the_rounding_floor():
+    # A stiff cube settles on its fixed face.  Near rest the energy differences of a
+    # Newton step fall below the FP64 resolution of the energy sum, which the Armijo
+    # slack absorbs, and once at rest g(x_n) is rounding noise, so only the floor
+    # ||g|| <= 1e-12 ||s|| can end the Newton loop.
+    spec = cube_scene(4, E=2e6, nu=0.4, dt=1 / 30, seed=0)
+    sc = O.Scene.from_spec(spec)
+    for n in range(60):
+        sc.set_targets(spec.targets_at(n))
+        rc, _, st = sc.step(O.PPN, 1e-4)
+        assert rc == 0 and st["newton_iters"] <= 2
+    assert st["newton_iters"] == 0  # already at rest: converged before any solve
+    x_rest, v_rest = sc.get_state()
+    # without the floor the relative test alone cannot stop, and without the slack
+    # the line search cannot certify the tiny decrease
+    p = O.default_params()
+    p.grad_floor = 0.0
+    p.newton_max_iter = 6
+    sc.set_params(p)
+    sc.set_targets(spec.targets_at(60))
+    rc, _, st = sc.step(O.PPN, 1e-4)
+    assert rc == 4 and st["newton_iters"] == 6
+    p = O.default_params()
+    p.ls_slack = 0.0
+    p.grad_floor = 0.0
+    p.newton_max_iter = 20
+    sc.set_params(p)
+    sc.set_state(x_rest, v_rest)
+    rc, _, _ = sc.step(O.PPN, 1e-4)
+    assert rc in (3, 4)
