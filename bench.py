@@ -323,6 +323,87 @@ def profile_pcg(iters, repeats=4):
     print(json.dumps({"profile_pcg": out, "source_sha256_16": pcg_source_hash(), "nnzb": nnzb}))
 
 
+def run_batched(n_scenes=64, steps=3, warmup=1, seed=0, tol=1e-4):
+    """Batched workload: n independent cube/beam scenes (tet counts log-uniform in
+    1k-50k, E log-uniform 1e4-1e7, nu in 0.3-0.48, dt in {1/30, 1/60, 1/120})
+    advancing together, one launch per phase over all of them (ppn_step_batch).
+    Returns scene-steps/s per mode, wall-clock around each batched step."""
+    import paper_2505_21013_gb300 as P
+    from ppn_inputs import random_batch_scenes
+
+    specs = random_batch_scenes(n_scenes, seed=seed)
+    out = {"n_scenes": n_scenes, "tets_total": int(sum(s.n_tets for s in specs)), "steps": steps}
+    for name, mode in (("ppn", P.MODE_PPN), ("pn", P.MODE_PN)):
+        scs = [P.Scene.from_spec(s, precision=P.PREC_MIXED) for s in specs]
+        lat, newton, proj, capped = [], 0, 0, 0
+        for n in range(warmup + steps):
+            for sc, spec in zip(scs, specs):
+                sc.set_targets(spec.targets_at(n))
+            t0 = time.perf_counter()
+            rc, st = P.ppn_step_batch(scs, [mode] * n_scenes, tol)
+            dt = time.perf_counter() - t0
+            if rc not in (0, P.ppn.PPN_ERR_NEWTON_MAXITER):
+                raise RuntimeError(f"batched step {n} returned status {rc}")
+            if n >= warmup:
+                lat.append(dt * 1e3)
+                newton += sum(x["newton_iters"] for x in st)
+                proj += sum(x["total_projections"] for x in st)
+                capped += sum(x["status"] == P.ppn.PPN_ERR_NEWTON_MAXITER for x in st)
+        for sc in scs:
+            sc.close()
+        out[name] = {"scene_steps_per_s": n_scenes * steps / (sum(lat) / 1e3), "ms_per_batched_step": sum(lat) / steps,
+                     "newton_iters": newton, "projections": proj, "steps_at_newton_cap": capped}
+    out["speedup_ppn_vs_pn"] = out["ppn"]["scene_steps_per_s"] / out["pn"]["scene_steps_per_s"]
+    return out
+
+
+def run_serving(n_scenes=32, n_req=600, rate_hz=500.0, seed=1, tol=1e-4, max_batch=64):
+    """Request-stream workload: resident scenes of 2k-200k tets (log-uniform),
+    Poisson arrivals at rate_hz, each request one time step of a uniformly
+    random scene, served with continuous batching (ppn_server_*).  Reports
+    completed steps/s and p50/p99 latency (submit to result) per mode."""
+    import numpy as np
+
+    import paper_2505_21013_gb300 as P
+    from ppn_inputs import poisson_arrivals, serving_scenes
+
+    specs = serving_scenes(n_scenes, seed=seed)
+    arrivals = poisson_arrivals(rate_hz, n_req, seed=seed)
+    which = np.random.default_rng(seed).integers(0, n_scenes, size=n_req)
+    out = {"n_scenes": n_scenes, "tets_total": int(sum(s.n_tets for s in specs)), "requests": n_req,
+           "rate_hz": rate_hz}
+    for name, mode in (("ppn", P.MODE_PPN), ("pn", P.MODE_PN)):
+        srv = P.Server(precision=P.PREC_MIXED, max_batch=max_batch)
+        ids = [srv.add_scene(s) for s in specs]
+        step_no = [0] * n_scenes
+        tickets = []
+        t0 = time.perf_counter()
+        for a, k in zip(arrivals, which):
+            now = time.perf_counter() - t0
+            if a > now:
+                time.sleep(a - now)
+            k = int(k)
+            tickets.append((ids[k], srv.submit(ids[k], mode, tol, specs[k].targets_at(step_no[k]))))
+            step_no[k] += 1
+        batch, capped = [], {}
+        for sid, t in tickets:
+            done, rc, _, stt, tm = srv.poll(t, sid)
+            if rc not in (0, P.ppn.PPN_ERR_NEWTON_MAXITER):
+                raise RuntimeError(f"serving request failed with status {rc}")
+            if rc:
+                k = ids.index(sid)
+                capped[specs[k].name] = {"tets": specs[k].n_tets, "E": specs[k].E, "nu": specs[k].nu,
+                                         "dt": specs[k].dt, "grad_norm2": stt["final_grad_norm2"]}
+            batch.append(tm["batch_max"])
+        st = srv.stats()
+        srv.close()
+        out[name] = {"steps_per_s": st["steps_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                     "mean_batch_max": float(np.mean(batch)), "resident_gb": st["resident_bytes"] / 1e9,
+                     "requests_at_newton_cap": capped}
+    out["speedup_ppn_vs_pn"] = out["ppn"]["steps_per_s"] / out["pn"]["steps_per_s"]
+    return out
+
+
 def oracle_sample(max_seconds=25.0):
     """Time the FP64 oracle on the first PPN steps of the same beam (bounded)."""
     from oracle import oracle as O
@@ -350,11 +431,21 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppn-only", action="store_true", help="skip the PN comparison run")
+    ap.add_argument("--workload", default="beam", choices=["beam", "batched", "serving"],
+                    help="beam: the headline line; batched / serving: the multi-scene workloads")
     ap.add_argument("--profile-pcg", type=int, default=0, metavar="ITERS",
                     help="run fixed-length PCG solves for an ncu capture instead of the benchmark")
     args = ap.parse_args()
     if args.profile_pcg:
         profile_pcg(args.profile_pcg)
+        return
+    if args.workload != "beam" and args.impl == "ours":
+        import torch
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        r = run_batched() if args.workload == "batched" else run_serving()
+        if int(os.environ.get("RANK", 0)) == 0:
+            print(json.dumps({"workload": args.workload, **r}))
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

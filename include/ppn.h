@@ -92,6 +92,9 @@ typedef struct {
   int init_guess;      /* 0: x_n ; 1: x_n + dt v_n */
   int pdn_countdown;   /* PDN: iterations that stay projected after an indefinite solve (4, Sec. 5.1) */
   int projection;      /* ppn_projection (PPN_PROJ_CLAMP) */
+  double grad_floor;   /* tol_kind 0 also stops at ||g||_2 <= grad_floor ||s||_2, s_v = m_v|x_v - xhat_v|/dt^2
+                        * + sum_e |g^e_v| (the rounding floor of the residual; 1e-12) */
+  double ls_slack;     /* the Armijo test allows ls_slack |E0| of energy rounding (1e-12) */
 } ppn_params;
 
 typedef struct {

@@ -28,7 +28,7 @@ template <typename T> using vec4_t = typename Vec4<T>::type;
 
 // Per-scene control block: written by kernels, copied to the host at sync points.
 struct Ctl {
-  double grad[2];        // ||g||_2^2 summed, ||g||_inf
+  double grad[3];        // ||g||_2^2, ||s||_2^2 (residual scale), ||g||_inf
   double energy[3];      // incremental potential, g^T dx, max |dx| over free vertices
   double pcg_rr0, pcg_rr, pcg_rz, pcg_dq, pcg_alpha, pcg_beta;
   int n_new;             // elements selected by the last selection
@@ -71,7 +71,7 @@ struct SceneDev {
   double4* uhat;           // xhat - X
   double4* u_probe;        // scratch displacement for probes
   // per-iteration
-  T* ge;                   // nt x GE_STRIDE
+  double* ge;              // nt x GE_STRIDE element gradients (FP64 in both precisions)
   T* He;                   // nt x HE_STRIDE
   T* dH;                   // nt x HE_STRIDE, clamping updates
   double4* g;              // assembled gradient

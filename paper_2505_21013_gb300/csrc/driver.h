@@ -396,7 +396,8 @@ struct Driver {
       HostState& h = H[i];
       const Ctl& c = G.h_ctl[i];
       h.gn2 = std::sqrt(c.grad[0]);
-      h.ginf = c.grad[1];
+      h.ginf = c.grad[2];
+      const double floor = Pi(i).grad_floor * std::sqrt(c.grad[1]);
       h.tot.final_grad_norm2 = h.gn2;
       if (!std::isfinite(h.gn2)) {
         h.status = PPN_ERR_NONFINITE;
@@ -404,7 +405,7 @@ struct Driver {
         continue;
       }
       if (h.k == 0) h.g0 = h.gn2;
-      if (Pi(i).tol_kind == 0 && h.gn2 <= h.tol * h.g0) {
+      if (Pi(i).tol_kind == 0 && (h.gn2 <= h.tol * h.g0 || h.gn2 <= floor)) {
         h.status = PPN_OK;
         h.running = false;
         continue;
@@ -611,7 +612,8 @@ struct Driver {
         if (!ls[i]) continue;
         HostState& h = H[i];
         const double Et = G.h_ctl[i].energy[0];
-        if (Et <= h.E0 + Pi(i).armijo_c * h.gamma * h.dd) {
+        // slack: the FP64 energy sums resolve E only to a few ulps
+        if (Et <= h.E0 + Pi(i).armijo_c * h.gamma * h.dd + Pi(i).ls_slack * std::fabs(h.E0)) {
           ls[i] = 0;
           accept[i] = 1;
           h.cur.gamma = h.gamma;

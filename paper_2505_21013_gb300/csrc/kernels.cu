@@ -68,21 +68,41 @@ __global__ void __launch_bounds__(TILE) k_element(const SceneDev<T>* scenes, con
   load_u(U, t.w, u[3]);
   T W[9], V, mu, lam;
   load_tetc(S.tetc, e, W, V, mu, lam);
-  T H[9];
-  disp_grad(u[0], u[1], u[2], u[3], W, H);
-  TetState<T> st;
-  tet_state(H, mu, lam, st);
-  T P[9];
-  snh_pk1_disp(st, mu, lam, P);
-  T dN[4][3];
-  shape_grads(W, dN);
-  T* ge = S.ge + (size_t)e * GE_STRIDE;
+  // g^e in FP64 in both precisions: the assembled residual drives convergence and
+  // selection, and near equilibrium it is a small sum of large element forces
+  double Wd[9], Hd[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Wd[k] = (double)W[k];
+  disp_grad(u[0], u[1], u[2], u[3], Wd, Hd);
+  TetState<double> sd;
+  tet_state(Hd, (double)mu, (double)lam, sd);
+  double Pd[9];
+  snh_pk1_disp(sd, (double)mu, (double)lam, Pd);
+  double dNd[4][3];
+  shape_grads(Wd, dNd);
+  double* ge = S.ge + (size_t)e * GE_STRIDE;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    T pa[3];
-    matvec3(P, dN[a], pa);
+    double pa[3];
+    matvec3(Pd, dNd[a], pa);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) ge[3 * a + k] = V * pa[k];
+    for (int k = 0; k < 3; ++k) ge[3 * a + k] = (double)V * pa[k];
+  }
+  // Hessian blocks in the storage type
+  TetState<T> st;
+  T dN[4][3];
+  if constexpr (sizeof(T) == sizeof(double)) {
+    st = sd;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dN[a][k] = dNd[a][k];
+  } else {
+    T H[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) H[k] = (T)Hd[k];
+    tet_state(H, mu, lam, st);
+    shape_grads(W, dN);
   }
   T cN[4][3];
 #pragma unroll
@@ -108,7 +128,7 @@ __global__ void __launch_bounds__(TILE) k_gradient(const SceneDev<T>* scenes, co
   const SceneDev<T>& S = scenes[tr.scene];
   if (!S.active) return;
   const int v = tr.tile * TILE + threadIdx.x;
-  double n2 = 0.0, ninf = 0.0;
+  double n2 = 0.0, ninf = 0.0, s2 = 0.0;
   if (v < S.nv) {
     double g[3] = {0.0, 0.0, 0.0};
     if (!S.fixed[v]) {
@@ -118,13 +138,19 @@ __global__ void __launch_bounds__(TILE) k_gradient(const SceneDev<T>* scenes, co
       g[0] = w * (uv.x - uh.x);
       g[1] = w * (uv.y - uh.y);
       g[2] = w * (uv.z - uh.z);
+      // s: the same terms in magnitude (the rounding scale of g)
+      double a[3] = {fabs(g[0]), fabs(g[1]), fabs(g[2])};
       for (int c = S.vt_ptr[v]; c < S.vt_ptr[v + 1]; ++c) {
         const int src = S.vt_src[c];
-        const T* ge = S.ge + (size_t)(src >> 2) * GE_STRIDE + 3 * (src & 3);
-        g[0] += (double)ge[0];
-        g[1] += (double)ge[1];
-        g[2] += (double)ge[2];
+        const double* ge = S.ge + (size_t)(src >> 2) * GE_STRIDE + 3 * (src & 3);
+        g[0] += ge[0];
+        g[1] += ge[1];
+        g[2] += ge[2];
+        a[0] += fabs(ge[0]);
+        a[1] += fabs(ge[1]);
+        a[2] += fabs(ge[2]);
       }
+      s2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
     }
     st_d4(S.g + v, make_double4(g[0], g[1], g[2], 0.0));
     const double m = fmax(fabs(g[0]), fmax(fabs(g[1]), fabs(g[2])));
@@ -133,12 +159,14 @@ __global__ void __launch_bounds__(TILE) k_gradient(const SceneDev<T>* scenes, co
     ninf = m;
   }
   const double s = block_sum<TILE>(n2, sm);
+  const double ss = block_sum<TILE>(s2, sm);
   const double mx = block_max<TILE>(ninf, sm);
   if (threadIdx.x == 0) {
     S.vpart[4 * tr.tile + 0] = s;
-    S.vpart[4 * tr.tile + 1] = mx;
+    S.vpart[4 * tr.tile + 1] = ss;
+    S.vpart[4 * tr.tile + 2] = mx;
   }
-  finish_reduction<TILE, 2>(S.vpart, &S.ctl->tiles_done[0], S.n_vtiles, 1, S.ctl->grad, sm);
+  finish_reduction<TILE, 3>(S.vpart, &S.ctl->tiles_done[0], S.n_vtiles, 2, S.ctl->grad, sm);
 }
 
 // ------------------------------------------------------------- K3 assembly

@@ -356,7 +356,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   s.vel = alloc<double4>(nv);
   s.uhat = alloc<double4>(nv);
   s.u_probe = alloc<double4>(nv);
-  s.ge = alloc<T>((size_t)nt * GE_STRIDE);
+  s.ge = alloc<double>((size_t)nt * GE_STRIDE);
   s.He = alloc<T>((size_t)nt * HE_STRIDE);
   s.dH = alloc<T>((size_t)nt * HE_STRIDE);
   s.g = alloc<double4>(nv);
@@ -599,9 +599,7 @@ static ppn_status probe_elements(SceneImpl<T>& s, const double* x, double* psi, 
   PPN_CU(cudaGetLastError());
   PPN_CU(cudaStreamSynchronize(s.stream));
   if (ge) {
-    std::vector<T> h((size_t)s.nt * GE_STRIDE);
-    PPN_CU(cudaMemcpy(h.data(), s.d.ge, sizeof(T) * h.size(), cudaMemcpyDeviceToHost));
-    for (size_t k = 0; k < h.size(); ++k) ge[k] = (double)h[k];
+    PPN_CU(cudaMemcpy(ge, s.d.ge, sizeof(double) * (size_t)s.nt * GE_STRIDE, cudaMemcpyDeviceToHost));
   }
   if (He) {
     std::vector<T> h((size_t)s.nt * HE_STRIDE);
@@ -649,7 +647,7 @@ static ppn_status probe_gradient(SceneImpl<T>& s, const double* x, const double*
   if ((rc = p.G->sync_ctl())) return rc;
   if (norms) {
     norms[0] = std::sqrt(p.G->h_ctl[0].grad[0]);
-    norms[1] = p.G->h_ctl[0].grad[1];
+    norms[1] = p.G->h_ctl[0].grad[2];
   }
   if (energy) *energy = p.G->h_ctl[0].energy[0];
   if (g) {
@@ -852,6 +850,8 @@ ppn_params ppn_default_params(void) {
   p.eig_eps = 1e-8;
   p.pdn_countdown = 4;
   p.projection = PPN_PROJ_CLAMP;
+  p.grad_floor = 1e-12;
+  p.ls_slack = 1e-12;
   p.pcg_rel_tol = 1e-4;
   p.armijo_c = 1e-4;
   p.gravity[0] = 0.0;

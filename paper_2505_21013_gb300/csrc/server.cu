@@ -304,7 +304,7 @@ ppn_status ppn_server_add_scene(ppn_server* S, const double* rest_xyz, int64_t n
   if (p.precision != S->cfg.precision) return fail(PPN_ERR_INVALID_ARG, "scene precision differs from the server's");
   // the element store alone is a lower bound of a scene's footprint
   const size_t fs = S->cfg.precision == PPN_PREC_FP64 ? 8 : 4;
-  const size_t lower = (size_t)n_tets * (2 * HE_STRIDE + GE_STRIDE) * fs;
+  const size_t lower = (size_t)n_tets * (2 * HE_STRIDE * fs + GE_STRIDE * sizeof(double));
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->resident + lower > S->budget) {

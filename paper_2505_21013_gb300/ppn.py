@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libppn.so")
 
 PPN_OK = 0
+PPN_ERR_NEWTON_MAXITER = 6
 PPN_ERR_ADMISSION = 10
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "DEGENERATE_TET", 5: "LINESEARCH",
                 6: "NEWTON_MAXITER", 7: "PCG_MAXITER", 8: "NONFINITE", 9: "TIMEOUT", 10: "ADMISSION"}
@@ -33,7 +34,8 @@ class ppn_params(C.Structure):
                 ("eig_eps", C.c_double), ("pcg_rel_tol", C.c_double), ("armijo_c", C.c_double),
                 ("gravity", C.c_double * 3), ("pcg_max_iter", C.c_int), ("newton_max_iter", C.c_int),
                 ("ls_max_halvings", C.c_int), ("precision", C.c_int), ("tol_kind", C.c_int),
-                ("init_guess", C.c_int), ("pdn_countdown", C.c_int), ("projection", C.c_int)]
+                ("init_guess", C.c_int), ("pdn_countdown", C.c_int), ("projection", C.c_int),
+                ("grad_floor", C.c_double), ("ls_slack", C.c_double)]
 
 
 class ppn_iter_stats(C.Structure):

@@ -14,6 +14,7 @@ from .scenes import (
     twisting_beam_scene,
     random_batch_scenes,
     serving_scenes,
+    poisson_arrivals,
     tiny_scene,
 )
 
@@ -25,5 +26,6 @@ __all__ = [
     "twisting_beam_scene",
     "random_batch_scenes",
     "serving_scenes",
+    "poisson_arrivals",
     "tiny_scene",
 ]

@@ -171,3 +171,23 @@ def test_mirroring_fp64_matches_oracle(mode_g, mode_o):
         disp = np.abs(xo - spec.rest).max()
         assert np.abs(x - xo).max() <= 1e-5 * disp
         assert abs(st["newton_iters"] - sto["newton_iters"]) <= 1
+
+
+@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
+def test_scene_at_rest_stops_at_the_rounding_floor(prec):
+    # a stiff cube settling on its face: near rest the Armijo slack accepts steps whose
+    # decrease is below the energy sum's resolution, and at rest the residual is
+    # rounding noise that only the floor ||g|| <= 1e-12 ||s|| stops
+    spec = cube_scene(4, E=2e6, nu=0.4, dt=1 / 30, seed=0)
+    g = P.Scene.from_spec(spec, precision=prec)
+    o = O.Scene.from_spec(spec)
+    for n in range(60):
+        tg = spec.targets_at(n)
+        g.set_targets(tg)
+        o.set_targets(tg)
+        rc, x, st = g.step(P.MODE_PPN, 1e-4)
+        rco, xo, sto = o.step(O.PPN, 1e-4)
+        assert rc == rco == 0
+    assert sto["newton_iters"] == 0 and st["newton_iters"] <= (0 if prec == P.PREC_FP64 else 1)
+    disp = np.abs(xo - spec.rest).max()
+    assert np.abs(x - xo).max() <= (1e-5 if prec == P.PREC_FP64 else 2e-3) * disp
