@@ -404,6 +404,51 @@ def run_serving(n_scenes=32, n_req=600, rate_hz=500.0, seed=1, tol=1e-4, max_bat
     return out
 
 
+def run_ablation(steps=8, tol=1e-4):
+    """Sensitivity of PPN to the tightening (alpha) and release (beta) rates of
+    Sec. 4 on a violently twisted beam (10x10x40 vertices, E = 1e5, nu = 0.45,
+    20 rad/s, dt = 1/30), where the unprojected Hessian turns indefinite: per
+    (alpha, beta) the device time of `steps` time steps, Newton iterations,
+    projected fraction and solves.  PN and plain Newton for reference."""
+    import math
+
+    import torch
+
+    import paper_2505_21013_gb300 as P
+    from ppn_inputs import twisting_beam_scene
+
+    spec = twisting_beam_scene(10, 10, 40, h=0.02, E=1e5, nu=0.45, omega=20.0, dt=1.0 / 30.0, seed=0)
+
+    def run(mode, alpha=0.5, beta=2.0):
+        p = P.ppn_default_params()
+        p.alpha, p.beta = alpha, beta
+        sc = P.Scene.from_spec(spec, params=p, precision=P.PREC_MIXED)
+        ms, newton, proj, att, cg, bad = 0.0, 0, 0, 0, 0, 0
+        for n in range(steps):
+            sc.set_targets(spec.targets_at(n))
+            rc, _, st = sc.step(mode, tol, want_x=False)
+            bad += rc != 0
+            ms += st["device_ms"]
+            newton += st["newton_iters"]
+            proj += st["total_projections"]
+            att += st["total_attempts"]
+            cg += st["total_cg_iters"]
+        sc.close()
+        torch.cuda.synchronize()
+        return {"alpha": alpha, "beta": beta, "ms": round(ms, 3), "newton_iters": newton,
+                "projected_fraction": round(proj / max(1, newton * spec.n_tets), 5), "solves": att,
+                "cg_iters": cg, "failed_steps": bad}
+
+    grid = [run(P.MODE_PPN, a, b) for a in (0.01, 0.1, 0.25, 0.5, 0.75, 0.9)
+            for b in (1.0, 2.0, 4.0, 16.0, math.inf)]
+    best = min(grid, key=lambda r: r["ms"])
+    default = next(r for r in grid if r["alpha"] == 0.5 and r["beta"] == 2.0)
+    return {"scene": "twisting_beam_10x10x40_omega20", "n_tets": spec.n_tets, "steps": steps,
+            "grid": grid, "pn": run(P.MODE_PN), "newton": run(P.MODE_NEWTON),
+            "best": {"alpha": best["alpha"], "beta": best["beta"], "ms": best["ms"]},
+            "default_over_best": round(default["ms"] / best["ms"], 3)}
+
+
 def oracle_sample(max_seconds=25.0):
     """Time the FP64 oracle on the first PPN steps of the same beam (bounded)."""
     from oracle import oracle as O
@@ -431,7 +476,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppn-only", action="store_true", help="skip the PN comparison run")
-    ap.add_argument("--workload", default="beam", choices=["beam", "batched", "serving"],
+    ap.add_argument("--workload", default="beam", choices=["beam", "batched", "serving", "ablation"],
                     help="beam: the headline line; batched / serving: the multi-scene workloads")
     ap.add_argument("--profile-pcg", type=int, default=0, metavar="ITERS",
                     help="run fixed-length PCG solves for an ncu capture instead of the benchmark")
@@ -443,7 +488,7 @@ def main():
         import torch
 
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-        r = run_batched() if args.workload == "batched" else run_serving()
+        r = {"batched": run_batched, "serving": run_serving, "ablation": run_ablation}[args.workload]()
         if int(os.environ.get("RANK", 0)) == 0:
             print(json.dumps({"workload": args.workload, **r}))
         return
