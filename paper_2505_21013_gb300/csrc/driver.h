@@ -49,6 +49,8 @@ struct Group {
   int pcg_ntiles = 0;
   size_t pcg_smem_bytes = 0;  // > 0: resident PCG layout chosen for that table
   int pcg_smem_blocks = 0, pcg_smem_grid = 0;
+  bool pcg_sr = false;          // the single-reduction FP32 kernel was chosen for that table
+  unsigned long long* d_flags = nullptr;  // its per-CTA publication flags
   GridBar* d_bar = nullptr;
   cudaStream_t st = nullptr;
   Staging staging;
@@ -124,6 +126,7 @@ struct Group {
       d_projtiles = alloc<TileRef>(cap_proj);
       d_ids = alloc<int>(cap_n);
       d_pcgtiles = alloc<TileRef>(cap_pt);
+      d_flags = alloc<unsigned long long>(XCH_MAX_CTAS_HOST);
       d_bar = alloc<GridBar>(1);
       if (!d_desc || !d_ctl || !d_ttiles || !d_vtiles || !d_btiles || !d_ptiles || !d_etiles ||
           !d_projtiles || !d_ids || !d_bar || !d_pcgtiles) {
@@ -136,6 +139,7 @@ struct Group {
     pcg_ids.clear();
     pcg_ntiles = 0;
     pcg_smem_bytes = 0;
+    pcg_sr = false;
     std::memset(h_bar, 0, sizeof(GridBar));
     PPN_CU(cudaMemset(d_bar, 0, sizeof(GridBar)));
     PPN_CU(cudaMemcpy(d_ttiles, tt.data(), sizeof(TileRef) * tt.size(), cudaMemcpyHostToDevice));
@@ -283,6 +287,7 @@ struct Driver {
       L.smem_bytes = G.pcg_smem_bytes;
       L.smem_blocks = G.pcg_smem_blocks;
       L.launch_seq = ++G.pcg_launch_seq;
+      L.flags = G.d_flags;
       L.n_pword = (int)sl.size();
       for (size_t k = 0; k < sl.size(); ++k) {
         L.pword[k] = G.h_desc[sl[k]].pword;
@@ -291,6 +296,12 @@ struct Driver {
       double bytes = 0.0;
       cudaError_t err = cudaSuccess;
       timed(FAM_PCG, bytes, [&] {
+        if constexpr (sizeof(T) == sizeof(float)) {
+          if (G.pcg_sr) {
+            err = launch_pcg_sr(reinterpret_cast<const SceneDev<float>*>(G.d_desc), L, G.st);
+            return;
+          }
+        }
         err = L.smem_bytes ? launch_pcg_smem<T>(G.d_desc, L, G.st) : launch_pcg<T>(G.d_desc, L, G.st);
       });
       if (err != cudaSuccess) {
@@ -301,9 +312,11 @@ struct Driver {
     return PPN_OK;
   }
 
-  // Choose the shared-memory-resident PCG when every CTA's rows fit.
+  // Choose the shared-memory-resident PCG when every CTA's rows fit: the
+  // single-reduction kernel for FP32 (unless PPN_PCG_STD is set), else the standard one.
   void plan_smem(const std::vector<int>& sl, const std::vector<TileRef>& tt) {
     G.pcg_smem_bytes = 0;
+    G.pcg_sr = false;
     if (std::getenv("PPN_PCG_GLOBAL")) return;
     const int n_tiles = (int)tt.size();
     const int grid = std::min(G.pcg_grid, n_tiles);
@@ -319,10 +332,20 @@ struct Driver {
       max_items = std::max(max_items, (t1 - t0) * PCG_TILE);
       max_blocks = std::max(max_blocks, blocks);
     }
-    const size_t bytes = pcg_smem_bytes(max_items, max_blocks, (int)sizeof(T));
-    if (bytes > (size_t)196 * 1024 || grid > 1024) return;
     int dev = 0;
     cudaGetDevice(&dev);
+    if (sizeof(T) == sizeof(float) && !std::getenv("PPN_PCG_STD") && grid <= 1024) {
+      const size_t pb = pcg_sr_smem_bytes(max_items, max_blocks);
+      if (pb <= (size_t)212 * 1024 && pcg_sr_max_grid(dev, pb) >= grid) {
+        G.pcg_smem_bytes = pb;
+        G.pcg_smem_blocks = max_blocks;
+        G.pcg_smem_grid = grid;
+        G.pcg_sr = true;
+        return;
+      }
+    }
+    const size_t bytes = pcg_smem_bytes(max_items, max_blocks, (int)sizeof(T));
+    if (bytes > (size_t)196 * 1024 || grid > 1024) return;
     const int mg = pcg_smem_max_grid(G.pcg_group, dev, bytes, (int)sizeof(T));
     if (mg < grid) return;
     G.pcg_smem_bytes = bytes;

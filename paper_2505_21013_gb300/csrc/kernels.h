@@ -32,7 +32,8 @@ struct GridBar {
   int pad;
 };
 
-constexpr int PCG_MAX_SCENES = 64;  // scenes per PCG launch (per-CTA scalar state in shared memory)
+constexpr int PCG_MAX_SCENES = 64;
+constexpr int XCH_MAX_CTAS_HOST = 1024;  // CTAs of one resident PCG launch  // scenes per PCG launch (per-CTA scalar state in shared memory)
 
 struct PcgLaunch {
   int n_tiles;           // PCG row tiles in the launch's tile table (TileRef.scene = slot)
@@ -46,6 +47,7 @@ struct PcgLaunch {
   size_t smem_bytes;     // > 0: shared-memory-resident kernel with this dynamic size
   int smem_blocks;       // block capacity of that layout (max blocks of one CTA)
   unsigned launch_seq;
+  unsigned long long* flags;  // single-reduction kernel: per-CTA publication flags (grid words)
   int n_pword;           // stamped partial arrays to clear before the launch
   void* pword[PCG_MAX_SCENES];
   size_t pword_bytes[PCG_MAX_SCENES];
@@ -55,6 +57,10 @@ struct PcgLaunch {
 size_t pcg_smem_bytes(int ni, int nb, int fsize);
 // co-resident grid of the resident PCG kernel with `smem` dynamic bytes (0: does not fit)
 int pcg_smem_max_grid(int group, int device, size_t smem, int fsize);
+// single-reduction FP32 PCG (pcg_sr.cu): shared memory for ni rows / nb blocks, co-resident grid, launch
+size_t pcg_sr_smem_bytes(int ni, int nb);
+int pcg_sr_max_grid(int device, size_t smem);
+cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cudaStream_t st);
 template <typename T>
 cudaError_t launch_pcg_smem(const SceneDev<T>* scenes, const PcgLaunch& L, cudaStream_t st);
 

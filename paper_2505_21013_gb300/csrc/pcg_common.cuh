@@ -98,6 +98,69 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 }
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---- stamped words.  A tile partial crosses the grid as N 64-bit words, each
+// carrying the phase stamp; stamp 0 is never used (the words are zeroed before
+// every launch).  FP32 partials: one word, stamp = the 32-bit phase counter in
+// the high half, the value's bits in the low half.  FP64 partials: hi and lo
+// words (hi = the value with its 16 low mantissa bits cleared, lo = value - hi,
+// exact), stamp in the 16 low bits of each.
+template <typename R>
+struct Words;
+template <>
+struct Words<float> {
+  static constexpr int N = 1;
+  __device__ static unsigned stamp(unsigned epoch) { return epoch; }
+  __device__ static unsigned long long filler(unsigned s) { return (unsigned long long)s << 32; }
+  __device__ static void split(float v, unsigned s, unsigned long long* w) {
+    w[0] = ((unsigned long long)s << 32) | __float_as_uint(v);
+  }
+  __device__ static bool has(unsigned long long w, unsigned s) { return (unsigned)(w >> 32) == s; }
+  __device__ static float join(const unsigned long long* w) { return __uint_as_float((unsigned)w[0]); }
+};
+template <>
+struct Words<double> {
+  static constexpr int N = 2;
+  __device__ static unsigned stamp(unsigned epoch) { return ((epoch - 1u) % 65535u) + 1u; }
+  __device__ static unsigned long long filler(unsigned s) { return s; }
+  __device__ static void split(double v, unsigned s, unsigned long long* w) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned long long hb = b & ~0xFFFFull;
+    const double lo = v - __longlong_as_double((long long)hb);
+    const unsigned long long lb = (unsigned long long)__double_as_longlong(lo) & ~0xFFFFull;
+    w[0] = hb | s;
+    w[1] = lb | s;
+  }
+  __device__ static bool has(unsigned long long w, unsigned s) { return (unsigned)(w & 0xFFFFull) == s; }
+  __device__ static double join(const unsigned long long* w) {
+    return __longlong_as_double((long long)(w[0] & ~0xFFFFull)) +
+           __longlong_as_double((long long)(w[1] & ~0xFFFFull));
+  }
+};
+// ---- FP32 z / d_prev records: one 32-byte record {z.xyz, 0, d.xyz, 0} per row
+// and parity buffer, so a neighbour gather is one 256-bit load.  Iteration k
+// reads buffer k & 1 (z_k, d_{k-1}) and writes d_k and z_{k+1} into the other.
+__device__ __forceinline__ void ld_rec(const float* p, float (&a)[8]) {
+  asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(a[0]), "=f"(a[1]), "=f"(a[2]), "=f"(a[3]), "=f"(a[4]), "=f"(a[5]), "=f"(a[6]), "=f"(a[7])
+               : "l"(p));
+}
+__device__ __forceinline__ void st_rec_half(float* p, float x, float y, float z) {
+  asm volatile("st.global.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(0.0f) : "memory");
+}
+__device__ __forceinline__ float* rec_ptr(float* base, int nv, int parity, int i) {
+  return base + ((size_t)parity * nv + i) * 8;
+}
+
+// bound of one wait, in polling rounds; a CTA that gives up flags a timeout
+constexpr unsigned kWaitSpins = 1u << 20;
+
 // per-scene fields a PCG kernel needs, copied to shared memory once per solve
 // so that no phase chases descriptor pointers through global memory
 template <typename T>
@@ -221,7 +284,7 @@ __device__ __forceinline__ void after_rz(SState<R>& s, R rz, R r2, double tol2, 
   }
 }
 
-constexpr int XCH_MAX_CTAS = 1024;  // CTAs of one resident PCG launch
+constexpr int XCH_MAX_CTAS = 1024;  // CTAs of one resident PCG launch (XCH_MAX_CTAS_HOST in kernels.h)
 
 template <typename R>
 __device__ __forceinline__ void init_state(SState<R>& s, R rz, R r2, R f) {

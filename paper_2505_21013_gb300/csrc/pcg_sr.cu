@@ -1,0 +1,573 @@
+// Single-reduction block-Jacobi PCG (the linear solve of Algorithm 1; Sec. 4.1
+// "Linear Solvers", Sec. 5.1) for the FP32 path: one grid-wide reduction and
+// one neighbour-only synchronisation per iteration, instead of the two
+// grid-wide reductions of the textbook recurrences.
+//
+// Method.  The recurrences of Chronopoulos & Gear (1989) for preconditioned
+// CG.  With u = M r, w = A u, s = A p, iteration i (i >= 1) computes
+//   x += alpha p, r -= alpha s, u = M r, w = A u           (local, then SpMV)
+//   gamma = r.u, delta = w.u, rho = r.r                     (one reduction)
+//   beta = gamma / gamma_prev, d = delta - beta gamma / alpha_prev  (= p^T A p)
+//   alpha = gamma / d, p = u + beta p, s = w + beta s.
+// In exact arithmetic these are the iterates of the standard kernels, with
+// the same stopping test on ||r|| / ||r0|| checked after each update, d equal
+// to the curvature p^T A p of the new direction (d <= 0: stop with the iterate
+// before it) and the same failed-diagonal-block exit.  Only s is carried by a
+// recurrence (w is recomputed by the SpMV every iteration), which keeps the
+// FP32 iteration counts and attained residuals those of the standard kernel.
+//
+// Data.  As in the resident kernel of pcg_smem.cu: each CTA keeps its rows'
+// BSR blocks, block-Jacobi inverse and vectors x, r, u, w, p, s in shared
+// memory.  Only u crosses CTAs, through a global array.
+//
+// Synchronisation.  A CTA publishes its u values, then a flag with the
+// iteration's stamp; before its SpMV it waits only for the flags of the CTAs
+// that own the columns of its rows (a contiguous CTA range found at set-up).
+// The reduction's tile partials go out as stamped words after the SpMV, and
+// every CTA sums them in tile order.  One u array suffices: a CTA overwrites
+// it only after it has seen every CTA's partials of the previous iteration,
+// which each CTA posts after finishing the SpMV that read the old values.
+// All waits are bounded.
+#include "pcg_common.cuh"
+
+namespace ppn {
+
+using namespace pcgdev;
+
+namespace {
+
+constexpr int NTP = 512;  // threads per CTA
+constexpr int GP = 2;     // lanes per BSR row in the SpMV
+constexpr int NQ = 4;     // reduction slots: gamma, delta, rho, failed diagonal blocks
+
+struct SrLayout {
+  float* lws;  // [(ni / PCG_TILE + 1) * 16 * NQ] per-warp partial sums (16 warps per pass cover 4 tiles)
+  int* it_i;
+  int* it_slot;
+  int* lrp;
+  int* lcol;
+  float* lval;
+  float* lP;
+  float *lx, *lr, *lu, *lw, *lp, *ls;  // [ni * 3] each
+};
+
+__host__ __device__ inline size_t up16(size_t b) { return (b + 15) & ~size_t(15); }
+
+__device__ __forceinline__ SrLayout carve_sr(char* base, int ni, int nb) {
+  SrLayout L;
+  const int ntl = ni / PCG_TILE + 1;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base + off;
+    off += up16(bytes);
+    return p;
+  };
+  L.lws = (float*)take(sizeof(float) * ntl * 16 * NQ);
+  L.it_i = (int*)take(sizeof(int) * ni);
+  L.it_slot = (int*)take(sizeof(int) * ni);
+  L.lrp = (int*)take(sizeof(int) * (ni + 1));
+  L.lcol = (int*)take(sizeof(int) * nb);
+  L.lval = (float*)take(sizeof(float) * 9 * nb);
+  L.lP = (float*)take(sizeof(float) * 9 * ni);
+  float** v[6] = {&L.lx, &L.lr, &L.lu, &L.lw, &L.lp, &L.ls};
+  for (float** p : v) *p = (float*)take(sizeof(float) * 3 * ni);
+  return L;
+}
+
+// u of row i: the first four floats of the row's 32-byte record in zrec
+__device__ __forceinline__ float* u_ptr(float* zrec, int i) { return zrec + (size_t)i * 8; }
+__device__ __forceinline__ void st_f4(float* p, float x, float y, float z) {
+  asm volatile("st.global.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(0.0f) : "memory");
+}
+__device__ __forceinline__ float4 ld_f4_cg(const float* p) {
+  float4 v;
+  asm volatile("ld.global.cg.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+
+// scalar step after the reduction of iteration `it` (it updates done so far):
+// stopping tests, then alpha and beta of the next direction, or the exits
+__device__ __forceinline__ void sr_step(SState<float>& s, float gam, float del, float rho, float fail, int it,
+                                        double tol2, int max_iter) {
+  s.rr = rho;
+  if (it == 0) {
+    s.rr0 = rho;
+    s.pfail = fail > 0.0f;
+    s.ind = fail > 0.0f;
+    s.iters = 0;
+    s.hitmax = 0;
+    s.nonfinite = !(rho == rho) || !(gam == gam);
+    if (s.ind || s.nonfinite || !(rho > 0.0f)) {
+      s.done = 1;
+      return;
+    }
+  }
+  if (!(rho == rho) || !(gam == gam) || !(del == del)) {
+    s.nonfinite = 1;
+    s.done = 1;
+    return;
+  }
+  if (it > 0 && rho <= (float)tol2 * s.rr0) {
+    s.done = 1;
+    return;
+  }
+  if (it > 0 && s.iters >= max_iter) {
+    s.hitmax = 1;
+    s.done = 1;
+    return;
+  }
+  const float beta = it > 0 ? gam / s.rz : 0.0f;
+  const float d = it > 0 ? del - beta * gam / s.alpha : del;  // p^T A p of the next direction
+  s.dq = d;
+  if (!(d > 0.0f)) {
+    if (!(d == d)) s.nonfinite = 1;
+    s.ind = 1;
+    s.done = 1;
+    return;
+  }
+  s.beta = beta;
+  s.alpha = gam / d;
+  s.rz = gam;
+}
+
+}  // namespace
+
+size_t pcg_sr_smem_bytes(int ni, int nb) {
+  const size_t ntl = ni / PCG_TILE + 1;
+  return up16(sizeof(float) * ntl * 16 * NQ) + 2 * up16(sizeof(int) * ni) + up16(sizeof(int) * (ni + 1)) +
+         up16(sizeof(int) * nb) + up16(sizeof(float) * 9 * nb) + up16(sizeof(float) * 9 * ni) +
+         6 * up16(sizeof(float) * 3 * ni);
+}
+
+__global__ void __launch_bounds__(NTP, 1)
+    k_pcg_sr(const SceneDev<float>* scenes, const TileRef* tiles, int n_tiles, const int* scene_ids,
+               int n_scenes, GridBar* bar, int b_from_g, int nb_cap, unsigned long long* flags) {
+  using W = Words<float>;
+  constexpr int RPP = NTP / GP;         // rows per SpMV pass
+  constexpr int U = 16 / GP;            // blocks per lane per gather round
+  constexpr int NW = NTP / 32;          // warps
+  static_assert(RPP % PCG_TILE == 0 && NTP % PCG_TILE == 0, "passes cover whole tiles");
+  extern __shared__ __align__(16) char dyn[];
+  __shared__ SState<float> st[PCG_MAX_SCENES];
+  __shared__ SceneLite<float> sl[PCG_MAX_SCENES];
+  __shared__ float s_sum[PCG_MAX_SCENES][NQ];
+  __shared__ int s_toff[PCG_MAX_SCENES];
+  __shared__ int s_to, s_all_done, s_lo, s_hi;
+  __shared__ int s_scan[NW];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane32 = tid & 31;
+  const int grid = (int)gridDim.x;
+  const int t0 = (int)(((long long)blockIdx.x * n_tiles) / grid);
+  const int t1 = (int)(((long long)(blockIdx.x + 1) * n_tiles) / grid);
+  const int ntl = t1 - t0;
+  const int n_items = ntl * PCG_TILE;
+  const SrLayout L = carve_sr(dyn, n_items, nb_cap);
+  if (tid == 0) {
+    s_to = 0;
+    s_lo = grid;
+    s_hi = -1;
+  }
+  for (int si = tid; si < n_scenes; si += NTP) {
+    load_lite(sl[si], scenes[scene_ids[si]]);
+    st[si].done = 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int o = 0;
+    for (int si = 0; si < n_scenes; ++si) {
+      s_toff[si] = o;
+      o += sl[si].n_ptiles;
+    }
+  }
+  for (int item = tid; item < n_items; item += NTP) {
+    const TileRef tr = tiles[t0 + item / PCG_TILE];
+    const int i = tr.tile * PCG_TILE + (item % PCG_TILE);
+    L.it_slot[item] = tr.scene;
+    L.it_i[item] = i < sl[tr.scene].nv ? i : -1;
+  }
+  __syncthreads();
+  // local row pointers (exclusive scan of the row lengths)
+  {
+    int carry = 0;
+    for (int base = 0; base < n_items; base += NTP) {
+      const int item = base + tid;
+      int len = 0;
+      if (item < n_items) {
+        const int i = L.it_i[item];
+        if (i >= 0) {
+          const SceneLite<float>& S = sl[L.it_slot[item]];
+          len = S.row_ptr[i + 1] - S.row_ptr[i];
+        }
+      }
+      int v = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane32 >= o) v += y;
+      }
+      if (lane32 == 31) s_scan[warp] = v;
+      __syncthreads();
+      if (tid < 32) {
+        int w = (tid < NW) ? s_scan[tid] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, w, o);
+          if (tid >= o) w += y;
+        }
+        if (tid < NW) s_scan[tid] = w;
+      }
+      __syncthreads();
+      const int excl = carry + v - len + (warp ? s_scan[warp - 1] : 0);
+      if (item < n_items) L.lrp[item] = excl;
+      const int total = s_scan[NW - 1];
+      __syncthreads();
+      carry += total;
+    }
+    if (tid == 0) L.lrp[n_items] = carry;
+    __syncthreads();
+  }
+  // copy this CTA's blocks; the CTAs owning their columns bound the neighbour range
+  {
+    int lo = grid, hi = -1;
+    for (int item = warp; item < n_items; item += NW) {
+      const int i = L.it_i[item];
+      if (i < 0) continue;
+      const int slot = L.it_slot[item];
+      const SceneLite<float>& S = sl[slot];
+      const int kb = S.row_ptr[i], ke = S.row_ptr[i + 1], lb = L.lrp[item];
+      const size_t nb = (size_t)S.nnzb;
+      for (int k = kb + lane32; k < ke; k += 32) {
+        const int b = lb + (k - kb);
+        const int j = S.col[k];
+        L.lcol[b] = j;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) L.lval[9 * b + c] = S.val[c * nb + k];
+        const long long gt = s_toff[slot] + j / PCG_TILE;  // tile in the launch's table
+        const int owner = (int)(((gt + 1) * grid + n_tiles - 1) / n_tiles) - 1;
+        lo = min(lo, owner);
+        hi = max(hi, owner);
+      }
+    }
+    atomicMin(&s_lo, lo);
+    atomicMax(&s_hi, hi);
+  }
+  __syncthreads();
+
+  // ---------------- exchange helpers
+  auto post_tile = [&](int lt, int k, float v, unsigned s) {
+    const TileRef tr = tiles[t0 + lt];
+    const SceneLite<float>& S = sl[tr.scene];
+    unsigned long long w[1];
+    W::split(v, s, w);
+    st_relaxed_u64(S.pword + (size_t)k * S.n_ptiles + tr.tile, w[0]);
+  };
+  // every CTA sums the tile words of quantities [0, nq) of every live scene in tile order
+  auto reduce = [&](int nq, unsigned s) -> bool {
+    for (int x = warp; x < n_scenes * nq; x += NW) {
+      const int si = x / nq, q = x % nq;
+      if (st[si].done) continue;  // warp-uniform
+      const SceneLite<float>& S = sl[si];
+      const int n = S.n_ptiles;
+      const unsigned long long* base = S.pword + (size_t)q * n;
+      float acc = 0.0f;
+      for (int tw = lane32; tw < n; tw += 32 * 8) {
+        unsigned long long w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int t = tw + 32 * u;
+          w[u] = t < n ? ld_relaxed_u64(base + t) : W::filler(s);
+        }
+        for (unsigned spins = 0;; ++spins) {
+          bool ready = true;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) ready &= W::has(w[u], s);
+          if (ready) break;
+          if (spins > kWaitSpins || *(volatile int*)&s_to) {
+            s_to = 1;
+            break;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (!W::has(w[u], s)) w[u] = ld_relaxed_u64(base + tw + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (tw + 32 * u < n) acc += W::join(&w[u]);
+      }
+      acc = warp_sum(acc);
+      if (lane32 == 0) s_sum[si][q] = acc;
+    }
+    __syncthreads();
+    return !s_to;
+  };
+  // publish this CTA's vector values for its neighbours: release, then the flag
+  auto publish_flag = [&](unsigned long long stamp) {
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_relaxed_u64(flags + blockIdx.x, stamp);
+    }
+  };
+  // wait until every CTA of the neighbour range has published `stamp`
+  auto wait_flags = [&](unsigned long long stamp) -> bool {
+    if (warp == 0) {
+      for (int c0 = s_lo + lane32; c0 <= s_hi; c0 += 32 * 4) {
+        unsigned long long w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = c0 + 32 * u;
+          w[u] = c <= s_hi ? ld_relaxed_u64(flags + c) : stamp;
+        }
+        for (unsigned spins = 0;; ++spins) {
+          bool ready = true;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) ready &= w[u] >= stamp;
+          if (ready) break;
+          if (spins > kWaitSpins || *(volatile int*)&s_to) {
+            s_to = 1;
+            break;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (w[u] < stamp) w[u] = ld_relaxed_u64(flags + c0 + 32 * u);
+        }
+      }
+      fence_acq_rel();  // acquire: the neighbours' values before this CTA's gathers
+    }
+    __syncthreads();
+    return !s_to;
+  };
+  // w = A u over this CTA's rows, u gathered from the global array (G lanes per row)
+  auto spmv = [&](float* ly) {
+    for (int base = 0; base < n_items; base += RPP) {
+      const int row = tid / GP, lane = tid % GP;
+      const int item = base + row;
+      float ax = 0.f, ay = 0.f, az = 0.f;
+      if (item < n_items) {
+        const int i = L.it_i[item];
+        const int slot = L.it_slot[item];
+        if (i >= 0 && !st[slot].done) {
+          const SceneLite<float>& S = sl[slot];
+          const float* vb = u_ptr(S.zrec, 0);
+          const int lb = L.lrp[item], le = L.lrp[item + 1];
+          for (int b0 = lb + lane; b0 < le; b0 += GP * U) {
+            float4 vj[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int b = b0 + GP * u;
+              if (b < le) vj[u] = ld_f4_cg(vb + (size_t)8 * L.lcol[b]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int b = b0 + GP * u;
+              if (b < le) {
+                const float* a = L.lval + 9 * b;
+                ax += a[0] * vj[u].x + a[1] * vj[u].y + a[2] * vj[u].z;
+                ay += a[3] * vj[u].x + a[4] * vj[u].y + a[5] * vj[u].z;
+                az += a[6] * vj[u].x + a[7] * vj[u].y + a[8] * vj[u].z;
+              }
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int o = GP / 2; o > 0; o >>= 1) {
+        ax += __shfl_down_sync(0xffffffffu, ax, o, GP);
+        ay += __shfl_down_sync(0xffffffffu, ay, o, GP);
+        az += __shfl_down_sync(0xffffffffu, az, o, GP);
+      }
+      if (lane == 0 && item < n_items) {
+        ly[3 * item] = ax;
+        ly[3 * item + 1] = ay;
+        ly[3 * item + 2] = az;
+      }
+    }
+    __syncthreads();
+  };
+
+  // partial sums of gamma = r.u, delta = w.u, rho = r.r (and failed blocks) per tile, posted
+  auto post_partials = [&](unsigned stamp, bool with_fail) {
+    for (int base = 0; base < n_items; base += NTP) {
+      const int item = base + tid;
+      float g = 0.f, d = 0.f, rr = 0.f;
+      const int i = item < n_items ? L.it_i[item] : -1;
+      const int slot = item < n_items ? L.it_slot[item] : 0;
+      if (i >= 0 && !st[slot].done) {
+        const int k = 3 * item;
+        const float r0 = L.lr[k], r1 = L.lr[k + 1], r2 = L.lr[k + 2];
+        const float u0 = L.lu[k], u1 = L.lu[k + 1], u2 = L.lu[k + 2];
+        g = r0 * u0 + r1 * u1 + r2 * u2;
+        d = L.lw[k] * u0 + L.lw[k + 1] * u1 + L.lw[k + 2] * u2;
+        rr = r0 * r0 + r1 * r1 + r2 * r2;
+      }
+      g = warp_sum(g);
+      d = warp_sum(d);
+      rr = warp_sum(rr);
+      if (lane32 == 0) {
+        float* o = L.lws + NQ * ((base >> 5) + warp);
+        o[0] = g;
+        o[1] = d;
+        o[2] = rr;
+      }
+    }
+    __syncthreads();
+    for (int lt = tid; lt < ntl; lt += NTP) {
+      if (st[L.it_slot[lt * PCG_TILE]].done) continue;
+      const float* w = L.lws + NQ * 4 * lt;
+      const int nq = with_fail ? NQ : 3;
+      for (int q = 0; q < nq; ++q) post_tile(lt, q, ((w[q] + w[NQ + q]) + w[2 * NQ + q]) + w[3 * NQ + q], stamp);
+    }
+  };
+  auto fail_out = [&]() {
+    if (tid == 0) atomicExch(&bar->timeout, 1);
+  };
+
+  // ---------------- set-up: P = block-Jacobi inverse, x = 0, r = b, u = P r
+  for (int base = 0; base < n_items; base += NTP) {
+    const int item = base + tid;
+    float fail = 0.0f;
+    const int i = item < n_items ? L.it_i[item] : -1;
+    if (i >= 0) {
+      const SceneLite<float>& S = sl[L.it_slot[item]];
+      const int bd = L.lrp[item] + (S.diag_idx[i] - S.row_ptr[i]);
+      float Pm[9];
+      const bool ok = spd_inv3(L.lval + 9 * bd, Pm);
+      float* P = S.Pinv + (size_t)9 * i;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        P[c] = Pm[c];
+        L.lP[9 * item + c] = Pm[c];
+      }
+      float r0, r1, r2;
+      if (b_from_g) {
+        const double4 g = ld_d4(S.g + i);
+        r0 = (float)(-g.x);
+        r1 = (float)(-g.y);
+        r2 = (float)(-g.z);
+      } else {
+        const float4 rv = ld_f4_cg(reinterpret_cast<const float*>(S.r + i));
+        r0 = rv.x;
+        r1 = rv.y;
+        r2 = rv.z;
+      }
+      const float u0 = Pm[0] * r0 + Pm[1] * r1 + Pm[2] * r2;
+      const float u1 = Pm[3] * r0 + Pm[4] * r1 + Pm[5] * r2;
+      const float u2 = Pm[6] * r0 + Pm[7] * r1 + Pm[8] * r2;
+      st_f4(u_ptr(S.zrec, i), u0, u1, u2);
+      const int k = 3 * item;
+      L.lr[k] = r0, L.lr[k + 1] = r1, L.lr[k + 2] = r2;
+      L.lu[k] = u0, L.lu[k + 1] = u1, L.lu[k + 2] = u2;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) L.lx[k + c] = L.lp[k + c] = L.ls[k + c] = 0.0f;
+      fail = ok ? 0.0f : 1.0f;
+    }
+    fail = warp_sum(fail);
+    if (lane32 == 0) L.lws[NQ * ((base >> 5) + warp) + 3] = fail;
+  }
+
+  for (int it = 0;; ++it) {
+    // ---- u released to the neighbours (set-up wrote u_0; later iterations below)
+    publish_flag((unsigned long long)it + 1);
+    if (!wait_flags((unsigned long long)it + 1)) return fail_out();
+    spmv(L.lw);  // w = A u
+    const unsigned s = W::stamp((unsigned)it + 1);
+    post_partials(s, it == 0);
+    if (!reduce(it == 0 ? NQ : 3, s)) return fail_out();
+    for (int si = tid; si < n_scenes; si += NTP)
+      if (!st[si].done)
+        sr_step(st[si], s_sum[si][0], s_sum[si][1], s_sum[si][2], it == 0 ? s_sum[si][3] : 0.0f, it,
+                sl[si].tol2, sl[si].max_iter);
+    __syncthreads();
+    if (tid == 0) {
+      int all = 1;
+      for (int si = 0; si < n_scenes; ++si) all &= st[si].done;
+      s_all_done = all;
+    }
+    __syncthreads();
+    if (s_all_done) break;
+    // ---- p = u + beta p, s = w + beta s; x += alpha p, r -= alpha s, u = M r (published)
+    for (int item = tid; item < n_items; item += NTP) {
+      const int i = L.it_i[item];
+      const int slot = L.it_slot[item];
+      if (i < 0 || st[slot].done) continue;
+      const float a = st[slot].alpha, b = st[slot].beta;
+      const int k = 3 * item;
+      float r[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float p = L.lu[k + c] + b * L.lp[k + c];
+        const float sv = L.lw[k + c] + b * L.ls[k + c];
+        L.lp[k + c] = p;
+        L.ls[k + c] = sv;
+        L.lx[k + c] += a * p;
+        r[c] = L.lr[k + c] - a * sv;
+        L.lr[k + c] = r[c];
+      }
+      const float* P = L.lP + 9 * item;
+      const float u0 = P[0] * r[0] + P[1] * r[1] + P[2] * r[2];
+      const float u1 = P[3] * r[0] + P[4] * r[1] + P[5] * r[2];
+      const float u2 = P[6] * r[0] + P[7] * r[1] + P[8] * r[2];
+      L.lu[k] = u0, L.lu[k + 1] = u1, L.lu[k + 2] = u2;
+      st_f4(u_ptr(sl[slot].zrec, i), u0, u1, u2);
+    }
+    for (int si = tid; si < n_scenes; si += NTP)
+      if (!st[si].done) st[si].iters += 1;
+    // (the barrier of the next publish_flag orders these updates)
+  }
+
+  // x of this CTA's rows to global memory; CTA 0 publishes the scalars
+  for (int item = tid; item < n_items; item += NTP) {
+    const int i = L.it_i[item];
+    if (i < 0) continue;
+    const float* lx = L.lx + 3 * item;
+    st_v(sl[L.it_slot[item]].dx + i, mk<float4, float>(lx[0], lx[1], lx[2]));
+  }
+  if (blockIdx.x == 0)
+    for (int si = tid; si < n_scenes; si += NTP) publish(st[si], sl[si].ctl);
+}
+
+int pcg_sr_max_grid(int device, size_t smem) {
+  const void* k = (const void*)k_pcg_sr;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NTP, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * prop.multiProcessorCount;
+}
+
+cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cudaStream_t st) {
+  if (L.n_scenes <= 0 || L.n_scenes > PCG_MAX_SCENES || L.n_tiles <= 0 || L.grid > XCH_MAX_CTAS || !L.flags)
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(L.bar, 0, sizeof(GridBar), st);
+  if (e != cudaSuccess) return e;
+  // flags and exchange words carry stamps of this launch only
+  e = cudaMemsetAsync(L.flags, 0, sizeof(unsigned long long) * L.grid, st);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < L.n_pword; ++k) {
+    e = cudaMemsetAsync(L.pword[k], 0, L.pword_bytes[k], st);
+    if (e != cudaSuccess) return e;
+  }
+  const TileRef* tiles = L.tiles;
+  int n_tiles = L.n_tiles;
+  const int* ids = L.scene_ids;
+  int n_scenes = L.n_scenes;
+  GridBar* bar = L.bar;
+  int bg = L.use_b_from_g;
+  int nb_cap = L.smem_blocks;
+  unsigned long long* flags = L.flags;
+  void* args[] = {(void*)&scenes, (void*)&tiles, (void*)&n_tiles, (void*)&ids,  (void*)&n_scenes,
+                  (void*)&bar,    (void*)&bg,    (void*)&nb_cap,  (void*)&flags};
+  const void* k = (const void*)k_pcg_sr;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel(k, dim3(L.grid), dim3(NTP), args, L.smem_bytes, st);
+}
+
+}  // namespace ppn
