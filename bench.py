@@ -116,8 +116,8 @@ def pcg_bytes_per_iter(info, fsize=4):
     return nnzb * (9 * fsize + 4) + nv * (4 + 4 * 16 + 4 * 16 + 9 * fsize + 3 * 16)
 
 
-PCG_SOURCES = ("pcg_smem.cu", "pcg_common.cuh", "common.cuh", "kernels.h")
-PCG_PROFILE = os.path.join(ROOT, "profiles", "k_pcg_s_twisting_beam_20x20x80.md")
+PCG_SOURCES = ("pcg_sr.cu", "pcg_common.cuh", "common.cuh", "kernels.h")
+PCG_PROFILE = os.path.join(ROOT, "profiles", "k_pcg_sr_twisting_beam_20x20x80.md")
 
 
 def pcg_source_hash():
@@ -263,7 +263,7 @@ def run_ours(args, rank, world, dist):
         achieved = alg_bytes / avg_s / 1e9
         peak = peaks["hbm_gbs"] if peaks else 6800.0
         prof = pcg_profile_traffic()
-        roof = {"bound": "hbm", "kernel": "k_pcg_s (resident cooperative block-Jacobi PCG)",
+        roof = {"bound": "hbm", "kernel": "k_pcg_sr (resident single-reduction block-Jacobi PCG)",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": round(prof["bytes"]) if prof else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
