@@ -312,40 +312,57 @@ struct Driver {
     return PPN_OK;
   }
 
-  // Choose the shared-memory-resident PCG when every CTA's rows fit: the
-  // single-reduction kernel for FP32 (unless PPN_PCG_STD is set), else the standard one.
+  // Choose the PCG kernel for the launch's tile table.  FP32 (unless
+  // PPN_PCG_STD is set): the single-reduction kernel, with the rows' BSR blocks
+  // resident in shared memory when they fit, else streamed from global memory.
+  // Otherwise the standard resident kernel when its layout fits, else the
+  // global-memory kernel.
   void plan_smem(const std::vector<int>& sl, const std::vector<TileRef>& tt) {
     G.pcg_smem_bytes = 0;
     G.pcg_sr = false;
     if (std::getenv("PPN_PCG_GLOBAL")) return;
     const int n_tiles = (int)tt.size();
-    const int grid = std::min(G.pcg_grid, n_tiles);
-    int max_items = 0, max_blocks = 0;
-    for (int b = 0; b < grid; ++b) {
-      const int t0 = (int)(((long long)b * n_tiles) / grid), t1 = (int)(((long long)(b + 1) * n_tiles) / grid);
-      int blocks = 0;
-      for (int t = t0; t < t1; ++t) {
-        const SceneImpl<T>& sc = *G.S[sl[tt[t].scene]];
-        const int r0 = tt[t].tile * PCG_TILE, r1 = std::min(sc.nv, r0 + PCG_TILE);
-        if (r1 > r0) blocks += (int)(sc.h_row_ptr[r1] - sc.h_row_ptr[r0]);
+    // largest rows / blocks of one CTA when n_tiles are split over `grid` CTAs
+    auto layout = [&](int grid, int& max_items, int& max_blocks) {
+      max_items = max_blocks = 0;
+      for (int b = 0; b < grid; ++b) {
+        const int t0 = (int)(((long long)b * n_tiles) / grid), t1 = (int)(((long long)(b + 1) * n_tiles) / grid);
+        int blocks = 0;
+        for (int t = t0; t < t1; ++t) {
+          const SceneImpl<T>& sc = *G.S[sl[tt[t].scene]];
+          const int r0 = tt[t].tile * PCG_TILE, r1 = std::min(sc.nv, r0 + PCG_TILE);
+          if (r1 > r0) blocks += (int)(sc.h_row_ptr[r1] - sc.h_row_ptr[r0]);
+        }
+        max_items = std::max(max_items, (t1 - t0) * PCG_TILE);
+        max_blocks = std::max(max_blocks, blocks);
       }
-      max_items = std::max(max_items, (t1 - t0) * PCG_TILE);
-      max_blocks = std::max(max_blocks, blocks);
-    }
-    int dev = 0;
+    };
+    int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
-    if (sizeof(T) == sizeof(float) && !std::getenv("PPN_PCG_STD") && grid <= 1024) {
-      const size_t pb = pcg_sr_smem_bytes(max_items, max_blocks);
-      if (pb <= (size_t)212 * 1024 && pcg_sr_max_grid(dev, pb) >= grid) {
-        G.pcg_smem_bytes = pb;
-        G.pcg_smem_blocks = max_blocks;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    int max_items = 0, max_blocks = 0;
+    if (sizeof(T) == sizeof(float) && !std::getenv("PPN_PCG_STD")) {
+      const int grid = std::min(n_tiles, std::min(n_sm, 1024));  // one CTA per SM
+      layout(grid, max_items, max_blocks);
+      const size_t res = pcg_sr_smem_bytes(max_items, max_blocks);
+      const size_t str = pcg_sr_smem_bytes(max_items, 0);
+      // PPN_PCG_STREAM: stream the blocks even when they would fit
+      const bool fit_res = !std::getenv("PPN_PCG_STREAM") && res <= (size_t)212 * 1024 &&
+                           pcg_sr_max_grid(dev, res, true) >= grid;
+      const bool fit_str = !fit_res && str <= (size_t)212 * 1024 && pcg_sr_max_grid(dev, str, false) >= grid;
+      if (fit_res || fit_str) {
+        G.pcg_smem_bytes = fit_res ? res : str;
+        G.pcg_smem_blocks = fit_res ? max_blocks : 0;  // 0: blocks streamed from global memory
         G.pcg_smem_grid = grid;
         G.pcg_sr = true;
         return;
       }
     }
+    const int grid = std::min(G.pcg_grid, n_tiles);
+    if (grid > 1024) return;
+    layout(grid, max_items, max_blocks);
     const size_t bytes = pcg_smem_bytes(max_items, max_blocks, (int)sizeof(T));
-    if (bytes > (size_t)196 * 1024 || grid > 1024) return;
+    if (bytes > (size_t)196 * 1024) return;
     const int mg = pcg_smem_max_grid(G.pcg_group, dev, bytes, (int)sizeof(T));
     if (mg < grid) return;
     G.pcg_smem_bytes = bytes;

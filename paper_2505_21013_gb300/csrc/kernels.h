@@ -59,7 +59,7 @@ size_t pcg_smem_bytes(int ni, int nb, int fsize);
 int pcg_smem_max_grid(int group, int device, size_t smem, int fsize);
 // single-reduction FP32 PCG (pcg_sr.cu): shared memory for ni rows / nb blocks, co-resident grid, launch
 size_t pcg_sr_smem_bytes(int ni, int nb);
-int pcg_sr_max_grid(int device, size_t smem);
+int pcg_sr_max_grid(int device, size_t smem, bool resident);
 cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cudaStream_t st);
 template <typename T>
 cudaError_t launch_pcg_smem(const SceneDev<T>* scenes, const PcgLaunch& L, cudaStream_t st);

@@ -16,9 +16,11 @@
 // recurrence (w is recomputed by the SpMV every iteration), which keeps the
 // FP32 iteration counts and attained residuals those of the standard kernel.
 //
-// Data.  As in the resident kernel of pcg_smem.cu: each CTA keeps its rows'
-// BSR blocks, block-Jacobi inverse and vectors x, r, u, w, p, s in shared
-// memory.  Only u crosses CTAs, through a global array.
+// Data.  Each CTA keeps its rows' block-Jacobi inverse and vectors x, r, u,
+// w, p, s in shared memory, and, when they fit (RES), its rows' BSR blocks as
+// well; otherwise the SpMV streams the blocks from global memory (L2 / HBM)
+// every iteration through the read-only path.  Only u crosses CTAs, through a
+// global array.
 //
 // Synchronisation.  A CTA publishes its u values, then a flag with the
 // iteration's stamp; before its SpMV it waits only for the flags of the CTAs
@@ -139,6 +141,7 @@ size_t pcg_sr_smem_bytes(int ni, int nb) {
          6 * up16(sizeof(float) * 3 * ni);
 }
 
+template <bool RES>
 __global__ void __launch_bounds__(NTP, 1)
     k_pcg_sr(const SceneDev<float>* scenes, const TileRef* tiles, int n_tiles, const int* scene_ids,
                int n_scenes, GridBar* bar, int b_from_g, int nb_cap, unsigned long long* flags) {
@@ -186,8 +189,8 @@ __global__ void __launch_bounds__(NTP, 1)
     L.it_i[item] = i < sl[tr.scene].nv ? i : -1;
   }
   __syncthreads();
-  // local row pointers (exclusive scan of the row lengths)
-  {
+  // local row pointers (exclusive scan of the row lengths), resident blocks only
+  if constexpr (RES) {
     int carry = 0;
     for (int base = 0; base < n_items; base += NTP) {
       const int item = base + tid;
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(NTP, 1)
     if (tid == 0) L.lrp[n_items] = carry;
     __syncthreads();
   }
-  // copy this CTA's blocks; the CTAs owning their columns bound the neighbour range
+  // copy this CTA's blocks (RES); the CTAs owning their columns bound the neighbour range
   {
     int lo = grid, hi = -1;
     for (int item = warp; item < n_items; item += NW) {
@@ -234,14 +237,16 @@ __global__ void __launch_bounds__(NTP, 1)
       if (i < 0) continue;
       const int slot = L.it_slot[item];
       const SceneLite<float>& S = sl[slot];
-      const int kb = S.row_ptr[i], ke = S.row_ptr[i + 1], lb = L.lrp[item];
+      const int kb = S.row_ptr[i], ke = S.row_ptr[i + 1];
       const size_t nb = (size_t)S.nnzb;
       for (int k = kb + lane32; k < ke; k += 32) {
-        const int b = lb + (k - kb);
         const int j = S.col[k];
-        L.lcol[b] = j;
+        if constexpr (RES) {
+          const int b = L.lrp[item] + (k - kb);
+          L.lcol[b] = j;
 #pragma unroll
-        for (int c = 0; c < 9; ++c) L.lval[9 * b + c] = S.val[c * nb + k];
+          for (int c = 0; c < 9; ++c) L.lval[9 * b + c] = S.val[c * nb + k];
+        }
         const long long gt = s_toff[slot] + j / PCG_TILE;  // tile in the launch's table
         const int owner = (int)(((gt + 1) * grid + n_tiles - 1) / n_tiles) - 1;
         lo = min(lo, owner);
@@ -349,22 +354,48 @@ __global__ void __launch_bounds__(NTP, 1)
         if (i >= 0 && !st[slot].done) {
           const SceneLite<float>& S = sl[slot];
           const float* vb = u_ptr(S.zrec, 0);
-          const int lb = L.lrp[item], le = L.lrp[item + 1];
-          for (int b0 = lb + lane; b0 < le; b0 += GP * U) {
-            float4 vj[U];
+          if constexpr (RES) {
+            const int lb = L.lrp[item], le = L.lrp[item + 1];
+            for (int b0 = lb + lane; b0 < le; b0 += GP * U) {
+              float4 vj[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-              const int b = b0 + GP * u;
-              if (b < le) vj[u] = ld_f4_cg(vb + (size_t)8 * L.lcol[b]);
+              for (int u = 0; u < U; ++u) {
+                const int b = b0 + GP * u;
+                if (b < le) vj[u] = ld_f4_cg(vb + (size_t)8 * L.lcol[b]);
+              }
+#pragma unroll
+              for (int u = 0; u < U; ++u) {
+                const int b = b0 + GP * u;
+                if (b < le) {
+                  const float* a = L.lval + 9 * b;
+                  ax += a[0] * vj[u].x + a[1] * vj[u].y + a[2] * vj[u].z;
+                  ay += a[3] * vj[u].x + a[4] * vj[u].y + a[5] * vj[u].z;
+                  az += a[6] * vj[u].x + a[7] * vj[u].y + a[8] * vj[u].z;
+                }
+              }
             }
+          } else {
+            // blocks from global memory (component-major values), read-only path
+            const int lb = S.row_ptr[i], le = S.row_ptr[i + 1];
+            const size_t nb = (size_t)S.nnzb;
+            for (int b0 = lb + lane; b0 < le; b0 += GP * U) {
+              float4 vj[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-              const int b = b0 + GP * u;
-              if (b < le) {
-                const float* a = L.lval + 9 * b;
-                ax += a[0] * vj[u].x + a[1] * vj[u].y + a[2] * vj[u].z;
-                ay += a[3] * vj[u].x + a[4] * vj[u].y + a[5] * vj[u].z;
-                az += a[6] * vj[u].x + a[7] * vj[u].y + a[8] * vj[u].z;
+              for (int u = 0; u < U; ++u) {
+                const int b = b0 + GP * u;
+                if (b < le) vj[u] = ld_f4_cg(vb + (size_t)8 * __ldg(S.col + b));
+              }
+#pragma unroll
+              for (int u = 0; u < U; ++u) {
+                const int b = b0 + GP * u;
+                if (b < le) {
+                  float a[9];
+#pragma unroll
+                  for (int c = 0; c < 9; ++c) a[c] = __ldg(S.val + c * nb + b);
+                  ax += a[0] * vj[u].x + a[1] * vj[u].y + a[2] * vj[u].z;
+                  ay += a[3] * vj[u].x + a[4] * vj[u].y + a[5] * vj[u].z;
+                  az += a[6] * vj[u].x + a[7] * vj[u].y + a[8] * vj[u].z;
+                }
               }
             }
           }
@@ -429,9 +460,17 @@ __global__ void __launch_bounds__(NTP, 1)
     const int i = item < n_items ? L.it_i[item] : -1;
     if (i >= 0) {
       const SceneLite<float>& S = sl[L.it_slot[item]];
-      const int bd = L.lrp[item] + (S.diag_idx[i] - S.row_ptr[i]);
+      float D[9];
+      if constexpr (RES) {
+        const int bd = L.lrp[item] + (S.diag_idx[i] - S.row_ptr[i]);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) D[c] = L.lval[9 * bd + c];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) D[c] = S.val[(size_t)c * S.nnzb + S.diag_idx[i]];
+      }
       float Pm[9];
-      const bool ok = spd_inv3(L.lval + 9 * bd, Pm);
+      const bool ok = spd_inv3(D, Pm);
       float* P = S.Pinv + (size_t)9 * i;
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
@@ -526,8 +565,8 @@ __global__ void __launch_bounds__(NTP, 1)
     for (int si = tid; si < n_scenes; si += NTP) publish(st[si], sl[si].ctl);
 }
 
-int pcg_sr_max_grid(int device, size_t smem) {
-  const void* k = (const void*)k_pcg_sr;
+int pcg_sr_max_grid(int device, size_t smem, bool resident) {
+  const void* k = resident ? (const void*)k_pcg_sr<true> : (const void*)k_pcg_sr<false>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -564,7 +603,8 @@ cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cud
   unsigned long long* flags = L.flags;
   void* args[] = {(void*)&scenes, (void*)&tiles, (void*)&n_tiles, (void*)&ids,  (void*)&n_scenes,
                   (void*)&bar,    (void*)&bg,    (void*)&nb_cap,  (void*)&flags};
-  const void* k = (const void*)k_pcg_sr;
+  // smem_blocks > 0: the rows' blocks are resident in shared memory
+  const void* k = nb_cap > 0 ? (const void*)k_pcg_sr<true> : (const void*)k_pcg_sr<false>;
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(k, dim3(L.grid), dim3(NTP), args, L.smem_bytes, st);

@@ -196,3 +196,17 @@ def test_tiny_meshes_and_ragged_sizes():
         assert np.abs(He - He_o).max() <= 1e-10 * np.abs(He_o).max()
         v = g.probe_assemble(x)
         assert np.abs(v - o.assemble(x)).max() <= 1e-10 * np.abs(v).max()
+
+
+def test_single_reduction_pcg_streamed_matrix_equals_resident(monkeypatch):
+    # the FP32 kernel with the BSR blocks streamed from global memory (used when the
+    # rows do not fit in shared memory) performs the same operations in the same order
+    spec = medium_spec(19)
+    vals = O.Scene.from_spec(spec).assemble(deformed(spec, 20, amp=0.3))
+    b = np.random.default_rng(21).standard_normal((spec.n_verts, 3))
+    b[spec.fixed] = 0
+    res = P.Scene.from_spec(spec, precision=P.PREC_MIXED).probe_pcg(vals, b, rel_tol=1e-6)
+    monkeypatch.setenv("PPN_PCG_STREAM", "1")
+    st = P.Scene.from_spec(spec, precision=P.PREC_MIXED).probe_pcg(vals, b, rel_tol=1e-6)
+    assert res[1] == st[1]
+    assert np.array_equal(res[0], st[0])
