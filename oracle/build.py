@@ -11,7 +11,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["snh.cpp", "tet.cpp", "eigen.cpp", "sparse.cpp", "newton.cpp"]
+SOURCES = ["snh.cpp", "tet.cpp", "eigen.cpp", "sparse.cpp", "contact.cpp", "newton.cpp"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

@@ -48,6 +48,7 @@ struct ora_scene {
   std::vector<int64_t> row_ptr;
   std::vector<int32_t> col;
   ora_params p;
+  std::vector<ora_obstacle> obst;
   ora_solve_hook hook = nullptr;
   void* hook_user = nullptr;
   std::vector<ora_iter_stats> iters;
@@ -70,6 +71,34 @@ void element(const ora_scene* s, int64_t e, const double* x, double* psi, double
   ora_tet_eval(Xc, xc, s->mu, s->lam, psi, g, H);
 }
 
+// Contact potential of one vertex at xv, summed over the obstacles: energy,
+// gradient (3) and Hessian (9), each optional.  Returns false when xv is not
+// strictly feasible (some distance <= 0); *active: some distance < dhat.
+bool vertex_contact(const ora_scene* s, const double* xv, double* E, double* g, double* H, bool* active) {
+  if (E) *E = 0.0;
+  if (g)
+    for (int k = 0; k < 3; ++k) g[k] = 0.0;
+  if (H)
+    for (int k = 0; k < 9; ++k) H[k] = 0.0;
+  if (active) *active = false;
+  const double kap = s->p.contact_kappa, dhat = s->p.contact_dhat;
+  for (const ora_obstacle& o : s->obst) {
+    double d, gd[3], Hd[9];
+    if (ora_obstacle_eval(&o, xv, &d, gd, Hd) != ORA_OK || !(d > 0.0)) return false;
+    if (d >= dhat) continue;
+    double b, db, ddb;
+    ora_barrier(d, dhat, &b, &db, &ddb);
+    if (active) *active = true;
+    if (E) *E += kap * b;
+    if (g)
+      for (int k = 0; k < 3; ++k) g[k] += kap * db * gd[k];
+    if (H)
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) H[3 * i + j] += kap * (ddb * gd[i] * gd[j] + db * Hd[3 * i + j]);
+  }
+  return true;
+}
+
 double energy(const ora_scene* s, const double* x, const double* xhat) {
   double E = 0.0;
   const double w = 0.5 / (s->dt * s->dt);
@@ -81,6 +110,12 @@ double energy(const ora_scene* s, const double* x, const double* xhat) {
       d2 += d * d;
     }
     E += w * s->mass[v] * d2;
+    if (!s->obst.empty()) {
+      double Ec;
+      if (!vertex_contact(s, x + 3 * v, &Ec, nullptr, nullptr, nullptr))
+        return std::numeric_limits<double>::infinity();  // not feasible
+      E += Ec;
+    }
   }
   for (int64_t e = 0; e < s->nt; ++e) {
     double psi;
@@ -99,6 +134,13 @@ void gradient_from(const ora_scene* s, const double* x, const double* xhat,
   for (int64_t e = 0; e < s->nt; ++e)
     for (int a = 0; a < 4; ++a)
       for (int k = 0; k < 3; ++k) g[3 * (int64_t)s->tets[4 * e + a] + k] += ge[12 * e + 3 * a + k];
+  if (!s->obst.empty())
+    for (int64_t v = 0; v < s->nv; ++v) {
+      if (s->fixed[v]) continue;
+      double gc[3];
+      vertex_contact(s, x + 3 * v, nullptr, gc, nullptr, nullptr);
+      for (int k = 0; k < 3; ++k) g[3 * v + k] += gc[k];
+    }
   for (int64_t v = 0; v < s->nv; ++v)
     if (s->fixed[v])
       for (int k = 0; k < 3; ++k) g[3 * v + k] = 0.0;
@@ -118,8 +160,11 @@ double residual_scale(const ora_scene* s, const double* x, const double* xhat, c
       for (int k = 0; k < 3; ++k) a[3 * (int64_t)s->tets[4 * e + i] + k] += std::fabs(ge[12 * e + 3 * i + k]);
   double n2 = 0.0;
   for (int64_t v = 0; v < s->nv; ++v)
-    if (!s->fixed[v])
-      for (int k = 0; k < 3; ++k) n2 += a[3 * v + k] * a[3 * v + k];
+    if (!s->fixed[v]) {
+      double gc[3] = {0, 0, 0};
+      if (!s->obst.empty()) vertex_contact(s, x + 3 * v, nullptr, gc, nullptr, nullptr);
+      for (int k = 0; k < 3; ++k) n2 += (a[3 * v + k] + std::fabs(gc[k])) * (a[3 * v + k] + std::fabs(gc[k]));
+    }
   return std::sqrt(n2);
 }
 
@@ -145,7 +190,9 @@ void scatter_element(const ora_scene* s, int64_t e, const double* M12, double* v
 }
 
 // unprojected H = M / dt^2 + sum_e S^eT H^e S^e with Dirichlet rows eliminated
-void assemble(const ora_scene* s, const std::vector<double>& He, std::vector<double>& vals) {
+// H = M / dt^2 + sum_e S^eT H^e S^e (+ the contact Hessians of the free vertices at x,
+// when x is given and the scene has obstacles); identity rows for Dirichlet vertices
+void assemble(const ora_scene* s, const double* x, const std::vector<double>& He, std::vector<double>& vals) {
   vals.assign(9 * s->col.size(), 0.0);
   for (int64_t e = 0; e < s->nt; ++e) scatter_element(s, e, &He[144 * e], vals.data());
   const double w = 1.0 / (s->dt * s->dt);
@@ -156,6 +203,11 @@ void assemble(const ora_scene* s, const std::vector<double>& He, std::vector<dou
         blk[3 * r + r] = 1.0;
       else
         blk[3 * r + r] += w * s->mass[v];
+    }
+    if (x && !s->fixed[v] && !s->obst.empty()) {
+      double Hc[9];
+      vertex_contact(s, x + 3 * v, nullptr, nullptr, Hc, nullptr);
+      for (int k = 0; k < 9; ++k) blk[k] += Hc[k];
     }
   }
 }
@@ -230,6 +282,9 @@ ora_params ora_default_params(void) {
   p.projection = ORA_PROJ_CLAMP;
   p.grad_floor = 1e-12;
   p.ls_slack = 1e-12;
+  p.contact_kappa = 1e3;
+  p.contact_dhat = 1e-3;
+  p.ccd_safety = 0.9;
   return p;
 }
 
@@ -394,7 +449,7 @@ void ora_scene_element_eval(const ora_scene* s, const double* x, double* psi_e, 
 void ora_scene_assemble(const ora_scene* s, const double* x, const uint8_t* proj, double* out) {
   std::vector<double> He(144 * s->nt), vals;
   for (int64_t e = 0; e < s->nt; ++e) element(s, e, x, nullptr, nullptr, &He[144 * e]);
-  assemble(s, He, vals);
+  assemble(s, x, He, vals);
   if (proj) {
     std::vector<double> dH(144);
     for (int64_t e = 0; e < s->nt; ++e)
@@ -426,7 +481,7 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
   const ora_params& p = s->p;
   std::vector<double> xn = s->x, vn = s->v, xhat(N), g(N), dx(N), xt(N);
   std::vector<double> He(144 * nt), ge(12 * nt), vals, dH(144);
-  std::vector<uint8_t> proj(nt), fresh(nt);
+  std::vector<uint8_t> proj(nt + nv), fresh(nt + nv);  // tets, then one contact element per vertex
   ora_scene_xhat(s, xhat.data());
   std::vector<double>& x = s->x;
   if (p.init_guess == 1)
@@ -469,18 +524,42 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
     st.grad_norm2 = gn2;
     st.grad_norminf = gninf;
 
+    // contact elements: one per free vertex within dhat of an obstacle, with its 3x3
+    // barrier Hessian (the per-vertex potential of the contact model)
+    std::vector<double> Hc;
+    std::vector<uint8_t> cact(nv, 0);
+    int n_elem = (int)nt;
+    if (!s->obst.empty()) {
+      Hc.assign(9 * (size_t)nv, 0.0);
+      for (int64_t v = 0; v < nv; ++v) {
+        if (s->fixed[v]) continue;
+        bool act = false;
+        vertex_contact(s, x.data() + 3 * v, nullptr, nullptr, &Hc[9 * v], &act);
+        cact[v] = act;
+        n_elem += act;
+      }
+    }
     // unprojected H (PN, and PDN within its countdown: every element clamped before assembly)
-    assemble(s, He, vals);
+    assemble(s, x.data(), He, vals);
     std::fill(proj.begin(), proj.end(), 0);
     int n_proj = 0;
+    auto project_one = [&](int64_t e) {  // in-place update with dH^e = Hhat^e - H^e
+      if (e < nt) {
+        ora_project(12, &He[144 * e], p.eig_eps, p.projection, nullptr, dH.data());
+        scatter_element(s, e, dH.data(), vals.data());
+      } else {
+        const int64_t v = e - nt;
+        double d3[9];
+        ora_project(3, &Hc[9 * v], p.eig_eps, p.projection, nullptr, d3);
+        double* blk = vals.data() + 9 * find_block(s, (int32_t)v, (int32_t)v);
+        for (int q = 0; q < 9; ++q) blk[q] += d3[q];
+      }
+      proj[e] = 1;
+    };
     auto project_all = [&]() {
-      for (int64_t e = 0; e < nt; ++e)
-        if (!proj[e]) {
-          ora_project(12, &He[144 * e], p.eig_eps, p.projection, nullptr, dH.data());
-          scatter_element(s, e, dH.data(), vals.data());
-          proj[e] = 1;
-        }
-      n_proj = (int)nt;
+      for (int64_t e = 0; e < nt + nv; ++e)
+        if (!proj[e] && (e < nt || cact[e - nt])) project_one(e);
+      n_proj = n_elem;
     };
     const bool pre = mode == ORA_PN || (mode == ORA_PDN && countdown > 0);
     if (pre) {
@@ -514,30 +593,36 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
       return info[1] != 0;
     };
 
-    bool ind = solve(pre ? (int)nt : 0, kInf);
+    bool ind = solve(pre ? n_elem : 0, kInf);
     bool fallback = ind && mode != ORA_PPN;
     if (mode == ORA_PDN && ind && !pre) {  // indefinite: project everything, solve again
       project_all();
-      st.n_new_projected = (int)nt;
-      ind = solve((int)nt, -1.0);
+      st.n_new_projected = n_elem;
+      ind = solve(n_elem, -1.0);
       fallback = ind;
       countdown = p.pdn_countdown;
     }
     if (mode == ORA_PPN) {
       while (ind) {
         if (delta == kInf) delta = p.alpha * gninf;
-        const int64_t n_new = select(s, g.data(), delta, proj.data(), fresh.data());
-        for (int64_t e = 0; e < nt; ++e)
-          if (fresh[e]) {
-            ora_project(12, &He[144 * e], p.eig_eps, p.projection, nullptr, dH.data());
-            scatter_element(s, e, dH.data(), vals.data());  // in-place update
-            proj[e] = 1;
+        int64_t n_new = select(s, g.data(), delta, proj.data(), fresh.data());
+        for (int64_t v = 0; v < nv; ++v) {  // contact elements: ||g_v||_inf > delta
+          const int64_t e = nt + v;
+          fresh[e] = 0;
+          if (!cact[v] || proj[e]) continue;
+          const double r = std::fmax(std::fabs(g[3 * v]), std::fmax(std::fabs(g[3 * v + 1]), std::fabs(g[3 * v + 2])));
+          if (r > delta || delta <= p.eps_delta) {
+            fresh[e] = 1;
+            ++n_new;
           }
+        }
+        for (int64_t e = 0; e < nt + nv; ++e)
+          if (fresh[e]) project_one(e);
         n_proj += (int)n_new;
         st.n_new_projected += (int)n_new;
         if (n_new > 0) ind = solve((int)n_new, delta);  // unchanged matrix: same verdict
         if (ind) {
-          if (n_proj == nt) {  // fully projected and still indefinite (rounding)
+          if (n_proj == n_elem) {  // fully projected and still indefinite (rounding)
             fallback = true;
             break;
           }
@@ -569,7 +654,16 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
     // backtracking line search for sufficient decrease (Armijo)
     const double E0 = energy(s, x.data(), xhat.data());
     st.energy = E0;
+    // intersection-based filtering: start at min(1, safety * first contact time)
     double gamma = 1.0, Et = 0.0;
+    if (!s->obst.empty()) {
+      double gmax = kInf;
+      for (int64_t v = 0; v < nv; ++v) {
+        if (s->fixed[v]) continue;
+        for (const ora_obstacle& o : s->obst) gmax = std::fmin(gmax, ora_obstacle_ccd(&o, x.data() + 3 * v, dx.data() + 3 * v));
+      }
+      gamma = std::fmin(1.0, p.ccd_safety * gmax);
+    }
     bool ok = false;
     for (int h = 0; h <= p.ls_max_halvings; ++h) {
       for (int64_t i = 0; i < N; ++i) xt[i] = x[i] + gamma * dx[i];
@@ -627,3 +721,7 @@ int ora_scene_attempts(const ora_scene* s, ora_attempt* buf, int cap) {
 }
 
 }  // extern "C"
+
+extern "C" void ora_scene_set_obstacles(ora_scene* s, const ora_obstacle* obs, int n) {
+  s->obst.assign(obs, obs + (n > 0 ? n : 0));
+}

@@ -16,6 +16,7 @@ from . import build as _build
 
 NEWTON, PN, PPN, PDN = 0, 1, 2, 3
 PROJ_CLAMP, PROJ_MIRROR = 0, 1
+OBST_PLANE, OBST_CYLINDER_IN, OBST_SPHERE_OUT = 0, 1, 2
 
 
 class Params(C.Structure):
@@ -24,7 +25,21 @@ class Params(C.Structure):
                 ("pcg_max_iter", C.c_int), ("newton_max_iter", C.c_int),
                 ("ls_max_halvings", C.c_int), ("tol_kind", C.c_int), ("init_guess", C.c_int),
                 ("pdn_countdown", C.c_int), ("projection", C.c_int), ("grad_floor", C.c_double),
-                ("ls_slack", C.c_double)]
+                ("ls_slack", C.c_double), ("contact_kappa", C.c_double), ("contact_dhat", C.c_double),
+                ("ccd_safety", C.c_double)]
+
+
+class Obstacle(C.Structure):
+    _fields_ = [("type", C.c_int), ("p", C.c_double * 3), ("a", C.c_double * 3), ("r", C.c_double)]
+
+
+def obstacle(kind, p, a=(0.0, 0.0, 0.0), r=0.0) -> Obstacle:
+    o = Obstacle()
+    o.type = kind
+    o.p[:] = [float(v) for v in p]
+    o.a[:] = [float(v) for v in a]
+    o.r = float(r)
+    return o
 
 
 class IterStats(C.Structure):
@@ -85,6 +100,10 @@ def lib():
         "ora_eigh": (I, [I, pd, pd, pd]),
         "ora_clamp": (I, [I, pd, D, pd, pd]),
         "ora_project": (I, [I, pd, D, I, pd, pd]),
+        "ora_barrier": (I, [D, D, pd, pd, pd]),
+        "ora_obstacle_eval": (I, [C.POINTER(Obstacle), pd, pd, pd, pd]),
+        "ora_obstacle_ccd": (D, [C.POINTER(Obstacle), pd, pd]),
+        "ora_scene_set_obstacles": (None, [P, C.POINTER(Obstacle), I]),
         "ora_pcg_bsr": (I, [I64, pl, pi, pd, pd, D, I, pd, C.POINTER(C.c_int)]),
         "ora_scene_create": (P, [pd, I64, pi, I64, D, D, D, D, pd, pi, I64, C.POINTER(Params)]),
         "ora_scene_destroy": (None, [P]),
@@ -189,6 +208,39 @@ def project(H, eps=1e-8, kind=PROJ_CLAMP):
     return Hh, dH
 
 
+_KINDS = {"plane": OBST_PLANE, "cylinder_in": OBST_CYLINDER_IN, "sphere_out": OBST_SPHERE_OUT}
+
+
+def obstacles_from(spec_list):
+    """ora_obstacle structs from (kind, point, axis_or_normal, radius) tuples."""
+    return [obstacle(_KINDS[k], p, a, r) for k, p, a, r in spec_list]
+
+
+def barrier(d, dhat):
+    """(b, b', b'') of the log barrier at distance d."""
+    out = [C.c_double(), C.c_double(), C.c_double()]
+    lib().ora_barrier(float(d), float(dhat), *[C.byref(o) for o in out])
+    return tuple(o.value for o in out)
+
+
+def obstacle_eval(o, x):
+    """(d, grad d, hess d) of an obstacle at point x."""
+    x = np.ascontiguousarray(x, np.float64)
+    d = C.c_double()
+    g = np.zeros(3)
+    H = np.zeros((3, 3))
+    rc = lib().ora_obstacle_eval(C.byref(o), _dp(x), C.byref(d), _dp(g), _dp(H))
+    if rc:
+        raise ValueError("obstacle evaluation failed")
+    return d.value, g, H
+
+
+def obstacle_ccd(o, x, dx):
+    x = np.ascontiguousarray(x, np.float64)
+    dx = np.ascontiguousarray(dx, np.float64)
+    return lib().ora_obstacle_ccd(C.byref(o), _dp(x), _dp(dx))
+
+
 def pcg_bsr(row_ptr, col, vals, b, rel_tol=1e-4, max_iter=1000):
     row_ptr = np.ascontiguousarray(row_ptr, np.int64)
     col = np.ascontiguousarray(col, np.int32)
@@ -255,6 +307,10 @@ class Scene:
         m = np.zeros(self.n_verts)
         lib().ora_scene_lumped_mass(self._h, _dp(m))
         return m
+
+    def set_obstacles(self, obstacles):
+        arr = (Obstacle * max(1, len(obstacles)))(*obstacles)
+        lib().ora_scene_set_obstacles(self._h, arr, len(obstacles))
 
     def set_params(self, p: Params):
         lib().ora_scene_set_params(self._h, C.byref(p))

@@ -76,7 +76,19 @@ typedef struct {
   int projection;      /* ORA_PROJ_CLAMP: max(lambda, eps); ORA_PROJ_MIRROR: max(|lambda|, eps) */
   double grad_floor;   /* tol_kind 0 also stops at ||g||_2 <= grad_floor ||s||_2 (rounding floor), default 1e-12 */
   double ls_slack;     /* Armijo test allows ls_slack |E0| of energy rounding, default 1e-12 */
+  double contact_kappa; /* barrier stiffness kappa [N/m], default 1e3 */
+  double contact_dhat;  /* barrier activation distance dhat [m], default 1e-3 */
+  double ccd_safety;    /* line search starts at min(1, ccd_safety * gamma_ccd), default 0.9 */
 } ora_params;
+
+/* analytic obstacles for frictionless log-barrier contact (contact.cpp) */
+enum { ORA_OBST_PLANE = 0, ORA_OBST_CYLINDER_IN = 1, ORA_OBST_SPHERE_OUT = 2 };
+typedef struct {
+  int type;   /* ORA_OBST_* */
+  double p[3]; /* plane point / axis point / centre */
+  double a[3]; /* plane unit normal (bodies on the positive side) / cylinder unit axis */
+  double r;    /* cylinder or sphere radius */
+} ora_obstacle;
 
 typedef struct {
   int newton_iter;
@@ -119,6 +131,8 @@ typedef struct ora_scene ora_scene;
  * delta schedule).  Return -1 to keep the real verdict, 0 or 1 to override. */
 typedef int (*ora_solve_hook)(int newton_iter, int attempt, int n_projected_total, void* user);
 
+/* obstacles of the scene (copied; replaces earlier ones; n = 0 removes contact) */
+void ora_scene_set_obstacles(ora_scene* s, const ora_obstacle* obs, int n);
 ora_params ora_default_params(void);
 const char* ora_last_error(void);
 
@@ -136,6 +150,12 @@ int ora_tet_eval(const double* X, const double* x, double mu, double lam_s,
 /* ---- dense symmetric eigen (cyclic Jacobi) and clamping ---- */
 int ora_eigh(int n, const double* A, double* w, double* Q);
 int ora_clamp(int n, const double* H, double eps, double* Hhat, double* dH);
+/* barrier b(d) and its first two derivatives; d <= 0 gives b = +inf and ORA_ERR_INVALID */
+int ora_barrier(double d, double dhat, double* b, double* db, double* ddb);
+/* distance to an obstacle with its gradient (3) and Hessian (9); any output may be NULL */
+int ora_obstacle_eval(const ora_obstacle* o, const double* x, double* d, double* grad, double* hess);
+/* first gamma > 0 at which x + gamma dx reaches the obstacle, or +infinity */
+double ora_obstacle_ccd(const ora_obstacle* o, const double* x, const double* dx);
 /* the same with a projection kind: ORA_PROJ_CLAMP or ORA_PROJ_MIRROR */
 int ora_project(int n, const double* H, double eps, int kind, double* Hhat, double* dH);
 

@@ -16,6 +16,8 @@ from .scenes import (
     serving_scenes,
     poisson_arrivals,
     tiny_scene,
+    drop_scene,
+    press_scene,
 )
 
 __all__ = [
@@ -28,4 +30,6 @@ __all__ = [
     "serving_scenes",
     "poisson_arrivals",
     "tiny_scene",
+    "drop_scene",
+    "press_scene",
 ]

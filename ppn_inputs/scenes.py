@@ -34,6 +34,9 @@ class SceneSpec:
     # targets(n) -> (n_fixed, 3) float64 positions of ``fixed`` at the end of step n
     targets: Optional[Callable[[int], np.ndarray]] = None
     meta: dict = field(default_factory=dict)
+    # obstacles(n) -> analytic surfaces at the end of step n, each a tuple
+    # (kind, point, axis_or_normal, radius) with kind "plane" | "cylinder_in" | "sphere_out"
+    obstacles: Optional[Callable[[int], list]] = None
 
     @property
     def n_verts(self) -> int:
@@ -47,6 +50,9 @@ class SceneSpec:
         if self.targets is None:
             return self.rest[self.fixed].copy()
         return np.ascontiguousarray(self.targets(n), dtype=np.float64)
+
+    def obstacles_at(self, n: int) -> list:
+        return [] if self.obstacles is None else list(self.obstacles(n))
 
 
 def _face(nx, ny, nz, axis, index):
@@ -152,3 +158,55 @@ def poisson_arrivals(rate_hz: float, n: int, seed: int = 0) -> np.ndarray:
     """Arrival times (s) of a Poisson stream."""
     rng = np.random.default_rng(seed)
     return np.cumsum(rng.exponential(1.0 / rate_hz, size=n))
+
+
+def drop_scene(cells=(3, 3, 3), size: float = 0.1, height: float = 0.002, E: float = 1e5,
+               nu: float = 0.4, rho: float = 1000.0, dt: float = 1.0 / 60.0, obstacle: str = "plane",
+               seed: int = 0, name: Optional[str] = None) -> SceneSpec:
+    """A free cube (no Dirichlet vertices) whose lowest face starts ``height`` above
+    the ground plane y = 0 and falls under gravity onto it.  ``obstacle`` = "sphere"
+    adds a sphere below the cube's centre that the cube lands on instead (its
+    contact Hessians are indefinite)."""
+    nx, ny, nz = (c + 1 for c in cells)
+    h = size / max(cells)
+    rest, tets = kuhn_grid(nx, ny, nz, h, jitter=0.01, seed=seed)
+    rest[:, 1] += height
+    centre = rest.mean(axis=0)
+    obst = [("plane", (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.0)]
+    if obstacle == "sphere":
+        r = 0.5 * size
+        obst = [("sphere_out", (centre[0], -r + 0.5 * height, centre[2]), (0.0, 0.0, 0.0), r)] + obst
+    return SceneSpec(name or f"drop{nx}x{ny}x{nz}", rest, tets, np.zeros(0, np.int32), E, nu, rho, dt,
+                     obstacles=lambda n: obst, meta={"kind": "drop", "h": h, "seed": seed})
+
+
+def press_scene(n: int = 40, boxes: int = 4, edge: float = 0.1, radius: float = 0.1, E: float = 1e5,
+                nu: float = 0.4, rho: float = 1000.0, dt: float = 1.0 / 60.0, press_speed: float = 0.05,
+                gap: float = 0.002, seed: int = 0, name: Optional[str] = None) -> SceneSpec:
+    """Stacked boxes of n^3 vertices (edge ``edge``) inside a vertical cylinder of
+    ``radius`` (axis y through the boxes' centre) on the ground plane y = 0, with a
+    press plane above them descending at ``press_speed`` (its rotation about the
+    vertical axis does not act on frictionless contact and is not modelled)."""
+    h = edge / (n - 1)
+    parts_x, parts_t = [], []
+    off = 0
+    for b in range(boxes):
+        x, t = kuhn_grid(n, n, n, h, jitter=0.005, seed=seed + b)
+        x[:, 0] -= edge / 2
+        x[:, 2] -= edge / 2
+        x[:, 1] += gap + b * (edge + gap)
+        parts_x.append(x)
+        parts_t.append(t + off)
+        off += x.shape[0]
+    rest = np.concatenate(parts_x)
+    tets = np.concatenate(parts_t).astype(np.int32)
+    top = float(rest[:, 1].max()) + gap
+
+    def obstacles(k):
+        y = top - press_speed * dt * (k + 1)
+        return [("plane", (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.0),
+                ("cylinder_in", (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), radius),
+                ("plane", (0.0, y, 0.0), (0.0, -1.0, 0.0), 0.0)]
+
+    return SceneSpec(name or f"press{boxes}x{n}", rest, tets, np.zeros(0, np.int32), E, nu, rho, dt,
+                     obstacles=obstacles, meta={"kind": "press", "h": h, "seed": seed})
