@@ -95,6 +95,9 @@ typedef struct {
   double grad_floor;   /* tol_kind 0 also stops at ||g||_2 <= grad_floor ||s||_2, s_v = m_v|x_v - xhat_v|/dt^2
                         * + sum_e |g^e_v| (the rounding floor of the residual; 1e-12) */
   double ls_slack;     /* the Armijo test allows ls_slack |E0| of energy rounding (1e-12) */
+  double contact_kappa; /* barrier stiffness kappa [N/m] of the contact potential (1e3) */
+  double contact_dhat;  /* barrier activation distance dhat [m] (1e-3) */
+  double ccd_safety;    /* the line search starts at min(1, ccd_safety x first contact time) (0.9) */
 } ppn_params;
 
 typedef struct {
@@ -227,6 +230,32 @@ PPN_API ppn_status ppn_probe_project(ppn_scene* s, const double* x, const int32_
  * side b (n_verts*3); info: [iterations, ind, precond_fail, hit_max] */
 PPN_API ppn_status ppn_probe_pcg(ppn_scene* s, const double* vals, const double* b, double rel_tol,
                          int max_iter, double* x, int* info);
+
+/* ---- Contact with analytic obstacles (the paper's frictionless IPC barrier potentials,
+ * backtracking line search with intersection-based filtering, Sec. 5.1) ----
+ *
+ * Every free vertex x gets the potential kappa b(d(x)) for each obstacle, with
+ * b(d) = -(d - dhat)^2 ln(d / dhat) for 0 < d < dhat and 0 beyond, d the distance:
+ *   PLANE        d = a . (x - p), bodies on the side the unit normal a points to
+ *   CYLINDER_IN  d = r - |(x - p) - (a . (x - p)) a|, bodies inside the cylinder of unit axis a
+ *   SPHERE_OUT   d = |x - p| - r, bodies outside the sphere
+ * A free vertex within dhat of an obstacle is one contact element of the projection
+ * heuristic (key ||g_v||_inf, 3x3 Hessian clamped like the tets' in PN/PPN/PDN).
+ * The line search starts at min(1, ccd_safety x the first time a vertex on
+ * x + gamma dx reaches an obstacle).  The state must be feasible (d > 0) when a
+ * step starts. */
+typedef enum { PPN_OBST_PLANE = 0, PPN_OBST_CYLINDER_IN = 1, PPN_OBST_SPHERE_OUT = 2 } ppn_obstacle_kind;
+typedef struct {
+  int type;    /* ppn_obstacle_kind */
+  double p[3]; /* plane point / axis point / centre [m] */
+  double a[3]; /* plane unit normal / cylinder unit axis */
+  double r;    /* cylinder or sphere radius [m] */
+} ppn_obstacle;
+#define PPN_MAX_OBSTACLES 8
+/* obstacles for the next steps (copied; n = 0 removes contact); moving obstacles
+ * are set before every step.  PPN_ERR_INVALID_ARG for n > PPN_MAX_OBSTACLES, an
+ * unknown type, a non-unit direction or a non-positive radius. */
+PPN_API ppn_status ppn_set_obstacles(ppn_scene* s, const ppn_obstacle* obs, int n);
 
 /* ---- Serving: time-step requests over resident scenes (continuous batching) ----
  *

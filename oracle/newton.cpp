@@ -48,7 +48,8 @@ struct ora_scene {
   std::vector<int64_t> row_ptr;
   std::vector<int32_t> col;
   ora_params p;
-  std::vector<ora_obstacle> obst;
+  std::vector<ora_obstacle> obst;      // applied poses (those the barrier acts with)
+  std::vector<ora_obstacle> obst_req;  // requested poses
   ora_solve_hook hook = nullptr;
   void* hook_user = nullptr;
   std::vector<ora_iter_stats> iters;
@@ -489,6 +490,29 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
       for (int k = 0; k < 3; ++k) x[3 * v + k] = xn[3 * v + k] + s->dt * vn[3 * v + k];
   for (size_t f = 0; f < s->fixed_list.size(); ++f)
     for (int k = 0; k < 3; ++k) x[3 * (int64_t)s->fixed_list[f] + k] = s->targets[3 * f + k];
+  // Moving planes: a plane advances toward the bodies by at most ccd_safety times the
+  // smallest distance of a free vertex to it; the rest of its motion waits for later
+  // steps.  Every obstacle must leave the initial iterate strictly feasible.
+  for (size_t k = 0; k < s->obst.size(); ++k) {
+    ora_obstacle& o = s->obst[k];
+    double m = kInf;
+    for (int64_t v = 0; v < nv; ++v) {
+      if (s->fixed[v]) continue;
+      double d;
+      if (ora_obstacle_eval(&o, x.data() + 3 * v, &d, nullptr, nullptr) != ORA_OK) d = -1.0;
+      m = std::fmin(m, d);
+    }
+    if (!(m > 0.0)) {
+      g_err = "the state is not feasible for obstacle " + std::to_string(k);
+      return ORA_ERR_INVALID;
+    }
+    const ora_obstacle& q = s->obst_req[k];
+    if (o.type == ORA_OBST_PLANE) {
+      const double adv = o.a[0] * (q.p[0] - o.p[0]) + o.a[1] * (q.p[1] - o.p[1]) + o.a[2] * (q.p[2] - o.p[2]);
+      const double f = adv > 0.0 ? std::fmin(1.0, p.ccd_safety * m / adv) : 1.0;
+      for (int c = 0; c < 3; ++c) o.p[c] += f * (q.p[c] - o.p[c]);
+    }
+  }
 
   s->iters.clear();
   s->attempts.clear();
@@ -722,6 +746,15 @@ int ora_scene_attempts(const ora_scene* s, ora_attempt* buf, int cap) {
 
 }  // extern "C"
 
+// Requested poses; the applied ones follow them at the next step (planes as far as
+// feasible).  A new set of a different size or kind is applied at once.
 extern "C" void ora_scene_set_obstacles(ora_scene* s, const ora_obstacle* obs, int n) {
-  s->obst.assign(obs, obs + (n > 0 ? n : 0));
+  s->obst_req.assign(obs, obs + (n > 0 ? n : 0));
+  bool same = s->obst.size() == s->obst_req.size();
+  for (size_t k = 0; same && k < s->obst.size(); ++k)
+    same = s->obst[k].type == s->obst_req[k].type && s->obst[k].a[0] == s->obst_req[k].a[0] &&
+           s->obst[k].a[1] == s->obst_req[k].a[1] && s->obst[k].a[2] == s->obst_req[k].a[2];
+  if (!same) s->obst = s->obst_req;
+  for (size_t k = 0; k < s->obst.size(); ++k)
+    if (s->obst[k].type != ORA_OBST_PLANE) s->obst[k] = s->obst_req[k];  // only planes are held back
 }

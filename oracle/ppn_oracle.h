@@ -131,7 +131,10 @@ typedef struct ora_scene ora_scene;
  * delta schedule).  Return -1 to keep the real verdict, 0 or 1 to override. */
 typedef int (*ora_solve_hook)(int newton_iter, int attempt, int n_projected_total, void* user);
 
-/* obstacles of the scene (copied; replaces earlier ones; n = 0 removes contact) */
+/* obstacles of the scene for the next step (copied).  A plane of the same normal as
+ * before is moved toward the bodies only as far as keeps the step's initial iterate
+ * feasible (ccd_safety x the smallest vertex distance); the rest follows in later
+ * steps.  A set of another size, kind or normal replaces the old one at once. */
 void ora_scene_set_obstacles(ora_scene* s, const ora_obstacle* obs, int n);
 ora_params ora_default_params(void);
 const char* ora_last_error(void);

@@ -26,12 +26,29 @@ template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = double4; };
 template <typename T> using vec4_t = typename Vec4<T>::type;
 
+// analytic obstacle of the contact model (contact.cuh)
+constexpr int OBST_PLANE = 0, OBST_CYLINDER_IN = 1, OBST_SPHERE_OUT = 2;
+constexpr int MAX_OBST = 8;
+struct ObstDev {
+  int type, pad;
+  double p[3];  // plane point / axis point / centre
+  double a[3];  // plane unit normal / cylinder unit axis
+  double r;     // radius
+};
+struct ObstSet {  // a scene's obstacles, in device memory (updated between steps)
+  int n, pad;
+  ObstDev o[MAX_OBST];
+};
+
 // Per-scene control block: written by kernels, copied to the host at sync points.
 struct Ctl {
-  double grad[3];        // ||g||_2^2, ||s||_2^2 (residual scale), ||g||_inf
+  double grad[4];        // ||g||_2^2, ||s||_2^2 (residual scale), contact elements, ||g||_inf
+  double ccd;            // 1 / (first contact time along dx), from the contact-time kernel
+  double gap[4];         // 1 / (smallest free-vertex distance) to obstacles k0..k0+3 (inf: not feasible)
   double energy[3];      // incremental potential, g^T dx, max |dx| over free vertices
   double pcg_rr0, pcg_rr, pcg_rz, pcg_dq, pcg_alpha, pcg_beta;
   int n_new;             // elements selected by the last selection
+  int n_new_c;           // contact elements selected by the last selection
   int pcg_iters;         // CG updates performed (x = sum of alpha d)
   int pcg_ind;           // negative curvature or a non-SPD diagonal block
   int pcg_precond_fail;
@@ -107,6 +124,12 @@ struct SceneDev {
   int mode;
   int proj_kind;           // ppn_projection: 0 clamp, 1 mirror
   int init_guess;          // 0: x_n ; 1: x_n + dt v_n
+  // contact against analytic obstacles
+  const ObstSet* obs;       // device: the scene's obstacles (obs->n = 0: no contact)
+  double kappa, dhat;
+  int* cproj_stamp;        // nv: Newton-iteration id at which the contact element was projected
+  int* cround_stamp;       // nv: selection round of that projection
+  T* dHc;                  // nv x 9: clamping update of the contact element
   int active;              // the scene takes part in the current launch
 };
 

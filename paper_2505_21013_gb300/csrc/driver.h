@@ -216,6 +216,7 @@ struct HostState {
   int halvings = 0;
   int countdown = 0;  // PDN: iterations left that assemble projected
   bool pre = false;   // this iteration projects every element before assembly
+  int n_elem = 0;     // elements of the current iteration: tets + contact elements
   double tol = 0;     // Newton tolerance of the current step
   ppn_iter_stats cur{};
   ppn_step_stats tot{};
@@ -397,7 +398,62 @@ struct Driver {
       launch_apply_targets<T>(G.d_desc, i, s.d_fixed_list, tg, s.nfixed, 0, G.st);
       s.ext_targets = nullptr;
     }
-    return check_launch();
+    ppn_status rc2 = check_launch();
+    if (rc2) return rc2;
+    return advance_obstacles(on);
+  }
+
+  // Feasibility of the initial iterates against the applied obstacles, and the
+  // advance of moving planes toward their requested poses (at most ccd_safety x
+  // the smallest free-vertex distance per step).
+  ppn_status advance_obstacles(const std::vector<char>& on) {
+    const int n = (int)G.S.size();
+    std::vector<char> ob(n, 0);
+    int kmax = 0;
+    for (int i = 0; i < n; ++i)
+      if (on[i] && G.S[i]->n_obst > 0) {
+        ob[i] = 1;
+        kmax = std::max(kmax, G.S[i]->n_obst);
+      }
+    if (kmax == 0) return PPN_OK;
+    G.set_active(ob);
+    ppn_status rc = G.upload_desc();
+    if (rc) return rc;
+    std::vector<std::vector<double>> gap(n, std::vector<double>(MAX_OBST, 0.0));
+    for (int k0 = 0; k0 < kmax; k0 += 4) {
+      launch_obst_gap<T>(G.d_desc, G.d_vtiles, G.n_vtiles, k0, G.st);
+      if ((rc = check_launch())) return rc;
+      if ((rc = G.sync_ctl())) return rc;
+      for (int i = 0; i < n; ++i)
+        if (ob[i])
+          for (int j = 0; j < 4 && k0 + j < MAX_OBST; ++j) gap[i][k0 + j] = G.h_ctl[i].gap[j];
+    }
+    for (int i = 0; i < n; ++i) {
+      if (!ob[i]) continue;
+      SceneImpl<T>& s = *G.S[i];
+      bool moved = false;
+      for (int k = 0; k < s.n_obst; ++k) {
+        if (!(gap[i][k] < std::numeric_limits<double>::infinity())) {
+          set_error("the state is not feasible for obstacle " + std::to_string(k));
+          H[i].status = PPN_ERR_INVALID_ARG;
+          H[i].running = false;
+          break;
+        }
+        ObstDev& o = s.obs_app.o[k];
+        const ObstDev& q = s.obs_req.o[k];
+        if (o.type != OBST_PLANE) continue;
+        const double adv = o.a[0] * (q.p[0] - o.p[0]) + o.a[1] * (q.p[1] - o.p[1]) + o.a[2] * (q.p[2] - o.p[2]);
+        const double m = gap[i][k] > 0.0 ? 1.0 / gap[i][k] : std::numeric_limits<double>::infinity();
+        const double f = adv > 0.0 ? std::min(1.0, Pi(i).ccd_safety * m / adv) : 1.0;
+        for (int c = 0; c < 3; ++c) {
+          const double pc = o.p[c] + f * (q.p[c] - o.p[c]);
+          moved |= pc != o.p[c];
+          o.p[c] = pc;
+        }
+      }
+      if (moved) PPN_CU(cudaMemcpyAsync(s.d_obs, &s.obs_app, sizeof(ObstSet), cudaMemcpyHostToDevice, G.st));
+    }
+    return PPN_OK;
   }
 
   bool any_running() const {
@@ -436,7 +492,8 @@ struct Driver {
       HostState& h = H[i];
       const Ctl& c = G.h_ctl[i];
       h.gn2 = std::sqrt(c.grad[0]);
-      h.ginf = c.grad[2];
+      h.ginf = c.grad[3];
+      h.n_elem = G.S[i]->nt + (int)c.grad[2];  // tets + contact elements
       const double floor = Pi(i).grad_floor * std::sqrt(c.grad[1]);
       h.tot.final_grad_norm2 = h.gn2;
       if (!std::isfinite(h.gn2)) {
@@ -477,7 +534,7 @@ struct Driver {
         if (pn_on[i]) G.h_desc[i].delta = -1.0;
       if ((rc = select_and_project(pn_on, true))) return rc;
       for (int i = 0; i < n; ++i)
-        if (pn_on[i]) H[i].n_proj = G.S[i]->nt;
+        if (pn_on[i]) H[i].n_proj = H[i].n_elem;
     }
     // ---- assembly and first solve
     G.set_active(solve_on);
@@ -491,7 +548,7 @@ struct Driver {
     bool any_retry = false, any_pdn = false;
     for (int i = 0; i < n; ++i) {
       if (!solve_on[i]) continue;
-      record_attempt(i, 0, H[i].pre ? G.S[i]->nt : 0, std::numeric_limits<double>::infinity());
+      record_attempt(i, 0, H[i].pre ? H[i].n_elem : 0, std::numeric_limits<double>::infinity());
       if (H[i].ind && H[i].mode == PPN_MODE_PPN) {
         retry[i] = 1;
         any_retry = true;
@@ -512,14 +569,17 @@ struct Driver {
       if ((rc = select_and_project(pdn, false))) return rc;
       G.set_active(pdn);
       if ((rc = G.upload_desc())) return rc;
-      timed(FAM_UPDATE, 0, [&] { launch_update<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st); });
+      timed(FAM_UPDATE, 0, [&] {
+          launch_update<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st);
+          if (any_obstacles(solve_on)) launch_update_contact<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st);
+        });
       if ((rc = check_launch())) return rc;
       if ((rc = solve(pdn, 1))) return rc;
       if ((rc = G.sync_ctl())) return rc;
       if ((rc = check_errors(pdn))) return rc;
       for (int i = 0; i < n; ++i)
         if (pdn[i]) {
-          record_attempt(i, 1, G.S[i]->nt, -1.0);
+          record_attempt(i, 1, H[i].n_elem, -1.0);
           H[i].countdown = Pi(i).pdn_countdown;
           if (H[i].ind) H[i].fallback = true;  // fully projected and still indefinite (rounding)
         }
@@ -538,18 +598,21 @@ struct Driver {
       std::vector<char> resolve(n, 0);
       bool any_resolve = false;
       for (int i = 0; i < n; ++i)
-        if (retry[i] && G.h_ctl[i].n_new > 0) {
+        if (retry[i] && G.h_ctl[i].n_new + G.h_ctl[i].n_new_c > 0) {
           resolve[i] = 1;
           any_resolve = true;
         }
       if (any_resolve) {
         G.set_active(resolve);
         if ((rc = G.upload_desc())) return rc;
-        timed(FAM_UPDATE, 0, [&] { launch_update<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st); });
+        timed(FAM_UPDATE, 0, [&] {
+          launch_update<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st);
+          if (any_obstacles(solve_on)) launch_update_contact<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st);
+        });
         if ((rc = check_launch())) return rc;
         if ((rc = solve(resolve, 1))) return rc;
         std::vector<int> n_new(n);
-        for (int i = 0; i < n; ++i) n_new[i] = G.h_ctl[i].n_new;
+        for (int i = 0; i < n; ++i) n_new[i] = G.h_ctl[i].n_new + G.h_ctl[i].n_new_c;
         if ((rc = G.sync_ctl())) return rc;
         if ((rc = check_errors(resolve))) return rc;
         for (int i = 0; i < n; ++i)
@@ -560,7 +623,7 @@ struct Driver {
         if (!retry[i]) continue;
         HostState& h = H[i];
         if (h.ind) {
-          if (h.n_proj >= G.S[i]->nt) {
+          if (h.n_proj >= h.n_elem) {
             h.fallback = true;  // fully projected and still indefinite (rounding)
             retry[i] = 0;
           } else {
@@ -630,6 +693,19 @@ struct Driver {
         if ((rc = energy(fb, true))) return rc;
       }
     }
+    // ---- intersection-based filtering: the first contact time along dx bounds the step
+    std::vector<double> gamma0(n, 1.0);
+    if (any_obstacles(solve_on)) {
+      std::vector<char> cc(n, 0);
+      for (int i = 0; i < n; ++i) cc[i] = solve_on[i] && G.S[i]->n_obst > 0;
+      G.set_active(cc);
+      if ((rc = G.upload_desc())) return rc;
+      launch_ccd<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st);
+      if ((rc = check_launch())) return rc;
+      if ((rc = G.sync_ctl())) return rc;
+      for (int i = 0; i < n; ++i)
+        if (cc[i] && G.h_ctl[i].ccd > 0.0) gamma0[i] = std::min(1.0, Pi(i).ccd_safety / G.h_ctl[i].ccd);
+    }
     // ---- backtracking line search (Armijo)
     std::vector<char> ls(n, 0);
     bool any_ls = false;
@@ -637,7 +713,7 @@ struct Driver {
       if (solve_on[i]) {
         ls[i] = 1;
         any_ls = true;
-        H[i].gamma = 1.0;
+        H[i].gamma = gamma0[i];
         H[i].halvings = 0;
         H[i].cur.dir_deriv = H[i].dd;
         H[i].cur.energy = H[i].E0;
@@ -784,6 +860,12 @@ struct Driver {
     return PPN_OK;
   }
 
+  bool any_obstacles(const std::vector<char>& on) const {
+    for (size_t i = 0; i < on.size(); ++i)
+      if (on[i] && G.S[i]->n_obst > 0) return true;
+    return false;
+  }
+
   // selection (delta in the descriptor; < 0 selects all) + clamping of the
   // newly selected elements.  pn: no host sync needed for the count.
   ppn_status select_and_project(const std::vector<char>& on, bool pn) {
@@ -792,8 +874,11 @@ struct Driver {
     ppn_status rc = G.upload_desc();
     if (rc) return rc;
     for (int i = 0; i < n; ++i)
-      if (on[i]) PPN_CU(cudaMemsetAsync(&G.d_ctl[i].n_new, 0, sizeof(int), G.st));
-    timed(FAM_SELECT, 0, [&] { launch_select<T>(G.d_desc, G.d_ttiles, G.n_ttiles, G.st); });
+      if (on[i]) PPN_CU(cudaMemsetAsync(&G.d_ctl[i].n_new, 0, 2 * sizeof(int), G.st));  // n_new, n_new_c
+    timed(FAM_SELECT, 0, [&] {
+      launch_select<T>(G.d_desc, G.d_ttiles, G.n_ttiles, G.st);
+      if (any_obstacles(on)) launch_select_contact<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st);  // clamps them too
+    });
     if ((rc = check_launch())) return rc;
     std::vector<TileRef> jt;
     if (pn) {
@@ -804,9 +889,9 @@ struct Driver {
       if ((rc = G.sync_ctl())) return rc;
       for (int i = 0; i < n; ++i)
         if (on[i]) {
-          const int nn = G.h_ctl[i].n_new;
-          H[i].n_proj += nn;
-          H[i].cur.n_new_projected += nn;
+          const int nn = G.h_ctl[i].n_new, nc = G.h_ctl[i].n_new_c;
+          H[i].n_proj += nn + nc;
+          H[i].cur.n_new_projected += nn + nc;
           for (int t = 0; t < (nn + PROJ_CTA - 1) / PROJ_CTA; ++t) jt.push_back({i, t});
         }
     }

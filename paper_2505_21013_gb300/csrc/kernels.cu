@@ -19,6 +19,7 @@
 //               and g^T dx, FP64 sums (line search, Sec. 5.1)
 //   small vector kernels: predictor, position update, velocity, fallback direction
 #include "common.cuh"
+#include "contact.cuh"
 #include "eigclamp.cuh"
 #include "kernels.h"
 
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(TILE) k_gradient(const SceneDev<T>* scenes, co
   const SceneDev<T>& S = scenes[tr.scene];
   if (!S.active) return;
   const int v = tr.tile * TILE + threadIdx.x;
-  double n2 = 0.0, ninf = 0.0, s2 = 0.0;
+  double n2 = 0.0, ninf = 0.0, s2 = 0.0, nc = 0.0;
   if (v < S.nv) {
     double g[3] = {0.0, 0.0, 0.0};
     if (!S.fixed[v]) {
@@ -150,6 +151,18 @@ __global__ void __launch_bounds__(TILE) k_gradient(const SceneDev<T>* scenes, co
         a[1] += fabs(ge[1]);
         a[2] += fabs(ge[2]);
       }
+      if (S.obs->n > 0) {  // barrier potentials of the analytic obstacles
+        const double4 X = ld_d4(S.X + v);
+        const double x[3] = {X.x + uv.x, X.y + uv.y, X.z + uv.z};
+        double gc[3];
+        bool act = false;
+        vertex_contact(S, x, nullptr, gc, nullptr, &act);
+        for (int k = 0; k < 3; ++k) {
+          g[k] += gc[k];
+          a[k] += fabs(gc[k]);
+        }
+        nc = act ? 1.0 : 0.0;
+      }
       s2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
     }
     st_d4(S.g + v, make_double4(g[0], g[1], g[2], 0.0));
@@ -160,13 +173,15 @@ __global__ void __launch_bounds__(TILE) k_gradient(const SceneDev<T>* scenes, co
   }
   const double s = block_sum<TILE>(n2, sm);
   const double ss = block_sum<TILE>(s2, sm);
+  const double cs = block_sum<TILE>(nc, sm);
   const double mx = block_max<TILE>(ninf, sm);
   if (threadIdx.x == 0) {
     S.vpart[4 * tr.tile + 0] = s;
     S.vpart[4 * tr.tile + 1] = ss;
-    S.vpart[4 * tr.tile + 2] = mx;
+    S.vpart[4 * tr.tile + 2] = cs;
+    S.vpart[4 * tr.tile + 3] = mx;
   }
-  finish_reduction<TILE, 3>(S.vpart, &S.ctl->tiles_done[0], S.n_vtiles, 2, S.ctl->grad, sm);
+  finish_reduction<TILE, 4>(S.vpart, &S.ctl->tiles_done[0], S.n_vtiles, 3, S.ctl->grad, sm);
 }
 
 // ------------------------------------------------------------- K3 assembly
@@ -186,7 +201,7 @@ __device__ __forceinline__ void add_elem_block(const T* rec, int a, int b, T* ac
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TILE) k_assemble(const SceneDev<T>* scenes, const TileRef* tiles) {
+__global__ void __launch_bounds__(TILE) k_assemble(const SceneDev<T>* scenes, const TileRef* tiles, int use_probe) {
   const TileRef tr = tiles[blockIdx.x];
   const SceneDev<T>& S = scenes[tr.scene];
   if (!S.active) return;
@@ -211,6 +226,17 @@ __global__ void __launch_bounds__(TILE) k_assemble(const SceneDev<T>* scenes, co
       acc[0] += m;
       acc[4] += m;
       acc[8] += m;
+      if (S.obs->n > 0) {  // contact element of vertex i (and its clamping, if projected before assembly)
+        const double4 X = ld_d4(S.X + i), u = ld_d4((use_probe ? S.u_probe : S.u) + i);
+        const double x[3] = {X.x + u.x, X.y + u.y, X.z + u.z};
+        double Hc[9];
+        vertex_contact(S, x, nullptr, nullptr, Hc, nullptr);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) acc[c] += (T)Hc[c];
+        if (S.cproj_stamp[i] == it)
+#pragma unroll
+          for (int c = 0; c < 9; ++c) acc[c] += S.dHc[(size_t)9 * i + c];
+      }
     }
   }
 #pragma unroll
@@ -306,6 +332,101 @@ __global__ void __launch_bounds__(PROJ_CTA) k_project(const SceneDev<T>* scenes,
   for (int k = 0; k < 90; ++k) dst[k] = out[k];
 }
 
+// ------------------------------------------------------ contact elements
+// Selection and clamping of contact elements (one per free vertex within dhat
+// of an obstacle): key ||g_v||_inf > delta (or delta <= eps_delta; delta < 0:
+// every contact element), not yet projected in this Newton iteration.  The
+// clamping update dHc of the vertex's 3x3 barrier Hessian is computed here.
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_select_contact(const SceneDev<T>* scenes, const TileRef* tiles) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active || S.obs->n == 0) return;
+  const int v = tr.tile * TILE + threadIdx.x;
+  if (v >= S.nv || S.fixed[v] || S.cproj_stamp[v] == S.it_id) return;
+  const bool all = S.delta < 0.0 || S.delta <= S.eps_delta;
+  if (!all && !(S.gmax[v] > S.delta)) return;
+  const double4 X = ld_d4(S.X + v), u = ld_d4(S.u + v);
+  const double x[3] = {X.x + u.x, X.y + u.y, X.z + u.z};
+  double Hc[9];
+  bool act = false;
+  vertex_contact(S, x, nullptr, nullptr, Hc, &act);
+  if (!act) return;
+  T H3[9], d3[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) H3[c] = (T)Hc[c];
+  clamp3(H3, (T)S.eig_eps, S.proj_kind == 1, d3);
+#pragma unroll
+  for (int c = 0; c < 9; ++c) S.dHc[(size_t)9 * v + c] = d3[c];
+  S.cproj_stamp[v] = S.it_id;
+  S.cround_stamp[v] = S.round_id;
+  atomicAdd(&S.ctl->n_new_c, 1);
+}
+
+// in-place update of the diagonal blocks of the contact elements selected in this round
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_update_contact(const SceneDev<T>* scenes, const TileRef* tiles) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active || S.obs->n == 0) return;
+  const int v = tr.tile * TILE + threadIdx.x;
+  if (v >= S.nv || S.fixed[v] || S.cround_stamp[v] != S.round_id || S.cproj_stamp[v] != S.it_id) return;
+  const size_t k = (size_t)S.diag_idx[v];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) S.val[(size_t)c * S.nnzb + k] += S.dHc[(size_t)9 * v + c];
+}
+
+// first contact time along dx over the free vertices and obstacles, reduced as
+// ctl->ccd = max 1 / gamma >= 0 (the reductions' max starts at 0; intersection-based
+// filtering of the line search: gamma_ccd = 1 / ctl->ccd)
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_ccd(const SceneDev<T>* scenes, const TileRef* tiles) {
+  __shared__ double sm[32];
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int v = tr.tile * TILE + threadIdx.x;
+  double inv = 0.0;
+  if (v < S.nv && !S.fixed[v]) {
+    const double4 X = ld_d4(S.X + v), u = ld_d4(S.u + v);
+    const vec4_t<T> d = S.dx[v];
+    const double x[3] = {X.x + u.x, X.y + u.y, X.z + u.z};
+    const double dx[3] = {(double)d.x, (double)d.y, (double)d.z};
+    for (int k = 0; k < S.obs->n; ++k) inv = fmax(inv, 1.0 / obst_ccd(S.obs->o[k], x, dx));
+  }
+  const double mx = block_max<TILE>(inv, sm);
+  if (threadIdx.x == 0) S.vpart[4 * tr.tile] = mx;
+  finish_reduction<TILE, 1>(S.vpart, &S.ctl->tiles_done[2], S.n_vtiles, 0, &S.ctl->ccd, sm);
+}
+
+// smallest distance of a free vertex to obstacles k0..k0+3, reduced as
+// ctl->gap[j] = max 1 / d (+inf when some vertex is not strictly feasible)
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_obst_gap(const SceneDev<T>* scenes, const TileRef* tiles, int k0) {
+  __shared__ double sm[32];
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int v = tr.tile * TILE + threadIdx.x;
+  double inv[4] = {0.0, 0.0, 0.0, 0.0};
+  if (v < S.nv && !S.fixed[v]) {
+    const double4 X = ld_d4(S.X + v), u = ld_d4(S.u + v);
+    const double x[3] = {X.x + u.x, X.y + u.y, X.z + u.z};
+    for (int j = 0; j < 4 && k0 + j < S.obs->n; ++j) {
+      double d, g[3], H[9];
+      const bool ok = obst_eval(S.obs->o[k0 + j], x, d, g, H);
+      inv[j] = ok && d > 0.0 ? 1.0 / d : std::numeric_limits<double>::infinity();
+    }
+  }
+  double mx[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) mx[j] = block_max<TILE>(inv[j], sm);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) S.vpart[4 * tr.tile + j] = mx[j];
+  finish_reduction<TILE, 4>(S.vpart, &S.ctl->tiles_done[3], S.n_vtiles, 0, S.ctl->gap, sm);
+}
+
 // ---------------------------------------------------------- K10 energy
 // tile index < n_ttiles: tet tile; otherwise vertex tile (index - n_ttiles).
 // Reductions: [0] incremental potential at u + gamma dx (FP64), [1] g^T dx,
@@ -364,6 +485,18 @@ __global__ void __launch_bounds__(TILE) k_energy(const SceneDev<T>* scenes, cons
         dmax = fmax(fabs((double)d.x), fmax(fabs((double)d.y), fabs((double)d.z)));
       }
       en = 0.5 * S.mass[v] * S.inv_dt2 * (d0 * d0 + d1 * d1 + d2 * d2);
+      if (S.obs->n > 0) {  // barrier potentials; +inf where a surface is reached
+        const double4 X = ld_d4(S.X + v);
+        double x[3] = {X.x + uv.x, X.y + uv.y, X.z + uv.z};
+        if (!use_probe && gam != 0.0) {
+          const vec4_t<T> d = S.dx[v];
+          x[0] += gam * (double)d.x;
+          x[1] += gam * (double)d.y;
+          x[2] += gam * (double)d.z;
+        }
+        double Ec;
+        en += vertex_contact(S, x, &Ec, nullptr, nullptr, nullptr) ? Ec : std::numeric_limits<double>::infinity();
+      }
     }
   }
   const double s0 = block_sum<TILE>(en, sm);
@@ -479,6 +612,22 @@ __global__ void k_fallback_dir(const SceneDev<T>* scenes, const TileRef* tiles, 
 
 // ---------------------------------------------------------------- launchers
 template <typename T>
+void launch_select_contact(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
+  if (n) k_select_contact<T><<<n, TILE, 0, st>>>(s, t);
+}
+template <typename T>
+void launch_update_contact(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
+  if (n) k_update_contact<T><<<n, TILE, 0, st>>>(s, t);
+}
+template <typename T>
+void launch_ccd(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
+  if (n) k_ccd<T><<<n, TILE, 0, st>>>(s, t);
+}
+template <typename T>
+void launch_obst_gap(const SceneDev<T>* s, const TileRef* t, int n, int k0, cudaStream_t st) {
+  if (n) k_obst_gap<T><<<n, TILE, 0, st>>>(s, t, k0);
+}
+template <typename T>
 void launch_element(const SceneDev<T>* s, const TileRef* t, int n, int probe, cudaStream_t st) {
   if (n) k_element<T><<<n, TILE, 0, st>>>(s, t, probe);
 }
@@ -487,8 +636,8 @@ void launch_gradient(const SceneDev<T>* s, const TileRef* t, int n, int probe, c
   if (n) k_gradient<T><<<n, TILE, 0, st>>>(s, t, probe);
 }
 template <typename T>
-void launch_assemble(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
-  if (n) k_assemble<T><<<n, TILE, 0, st>>>(s, t);
+void launch_assemble(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st, int use_probe) {
+  if (n) k_assemble<T><<<n, TILE, 0, st>>>(s, t, use_probe);
 }
 template <typename T>
 void launch_update(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
@@ -535,12 +684,16 @@ void launch_fallback(const SceneDev<T>* s, const TileRef* t, int n, int kind, cu
 #define PPN_INST(T)                                                                            \
   template void launch_element<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
   template void launch_gradient<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
-  template void launch_assemble<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);     \
+  template void launch_assemble<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t, int); \
   template void launch_update<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \
   template void launch_select<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \
   template void launch_project<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
   template void launch_energy<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);  \
   template void launch_predict<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \
+  template void launch_select_contact<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \
+  template void launch_update_contact<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \
+  template void launch_ccd<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \
+  template void launch_obst_gap<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
   template void launch_apply_targets<T>(const SceneDev<T>*, int, const int*, const double*, int, \
                                         int, cudaStream_t);                                    \
   template void launch_axpy_u<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \

@@ -11,12 +11,18 @@ constexpr int PROJ_CTA = 128;  // threads per CTA of the projection kernel (regi
 
 template <typename T> void launch_element(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
 template <typename T> void launch_gradient(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
-template <typename T> void launch_assemble(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
+template <typename T> void launch_assemble(const SceneDev<T>*, const TileRef*, int, cudaStream_t, int use_probe = 0);
 template <typename T> void launch_update(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
 template <typename T> void launch_select(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
 template <typename T> void launch_project(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
 template <typename T> void launch_energy(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
 template <typename T> void launch_predict(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
+// contact elements (vertex tiles): selection + clamping, in-place update, first contact time
+template <typename T> void launch_select_contact(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
+template <typename T> void launch_update_contact(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
+template <typename T> void launch_ccd(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
+// smallest free-vertex distance to obstacles k0..k0+3 (ctl->gap)
+template <typename T> void launch_obst_gap(const SceneDev<T>*, const TileRef*, int, int k0, cudaStream_t);
 template <typename T>
 void launch_apply_targets(const SceneDev<T>*, int, const int*, const double*, int, int, cudaStream_t);
 template <typename T> void launch_gmax(const SceneDev<T>*, const TileRef*, int, cudaStream_t);

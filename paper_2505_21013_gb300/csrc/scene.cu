@@ -363,6 +363,11 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   s.gmax = alloc<double>(nv);
   s.val = alloc<T>((size_t)9 * nnzb);
   s.proj_stamp = alloc<int>(nt);
+  s.cproj_stamp = alloc<int>(nv);
+  d_obs = alloc<ObstSet>(1);
+  s.obs = d_obs;
+  s.cround_stamp = alloc<int>(nv);
+  s.dHc = alloc<T>((size_t)9 * nv);
   s.round_stamp = alloc<int>(nt);
   s.sel_list = alloc<int>(nt);
   s.dx = alloc<V4>(nv);
@@ -397,7 +402,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   if (!d_tets || !d_tetc || !d_mass || !d_fixed || !d_X || !d_vt_ptr || !d_vt_src || !d_row_ptr ||
       !d_col || !d_blk_row || !d_blk_ptr || !d_blk_src || !d_diag || !s.u || !s.u_n || !s.vel ||
       !s.uhat || !s.u_probe || !s.ge || !s.He || !s.dH || !s.g || !s.gmax || !s.val ||
-      !s.proj_stamp || !s.round_stamp || !s.sel_list || !s.dx || !s.r || !s.z || !s.q || !s.d0 ||
+      !s.proj_stamp || !s.round_stamp || !s.cproj_stamp || !d_obs || !s.cround_stamp || !s.dHc || !s.sel_list || !s.dx || !s.r || !s.z || !s.q || !s.d0 ||
       !s.d1 || !s.Pinv || !s.vpart || !s.tpart || !s.ppart || !s.pword || (sizeof(T) == 4 && !s.zrec) || !s.ctl || !d_desc || !d_ids ||
       !d_bar || !d_fixed_list || !d_targets || !d_xyz || !d_ttiles || !d_vtiles || !d_btiles ||
       !d_ptiles || !d_etiles || !d_projtiles) {
@@ -440,6 +445,9 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   PPN_CU(cudaMemset(s.vel, 0, sizeof(double4) * nv));
   PPN_CU(cudaMemset(s.dx, 0, sizeof(V4) * nv));
   PPN_CU(cudaMemset(s.proj_stamp, 0xff, sizeof(int) * nt));
+  PPN_CU(cudaMemset(s.cproj_stamp, 0xff, sizeof(int) * nv));
+  PPN_CU(cudaMemset(d_obs, 0, sizeof(ObstSet)));
+  PPN_CU(cudaMemset(s.cround_stamp, 0xff, sizeof(int) * nv));
   PPN_CU(cudaMemset(s.round_stamp, 0xff, sizeof(int) * nt));
   PPN_CU(cudaMemset(s.ctl, 0, sizeof(Ctl)));
   PPN_CU(cudaMemset(s.vpart, 0, sizeof(double) * 4 * n_vtiles));
@@ -463,6 +471,8 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   for (int k = 0; k < 3; ++k) s.grav[k] = params.gravity[k];
   s.eps_delta = params.eps_delta;
   s.eig_eps = params.eig_eps;
+  s.kappa = params.contact_kappa;
+  s.dhat = params.contact_dhat;
   s.proj_kind = params.projection;
   s.init_guess = params.init_guess;
   s.delta = std::numeric_limits<double>::infinity();
@@ -647,7 +657,7 @@ static ppn_status probe_gradient(SceneImpl<T>& s, const double* x, const double*
   if ((rc = p.G->sync_ctl())) return rc;
   if (norms) {
     norms[0] = std::sqrt(p.G->h_ctl[0].grad[0]);
-    norms[1] = p.G->h_ctl[0].grad[2];
+    norms[1] = p.G->h_ctl[0].grad[3];
   }
   if (energy) *energy = p.G->h_ctl[0].energy[0];
   if (g) {
@@ -705,7 +715,7 @@ static ppn_status probe_assemble(SceneImpl<T>& s, const double* x, const uint8_t
       }
   PPN_CU(cudaMemcpyAsync(s.d.proj_stamp, stamp.data(), sizeof(int) * s.nt, cudaMemcpyHostToDevice, s.stream));
   if ((rc = probe_clamp_list(s, p, sel))) return rc;
-  launch_assemble<T>(p.G->d_desc, p.G->d_btiles, p.G->n_btiles, s.stream);
+  launch_assemble<T>(p.G->d_desc, p.G->d_btiles, p.G->n_btiles, s.stream, 1);
   PPN_CU(cudaGetLastError());
   PPN_CU(cudaStreamSynchronize(s.stream));
   return read_bsr(s, vals);
@@ -852,6 +862,9 @@ ppn_params ppn_default_params(void) {
   p.projection = PPN_PROJ_CLAMP;
   p.grad_floor = 1e-12;
   p.ls_slack = 1e-12;
+  p.contact_kappa = 1e3;
+  p.contact_dhat = 1e-3;
+  p.ccd_safety = 0.9;
   p.pcg_rel_tol = 1e-4;
   p.armijo_c = 1e-4;
   p.gravity[0] = 0.0;
@@ -958,6 +971,49 @@ ppn_status ppn_set_kinematic_targets(ppn_scene* s, const double* xyz) {
     PPN_CU(cudaMemcpyAsync(x.d_targets, xyz, sizeof(double) * 3 * x.nfixed, cudaMemcpyHostToDevice, x.stream));
     PPN_CU(cudaStreamSynchronize(x.stream));
     x.ext_targets = nullptr;
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_set_obstacles(ppn_scene* s, const ppn_obstacle* obs, int n) {
+  if (n < 0 || n > PPN_MAX_OBSTACLES || (n > 0 && !obs)) {
+    set_error("obstacle count out of range");
+    return PPN_ERR_INVALID_ARG;
+  }
+  ObstSet h{};
+  h.n = n;
+  for (int k = 0; k < n; ++k) {
+    const ppn_obstacle& o = obs[k];
+    const double na = std::sqrt(o.a[0] * o.a[0] + o.a[1] * o.a[1] + o.a[2] * o.a[2]);
+    const bool dir = o.type == PPN_OBST_SPHERE_OUT || std::fabs(na - 1.0) < 1e-9;
+    const bool rad = o.type == PPN_OBST_PLANE || o.r > 0.0;
+    if (o.type < PPN_OBST_PLANE || o.type > PPN_OBST_SPHERE_OUT || !dir || !rad) {
+      set_error("invalid obstacle " + std::to_string(k) + " (type, unit direction, radius)");
+      return PPN_ERR_INVALID_ARG;
+    }
+    h.o[k].type = o.type;
+    for (int c = 0; c < 3; ++c) {
+      h.o[k].p[c] = o.p[c];
+      h.o[k].a[c] = o.a[c];
+    }
+    h.o[k].r = o.r;
+  }
+  // Requested poses.  A plane of the same normal as before is moved toward the
+  // bodies at the next step only as far as keeps that step's initial iterate
+  // feasible (ccd_safety x the smallest vertex distance), the rest in later steps;
+  // other obstacles, and a set of another size, kind or normal, apply at once.
+  return dispatch(s, [&](auto& x) {
+    bool same = x.obs_app.n == n;
+    for (int k = 0; same && k < n; ++k)
+      same = x.obs_app.o[k].type == h.o[k].type && x.obs_app.o[k].a[0] == h.o[k].a[0] &&
+             x.obs_app.o[k].a[1] == h.o[k].a[1] && x.obs_app.o[k].a[2] == h.o[k].a[2];
+    x.obs_req = h;
+    if (!same) x.obs_app = h;
+    for (int k = 0; k < n; ++k)
+      if (h.o[k].type != PPN_OBST_PLANE) x.obs_app.o[k] = h.o[k];
+    PPN_CU(cudaStreamSynchronize(x.stream));
+    PPN_CU(cudaMemcpy(x.d_obs, &x.obs_app, sizeof(ObstSet), cudaMemcpyHostToDevice));
+    x.n_obst = n;
     return PPN_OK;
   });
 }

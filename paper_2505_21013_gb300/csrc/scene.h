@@ -83,6 +83,9 @@ struct SceneImpl {
   double* d_targets = nullptr;
   const double* ext_targets = nullptr;  // device targets given by the caller for the next step
   double* d_xyz = nullptr;              // nv x 3 output staging
+  ObstSet* d_obs = nullptr;             // the scene's obstacles as applied (device)
+  int n_obst = 0;                       // host copy of their count
+  ObstSet obs_app{}, obs_req{};         // applied and requested poses (host)
   Ctl* h_ctl = nullptr;                 // pinned
   cudaStream_t stream = nullptr;
   bool own_stream = false;

@@ -35,7 +35,28 @@ class ppn_params(C.Structure):
                 ("gravity", C.c_double * 3), ("pcg_max_iter", C.c_int), ("newton_max_iter", C.c_int),
                 ("ls_max_halvings", C.c_int), ("precision", C.c_int), ("tol_kind", C.c_int),
                 ("init_guess", C.c_int), ("pdn_countdown", C.c_int), ("projection", C.c_int),
-                ("grad_floor", C.c_double), ("ls_slack", C.c_double)]
+                ("grad_floor", C.c_double), ("ls_slack", C.c_double), ("contact_kappa", C.c_double),
+                ("contact_dhat", C.c_double), ("ccd_safety", C.c_double)]
+
+
+class ppn_obstacle(C.Structure):
+    _fields_ = [("type", C.c_int), ("p", C.c_double * 3), ("a", C.c_double * 3), ("r", C.c_double)]
+
+
+OBST_KINDS = {"plane": 0, "cylinder_in": 1, "sphere_out": 2}
+
+
+def obstacles_from(spec_list):
+    """ppn_obstacle structs from (kind, point, axis_or_normal, radius) tuples."""
+    out = []
+    for kind, p, a, r in spec_list:
+        o = ppn_obstacle()
+        o.type = OBST_KINDS[kind]
+        o.p[:] = [float(v) for v in p]
+        o.a[:] = [float(v) for v in a]
+        o.r = float(r)
+        out.append(o)
+    return out
 
 
 class ppn_iter_stats(C.Structure):
@@ -129,6 +150,7 @@ SIGNATURES = {
     "ppn_server_poll": (_st, [_P, C.c_int64, C.c_int, C.POINTER(C.c_int), _pd, C.POINTER(ppn_step_stats),
                               C.POINTER(ppn_request_times)]),
     "ppn_server_get_stats": (_st, [_P, C.POINTER(ppn_server_stats)]),
+    "ppn_set_obstacles": (_st, [_P, C.POINTER(ppn_obstacle), C.c_int]),
     "ppn_pcg_solve_static": (_st, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                    C.c_void_p, C.c_double, C.c_int32, C.POINTER(C.c_int32), C.c_void_p]),
 }
@@ -245,6 +267,12 @@ class Scene:
     def set_targets(self, xyz):
         xyz = _arr(xyz, np.float64)
         _check(lib().ppn_set_kinematic_targets(self._h, _d(xyz)), "ppn_set_kinematic_targets")
+
+    def set_obstacles(self, spec_list):
+        """Obstacles as (kind, point, axis_or_normal, radius) tuples (see include/ppn.h)."""
+        obs = obstacles_from(spec_list)
+        arr = (ppn_obstacle * max(1, len(obs)))(*obs)
+        _check(lib().ppn_set_obstacles(self._h, arr, len(obs)), "ppn_set_obstacles")
 
     def set_targets_device(self, ptr: int):
         _check(lib().ppn_set_kinematic_targets_device(self._h, C.c_void_p(ptr)),

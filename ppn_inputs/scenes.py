@@ -180,21 +180,29 @@ def drop_scene(cells=(3, 3, 3), size: float = 0.1, height: float = 0.002, E: flo
                      obstacles=lambda n: obst, meta={"kind": "drop", "h": h, "seed": seed})
 
 
-def press_scene(n: int = 40, boxes: int = 4, edge: float = 0.1, radius: float = 0.1, E: float = 1e5,
+def press_scene(n: int = 40, boxes: int = 4, edge: float = 0.06, radius: float = 0.1, E: float = 1e5,
                 nu: float = 0.4, rho: float = 1000.0, dt: float = 1.0 / 60.0, press_speed: float = 0.05,
                 gap: float = 0.002, seed: int = 0, name: Optional[str] = None) -> SceneSpec:
-    """Stacked boxes of n^3 vertices (edge ``edge``) inside a vertical cylinder of
-    ``radius`` (axis y through the boxes' centre) on the ground plane y = 0, with a
-    press plane above them descending at ``press_speed`` (its rotation about the
-    vertical axis does not act on frictionless contact and is not modelled)."""
+    """Boxes of n^3 vertices (edge ``edge``) side by side on a square grid with
+    ``gap`` between them, standing on the ground plane y = 0 inside a vertical
+    cylinder of ``radius`` (axis y through the grid's centre), under a press plane
+    that starts ``gap`` above them and descends at ``press_speed``.  (Boxes do not
+    touch each other: contact is with the analytic obstacles only.  The press's
+    rotation about the vertical axis does not act on frictionless contact.)
+    ``obstacles_at(-1)`` is the initial pose."""
     h = edge / (n - 1)
+    k = int(np.ceil(np.sqrt(boxes)))
+    width = k * edge + (k - 1) * gap
+    if np.hypot(width / 2, width / 2) >= radius - gap:
+        raise ValueError("the boxes do not fit inside the cylinder")
     parts_x, parts_t = [], []
     off = 0
     for b in range(boxes):
+        i, j = b % k, b // k
         x, t = kuhn_grid(n, n, n, h, jitter=0.005, seed=seed + b)
-        x[:, 0] -= edge / 2
-        x[:, 2] -= edge / 2
-        x[:, 1] += gap + b * (edge + gap)
+        x[:, 0] += -width / 2 + i * (edge + gap)
+        x[:, 2] += -width / 2 + j * (edge + gap)
+        x[:, 1] += gap
         parts_x.append(x)
         parts_t.append(t + off)
         off += x.shape[0]
@@ -202,8 +210,8 @@ def press_scene(n: int = 40, boxes: int = 4, edge: float = 0.1, radius: float = 
     tets = np.concatenate(parts_t).astype(np.int32)
     top = float(rest[:, 1].max()) + gap
 
-    def obstacles(k):
-        y = top - press_speed * dt * (k + 1)
+    def obstacles(step):
+        y = top - press_speed * dt * (step + 1)
         return [("plane", (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.0),
                 ("cylinder_in", (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), radius),
                 ("plane", (0.0, y, 0.0), (0.0, -1.0, 0.0), 0.0)]

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
-from ppn_inputs import drop_scene
+from ppn_inputs import drop_scene, press_scene
 
 DHAT = 1e-3
 
@@ -150,3 +150,25 @@ def test_convex_obstacle_contact_is_projected_by_pn_and_ppn():
         totals[mode] = tot
     assert totals[O.PN] > 25 * spec.n_tets  # tets plus contact elements every iteration
     assert totals[O.PPN] < totals[O.PN]
+
+
+def test_moving_press_plane_is_held_back_by_the_bodies():
+    # the press plane may advance toward the bodies by at most ccd_safety x the smallest
+    # vertex distance per step, so the state stays feasible although the requested
+    # motion (5 mm per step) is larger than the gap the bodies leave
+    spec = press_scene(n=5, boxes=4, press_speed=0.3, dt=1 / 60, seed=1)
+    sc = O.Scene.from_spec(spec)
+    sc.set_obstacles(O.obstacles_from(spec.obstacles_at(-1)))
+    top0 = spec.rest[:, 1].max()
+    for n in range(12):
+        sc.set_obstacles(O.obstacles_from(spec.obstacles_at(n)))
+        rc, x, st = sc.step(O.PPN, 1e-6)
+        assert rc == 0
+        assert x[:, 1].min() > 0 and (np.hypot(x[:, 0], x[:, 2]) < 0.1).all()
+    assert x[:, 1].max() < top0 - 0.003  # compressed by the press
+    assert x[:, 1].max() > spec.obstacles_at(11)[2][1][1]  # which lags behind its requested pose
+    # a state that an obstacle does not leave feasible is rejected
+    bad = O.Scene.from_spec(spec)
+    bad.set_obstacles(O.obstacles_from([("plane", (0.0, 0.01, 0.0), (0.0, 1.0, 0.0), 0.0)]))
+    rc, _, _ = bad.step(O.PPN, 1e-6)
+    assert rc == 1
