@@ -449,6 +449,73 @@ def run_ablation(steps=8, tol=1e-4):
             "default_over_best": round(default["ms"] / best["ms"], 3)}
 
 
+def run_contact(steps=10, warmup=3, n=40, tol=1e-4):
+    """Large contact-rich workload: 4 boxes of n^3 vertices side by side in a
+    rigid analytic cylinder (radius 0.1 m) on the ground plane, under a press
+    plane descending at 0.05 m/s, frictionless log-barrier contact (dhat = 1 mm),
+    dt = 1/60, mixed precision.  Device time per step by CUDA events on the
+    scene's stream (inputs resident; obstacle poses are a few hundred bytes
+    per step), PPN and PN from the same initial state."""
+    import torch
+
+    import paper_2505_21013_gb300 as P
+    from ppn_inputs import press_scene
+
+    spec = press_scene(n=n, boxes=4, press_speed=0.05, dt=1.0 / 60.0, seed=0)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {"scene": f"press_4x{n}^3", "n_verts": spec.n_verts, "n_tets": spec.n_tets, "steps": steps,
+           "warmup": warmup, "dhat_m": 1e-3, "l2": "flushed between steps (256 MB write)"}
+
+    def run(mode, profile=False):
+        sc = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
+        sc.set_stream(stream.cuda_stream)
+        sc.set_obstacles(spec.obstacles_at(-1))
+        lat, newton, proj, cg = [], 0, 0, 0
+        for k in range(warmup + steps):
+            if profile and k == warmup:
+                torch.cuda.synchronize()
+                sc.set_profiling(True)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            sc.set_obstacles(spec.obstacles_at(k))
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            rc, x, st = sc.step(mode, tol, want_x=k == warmup + steps - 1)
+            ev1.record(stream)
+            if rc != 0:
+                raise RuntimeError(f"contact step {k} returned status {rc}")
+            ev1.synchronize()
+            if k >= warmup:
+                lat.append(ev0.elapsed_time(ev1))
+                newton += st["newton_iters"]
+                proj += st["total_projections"]
+                cg += st["total_cg_iters"]
+        info, kt = sc.info(), sc.kernel_times() if profile else None
+        sc.close()
+        r = {"steps_per_s": steps / (sum(lat) / 1e3), "ms_per_step": sum(lat) / steps,
+             "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99), "newton_iters": newton,
+             "projections": proj, "cg_iters": cg, "min_height_m": float(x[:, 1].min()),
+             "top_m": float(x[:, 1].max()), "nnzb": info["nnzb"]}
+        return r, info, kt
+
+    out["ppn"], info, _ = run(P.MODE_PPN)
+    out["pn"], _, _ = run(P.MODE_PN)
+    # per-family device time of the same PPN steps (an untimed pass: the events add host work)
+    prof, _, kt = run(P.MODE_PPN, profile=True)
+    out["kernel_ms"] = {k: round(v["total_ms"], 3) for k, v in kt.items()}
+    pcg = kt["pcg"]
+    if prof["cg_iters"]:
+        us = pcg["total_ms"] * 1e3 / prof["cg_iters"]
+        peak = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
+        gbs = pcg_bytes_per_iter(info) / (us * 1e-6) / 1e9
+        out["pcg"] = {"launches": pcg["launches"], "cg_iters": prof["cg_iters"], "us_per_cg_iter": round(us, 2),
+                      "algorithmic_gb_per_iter": round(pcg_bytes_per_iter(info) / 1e9, 4),
+                      "achieved_gbs": round(gbs, 1), "hbm_frac_of_measured": round(gbs / peak, 4)}
+    out["speedup_ppn_vs_pn"] = out["ppn"]["steps_per_s"] / out["pn"]["steps_per_s"]
+    return out
+
+
 def oracle_sample(max_seconds=25.0):
     """Time the FP64 oracle on the first PPN steps of the same beam (bounded)."""
     from oracle import oracle as O
@@ -476,8 +543,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppn-only", action="store_true", help="skip the PN comparison run")
-    ap.add_argument("--workload", default="beam", choices=["beam", "batched", "serving", "ablation"],
-                    help="beam: the headline line; batched / serving: the multi-scene workloads")
+    ap.add_argument("--workload", default="beam", choices=["beam", "batched", "serving", "ablation", "contact"],
+                    help="beam: the headline line; batched / serving: the multi-scene workloads; "
+                         "ablation: the alpha/beta sweep; contact: boxes under a press in a cylinder")
     ap.add_argument("--profile-pcg", type=int, default=0, metavar="ITERS",
                     help="run fixed-length PCG solves for an ncu capture instead of the benchmark")
     args = ap.parse_args()
@@ -488,7 +556,10 @@ def main():
         import torch
 
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-        r = {"batched": run_batched, "serving": run_serving, "ablation": run_ablation}[args.workload]()
+        if args.workload == "contact":
+            r = run_contact(steps=args.steps, warmup=args.warmup)
+        else:
+            r = {"batched": run_batched, "serving": run_serving, "ablation": run_ablation}[args.workload]()
         if int(os.environ.get("RANK", 0)) == 0:
             print(json.dumps({"workload": args.workload, **r}))
         return

@@ -15,6 +15,8 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -30,6 +32,42 @@ namespace ppn {
       return _e == cudaErrorMemoryAllocation ? PPN_ERR_OOM : PPN_ERR_CUDA;                \
     }                                                                                     \
   } while (0)
+
+// Online choice between the two streamed layouts of the single-reduction FP32
+// PCG (vectors in shared memory with the blocks streamed, or everything in
+// global memory), which give bitwise-identical results.  Per shape class (CTA
+// tiles, blocks per row) the first launches alternate the layouts, each timed
+// by CUDA events on the launching stream; later launches take the layout with
+// the smaller time per CG iteration.  Shared by all groups of the process.
+struct PcgTuner {
+  static constexpr int kExplore = 3;  // timed launches per layout before choosing
+  struct Rec {
+    double ms[2] = {0.0, 0.0};
+    long long iters[2] = {0, 0};
+    int n[2] = {0, 0};
+  };
+  std::mutex mu;
+  std::map<std::pair<int, int>, Rec> recs;
+  // 0: SR_STREAM, 1: SR_GLOBAL
+  int choose(std::pair<int, int> key) {
+    std::lock_guard<std::mutex> lk(mu);
+    const Rec& r = recs[key];
+    if (r.n[0] < kExplore || r.n[1] < kExplore) return r.n[0] <= r.n[1] ? 0 : 1;
+    return r.ms[0] / (double)r.iters[0] <= r.ms[1] / (double)r.iters[1] ? 0 : 1;
+  }
+  void report(std::pair<int, int> key, int k, double ms, long long iters) {
+    if (iters <= 0 || !(ms > 0.0)) return;
+    std::lock_guard<std::mutex> lk(mu);
+    Rec& r = recs[key];
+    r.ms[k] += ms;
+    r.iters[k] += iters;
+    r.n[k] += 1;
+  }
+};
+inline PcgTuner& pcg_tuner() {
+  static PcgTuner t;
+  return t;
+}
 
 template <typename T>
 struct Group {
@@ -50,6 +88,15 @@ struct Group {
   size_t pcg_smem_bytes = 0;  // > 0: resident PCG layout chosen for that table
   int pcg_smem_blocks = 0, pcg_smem_grid = 0;
   bool pcg_sr = false;          // the single-reduction FP32 kernel was chosen for that table
+  int pcg_sr_mode = 0;          // its layout (SR_RES, SR_STREAM, SR_GLOBAL)
+  // layout chosen per launch by the tuner (SR_STREAM and SR_GLOBAL both fit)
+  bool pcg_tune = false;
+  std::pair<int, int> tune_key{0, 0};
+  size_t tune_bytes[2] = {0, 0};  // dynamic shared memory of SR_STREAM, SR_GLOBAL
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+  bool tune_pending = false;      // a timed launch awaits its sync
+  int tune_choice = 0;
+  std::vector<int> tune_slots;
   unsigned long long* d_flags = nullptr;  // its per-CTA publication flags
   GridBar* d_bar = nullptr;
   cudaStream_t st = nullptr;
@@ -59,9 +106,14 @@ struct Group {
   std::vector<void*> allocs;
   // capacities of the device tables (a group can be rebuilt for new members)
   size_t cap_n = 0, cap_tt = 0, cap_vt = 0, cap_bt = 0, cap_pt = 0, cap_et = 0, cap_proj = 0;
-  ~Group() { release(); }
+  ~Group() {
+    release();
+    for (cudaEvent_t& e : tune_ev)
+      if (e) cudaEventDestroy(e);
+  }
   void release() {
     if (st) cudaStreamSynchronize(st);
+    tune_pending = false;
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
     if (h_ctl) cudaFreeHost(h_ctl);
@@ -195,6 +247,17 @@ struct Group {
     PPN_CU(cudaStreamSynchronize(st));
     staging.reset();
     if (timer) timer->collect();
+    if (tune_pending) {  // the timed PCG launch has finished: its time per CG iteration
+      tune_pending = false;
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, tune_ev[0], tune_ev[1]) == cudaSuccess) {
+        int it = 0;
+        for (int k : tune_slots) it = std::max(it, h_ctl[k].pcg_iters);
+        pcg_tuner().report(tune_key, tune_choice, ms, it);
+      } else {
+        cudaGetLastError();
+      }
+    }
     return PPN_OK;
   }
   void set_active(const std::vector<char>& on) {
@@ -287,6 +350,19 @@ struct Driver {
       L.use_b_from_g = b_from_g;
       L.smem_bytes = G.pcg_smem_bytes;
       L.smem_blocks = G.pcg_smem_blocks;
+      L.sr_mode = G.pcg_sr_mode;
+      const bool tune = G.pcg_sr && G.pcg_tune && ids.size() <= (size_t)PCG_MAX_SCENES;
+      if (tune) {
+        G.tune_choice = pcg_tuner().choose(G.tune_key);
+        L.sr_mode = G.tune_choice ? SR_GLOBAL : SR_STREAM;
+        L.smem_bytes = G.tune_bytes[G.tune_choice];
+        for (cudaEvent_t& e : G.tune_ev)
+          if (!e && cudaEventCreate(&e) != cudaSuccess) {
+            set_error("cudaEventCreate failed");
+            return PPN_ERR_CUDA;
+          }
+        PPN_CU(cudaEventRecord(G.tune_ev[0], G.st));
+      }
       L.launch_seq = ++G.pcg_launch_seq;
       L.flags = G.d_flags;
       L.n_pword = (int)sl.size();
@@ -309,18 +385,24 @@ struct Driver {
         set_error(std::string("PCG launch: ") + cudaGetErrorString(err));
         return PPN_ERR_CUDA;
       }
+      if (tune) {
+        PPN_CU(cudaEventRecord(G.tune_ev[1], G.st));
+        G.tune_pending = true;
+        G.tune_slots = sl;
+      }
     }
     return PPN_OK;
   }
 
   // Choose the PCG kernel for the launch's tile table.  FP32 (unless
   // PPN_PCG_STD is set): the single-reduction kernel, with the rows' BSR blocks
-  // resident in shared memory when they fit, else streamed from global memory.
-  // Otherwise the standard resident kernel when its layout fits, else the
-  // global-memory kernel.
+  // and vectors resident in shared memory when they fit, else the vectors
+  // alone, else neither.  Otherwise the standard resident kernel when its
+  // layout fits, else the global-memory kernel.
   void plan_smem(const std::vector<int>& sl, const std::vector<TileRef>& tt) {
     G.pcg_smem_bytes = 0;
     G.pcg_sr = false;
+    G.pcg_tune = false;
     if (std::getenv("PPN_PCG_GLOBAL")) return;
     const int n_tiles = (int)tt.size();
     // largest rows / blocks of one CTA when n_tiles are split over `grid` CTAs
@@ -345,17 +427,31 @@ struct Driver {
     if (sizeof(T) == sizeof(float) && !std::getenv("PPN_PCG_STD")) {
       const int grid = std::min(n_tiles, std::min(n_sm, 1024));  // one CTA per SM
       layout(grid, max_items, max_blocks);
-      const size_t res = pcg_sr_smem_bytes(max_items, max_blocks);
-      const size_t str = pcg_sr_smem_bytes(max_items, 0);
-      // PPN_PCG_STREAM: stream the blocks even when they would fit
-      const bool fit_res = !std::getenv("PPN_PCG_STREAM") && res <= (size_t)212 * 1024 &&
-                           pcg_sr_max_grid(dev, res, true) >= grid;
-      const bool fit_str = !fit_res && str <= (size_t)212 * 1024 && pcg_sr_max_grid(dev, str, false) >= grid;
-      if (fit_res || fit_str) {
-        G.pcg_smem_bytes = fit_res ? res : str;
-        G.pcg_smem_blocks = fit_res ? max_blocks : 0;  // 0: blocks streamed from global memory
+      // blocks resident when they fit; otherwise the streamed layouts, chosen per
+      // launch by the tuner when both fit (PPN_PCG_STREAM / PPN_PCG_SR_GLOBAL:
+      // start at the streamed / global layout, no tuning)
+      const bool f_str = std::getenv("PPN_PCG_STREAM") != nullptr, f_gl = std::getenv("PPN_PCG_SR_GLOBAL") != nullptr;
+      const int first = f_gl ? SR_GLOBAL : f_str ? SR_STREAM : SR_RES;
+      bool fits[3] = {false, false, false};
+      size_t bytes[3];
+      for (int mode = first; mode <= SR_GLOBAL; ++mode) {
+        bytes[mode] = pcg_sr_smem_bytes(max_items, mode == SR_RES ? max_blocks : 0, mode);
+        fits[mode] = bytes[mode] <= (size_t)212 * 1024 && pcg_sr_max_grid(dev, bytes[mode], mode) >= grid;
+        if (fits[mode] && (mode == SR_RES || f_str || f_gl)) break;
+      }
+      for (int mode = first; mode <= SR_GLOBAL; ++mode) {
+        if (!fits[mode]) continue;
+        G.pcg_smem_bytes = bytes[mode];
+        G.pcg_smem_blocks = mode == SR_RES ? max_blocks : 0;
         G.pcg_smem_grid = grid;
         G.pcg_sr = true;
+        G.pcg_sr_mode = mode;
+        G.pcg_tune = mode == SR_STREAM && fits[SR_GLOBAL];
+        if (G.pcg_tune) {
+          G.tune_key = {(max_items + PCG_TILE - 1) / PCG_TILE, max_blocks / std::max(1, max_items)};
+          G.tune_bytes[0] = bytes[SR_STREAM];
+          G.tune_bytes[1] = bytes[SR_GLOBAL];
+        }
         return;
       }
     }

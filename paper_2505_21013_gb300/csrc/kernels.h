@@ -52,6 +52,7 @@ struct PcgLaunch {
   int use_b_from_g;      // 1: b = -g of the scene; 0: b given in r (probe)
   size_t smem_bytes;     // > 0: shared-memory-resident kernel with this dynamic size
   int smem_blocks;       // block capacity of that layout (max blocks of one CTA)
+  int sr_mode;           // single-reduction kernel: SR_RES, SR_STREAM or SR_GLOBAL
   unsigned launch_seq;
   unsigned long long* flags;  // single-reduction kernel: per-CTA publication flags (grid words)
   int n_pword;           // stamped partial arrays to clear before the launch
@@ -63,9 +64,13 @@ struct PcgLaunch {
 size_t pcg_smem_bytes(int ni, int nb, int fsize);
 // co-resident grid of the resident PCG kernel with `smem` dynamic bytes (0: does not fit)
 int pcg_smem_max_grid(int group, int device, size_t smem, int fsize);
-// single-reduction FP32 PCG (pcg_sr.cu): shared memory for ni rows / nb blocks, co-resident grid, launch
-size_t pcg_sr_smem_bytes(int ni, int nb);
-int pcg_sr_max_grid(int device, size_t smem, bool resident);
+// single-reduction FP32 PCG (pcg_sr.cu).  Layouts: BSR blocks and vectors in
+// shared memory (SR_RES); vectors in shared memory, blocks streamed (SR_STREAM);
+// both in global memory (SR_GLOBAL).  Shared memory for ni rows / nb blocks,
+// co-resident grid, launch.
+constexpr int SR_RES = 0, SR_STREAM = 1, SR_GLOBAL = 2;
+size_t pcg_sr_smem_bytes(int ni, int nb, int mode);
+int pcg_sr_max_grid(int device, size_t smem, int mode);
 cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cudaStream_t st);
 template <typename T>
 cudaError_t launch_pcg_smem(const SceneDev<T>* scenes, const PcgLaunch& L, cudaStream_t st);

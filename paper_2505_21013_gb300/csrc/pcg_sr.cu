@@ -16,11 +16,14 @@
 // recurrence (w is recomputed by the SpMV every iteration), which keeps the
 // FP32 iteration counts and attained residuals those of the standard kernel.
 //
-// Data.  Each CTA keeps its rows' block-Jacobi inverse and vectors x, r, u,
-// w, p, s in shared memory, and, when they fit (RES), its rows' BSR blocks as
-// well; otherwise the SpMV streams the blocks from global memory (L2 / HBM)
-// every iteration through the read-only path.  Only u crosses CTAs, through a
-// global array.
+// Data.  Three layouts (SR_RES, SR_STREAM, SR_GLOBAL).  SR_RES and SR_STREAM
+// keep each CTA's rows' block-Jacobi inverse and vectors x, r, u, w, p, s in
+// shared memory; SR_RES also keeps the rows' BSR blocks there, SR_STREAM
+// streams them from global memory (L2 / HBM) every iteration through the
+// read-only path.  SR_GLOBAL, for rows that do not fit, keeps the vectors in
+// the scene's global PCG arrays as well (x in dx, r in z, w in q, p in d0,
+// s in d1, the inverse in Pinv), each row touched only by its own CTA.  In
+// every layout only u crosses CTAs, through a global array.
 //
 // Synchronisation.  A CTA publishes its u values, then a flag with the
 // iteration's stamp; before its SpMV it waits only for the flags of the CTAs
@@ -39,41 +42,44 @@ using namespace pcgdev;
 namespace {
 
 constexpr int NTP = 512;  // threads per CTA
-constexpr int GP = 2;     // lanes per BSR row in the SpMV
 constexpr int NQ = 4;     // reduction slots: gamma, delta, rho, failed diagonal blocks
 
 struct SrLayout {
-  float* lws;  // [(ni / PCG_TILE + 1) * 16 * NQ] per-warp partial sums (16 warps per pass cover 4 tiles)
-  int* it_i;
-  int* it_slot;
-  int* lrp;
-  int* lcol;
-  float* lval;
-  float* lP;
-  float *lx, *lr, *lu, *lw, *lp, *ls;  // [ni * 3] each
+  float* lws;    // [(ni / PCG_TILE + 1) * 16 * NQ] per-warp partial sums (16 warps per pass cover 4 tiles)
+  TileRef* ltt;  // [ni / PCG_TILE + 1] the CTA's tiles
+  int* lrp;      // SR_RES: [ni + 1] local row pointers
+  int* lcol;     // SR_RES: [nb]
+  float* lval;   // SR_RES: [nb * 9]
+  float* lP;     // SR_RES, SR_STREAM: [ni * 9]
+  float *lx, *lr, *lu, *lw, *lp, *ls;  // SR_RES, SR_STREAM: [ni * 3] each
 };
 
 __host__ __device__ inline size_t up16(size_t b) { return (b + 15) & ~size_t(15); }
 
-__device__ __forceinline__ SrLayout carve_sr(char* base, int ni, int nb) {
-  SrLayout L;
+// the layout's pieces in carving order (nullptr base: sizes only)
+__host__ __device__ inline size_t carve_sr(char* base, int ni, int nb, int mode, SrLayout* L) {
   const int ntl = ni / PCG_TILE + 1;
   size_t off = 0;
   auto take = [&](size_t bytes) {
-    char* p = base + off;
+    char* p = base ? base + off : nullptr;
     off += up16(bytes);
     return p;
   };
-  L.lws = (float*)take(sizeof(float) * ntl * 16 * NQ);
-  L.it_i = (int*)take(sizeof(int) * ni);
-  L.it_slot = (int*)take(sizeof(int) * ni);
-  L.lrp = (int*)take(sizeof(int) * (ni + 1));
-  L.lcol = (int*)take(sizeof(int) * nb);
-  L.lval = (float*)take(sizeof(float) * 9 * nb);
-  L.lP = (float*)take(sizeof(float) * 9 * ni);
-  float** v[6] = {&L.lx, &L.lr, &L.lu, &L.lw, &L.lp, &L.ls};
-  for (float** p : v) *p = (float*)take(sizeof(float) * 3 * ni);
-  return L;
+  SrLayout l{};
+  l.lws = (float*)take(sizeof(float) * ntl * 16 * NQ);
+  l.ltt = (TileRef*)take(sizeof(TileRef) * ntl);
+  if (mode == SR_RES) {
+    l.lrp = (int*)take(sizeof(int) * (ni + 1));
+    l.lcol = (int*)take(sizeof(int) * nb);
+    l.lval = (float*)take(sizeof(float) * 9 * nb);
+  }
+  if (mode != SR_GLOBAL) {
+    l.lP = (float*)take(sizeof(float) * 9 * ni);
+    float** v[6] = {&l.lx, &l.lr, &l.lu, &l.lw, &l.lp, &l.ls};
+    for (float** q : v) *q = (float*)take(sizeof(float) * 3 * ni);
+  }
+  if (L) *L = l;
+  return off;
 }
 
 // u of row i: the first four floats of the row's 32-byte record in zrec
@@ -134,18 +140,15 @@ __device__ __forceinline__ void sr_step(SState<float>& s, float gam, float del, 
 
 }  // namespace
 
-size_t pcg_sr_smem_bytes(int ni, int nb) {
-  const size_t ntl = ni / PCG_TILE + 1;
-  return up16(sizeof(float) * ntl * 16 * NQ) + 2 * up16(sizeof(int) * ni) + up16(sizeof(int) * (ni + 1)) +
-         up16(sizeof(int) * nb) + up16(sizeof(float) * 9 * nb) + up16(sizeof(float) * 9 * ni) +
-         6 * up16(sizeof(float) * 3 * ni);
-}
+size_t pcg_sr_smem_bytes(int ni, int nb, int mode) { return carve_sr(nullptr, ni, nb, mode, nullptr); }
 
-template <bool RES>
+template <int MODE>
 __global__ void __launch_bounds__(NTP, 1)
     k_pcg_sr(const SceneDev<float>* scenes, const TileRef* tiles, int n_tiles, const int* scene_ids,
                int n_scenes, GridBar* bar, int b_from_g, int nb_cap, unsigned long long* flags) {
   using W = Words<float>;
+  constexpr bool RES = MODE == SR_RES, GV = MODE == SR_GLOBAL;
+  constexpr int GP = 2;                 // lanes per BSR row in the SpMV
   constexpr int RPP = NTP / GP;         // rows per SpMV pass
   constexpr int U = 16 / GP;            // blocks per lane per gather round
   constexpr int NW = NTP / 32;          // warps
@@ -164,7 +167,8 @@ __global__ void __launch_bounds__(NTP, 1)
   const int t1 = (int)(((long long)(blockIdx.x + 1) * n_tiles) / grid);
   const int ntl = t1 - t0;
   const int n_items = ntl * PCG_TILE;
-  const SrLayout L = carve_sr(dyn, n_items, nb_cap);
+  SrLayout L;
+  carve_sr(dyn, n_items, nb_cap, MODE, &L);
   if (tid == 0) {
     s_to = 0;
     s_lo = grid;
@@ -174,6 +178,7 @@ __global__ void __launch_bounds__(NTP, 1)
     load_lite(sl[si], scenes[scene_ids[si]]);
     st[si].done = 0;
   }
+  for (int lt = tid; lt < ntl; lt += NTP) L.ltt[lt] = tiles[t0 + lt];
   __syncthreads();
   if (tid == 0) {
     int o = 0;
@@ -182,12 +187,13 @@ __global__ void __launch_bounds__(NTP, 1)
       o += sl[si].n_ptiles;
     }
   }
-  for (int item = tid; item < n_items; item += NTP) {
-    const TileRef tr = tiles[t0 + item / PCG_TILE];
-    const int i = tr.tile * PCG_TILE + (item % PCG_TILE);
-    L.it_slot[item] = tr.scene;
-    L.it_i[item] = i < sl[tr.scene].nv ? i : -1;
-  }
+  // row of a local item (-1: past the scene's last row) and its slot
+  auto row_of = [&](int item, int& slot) -> int {
+    const TileRef tr = L.ltt[item / PCG_TILE];
+    slot = tr.scene;
+    const int i = tr.tile * PCG_TILE + item % PCG_TILE;
+    return i < sl[slot].nv ? i : -1;
+  };
   __syncthreads();
   // local row pointers (exclusive scan of the row lengths), resident blocks only
   if constexpr (RES) {
@@ -196,11 +202,9 @@ __global__ void __launch_bounds__(NTP, 1)
       const int item = base + tid;
       int len = 0;
       if (item < n_items) {
-        const int i = L.it_i[item];
-        if (i >= 0) {
-          const SceneLite<float>& S = sl[L.it_slot[item]];
-          len = S.row_ptr[i + 1] - S.row_ptr[i];
-        }
+        int slot;
+        const int i = row_of(item, slot);
+        if (i >= 0) len = sl[slot].row_ptr[i + 1] - sl[slot].row_ptr[i];
       }
       int v = len;
 #pragma unroll
@@ -233,9 +237,9 @@ __global__ void __launch_bounds__(NTP, 1)
   {
     int lo = grid, hi = -1;
     for (int item = warp; item < n_items; item += NW) {
-      const int i = L.it_i[item];
+      int slot;
+      const int i = row_of(item, slot);
       if (i < 0) continue;
-      const int slot = L.it_slot[item];
       const SceneLite<float>& S = sl[slot];
       const int kb = S.row_ptr[i], ke = S.row_ptr[i + 1];
       const size_t nb = (size_t)S.nnzb;
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(NTP, 1)
 
   // ---------------- exchange helpers
   auto post_tile = [&](int lt, int k, float v, unsigned s) {
-    const TileRef tr = tiles[t0 + lt];
+    const TileRef tr = L.ltt[lt];
     const SceneLite<float>& S = sl[tr.scene];
     unsigned long long w[1];
     W::split(v, s, w);
@@ -342,60 +346,58 @@ __global__ void __launch_bounds__(NTP, 1)
     __syncthreads();
     return !s_to;
   };
-  // w = A u over this CTA's rows, u gathered from the global array (G lanes per row)
-  auto spmv = [&](float* ly) {
+  // w = A u over this CTA's rows, u gathered from the global array (GP lanes per row)
+  auto spmv = [&]() {
     for (int base = 0; base < n_items; base += RPP) {
       const int row = tid / GP, lane = tid % GP;
       const int item = base + row;
       float ax = 0.f, ay = 0.f, az = 0.f;
-      if (item < n_items) {
-        const int i = L.it_i[item];
-        const int slot = L.it_slot[item];
-        if (i >= 0 && !st[slot].done) {
-          const SceneLite<float>& S = sl[slot];
-          const float* vb = u_ptr(S.zrec, 0);
-          if constexpr (RES) {
-            const int lb = L.lrp[item], le = L.lrp[item + 1];
-            for (int b0 = lb + lane; b0 < le; b0 += GP * U) {
-              float4 vj[U];
+      int slot = 0, i = -1;
+      if (item < n_items) i = row_of(item, slot);
+      if (i >= 0 && !st[slot].done) {
+        const SceneLite<float>& S = sl[slot];
+        const float* vb = u_ptr(S.zrec, 0);
+        if constexpr (RES) {
+          const int lb = L.lrp[item], le = L.lrp[item + 1];
+          for (int b0 = lb + lane; b0 < le; b0 += GP * U) {
+            float4 vj[U];
 #pragma unroll
-              for (int u = 0; u < U; ++u) {
-                const int b = b0 + GP * u;
-                if (b < le) vj[u] = ld_f4_cg(vb + (size_t)8 * L.lcol[b]);
-              }
+            for (int u = 0; u < U; ++u) {
+              const int b = b0 + GP * u;
+              if (b < le) vj[u] = ld_f4_cg(vb + (size_t)8 * L.lcol[b]);
+            }
 #pragma unroll
-              for (int u = 0; u < U; ++u) {
-                const int b = b0 + GP * u;
-                if (b < le) {
-                  const float* a = L.lval + 9 * b;
-                  ax += a[0] * vj[u].x + a[1] * vj[u].y + a[2] * vj[u].z;
-                  ay += a[3] * vj[u].x + a[4] * vj[u].y + a[5] * vj[u].z;
-                  az += a[6] * vj[u].x + a[7] * vj[u].y + a[8] * vj[u].z;
-                }
+            for (int u = 0; u < U; ++u) {
+              const int b = b0 + GP * u;
+              if (b < le) {
+                const float* a = L.lval + 9 * b;
+                ax += a[0] * vj[u].x + a[1] * vj[u].y + a[2] * vj[u].z;
+                ay += a[3] * vj[u].x + a[4] * vj[u].y + a[5] * vj[u].z;
+                az += a[6] * vj[u].x + a[7] * vj[u].y + a[8] * vj[u].z;
               }
             }
-          } else {
-            // blocks from global memory (component-major values), read-only path
-            const int lb = S.row_ptr[i], le = S.row_ptr[i + 1];
-            const size_t nb = (size_t)S.nnzb;
-            for (int b0 = lb + lane; b0 < le; b0 += GP * U) {
-              float4 vj[U];
+          }
+        } else {
+          // blocks from global memory (component-major values), read-only path
+          const int lb = S.row_ptr[i], le = S.row_ptr[i + 1];
+          const size_t nb = (size_t)S.nnzb;
+          for (int b0 = lb + lane; b0 < le; b0 += GP * U) {
+            float4 vj[U];
 #pragma unroll
-              for (int u = 0; u < U; ++u) {
-                const int b = b0 + GP * u;
-                if (b < le) vj[u] = ld_f4_cg(vb + (size_t)8 * __ldg(S.col + b));
-              }
+            for (int u = 0; u < U; ++u) {
+              const int b = b0 + GP * u;
+              if (b < le) vj[u] = ld_f4_cg(vb + (size_t)8 * __ldg(S.col + b));
+            }
 #pragma unroll
-              for (int u = 0; u < U; ++u) {
-                const int b = b0 + GP * u;
-                if (b < le) {
-                  float a[9];
+            for (int u = 0; u < U; ++u) {
+              const int b = b0 + GP * u;
+              if (b < le) {
+                float a[9];
 #pragma unroll
-                  for (int c = 0; c < 9; ++c) a[c] = __ldg(S.val + c * nb + b);
-                  ax += a[0] * vj[u].x + a[1] * vj[u].y + a[2] * vj[u].z;
-                  ay += a[3] * vj[u].x + a[4] * vj[u].y + a[5] * vj[u].z;
-                  az += a[6] * vj[u].x + a[7] * vj[u].y + a[8] * vj[u].z;
-                }
+                for (int c = 0; c < 9; ++c) a[c] = __ldg(S.val + c * nb + b);
+                ax += a[0] * vj[u].x + a[1] * vj[u].y + a[2] * vj[u].z;
+                ay += a[3] * vj[u].x + a[4] * vj[u].y + a[5] * vj[u].z;
+                az += a[6] * vj[u].x + a[7] * vj[u].y + a[8] * vj[u].z;
               }
             }
           }
@@ -408,9 +410,13 @@ __global__ void __launch_bounds__(NTP, 1)
         az += __shfl_down_sync(0xffffffffu, az, o, GP);
       }
       if (lane == 0 && item < n_items) {
-        ly[3 * item] = ax;
-        ly[3 * item + 1] = ay;
-        ly[3 * item + 2] = az;
+        if constexpr (GV) {
+          if (i >= 0) st_f4(reinterpret_cast<float*>(sl[slot].q + i), ax, ay, az);
+        } else {
+          L.lw[3 * item] = ax;
+          L.lw[3 * item + 1] = ay;
+          L.lw[3 * item + 2] = az;
+        }
       }
     }
     __syncthreads();
@@ -421,15 +427,30 @@ __global__ void __launch_bounds__(NTP, 1)
     for (int base = 0; base < n_items; base += NTP) {
       const int item = base + tid;
       float g = 0.f, d = 0.f, rr = 0.f;
-      const int i = item < n_items ? L.it_i[item] : -1;
-      const int slot = item < n_items ? L.it_slot[item] : 0;
+      int slot = 0;
+      const int i = item < n_items ? row_of(item, slot) : -1;
       if (i >= 0 && !st[slot].done) {
-        const int k = 3 * item;
-        const float r0 = L.lr[k], r1 = L.lr[k + 1], r2 = L.lr[k + 2];
-        const float u0 = L.lu[k], u1 = L.lu[k + 1], u2 = L.lu[k + 2];
-        g = r0 * u0 + r1 * u1 + r2 * u2;
-        d = L.lw[k] * u0 + L.lw[k + 1] * u1 + L.lw[k + 2] * u2;
-        rr = r0 * r0 + r1 * r1 + r2 * r2;
+        float r[3], u[3], w[3];
+        if constexpr (GV) {
+          const SceneLite<float>& S = sl[slot];
+          const float4 rv = ld_f4_cg(reinterpret_cast<const float*>(S.z + i));
+          const float4 uv = ld_f4_cg(u_ptr(S.zrec, i));
+          const float4 wv = ld_f4_cg(reinterpret_cast<const float*>(S.q + i));
+          r[0] = rv.x, r[1] = rv.y, r[2] = rv.z;
+          u[0] = uv.x, u[1] = uv.y, u[2] = uv.z;
+          w[0] = wv.x, w[1] = wv.y, w[2] = wv.z;
+        } else {
+          const int k = 3 * item;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            r[c] = L.lr[k + c];
+            u[c] = L.lu[k + c];
+            w[c] = L.lw[k + c];
+          }
+        }
+        g = r[0] * u[0] + r[1] * u[1] + r[2] * u[2];
+        d = w[0] * u[0] + w[1] * u[1] + w[2] * u[2];
+        rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
       }
       g = warp_sum(g);
       d = warp_sum(d);
@@ -443,7 +464,7 @@ __global__ void __launch_bounds__(NTP, 1)
     }
     __syncthreads();
     for (int lt = tid; lt < ntl; lt += NTP) {
-      if (st[L.it_slot[lt * PCG_TILE]].done) continue;
+      if (st[L.ltt[lt].scene].done) continue;
       const float* w = L.lws + NQ * 4 * lt;
       const int nq = with_fail ? NQ : 3;
       for (int q = 0; q < nq; ++q) post_tile(lt, q, ((w[q] + w[NQ + q]) + w[2 * NQ + q]) + w[3 * NQ + q], stamp);
@@ -457,9 +478,10 @@ __global__ void __launch_bounds__(NTP, 1)
   for (int base = 0; base < n_items; base += NTP) {
     const int item = base + tid;
     float fail = 0.0f;
-    const int i = item < n_items ? L.it_i[item] : -1;
+    int slot = 0;
+    const int i = item < n_items ? row_of(item, slot) : -1;
     if (i >= 0) {
-      const SceneLite<float>& S = sl[L.it_slot[item]];
+      const SceneLite<float>& S = sl[slot];
       float D[9];
       if constexpr (RES) {
         const int bd = L.lrp[item] + (S.diag_idx[i] - S.row_ptr[i]);
@@ -475,7 +497,7 @@ __global__ void __launch_bounds__(NTP, 1)
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
         P[c] = Pm[c];
-        L.lP[9 * item + c] = Pm[c];
+        if constexpr (!GV) L.lP[9 * item + c] = Pm[c];
       }
       float r0, r1, r2;
       if (b_from_g) {
@@ -493,11 +515,18 @@ __global__ void __launch_bounds__(NTP, 1)
       const float u1 = Pm[3] * r0 + Pm[4] * r1 + Pm[5] * r2;
       const float u2 = Pm[6] * r0 + Pm[7] * r1 + Pm[8] * r2;
       st_f4(u_ptr(S.zrec, i), u0, u1, u2);
-      const int k = 3 * item;
-      L.lr[k] = r0, L.lr[k + 1] = r1, L.lr[k + 2] = r2;
-      L.lu[k] = u0, L.lu[k + 1] = u1, L.lu[k + 2] = u2;
+      if constexpr (GV) {
+        st_f4(reinterpret_cast<float*>(S.z + i), r0, r1, r2);
+        st_f4(reinterpret_cast<float*>(S.dx + i), 0.f, 0.f, 0.f);
+        st_f4(reinterpret_cast<float*>(S.d0 + i), 0.f, 0.f, 0.f);
+        st_f4(reinterpret_cast<float*>(S.d1 + i), 0.f, 0.f, 0.f);
+      } else {
+        const int k = 3 * item;
+        L.lr[k] = r0, L.lr[k + 1] = r1, L.lr[k + 2] = r2;
+        L.lu[k] = u0, L.lu[k + 1] = u1, L.lu[k + 2] = u2;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) L.lx[k + c] = L.lp[k + c] = L.ls[k + c] = 0.0f;
+        for (int c = 0; c < 3; ++c) L.lx[k + c] = L.lp[k + c] = L.ls[k + c] = 0.0f;
+      }
       fail = ok ? 0.0f : 1.0f;
     }
     fail = warp_sum(fail);
@@ -508,7 +537,7 @@ __global__ void __launch_bounds__(NTP, 1)
     // ---- u released to the neighbours (set-up wrote u_0; later iterations below)
     publish_flag((unsigned long long)it + 1);
     if (!wait_flags((unsigned long long)it + 1)) return fail_out();
-    spmv(L.lw);  // w = A u
+    spmv();  // w = A u
     const unsigned s = W::stamp((unsigned)it + 1);
     post_partials(s, it == 0);
     if (!reduce(it == 0 ? NQ : 3, s)) return fail_out();
@@ -526,47 +555,80 @@ __global__ void __launch_bounds__(NTP, 1)
     if (s_all_done) break;
     // ---- p = u + beta p, s = w + beta s; x += alpha p, r -= alpha s, u = M r (published)
     for (int item = tid; item < n_items; item += NTP) {
-      const int i = L.it_i[item];
-      const int slot = L.it_slot[item];
+      int slot;
+      const int i = row_of(item, slot);
       if (i < 0 || st[slot].done) continue;
       const float a = st[slot].alpha, b = st[slot].beta;
-      const int k = 3 * item;
-      float r[3];
+      const SceneLite<float>& S = sl[slot];
+      float r[3], P[9];
+      if constexpr (GV) {
+        const float4 uv = ld_f4_cg(u_ptr(S.zrec, i));
+        const float4 pv = ld_f4_cg(reinterpret_cast<const float*>(S.d0 + i));
+        const float4 wv = ld_f4_cg(reinterpret_cast<const float*>(S.q + i));
+        const float4 sv = ld_f4_cg(reinterpret_cast<const float*>(S.d1 + i));
+        const float4 xv = ld_f4_cg(reinterpret_cast<const float*>(S.dx + i));
+        const float4 rv = ld_f4_cg(reinterpret_cast<const float*>(S.z + i));
+        const float p0 = uv.x + b * pv.x, p1 = uv.y + b * pv.y, p2 = uv.z + b * pv.z;
+        const float s0 = wv.x + b * sv.x, s1 = wv.y + b * sv.y, s2 = wv.z + b * sv.z;
+        st_f4(reinterpret_cast<float*>(S.d0 + i), p0, p1, p2);
+        st_f4(reinterpret_cast<float*>(S.d1 + i), s0, s1, s2);
+        st_f4(reinterpret_cast<float*>(S.dx + i), xv.x + a * p0, xv.y + a * p1, xv.z + a * p2);
+        r[0] = rv.x - a * s0;
+        r[1] = rv.y - a * s1;
+        r[2] = rv.z - a * s2;
+        st_f4(reinterpret_cast<float*>(S.z + i), r[0], r[1], r[2]);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float p = L.lu[k + c] + b * L.lp[k + c];
-        const float sv = L.lw[k + c] + b * L.ls[k + c];
-        L.lp[k + c] = p;
-        L.ls[k + c] = sv;
-        L.lx[k + c] += a * p;
-        r[c] = L.lr[k + c] - a * sv;
-        L.lr[k + c] = r[c];
+        for (int c = 0; c < 9; ++c) P[c] = __ldcg(S.Pinv + (size_t)9 * i + c);
+      } else {
+        const int k = 3 * item;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float p = L.lu[k + c] + b * L.lp[k + c];
+          const float sv = L.lw[k + c] + b * L.ls[k + c];
+          L.lp[k + c] = p;
+          L.ls[k + c] = sv;
+          L.lx[k + c] += a * p;
+          r[c] = L.lr[k + c] - a * sv;
+          L.lr[k + c] = r[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) P[c] = L.lP[9 * item + c];
       }
-      const float* P = L.lP + 9 * item;
       const float u0 = P[0] * r[0] + P[1] * r[1] + P[2] * r[2];
       const float u1 = P[3] * r[0] + P[4] * r[1] + P[5] * r[2];
       const float u2 = P[6] * r[0] + P[7] * r[1] + P[8] * r[2];
-      L.lu[k] = u0, L.lu[k + 1] = u1, L.lu[k + 2] = u2;
-      st_f4(u_ptr(sl[slot].zrec, i), u0, u1, u2);
+      if constexpr (!GV) {
+        const int k = 3 * item;
+        L.lu[k] = u0, L.lu[k + 1] = u1, L.lu[k + 2] = u2;
+      }
+      st_f4(u_ptr(S.zrec, i), u0, u1, u2);
     }
     for (int si = tid; si < n_scenes; si += NTP)
       if (!st[si].done) st[si].iters += 1;
     // (the barrier of the next publish_flag orders these updates)
   }
 
-  // x of this CTA's rows to global memory; CTA 0 publishes the scalars
-  for (int item = tid; item < n_items; item += NTP) {
-    const int i = L.it_i[item];
-    if (i < 0) continue;
-    const float* lx = L.lx + 3 * item;
-    st_v(sl[L.it_slot[item]].dx + i, mk<float4, float>(lx[0], lx[1], lx[2]));
+  // x of this CTA's rows to global memory (SR_GLOBAL: already there); CTA 0 publishes the scalars
+  if constexpr (!GV) {
+    for (int item = tid; item < n_items; item += NTP) {
+      int slot;
+      const int i = row_of(item, slot);
+      if (i < 0) continue;
+      const float* lx = L.lx + 3 * item;
+      st_v(sl[slot].dx + i, mk<float4, float>(lx[0], lx[1], lx[2]));
+    }
   }
   if (blockIdx.x == 0)
     for (int si = tid; si < n_scenes; si += NTP) publish(st[si], sl[si].ctl);
 }
 
-int pcg_sr_max_grid(int device, size_t smem, bool resident) {
-  const void* k = resident ? (const void*)k_pcg_sr<true> : (const void*)k_pcg_sr<false>;
+static const void* sr_kernel(int mode) {
+  return mode == SR_RES ? (const void*)k_pcg_sr<SR_RES>
+                        : mode == SR_STREAM ? (const void*)k_pcg_sr<SR_STREAM> : (const void*)k_pcg_sr<SR_GLOBAL>;
+}
+
+int pcg_sr_max_grid(int device, size_t smem, int mode) {
+  const void* k = sr_kernel(mode);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -582,7 +644,8 @@ int pcg_sr_max_grid(int device, size_t smem, bool resident) {
 }
 
 cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cudaStream_t st) {
-  if (L.n_scenes <= 0 || L.n_scenes > PCG_MAX_SCENES || L.n_tiles <= 0 || L.grid > XCH_MAX_CTAS || !L.flags)
+  if (L.n_scenes <= 0 || L.n_scenes > PCG_MAX_SCENES || L.n_tiles <= 0 || L.grid > XCH_MAX_CTAS || !L.flags ||
+      L.sr_mode < SR_RES || L.sr_mode > SR_GLOBAL || (L.sr_mode == SR_RES) != (L.smem_blocks > 0))
     return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(L.bar, 0, sizeof(GridBar), st);
   if (e != cudaSuccess) return e;
@@ -603,8 +666,7 @@ cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cud
   unsigned long long* flags = L.flags;
   void* args[] = {(void*)&scenes, (void*)&tiles, (void*)&n_tiles, (void*)&ids,  (void*)&n_scenes,
                   (void*)&bar,    (void*)&bg,    (void*)&nb_cap,  (void*)&flags};
-  // smem_blocks > 0: the rows' blocks are resident in shared memory
-  const void* k = nb_cap > 0 ? (const void*)k_pcg_sr<true> : (const void*)k_pcg_sr<false>;
+  const void* k = sr_kernel(L.sr_mode);
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(k, dim3(L.grid), dim3(NTP), args, L.smem_bytes, st);

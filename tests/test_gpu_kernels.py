@@ -198,15 +198,48 @@ def test_tiny_meshes_and_ragged_sizes():
         assert np.abs(v - o.assemble(x)).max() <= 1e-10 * np.abs(v).max()
 
 
-def test_single_reduction_pcg_streamed_matrix_equals_resident(monkeypatch):
-    # the FP32 kernel with the BSR blocks streamed from global memory (used when the
-    # rows do not fit in shared memory) performs the same operations in the same order
+def test_single_reduction_pcg_layouts(monkeypatch):
+    # the FP32 kernel with the BSR blocks streamed from global memory, and with the
+    # vectors in global memory too (the layouts for rows that do not fit in shared
+    # memory), performs the same operations in the same order as the resident one
     spec = medium_spec(19)
-    vals = O.Scene.from_spec(spec).assemble(deformed(spec, 20, amp=0.3))
+    o = O.Scene.from_spec(spec)
+    vals = o.assemble(spec.rest)  # K + M / dt^2 at rest: SPD
+    rp, col = o.pattern()
     b = np.random.default_rng(21).standard_normal((spec.n_verts, 3))
     b[spec.fixed] = 0
     res = P.Scene.from_spec(spec, precision=P.PREC_MIXED).probe_pcg(vals, b, rel_tol=1e-6)
     monkeypatch.setenv("PPN_PCG_STREAM", "1")
     st = P.Scene.from_spec(spec, precision=P.PREC_MIXED).probe_pcg(vals, b, rel_tol=1e-6)
-    assert res[1] == st[1]
-    assert np.array_equal(res[0], st[0])
+    monkeypatch.delenv("PPN_PCG_STREAM")
+    monkeypatch.setenv("PPN_PCG_SR_GLOBAL", "1")
+    gl = P.Scene.from_spec(spec, precision=P.PREC_MIXED).probe_pcg(vals, b, rel_tol=1e-6)
+    assert res[1] == st[1] == gl[1]
+    assert np.array_equal(res[0], st[0]) and np.array_equal(res[0], gl[0])
+    # solved to 1e-6 in FP32: the true residual well within 1e-4
+    assert not res[1]["ind"] and not res[1]["hit_max"]
+    r = b.reshape(-1) - np.add.reduceat(np.einsum("kij,kj->ki", vals, res[0][col]), rp[:-1]).reshape(-1)
+    assert np.linalg.norm(r) <= 1e-4 * np.linalg.norm(b)
+
+
+def test_tuned_streamed_layouts_give_identical_steps(monkeypatch):
+    # 60k vertices: 3 PCG tiles per CTA, too many blocks for the resident layout, so
+    # the tuner alternates the two streamed layouts over the first launches; the
+    # steps equal those of a run held to the global-memory layout, bit for bit
+    spec = twisting_beam_scene(20, 20, 150, h=0.01, E=1e6, nu=0.45, omega=2.0, dt=1.0 / 30.0, seed=3)
+    out = []
+    for env in (None, "PPN_PCG_SR_GLOBAL"):
+        if env:
+            monkeypatch.setenv(env, "1")
+        sc = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
+        xs = []
+        for n in range(3):
+            sc.set_targets(spec.targets_at(n))
+            rc, x, st = sc.step(P.MODE_PPN, 1e-4)
+            assert rc == 0
+            xs.append((x, st["newton_iters"], st["total_cg_iters"]))
+        sc.close()
+        out.append(xs)
+    for (xa, na, ca), (xb, nb, cb) in zip(*out):
+        assert na == nb and ca == cb
+        assert np.array_equal(xa, xb)
