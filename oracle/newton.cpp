@@ -15,6 +15,11 @@
 //               pdn_countdown iterations (countdown 4) before trying
 //               unprojected again.  The countdown starts at 0 every time step.
 // The step then takes a backtracking line search (Sec. 5.1) and updates x.
+// Dirichlet vertices are eliminated (their targets set, zero gradient, identity
+// rows) unless params.dirichlet_penalty = k > 0: then, as Sec. 5.1 enforces
+// Dirichlet constraints with penalty potentials, they stay free and carry
+// k m_v / (2 dt^2) |x_v - t_v|^2 (a stiffness k times the vertex's inertia term).
+// Either way the initial iterate starts them at their targets.
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -41,9 +46,10 @@ struct ora_scene {
   std::vector<int32_t> tets;
   double mu = 0, lam = 0, rho = 0, dt = 0, grav[3] = {0, 0, 0};
   std::vector<double> mass;
-  std::vector<uint8_t> fixed;
-  std::vector<int32_t> fixed_list;
+  std::vector<uint8_t> fixed;          // eliminated Dirichlet vertices (none with a penalty)
+  std::vector<int32_t> fixed_list;     // Dirichlet vertices, in the order of `targets`
   std::vector<double> targets;
+  std::vector<int32_t> pen;            // penalty: the vertex's index in fixed_list, else -1
   std::vector<double> x, v;
   std::vector<int64_t> row_ptr;
   std::vector<int32_t> col;
@@ -100,6 +106,12 @@ bool vertex_contact(const ora_scene* s, const double* xv, double* E, double* g, 
   return true;
 }
 
+// penalty weight k m_v / dt^2 of a Dirichlet vertex held by a penalty potential (0 otherwise)
+double pen_weight(const ora_scene* s, int64_t v) {
+  return s->pen.empty() || s->pen[v] < 0 ? 0.0 : s->p.dirichlet_penalty * s->mass[v] / (s->dt * s->dt);
+}
+const double* pen_target(const ora_scene* s, int64_t v) { return &s->targets[3 * (size_t)s->pen[v]]; }
+
 double energy(const ora_scene* s, const double* x, const double* xhat) {
   double E = 0.0;
   const double w = 0.5 / (s->dt * s->dt);
@@ -111,6 +123,12 @@ double energy(const ora_scene* s, const double* x, const double* xhat) {
       d2 += d * d;
     }
     E += w * s->mass[v] * d2;
+    if (const double wp = pen_weight(s, v)) {  // Dirichlet penalty potential
+      const double* t = pen_target(s, v);
+      double p2 = 0.0;
+      for (int k = 0; k < 3; ++k) p2 += (x[3 * v + k] - t[k]) * (x[3 * v + k] - t[k]);
+      E += 0.5 * wp * p2;
+    }
     if (!s->obst.empty()) {
       double Ec;
       if (!vertex_contact(s, x + 3 * v, &Ec, nullptr, nullptr, nullptr))
@@ -135,6 +153,9 @@ void gradient_from(const ora_scene* s, const double* x, const double* xhat,
   for (int64_t e = 0; e < s->nt; ++e)
     for (int a = 0; a < 4; ++a)
       for (int k = 0; k < 3; ++k) g[3 * (int64_t)s->tets[4 * e + a] + k] += ge[12 * e + 3 * a + k];
+  for (int64_t v = 0; v < s->nv; ++v)
+    if (const double wp = pen_weight(s, v))
+      for (int k = 0; k < 3; ++k) g[3 * v + k] += wp * (x[3 * v + k] - pen_target(s, v)[k]);
   if (!s->obst.empty())
     for (int64_t v = 0; v < s->nv; ++v) {
       if (s->fixed[v]) continue;
@@ -159,6 +180,9 @@ double residual_scale(const ora_scene* s, const double* x, const double* xhat, c
   for (int64_t e = 0; e < s->nt; ++e)
     for (int i = 0; i < 4; ++i)
       for (int k = 0; k < 3; ++k) a[3 * (int64_t)s->tets[4 * e + i] + k] += std::fabs(ge[12 * e + 3 * i + k]);
+  for (int64_t v = 0; v < s->nv; ++v)
+    if (const double wp = pen_weight(s, v))
+      for (int k = 0; k < 3; ++k) a[3 * v + k] += std::fabs(wp * (x[3 * v + k] - pen_target(s, v)[k]));
   double n2 = 0.0;
   for (int64_t v = 0; v < s->nv; ++v)
     if (!s->fixed[v]) {
@@ -190,9 +214,9 @@ void scatter_element(const ora_scene* s, int64_t e, const double* M12, double* v
   }
 }
 
-// unprojected H = M / dt^2 + sum_e S^eT H^e S^e with Dirichlet rows eliminated
 // H = M / dt^2 + sum_e S^eT H^e S^e (+ the contact Hessians of the free vertices at x,
-// when x is given and the scene has obstacles); identity rows for Dirichlet vertices
+// when x is given and the scene has obstacles); identity rows for eliminated Dirichlet
+// vertices, k m_v / dt^2 I added on the diagonal of penalised ones
 void assemble(const ora_scene* s, const double* x, const std::vector<double>& He, std::vector<double>& vals) {
   vals.assign(9 * s->col.size(), 0.0);
   for (int64_t e = 0; e < s->nt; ++e) scatter_element(s, e, &He[144 * e], vals.data());
@@ -203,7 +227,7 @@ void assemble(const ora_scene* s, const double* x, const std::vector<double>& He
       if (s->fixed[v])
         blk[3 * r + r] = 1.0;
       else
-        blk[3 * r + r] += w * s->mass[v];
+        blk[3 * r + r] += w * s->mass[v] + pen_weight(s, v);
     }
     if (x && !s->fixed[v] && !s->obst.empty()) {
       double Hc[9];
@@ -286,6 +310,7 @@ ora_params ora_default_params(void) {
   p.contact_kappa = 1e3;
   p.contact_dhat = 1e-3;
   p.ccd_safety = 0.9;
+  p.dirichlet_penalty = 0.0;
   return p;
 }
 
@@ -342,13 +367,23 @@ ora_scene* ora_scene_create(const double* rest, int64_t n_v, const int32_t* tets
     for (int a = 0; a < 4; ++a) s->mass[s->tets[4 * e + a]] += rho * (det / 6.0) / 4.0;
   }
   s->fixed.assign(n_v, 0);
+  if (!(s->p.dirichlet_penalty >= 0.0)) {
+    g_err = "dirichlet_penalty must be >= 0";
+    delete s;
+    return nullptr;
+  }
+  const bool penalty = s->p.dirichlet_penalty > 0.0;
+  if (penalty) s->pen.assign(n_v, -1);
   for (int64_t f = 0; f < n_fixed; ++f) {
-    if (fixed[f] < 0 || fixed[f] >= n_v) {
-      g_err = "fixed index out of range";
+    if (fixed[f] < 0 || fixed[f] >= n_v || (penalty && s->pen[fixed[f]] >= 0)) {
+      g_err = "fixed index out of range (or repeated, with a penalty)";
       delete s;
       return nullptr;
     }
-    s->fixed[fixed[f]] = 1;
+    if (penalty)
+      s->pen[fixed[f]] = (int32_t)s->fixed_list.size();
+    else
+      s->fixed[fixed[f]] = 1;
     s->fixed_list.push_back(fixed[f]);
   }
   for (int64_t v = 0; v < n_v; ++v)
@@ -402,7 +437,13 @@ void ora_scene_lumped_mass(const ora_scene* s, double* m) {
   std::memcpy(m, s->mass.data(), sizeof(double) * s->nv);
 }
 
-void ora_scene_set_params(ora_scene* s, const ora_params* p) { s->p = *p; }
+void ora_scene_set_params(ora_scene* s, const ora_params* p) {
+  // the Dirichlet treatment (elimination or penalty) is fixed at creation; a
+  // penalty scene may change its stiffness
+  const double k = s->p.dirichlet_penalty;
+  s->p = *p;
+  if ((p->dirichlet_penalty > 0.0) != (k > 0.0) || !(p->dirichlet_penalty >= 0.0)) s->p.dirichlet_penalty = k;
+}
 
 int ora_scene_set_targets(ora_scene* s, const double* xyz) {
   std::memcpy(s->targets.data(), xyz, sizeof(double) * s->targets.size());

@@ -79,6 +79,8 @@ typedef struct {
   double contact_kappa; /* barrier stiffness kappa [N/m], default 1e3 */
   double contact_dhat;  /* barrier activation distance dhat [m], default 1e-3 */
   double ccd_safety;    /* line search starts at min(1, ccd_safety * gamma_ccd), default 0.9 */
+  double dirichlet_penalty; /* 0: Dirichlet vertices eliminated (default); k > 0: they stay free and
+                               carry the penalty potential k m_v / (2 dt^2) |x_v - t_v|^2 */
 } ora_params;
 
 /* analytic obstacles for frictionless log-barrier contact (contact.cpp) */
@@ -176,6 +178,8 @@ int64_t ora_scene_nnzb(const ora_scene* s);
 void ora_scene_pattern(const ora_scene* s, int64_t* row_ptr, int32_t* col);
 void ora_scene_tets(const ora_scene* s, int32_t* tets);           /* after orientation */
 void ora_scene_lumped_mass(const ora_scene* s, double* m);
+/* replaces the parameters; dirichlet_penalty keeps its creation value when it
+   would switch between elimination (0) and penalty (> 0) */
 void ora_scene_set_params(ora_scene* s, const ora_params* p);
 int ora_scene_set_targets(ora_scene* s, const double* xyz_fixed);
 void ora_scene_get_state(const ora_scene* s, double* x, double* v);
