@@ -98,6 +98,10 @@ typedef struct {
   double contact_kappa; /* barrier stiffness kappa [N/m] of the contact potential (1e3) */
   double contact_dhat;  /* barrier activation distance dhat [m] (1e-3) */
   double ccd_safety;    /* the line search starts at min(1, ccd_safety x first contact time) (0.9) */
+  double dirichlet_penalty; /* 0: Dirichlet vertices eliminated (default).  k > 0: Dirichlet
+                             * constraints by penalty potentials (Sec. 5.1): the constrained vertices
+                             * stay free and carry k m_v / (2 dt^2) |x_v - t_v|^2, t_v the target; new
+                             * targets take effect at once.  Fixed at scene creation; finite, >= 0. */
 } ppn_params;
 
 typedef struct {

@@ -151,6 +151,15 @@ __global__ void __launch_bounds__(TILE) k_gradient(const SceneDev<T>* scenes, co
         a[1] += fabs(ge[1]);
         a[2] += fabs(ge[2]);
       }
+      if (S.pen_k > 0.0 && S.con[v]) {  // Dirichlet penalty potential: k m / dt^2 (u - t)
+        const double4 t = ld_d4(S.tgt + v);
+        const double wp = S.pen_k * w;
+        const double p[3] = {wp * (uv.x - t.x), wp * (uv.y - t.y), wp * (uv.z - t.z)};
+        for (int k = 0; k < 3; ++k) {
+          g[k] += p[k];
+          a[k] += fabs(p[k]);
+        }
+      }
       if (S.obs->n > 0) {  // barrier potentials of the analytic obstacles
         const double4 X = ld_d4(S.X + v);
         const double x[3] = {X.x + uv.x, X.y + uv.y, X.z + uv.z};
@@ -221,8 +230,8 @@ __global__ void __launch_bounds__(TILE) k_assemble(const SceneDev<T>* scenes, co
       add_elem_block(S.He + (size_t)e * HE_STRIDE, a, b, acc);
       if (S.proj_stamp[e] == it) add_elem_block(S.dH + (size_t)e * HE_STRIDE, a, b, acc);
     }
-    if (i == j) {
-      const T m = (T)(S.mass[i] * S.inv_dt2);
+    if (i == j) {  // inertia, and the Dirichlet penalty k m / dt^2 of a constrained vertex
+      const T m = (T)(S.mass[i] * S.inv_dt2 * (S.pen_k > 0.0 && S.con[i] ? 1.0 + S.pen_k : 1.0));
       acc[0] += m;
       acc[4] += m;
       acc[8] += m;
@@ -485,6 +494,17 @@ __global__ void __launch_bounds__(TILE) k_energy(const SceneDev<T>* scenes, cons
         dmax = fmax(fabs((double)d.x), fmax(fabs((double)d.y), fabs((double)d.z)));
       }
       en = 0.5 * S.mass[v] * S.inv_dt2 * (d0 * d0 + d1 * d1 + d2 * d2);
+      if (S.pen_k > 0.0 && S.con[v]) {  // Dirichlet penalty potential at u + gamma dx
+        const double4 t = ld_d4(S.tgt + v);
+        double p0 = uv.x - t.x, p1 = uv.y - t.y, p2 = uv.z - t.z;
+        if (!use_probe && gam != 0.0) {
+          const vec4_t<T> d = S.dx[v];
+          p0 += gam * (double)d.x;
+          p1 += gam * (double)d.y;
+          p2 += gam * (double)d.z;
+        }
+        en += 0.5 * S.pen_k * S.mass[v] * S.inv_dt2 * (p0 * p0 + p1 * p1 + p2 * p2);
+      }
       if (S.obs->n > 0) {  // barrier potentials; +inf where a surface is reached
         const double4 X = ld_d4(S.X + v);
         double x[3] = {X.x + uv.x, X.y + uv.y, X.z + uv.z};
@@ -543,6 +563,8 @@ __global__ void k_predict(const SceneDev<T>* scenes, const TileRef* tiles, const
     st_d4(S.u + v, make_double4(u.x + dt * w.x, u.y + dt * w.y, u.z + dt * w.z, 0.0));
 }
 
+// Dirichlet targets (positions) into u (use_probe 0), u_probe (1) or neither (2);
+// with a penalty also into the per-vertex targets of the penalty potential
 template <typename T>
 __global__ void k_apply_targets(const SceneDev<T>* scenes, int scene, const int* fixed_list,
                                 const double* targets, int n_fixed, int use_probe) {
@@ -551,8 +573,9 @@ __global__ void k_apply_targets(const SceneDev<T>* scenes, int scene, const int*
   if (f >= n_fixed) return;
   const int v = fixed_list[f];
   const double4 X = ld_d4(S.X + v);
-  double4* U = use_probe ? S.u_probe : S.u;
-  st_d4(U + v, make_double4(targets[3 * f] - X.x, targets[3 * f + 1] - X.y, targets[3 * f + 2] - X.z, 0.0));
+  const double4 t = make_double4(targets[3 * f] - X.x, targets[3 * f + 1] - X.y, targets[3 * f + 2] - X.z, 0.0);
+  if (use_probe < 2) st_d4((use_probe ? S.u_probe : S.u) + v, t);
+  if (S.pen_k > 0.0) st_d4(S.tgt + v, t);  // the penalty's target
 }
 
 // u += gamma dx on free vertices

@@ -169,6 +169,11 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
     set_error("invalid parameters (projection kind, pdn_countdown, alpha in (0,1), beta >= 1, eig_eps >= 0)");
     return PPN_ERR_INVALID_ARG;
   }
+  if (!(params.dirichlet_penalty >= 0.0) || !std::isfinite(params.dirichlet_penalty)) {
+    set_error("dirichlet_penalty must be finite and >= 0");
+    return PPN_ERR_INVALID_ARG;
+  }
+  const bool penalty = params.dirichlet_penalty > 0.0;
   dt = dt_;
   nv = (int)n_verts;
   nt = (int)n_tets;
@@ -240,7 +245,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
     fixed_list[f] = v;
   }
   for (int v = 0; v < nv; ++v)
-    if (!fixed_flag[v] && !(mass[v] > 0)) {
+    if ((penalty || !fixed_flag[v]) && !(mass[v] > 0)) {
       set_error("free vertex " + std::to_string(v) + " has no incident tet");
       return PPN_ERR_INVALID_ARG;
     }
@@ -342,6 +347,8 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   T* d_tetc = alloc<T>((size_t)nt * TETC_STRIDE);
   double* d_mass = alloc<double>(nv);
   uint8_t* d_fixed = alloc<uint8_t>(nv);
+  uint8_t* d_con = alloc<uint8_t>(nv);
+  s.tgt = alloc<double4>(nv);
   double4* d_X = alloc<double4>(nv);
   int* d_vt_ptr = alloc<int>(nv + 1);
   int* d_vt_src = alloc<int>((size_t)4 * nt);
@@ -399,7 +406,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   d_ptiles = alloc<TileRef>(pt.size());
   d_etiles = alloc<TileRef>(et.size());
   d_projtiles = alloc<TileRef>(jt.size());
-  if (!d_tets || !d_tetc || !d_mass || !d_fixed || !d_X || !d_vt_ptr || !d_vt_src || !d_row_ptr ||
+  if (!d_tets || !d_tetc || !d_mass || !d_fixed || !d_con || !s.tgt || !d_X || !d_vt_ptr || !d_vt_src || !d_row_ptr ||
       !d_col || !d_blk_row || !d_blk_ptr || !d_blk_src || !d_diag || !s.u || !s.u_n || !s.vel ||
       !s.uhat || !s.u_probe || !s.ge || !s.He || !s.dH || !s.g || !s.gmax || !s.val ||
       !s.proj_stamp || !s.round_stamp || !s.cproj_stamp || !d_obs || !s.cround_stamp || !s.dHc || !s.sel_list || !s.dx || !s.r || !s.z || !s.q || !s.d0 ||
@@ -419,7 +426,11 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   PPN_CU(up(d_tets, h_tets.data(), sizeof(int4) * nt));
   PPN_CU(up(d_tetc, h_tetc.data(), sizeof(T) * h_tetc.size()));
   PPN_CU(up(d_mass, mass.data(), sizeof(double) * nv));
-  PPN_CU(up(d_fixed, fixed_flag.data(), nv));
+  // elimination: the Dirichlet vertices are fixed; penalty: they are free and constrained
+  const std::vector<uint8_t> none(nv, 0);
+  PPN_CU(up(d_fixed, penalty ? none.data() : fixed_flag.data(), nv));
+  PPN_CU(up(d_con, penalty ? fixed_flag.data() : none.data(), nv));
+  PPN_CU(cudaMemset(s.tgt, 0, sizeof(double4) * nv));  // targets start at the rest positions
   PPN_CU(up(d_X, X4.data(), sizeof(double4) * nv));
   PPN_CU(up(d_vt_ptr, vt_ptr.data(), sizeof(int) * (nv + 1)));
   PPN_CU(up(d_vt_src, vt_src.data(), sizeof(int) * vt_src.size()));
@@ -473,6 +484,8 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   s.eig_eps = params.eig_eps;
   s.kappa = params.contact_kappa;
   s.dhat = params.contact_dhat;
+  s.pen_k = params.dirichlet_penalty;
+  s.con = d_con;
   s.proj_kind = params.projection;
   s.init_guess = params.init_guess;
   s.delta = std::numeric_limits<double>::infinity();
@@ -482,6 +495,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   s.round_id = 0;
   s.active = 1;
   d = s;
+  PPN_CU(up(d_desc, &s, sizeof(SceneDev<T>)));  // for single-scene launches outside a step
   PPN_CU(cudaMallocHost(&h_ctl, sizeof(Ctl)));
   int dev = 0;
   PPN_CU(cudaGetDevice(&dev));
@@ -865,6 +879,7 @@ ppn_params ppn_default_params(void) {
   p.contact_kappa = 1e3;
   p.contact_dhat = 1e-3;
   p.ccd_safety = 0.9;
+  p.dirichlet_penalty = 0.0;
   p.pcg_rel_tol = 1e-4;
   p.armijo_c = 1e-4;
   p.gravity[0] = 0.0;
@@ -969,6 +984,10 @@ ppn_status ppn_set_kinematic_targets(ppn_scene* s, const double* xyz) {
       return PPN_ERR_INVALID_ARG;
     }
     PPN_CU(cudaMemcpyAsync(x.d_targets, xyz, sizeof(double) * 3 * x.nfixed, cudaMemcpyHostToDevice, x.stream));
+    // a penalty's targets take effect at once (positions are set at the next step)
+    if (x.params.dirichlet_penalty > 0.0)
+      launch_apply_targets(x.d_desc, 0, x.d_fixed_list, x.d_targets, x.nfixed, 2, x.stream);
+    PPN_CU(cudaGetLastError());
     PPN_CU(cudaStreamSynchronize(x.stream));
     x.ext_targets = nullptr;
     return PPN_OK;

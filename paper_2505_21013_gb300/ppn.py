@@ -36,7 +36,7 @@ class ppn_params(C.Structure):
                 ("ls_max_halvings", C.c_int), ("precision", C.c_int), ("tol_kind", C.c_int),
                 ("init_guess", C.c_int), ("pdn_countdown", C.c_int), ("projection", C.c_int),
                 ("grad_floor", C.c_double), ("ls_slack", C.c_double), ("contact_kappa", C.c_double),
-                ("contact_dhat", C.c_double), ("ccd_safety", C.c_double)]
+                ("contact_dhat", C.c_double), ("ccd_safety", C.c_double), ("dirichlet_penalty", C.c_double)]
 
 
 class ppn_obstacle(C.Structure):
