@@ -316,9 +316,12 @@ def profile_pcg(iters, repeats=4):
     b[spec.fixed] = 0
     out = []
     for _ in range(repeats):
+        sc.set_profiling(True)  # resets the per-family CUDA-event times
         t0 = time.perf_counter()
         _, inf = sc.probe_pcg(vals, b, rel_tol=1e-30, max_iter=iters)
-        out.append({"iters": inf["iters"], "host_ms": (time.perf_counter() - t0) * 1e3})
+        dev = sc.kernel_times()["pcg"]["total_ms"]
+        out.append({"iters": inf["iters"], "host_ms": (time.perf_counter() - t0) * 1e3, "device_ms": dev})
+        sc.set_profiling(False)
     sc.close()
     print(json.dumps({"profile_pcg": out, "source_sha256_16": pcg_source_hash(), "nnzb": nnzb}))
 

@@ -153,12 +153,13 @@ __global__ void __launch_bounds__(NTP, 1)
   constexpr int U = 16 / GP;            // blocks per lane per gather round
   constexpr int NW = NTP / 32;          // warps
   static_assert(RPP % PCG_TILE == 0 && NTP % PCG_TILE == 0, "passes cover whole tiles");
+  static_assert(PCG_MAX_SCENES <= NTP, "one thread per scene in the scalar step");
   extern __shared__ __align__(16) char dyn[];
   __shared__ SState<float> st[PCG_MAX_SCENES];
   __shared__ SceneLite<float> sl[PCG_MAX_SCENES];
   __shared__ float s_sum[PCG_MAX_SCENES][NQ];
   __shared__ int s_toff[PCG_MAX_SCENES];
-  __shared__ int s_to, s_all_done, s_lo, s_hi;
+  __shared__ int s_to, s_lo, s_hi;
   __shared__ int s_scan[NW];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane32 = tid & 31;
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(NTP, 1)
   auto publish_flag = [&](unsigned long long stamp) {
     __syncthreads();
     if (tid == 0) {
-      __threadfence();
+      fence_acq_rel();  // release (cumulative over the CTA's writes ordered by the barrier)
       st_relaxed_u64(flags + blockIdx.x, stamp);
     }
   };
@@ -541,18 +542,15 @@ __global__ void __launch_bounds__(NTP, 1)
     const unsigned s = W::stamp((unsigned)it + 1);
     post_partials(s, it == 0);
     if (!reduce(it == 0 ? NQ : 3, s)) return fail_out();
-    for (int si = tid; si < n_scenes; si += NTP)
-      if (!st[si].done)
-        sr_step(st[si], s_sum[si][0], s_sum[si][1], s_sum[si][2], it == 0 ? s_sum[si][3] : 0.0f, it,
-                sl[si].tol2, sl[si].max_iter);
-    __syncthreads();
-    if (tid == 0) {
-      int all = 1;
-      for (int si = 0; si < n_scenes; ++si) all &= st[si].done;
-      s_all_done = all;
+    // one thread per scene (n_scenes <= PCG_MAX_SCENES < NTP); the barrier also finds whether all are done
+    int done = 1;
+    if (tid < n_scenes) {
+      if (!st[tid].done)
+        sr_step(st[tid], s_sum[tid][0], s_sum[tid][1], s_sum[tid][2], it == 0 ? s_sum[tid][3] : 0.0f, it,
+                sl[tid].tol2, sl[tid].max_iter);
+      done = st[tid].done;
     }
-    __syncthreads();
-    if (s_all_done) break;
+    if (__syncthreads_and(done)) break;
     // ---- p = u + beta p, s = w + beta s; x += alpha p, r -= alpha s, u = M r (published)
     for (int item = tid; item < n_items; item += NTP) {
       int slot;
