@@ -296,20 +296,30 @@ def run_ours(args, rank, world, dist):
     return r
 
 
-def profile_pcg(iters, repeats=4):
+def profile_pcg(iters, repeats=4, workload="beam"):
     """Fixed-length PCG solves on the workload's assembled system (for ncu
-    captures of the resident PCG kernel): one PPN step, then `repeats` solves
-    of exactly `iters` CG iterations on the Hessian at that state."""
+    captures of the PCG kernel): one PPN step, then `repeats` solves of exactly
+    `iters` CG iterations on the Hessian at that state.  workload "contact": the
+    press scene (4 boxes of 40^3 vertices) at its initial pose, no step."""
     import numpy as np
 
     import paper_2505_21013_gb300 as P
 
-    spec = build_spec()
-    sc = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
-    sc.set_targets(spec.targets_at(0))
-    rc, x, _ = sc.step(P.MODE_PPN, WORKLOAD["tol"], want_x=True)
-    if rc != 0:
-        raise RuntimeError(f"step returned status {rc}")
+    if workload == "contact":
+        # the Hessian at the initial pose (K + M / dt^2; no PCG launch before the probes)
+        from ppn_inputs import press_scene
+
+        spec = press_scene(n=40, boxes=4, press_speed=0.05, dt=1.0 / 60.0, seed=0)
+        sc = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
+        sc.set_obstacles(spec.obstacles_at(-1))
+        x = spec.rest
+    else:
+        spec = build_spec()
+        sc = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
+        sc.set_targets(spec.targets_at(0))
+        rc, x, _ = sc.step(P.MODE_PPN, WORKLOAD["tol"], want_x=True)
+        if rc != 0:
+            raise RuntimeError(f"step returned status {rc}")
     nnzb = sc.info()["nnzb"]
     vals = sc.probe_assemble(x)
     b = np.random.default_rng(0).standard_normal((spec.n_verts, 3))
@@ -553,7 +563,7 @@ def main():
                     help="run fixed-length PCG solves for an ncu capture instead of the benchmark")
     args = ap.parse_args()
     if args.profile_pcg:
-        profile_pcg(args.profile_pcg)
+        profile_pcg(args.profile_pcg, workload=args.workload)
         return
     if args.workload != "beam" and args.impl == "ours":
         import torch

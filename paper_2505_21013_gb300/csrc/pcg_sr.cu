@@ -93,6 +93,25 @@ __device__ __forceinline__ float4 ld_f4_cg(const float* p) {
   return v;
 }
 
+// The streamed BSR blocks are read once per SpMV and would evict the vectors
+// from L2; they are loaded with an evict-first L2 policy so that the vectors
+// (and u, gathered by every CTA) stay resident.
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float ld_stream(const float* a, unsigned long long pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ int ld_stream(const int* a, unsigned long long pol) {
+  int v;
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  return v;
+}
+
 // scalar step after the reduction of iteration `it` (it updates done so far):
 // stopping tests, then alpha and beta of the next direction, or the exits
 __device__ __forceinline__ void sr_step(SState<float>& s, float gam, float del, float rho, float fail, int it,
@@ -348,6 +367,7 @@ __global__ void __launch_bounds__(NTP, 1)
     return !s_to;
   };
   // w = A u over this CTA's rows, u gathered from the global array (GP lanes per row)
+  const unsigned long long pol = RES ? 0ull : l2_evict_first();
   auto spmv = [&]() {
     for (int base = 0; base < n_items; base += RPP) {
       const int row = tid / GP, lane = tid % GP;
@@ -379,7 +399,7 @@ __global__ void __launch_bounds__(NTP, 1)
             }
           }
         } else {
-          // blocks from global memory (component-major values), read-only path
+          // blocks from global memory (component-major values), read-only path, evict-first in L2
           const int lb = S.row_ptr[i], le = S.row_ptr[i + 1];
           const size_t nb = (size_t)S.nnzb;
           for (int b0 = lb + lane; b0 < le; b0 += GP * U) {
@@ -387,7 +407,7 @@ __global__ void __launch_bounds__(NTP, 1)
 #pragma unroll
             for (int u = 0; u < U; ++u) {
               const int b = b0 + GP * u;
-              if (b < le) vj[u] = ld_f4_cg(vb + (size_t)8 * __ldg(S.col + b));
+              if (b < le) vj[u] = ld_f4_cg(vb + (size_t)8 * ld_stream(S.col + b, pol));
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -395,7 +415,7 @@ __global__ void __launch_bounds__(NTP, 1)
               if (b < le) {
                 float a[9];
 #pragma unroll
-                for (int c = 0; c < 9; ++c) a[c] = __ldg(S.val + c * nb + b);
+                for (int c = 0; c < 9; ++c) a[c] = ld_stream(S.val + c * nb + b, pol);
                 ax += a[0] * vj[u].x + a[1] * vj[u].y + a[2] * vj[u].z;
                 ay += a[3] * vj[u].x + a[4] * vj[u].y + a[5] * vj[u].z;
                 az += a[6] * vj[u].x + a[7] * vj[u].y + a[8] * vj[u].z;
