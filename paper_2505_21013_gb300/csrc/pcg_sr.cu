@@ -45,7 +45,7 @@ constexpr int NTP = 512;  // threads per CTA
 constexpr int NQ = 4;     // reduction slots: gamma, delta, rho, failed diagonal blocks
 
 struct SrLayout {
-  float* lws;    // [(ni / PCG_TILE + 1) * 16 * NQ] per-warp partial sums (16 warps per pass cover 4 tiles)
+  float* lws;    // [(ni / PCG_TILE + 1) * 16 * NQ] partial sums per 16-row group (8 per tile)
   TileRef* ltt;  // [ni / PCG_TILE + 1] the CTA's tiles
   int* lrp;      // SR_RES: [ni + 1] local row pointers
   int* lcol;     // SR_RES: [nb]
@@ -430,6 +430,8 @@ __global__ void __launch_bounds__(NTP, 1)
         ay += __shfl_down_sync(0xffffffffu, ay, o, GP);
         az += __shfl_down_sync(0xffffffffu, az, o, GP);
       }
+      // w of the row, and its terms of gamma = r.u, delta = w.u, rho = r.r
+      float g = 0.f, d = 0.f, rr = 0.f;
       if (lane == 0 && item < n_items) {
         if constexpr (GV) {
           if (i >= 0) st_f4(reinterpret_cast<float*>(sl[slot].q + i), ax, ay, az);
@@ -438,57 +440,51 @@ __global__ void __launch_bounds__(NTP, 1)
           L.lw[3 * item + 1] = ay;
           L.lw[3 * item + 2] = az;
         }
-      }
-    }
-    __syncthreads();
-  };
-
-  // partial sums of gamma = r.u, delta = w.u, rho = r.r (and failed blocks) per tile, posted
-  auto post_partials = [&](unsigned stamp, bool with_fail) {
-    for (int base = 0; base < n_items; base += NTP) {
-      const int item = base + tid;
-      float g = 0.f, d = 0.f, rr = 0.f;
-      int slot = 0;
-      const int i = item < n_items ? row_of(item, slot) : -1;
-      if (i >= 0 && !st[slot].done) {
-        float r[3], u[3], w[3];
-        if constexpr (GV) {
-          const SceneLite<float>& S = sl[slot];
-          const float4 rv = ld_f4_cg(reinterpret_cast<const float*>(S.z + i));
-          const float4 uv = ld_f4_cg(u_ptr(S.zrec, i));
-          const float4 wv = ld_f4_cg(reinterpret_cast<const float*>(S.q + i));
-          r[0] = rv.x, r[1] = rv.y, r[2] = rv.z;
-          u[0] = uv.x, u[1] = uv.y, u[2] = uv.z;
-          w[0] = wv.x, w[1] = wv.y, w[2] = wv.z;
-        } else {
-          const int k = 3 * item;
+        if (i >= 0 && !st[slot].done) {
+          float r[3], u[3];
+          if constexpr (GV) {
+            const float4 rv = ld_f4_cg(reinterpret_cast<const float*>(sl[slot].z + i));
+            const float4 uv = ld_f4_cg(u_ptr(sl[slot].zrec, i));
+            r[0] = rv.x, r[1] = rv.y, r[2] = rv.z;
+            u[0] = uv.x, u[1] = uv.y, u[2] = uv.z;
+          } else {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            r[c] = L.lr[k + c];
-            u[c] = L.lu[k + c];
-            w[c] = L.lw[k + c];
+            for (int c = 0; c < 3; ++c) {
+              r[c] = L.lr[3 * item + c];
+              u[c] = L.lu[3 * item + c];
+            }
           }
+          g = r[0] * u[0] + r[1] * u[1] + r[2] * u[2];
+          d = ax * u[0] + ay * u[1] + az * u[2];
+          rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
         }
-        g = r[0] * u[0] + r[1] * u[1] + r[2] * u[2];
-        d = w[0] * u[0] + w[1] * u[1] + w[2] * u[2];
-        rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
       }
+      // per group of 16 rows (one warp of the pass), in a fixed order
       g = warp_sum(g);
       d = warp_sum(d);
       rr = warp_sum(rr);
       if (lane32 == 0) {
-        float* o = L.lws + NQ * ((base >> 5) + warp);
+        float* o = L.lws + NQ * ((base >> 4) + warp);
         o[0] = g;
         o[1] = d;
         o[2] = rr;
       }
     }
     __syncthreads();
+  };
+
+  // tile sums of gamma = r.u, delta = w.u, rho = r.r (and failed blocks) from the SpMV's
+  // 16-row group sums (8 groups per tile, a fixed tree), posted
+  auto post_partials = [&](unsigned stamp, bool with_fail) {
     for (int lt = tid; lt < ntl; lt += NTP) {
       if (st[L.ltt[lt].scene].done) continue;
-      const float* w = L.lws + NQ * 4 * lt;
+      const float* w = L.lws + NQ * 8 * lt;
       const int nq = with_fail ? NQ : 3;
-      for (int q = 0; q < nq; ++q) post_tile(lt, q, ((w[q] + w[NQ + q]) + w[2 * NQ + q]) + w[3 * NQ + q], stamp);
+      for (int q = 0; q < nq; ++q) {
+        const float a = (w[q] + w[NQ + q]) + (w[2 * NQ + q] + w[3 * NQ + q]);
+        const float b = (w[4 * NQ + q] + w[5 * NQ + q]) + (w[6 * NQ + q] + w[7 * NQ + q]);
+        post_tile(lt, q, a + b, stamp);
+      }
     }
   };
   auto fail_out = [&]() {
@@ -550,8 +546,11 @@ __global__ void __launch_bounds__(NTP, 1)
       }
       fail = ok ? 0.0f : 1.0f;
     }
-    fail = warp_sum(fail);
-    if (lane32 == 0) L.lws[NQ * ((base >> 5) + warp) + 3] = fail;
+    fail = warp_sum(fail);  // the warp's 32 rows: its first 16-row group takes the count
+    if (lane32 == 0) {
+      L.lws[NQ * ((base >> 4) + 2 * warp) + 3] = fail;
+      L.lws[NQ * ((base >> 4) + 2 * warp + 1) + 3] = 0.0f;
+    }
   }
 
   for (int it = 0;; ++it) {
