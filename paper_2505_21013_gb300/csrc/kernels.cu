@@ -209,47 +209,103 @@ __device__ __forceinline__ void add_elem_block(const T* rec, int a, int b, T* ac
   }
 }
 
+// contact element of vertex i (and its clamping, if projected before assembly),
+// added to its diagonal block; out of line, off the assembly's main path
 template <typename T>
-__global__ void __launch_bounds__(TILE) k_assemble(const SceneDev<T>* scenes, const TileRef* tiles, int use_probe) {
+__device__ __noinline__ void add_contact_block(const SceneDev<T>& S, int i, int use_probe, int it, T* acc) {
+  const double4 X = ld_d4(S.X + i), u = ld_d4((use_probe ? S.u_probe : S.u) + i);
+  const double x[3] = {X.x + u.x, X.y + u.y, X.z + u.z};
+  double Hc[9];
+  vertex_contact(S, x, nullptr, nullptr, Hc, nullptr);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) acc[q] += (T)Hc[q];
+  if (S.cproj_stamp[i] == it)
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] += S.dHc[(size_t)9 * i + q];
+}
+
+// A warp assembles 32 consecutive blocks from their contribution list (the
+// blocks' (tet, a, b) sources, contiguous in blk_src), 32 contributions at a time:
+// lane l loads contribution c0 + l, a segmented scan across the warp sums the
+// contributions of each block in the chunk, and the last lane of each block's
+// run adds the run's sum to the block's total in shared memory (chunks in
+// order).  Work per warp follows the number of contributions, not the longest
+// block (a diagonal block has ~24, an off-diagonal one ~4-6).  Then lane l writes
+// block k0 + l, with the inertia (and contact) terms on the diagonal.
+template <typename T>
+__global__ void __launch_bounds__(TILE, 4) k_assemble(const SceneDev<T>* scenes, const TileRef* tiles, int use_probe) {
+  constexpr int NWA = TILE / 32;
+  __shared__ T s_acc[NWA][32][9];
+  __shared__ int s_end[NWA][32];
   const TileRef tr = tiles[blockIdx.x];
   const SceneDev<T>& S = scenes[tr.scene];
   if (!S.active) return;
-  const int k = tr.tile * TILE + threadIdx.x;
-  if (k >= S.nnzb) return;
-  const int i = S.blk_row[k], j = S.col[k];
-  T acc[9];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k0 = tr.tile * TILE + warp * 32;
+  if (k0 >= S.nnzb) return;  // warp-uniform
+  const int nk = min(32, S.nnzb - k0);
+  const int it = S.it_id;
 #pragma unroll
-  for (int c = 0; c < 9; ++c) acc[c] = (T)0;
-  if (S.fixed[i] || S.fixed[j]) {
-    if (i == j) acc[0] = acc[4] = acc[8] = (T)1;
-  } else {
-    const int it = S.it_id;
-    for (int c = S.blk_ptr[k]; c < S.blk_ptr[k + 1]; ++c) {
+  for (int c = 0; c < 9; ++c) s_acc[warp][lane][c] = (T)0;
+  s_end[warp][lane] = S.blk_ptr[k0 + min(lane, nk - 1) + 1];  // end of each block's contributions
+  const int cb = S.blk_ptr[k0], ce = s_end[warp][nk - 1];
+  __syncwarp();
+  for (int cbase = cb; cbase < ce; cbase += 32) {
+    const int c = cbase + lane;
+    T v[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v[q] = (T)0;
+    int bl = nk;  // local block of contribution c: the number of block ends <= c
+    if (c < ce) {
+      int lo = 0, hi = nk - 1;  // first block whose end is > c
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_end[warp][mid] > c) hi = mid; else lo = mid + 1;
+      }
+      bl = lo;
       const int src = S.blk_src[c];
       const int e = src >> 4, a = (src >> 2) & 3, b = src & 3;
-      add_elem_block(S.He + (size_t)e * HE_STRIDE, a, b, acc);
-      if (S.proj_stamp[e] == it) add_elem_block(S.dH + (size_t)e * HE_STRIDE, a, b, acc);
+      add_elem_block(S.He + (size_t)e * HE_STRIDE, a, b, v);
+      if (S.proj_stamp[e] == it) add_elem_block(S.dH + (size_t)e * HE_STRIDE, a, b, v);
     }
+    // inclusive sums over each run of equal bl (bl non-decreasing across lanes)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int bo = __shfl_up_sync(0xffffffffu, bl, o);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const T x = __shfl_up_sync(0xffffffffu, v[q], o);
+        if (lane >= o && bo == bl) v[q] += x;
+      }
+    }
+    const int bn = __shfl_down_sync(0xffffffffu, bl, 1);
+    if (c < ce && (lane == 31 || bn != bl)) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) s_acc[warp][bl][q] += v[q];
+    }
+    __syncwarp();
+  }
+  if (lane >= nk) return;
+  const int k = k0 + lane;
+  const int i = S.blk_row[k], j = S.col[k];
+  T acc[9];
+  if (S.fixed[i] || S.fixed[j]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] = (T)0;
+    if (i == j) acc[0] = acc[4] = acc[8] = (T)1;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] = s_acc[warp][lane][q];
     if (i == j) {  // inertia, and the Dirichlet penalty k m / dt^2 of a constrained vertex
       const T m = (T)(S.mass[i] * S.inv_dt2 * (S.pen_k > 0.0 && S.con[i] ? 1.0 + S.pen_k : 1.0));
       acc[0] += m;
       acc[4] += m;
       acc[8] += m;
-      if (S.obs->n > 0) {  // contact element of vertex i (and its clamping, if projected before assembly)
-        const double4 X = ld_d4(S.X + i), u = ld_d4((use_probe ? S.u_probe : S.u) + i);
-        const double x[3] = {X.x + u.x, X.y + u.y, X.z + u.z};
-        double Hc[9];
-        vertex_contact(S, x, nullptr, nullptr, Hc, nullptr);
-#pragma unroll
-        for (int c = 0; c < 9; ++c) acc[c] += (T)Hc[c];
-        if (S.cproj_stamp[i] == it)
-#pragma unroll
-          for (int c = 0; c < 9; ++c) acc[c] += S.dHc[(size_t)9 * i + c];
-      }
+      if (S.obs->n > 0) add_contact_block(S, i, use_probe, it, acc);
     }
   }
 #pragma unroll
-  for (int c = 0; c < 9; ++c) S.val[(size_t)c * S.nnzb + k] = acc[c];
+  for (int q = 0; q < 9; ++q) S.val[(size_t)q * S.nnzb + k] = acc[q];
 }
 
 // ----------------------------------------------------- K6 incremental update
