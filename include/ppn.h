@@ -232,6 +232,16 @@ PPN_API ppn_status ppn_probe_project(ppn_scene* s, const double* x, const int32_
                              double* dH);
 /* block-Jacobi PCG on the scene's pattern with values vals (nnzb*9) and right-hand
  * side b (n_verts*3); info: [iterations, ind, precond_fail, hit_max] */
+/* Bounded-wait check (the grid-wide waits of the PCG kernels, Sec. 4.1 "Linear
+ * Solvers" runs the solve as one resident kernel): one warp polls n_words stamped
+ * 64-bit words in device memory with the PCG's wait routine, at most spin_limit
+ * rounds.  preset != 0 sets the words first (the wait succeeds: PPN_OK); preset
+ * == 0 leaves them at zero, nothing else writes them, and the wait runs out:
+ * PPN_ERR_TIMEOUT.  The device stays usable either way.  1 <= n_words <= 4096,
+ * 1 <= spin_limit <= 1<<20, else PPN_ERR_INVALID_ARG.  Allocates and frees its own
+ * words on the current device. */
+PPN_API ppn_status ppn_probe_bounded_wait(int n_words, int spin_limit, int preset);
+
 PPN_API ppn_status ppn_probe_pcg(ppn_scene* s, const double* vals, const double* b, double rel_tol,
                          int max_iter, double* x, int* info);
 

@@ -72,6 +72,9 @@ constexpr int SR_RES = 0, SR_STREAM = 1, SR_GLOBAL = 2;
 size_t pcg_sr_smem_bytes(int ni, int nb, int mode);
 int pcg_sr_max_grid(int device, size_t smem, int mode);
 cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cudaStream_t st);
+// one warp waits (at most `limit` polling rounds) for n stamped words to reach `stamp`; *out = 1 if it ran out
+cudaError_t launch_wait_probe(const unsigned long long* w, int n, unsigned long long stamp, unsigned limit, int* out,
+                              cudaStream_t st);
 template <typename T>
 cudaError_t launch_pcg_smem(const SceneDev<T>* scenes, const PcgLaunch& L, cudaStream_t st);
 

@@ -161,6 +161,32 @@ __device__ __forceinline__ float* rec_ptr(float* base, int nv, int parity, int i
 // bound of one wait, in polling rounds; a CTA that gives up flags a timeout
 constexpr unsigned kWaitSpins = 1u << 20;
 
+// One warp polls the stamped words W[LO..HI] (four per lane per round, LANE the
+// lane index) until each is >= STAMP.  It gives up after LIMIT rounds on some
+// chunk, or at once when the expression GAVE_UP is true (another warp gave up),
+// and then runs GIVE_UP.  A macro, so that the PCG kernels' wait compiles as the
+// loop written in place (the kernels sit at the register limit, where an
+// out-of-line form measured slower) and the bounded-wait check runs the same text.
+#define PPN_WARP_WAIT_STAMPS(W, LO, HI, STAMP, LIMIT, LANE, GAVE_UP, GIVE_UP)      \
+  for (int c0 = (LO) + (LANE); c0 <= (HI); c0 += 32 * 4) {                        \
+    unsigned long long w_[4];                                                     \
+    _Pragma("unroll") for (int u = 0; u < 4; ++u) {                               \
+      const int c = c0 + 32 * u;                                                  \
+      w_[u] = c <= (HI) ? ld_relaxed_u64((W) + c) : (STAMP);                      \
+    }                                                                             \
+    for (unsigned spins = 0;; ++spins) {                                          \
+      bool ready = true;                                                          \
+      _Pragma("unroll") for (int u = 0; u < 4; ++u) ready &= w_[u] >= (STAMP);    \
+      if (ready) break;                                                           \
+      if (spins > (LIMIT) || (GAVE_UP)) {                                         \
+        GIVE_UP;                                                                  \
+        break;                                                                    \
+      }                                                                           \
+      _Pragma("unroll") for (int u = 0; u < 4; ++u) if (w_[u] < (STAMP)) w_[u] =  \
+          ld_relaxed_u64((W) + c0 + 32 * u);                                      \
+    }                                                                             \
+  }
+
 // per-scene fields a PCG kernel needs, copied to shared memory once per solve
 // so that no phase chases descriptor pointers through global memory
 template <typename T>

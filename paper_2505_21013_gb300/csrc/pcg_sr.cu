@@ -340,27 +340,7 @@ __global__ void __launch_bounds__(NTP, 1)
   // wait until every CTA of the neighbour range has published `stamp`
   auto wait_flags = [&](unsigned long long stamp) -> bool {
     if (warp == 0) {
-      for (int c0 = s_lo + lane32; c0 <= s_hi; c0 += 32 * 4) {
-        unsigned long long w[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int c = c0 + 32 * u;
-          w[u] = c <= s_hi ? ld_relaxed_u64(flags + c) : stamp;
-        }
-        for (unsigned spins = 0;; ++spins) {
-          bool ready = true;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) ready &= w[u] >= stamp;
-          if (ready) break;
-          if (spins > kWaitSpins || *(volatile int*)&s_to) {
-            s_to = 1;
-            break;
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (w[u] < stamp) w[u] = ld_relaxed_u64(flags + c0 + 32 * u);
-        }
-      }
+      PPN_WARP_WAIT_STAMPS(flags, s_lo, s_hi, stamp, kWaitSpins, lane32, *(volatile int*)&s_to, s_to = 1);
       fence_acq_rel();  // acquire: the neighbours' values before this CTA's gathers
     }
     __syncthreads();
@@ -637,6 +617,26 @@ __global__ void __launch_bounds__(NTP, 1)
   }
   if (blockIdx.x == 0)
     for (int si = tid; si < n_scenes; si += NTP) publish(st[si], sl[si].ctl);
+}
+
+// One warp waits, through the PCG's flag-wait helper, on n stamped words that
+// nothing else writes; out = 1 when the wait ran out.  Exercises the bounded-wait
+// path without a second party.
+__global__ void k_wait_probe(const unsigned long long* w, int n, unsigned long long stamp, unsigned limit, int* out) {
+  __shared__ int s_to;
+  if (threadIdx.x == 0) s_to = 0;
+  __syncwarp();
+  const int lane32 = threadIdx.x & 31;
+  PPN_WARP_WAIT_STAMPS(w, 0, n - 1, stamp, limit, lane32, *(volatile int*)&s_to, s_to = 1);
+  __syncwarp();
+  if (threadIdx.x == 0) *out = s_to ? 1 : 0;
+}
+
+cudaError_t launch_wait_probe(const unsigned long long* w, int n, unsigned long long stamp, unsigned limit, int* out,
+                              cudaStream_t st) {
+  if (n <= 0) return cudaErrorInvalidValue;
+  k_wait_probe<<<1, 32, 0, st>>>(w, n, stamp, limit, out);
+  return cudaGetLastError();
 }
 
 static const void* sr_kernel(int mode) {

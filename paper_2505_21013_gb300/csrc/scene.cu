@@ -1249,6 +1249,38 @@ ppn_status ppn_probe_project(ppn_scene* s, const double* x, const int32_t* sel, 
   return dispatch(s, [&](auto& sc) { return probe_project(sc, x, sel, n_sel, dH); });
 }
 
+ppn_status ppn_probe_bounded_wait(int n_words, int spin_limit, int preset) {
+  if (n_words < 1 || n_words > 4096 || spin_limit < 1 || spin_limit > (1 << 20)) {
+    set_error("n_words in [1, 4096], spin_limit in [1, 2^20]");
+    return PPN_ERR_INVALID_ARG;
+  }
+  unsigned long long* w = nullptr;
+  int* out = nullptr;
+  PPN_CU(cudaMalloc(&w, sizeof(unsigned long long) * n_words));
+  if (cudaMalloc(&out, sizeof(int)) != cudaSuccess) {
+    cudaFree(w);
+    set_error("cudaMalloc failed");
+    return PPN_ERR_OOM;
+  }
+  const unsigned long long stamp = 1;
+  std::vector<unsigned long long> h(n_words, preset ? stamp : 0ull);
+  int timed_out = -1;
+  cudaError_t e = cudaMemcpy(w, h.data(), sizeof(unsigned long long) * n_words, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_wait_probe(w, n_words, stamp, (unsigned)spin_limit, out, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(&timed_out, out, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(w);
+  cudaFree(out);
+  if (e != cudaSuccess) {
+    set_error(std::string("bounded-wait probe: ") + cudaGetErrorString(e));
+    return PPN_ERR_CUDA;
+  }
+  if (timed_out) {
+    set_error("bounded-wait probe: the wait ran out");
+    return PPN_ERR_TIMEOUT;
+  }
+  return PPN_OK;
+}
+
 ppn_status ppn_probe_pcg(ppn_scene* s, const double* vals, const double* b, double rel_tol,
                          int max_iter, double* x, int* info) {
   if (!vals || !b || !x) return PPN_ERR_INVALID_ARG;

@@ -140,6 +140,7 @@ SIGNATURES = {
     "ppn_probe_select": (_st, [_P, _pd, C.c_double, _pu, _pu, _pl]),
     "ppn_probe_project": (_st, [_P, _pd, _pi, C.c_int64, _pd]),
     "ppn_probe_pcg": (_st, [_P, _pd, _pd, C.c_double, C.c_int, _pd, C.POINTER(C.c_int)]),
+    "ppn_probe_bounded_wait": (_st, [C.c_int, C.c_int, C.c_int]),
     "ppn_server_default_config": (ppn_server_config, []),
     "ppn_server_create": (_st, [C.POINTER(ppn_server_config), C.POINTER(_P)]),
     "ppn_server_destroy": (None, [_P]),
@@ -392,6 +393,11 @@ class Scene:
                "ppn_probe_pcg")
         return x.reshape(-1, 3), {"iters": info[0], "ind": bool(info[1]), "precond_fail": bool(info[2]),
                                   "hit_max": bool(info[3])}
+
+
+def probe_bounded_wait(n_words: int, spin_limit: int, preset: bool) -> int:
+    """``ppn_probe_bounded_wait``: the status (PPN_OK, or 9 = PPN_ERR_TIMEOUT when the wait ran out)."""
+    return int(lib().ppn_probe_bounded_wait(int(n_words), int(spin_limit), 1 if preset else 0))
 
 
 def ppn_step_batch(scenes, modes, tol):

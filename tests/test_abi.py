@@ -59,3 +59,7 @@ def test_invalid_arguments_are_rejected_without_a_gpu(libpath):
     rc = L.ppn_create_scene(None, 0, None, 0, None, 0.0, None, 0, None, C.byref(out))
     assert rc == 1 and not out.value
     assert L.ppn_last_error()
+    # the bounded-wait probe checks its arguments before touching the device
+    assert L.ppn_probe_bounded_wait(0, 10, 0) == 1
+    assert L.ppn_probe_bounded_wait(8, 0, 0) == 1
+    assert L.ppn_probe_bounded_wait(8, (1 << 20) + 1, 1) == 1
