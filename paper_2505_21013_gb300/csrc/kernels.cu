@@ -55,68 +55,84 @@ __device__ __forceinline__ void load_u(const double4* U, int v, double* out) {
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_element(const SceneDev<T>* scenes, const TileRef* tiles,
                                                   int use_probe) {
+  // each 3x3 block goes through shared memory so that a warp writes its 32 tets'
+  // blocks as 36-byte runs (one warp store covers ~4 tets, not 32 records)
+  __shared__ T s_blk[TILE / 32][32][9];
   const TileRef tr = tiles[blockIdx.x];
   const SceneDev<T>& S = scenes[tr.scene];
   if (!S.active) return;
-  const int e = tr.tile * TILE + threadIdx.x;
-  if (e >= S.nt) return;
-  const int4 t = S.tets[e];
-  const double4* U = use_probe ? S.u_probe : S.u;
-  double u[4][3];
-  load_u(U, t.x, u[0]);
-  load_u(U, t.y, u[1]);
-  load_u(U, t.z, u[2]);
-  load_u(U, t.w, u[3]);
-  T W[9], V, mu, lam;
-  load_tetc(S.tetc, e, W, V, mu, lam);
-  // g^e in FP64 in both precisions: the assembled residual drives convergence and
-  // selection, and near equilibrium it is a small sum of large element forces
-  double Wd[9], Hd[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) Wd[k] = (double)W[k];
-  disp_grad(u[0], u[1], u[2], u[3], Wd, Hd);
-  TetState<double> sd;
-  tet_state(Hd, (double)mu, (double)lam, sd);
-  double Pd[9];
-  snh_pk1_disp(sd, (double)mu, (double)lam, Pd);
-  double dNd[4][3];
-  shape_grads(Wd, dNd);
-  double* ge = S.ge + (size_t)e * GE_STRIDE;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    double pa[3];
-    matvec3(Pd, dNd[a], pa);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) ge[3 * a + k] = (double)V * pa[k];
-  }
-  // Hessian blocks in the storage type
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int e0 = tr.tile * TILE + wid * 32;  // the warp's first tet
+  if (e0 >= S.nt) return;                    // warp-uniform
+  const int e = e0 + lane;
+  const bool valid = e < S.nt;
+  T dN[4][3], cN[4][3], V = (T)0, mu = (T)0, lam = (T)0;
   TetState<T> st;
-  T dN[4][3];
-  if constexpr (sizeof(T) == sizeof(double)) {
-    st = sd;
+  if (valid) {
+    const int4 t = S.tets[e];
+    const double4* U = use_probe ? S.u_probe : S.u;
+    double u[4][3];
+    load_u(U, t.x, u[0]);
+    load_u(U, t.y, u[1]);
+    load_u(U, t.z, u[2]);
+    load_u(U, t.w, u[3]);
+    T W[9];
+    load_tetc(S.tetc, e, W, V, mu, lam);
+    // g^e in FP64 in both precisions: the assembled residual drives convergence and
+    // selection, and near equilibrium it is a small sum of large element forces
+    double Wd[9], Hd[9];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 9; ++k) Wd[k] = (double)W[k];
+    disp_grad(u[0], u[1], u[2], u[3], Wd, Hd);
+    TetState<double> sd;
+    tet_state(Hd, (double)mu, (double)lam, sd);
+    double Pd[9];
+    snh_pk1_disp(sd, (double)mu, (double)lam, Pd);
+    double dNd[4][3];
+    shape_grads(Wd, dNd);
+    double* ge = S.ge + (size_t)e * GE_STRIDE;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) dN[a][k] = dNd[a][k];
-  } else {
-    T H[9];
+    for (int a = 0; a < 4; ++a) {
+      double pa[3];
+      matvec3(Pd, dNd[a], pa);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) H[k] = (T)Hd[k];
-    tet_state(H, mu, lam, st);
-    shape_grads(W, dN);
+      for (int k = 0; k < 3; ++k) ge[3 * a + k] = (double)V * pa[k];
+    }
+    // Hessian blocks in the storage type
+    if constexpr (sizeof(T) == sizeof(double)) {
+      st = sd;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dN[a][k] = dNd[a][k];
+    } else {
+      T H[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) H[k] = (T)Hd[k];
+      tet_state(H, mu, lam, st);
+      shape_grads(W, dN);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) matvec3(st.C, dN[a], cN[a]);
   }
-  T cN[4][3];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) matvec3(st.C, dN[a], cN[a]);
-  T* he = S.He + (size_t)e * HE_STRIDE;
+  const int n_here = min(32, S.nt - e0);
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = a; b < 4; ++b) {
-      T blk[9];
-      hess_block(st, V, mu, lam, dN[a], dN[b], cN[a], cN[b], blk);
+      if (valid) {
+        T blk[9];
+        hess_block(st, V, mu, lam, dN[a], dN[b], cN[a], cN[b], blk);
 #pragma unroll
-      for (int k = 0; k < 9; ++k) he[9 * tri4(a, b) + k] = blk[k];
+        for (int k = 0; k < 9; ++k) s_blk[wid][lane][k] = blk[k];
+      }
+      __syncwarp();
+      const size_t off = (size_t)9 * tri4(a, b);
+      for (int j = lane; j < 9 * n_here; j += 32) {
+        const int t = j / 9, k = j - 9 * t;
+        S.He[(size_t)(e0 + t) * HE_STRIDE + off + k] = s_blk[wid][t][k];
+      }
+      __syncwarp();
     }
 }
 
