@@ -375,8 +375,8 @@ ora_scene* ora_scene_create(const double* rest, int64_t n_v, const int32_t* tets
   const bool penalty = s->p.dirichlet_penalty > 0.0;
   if (penalty) s->pen.assign(n_v, -1);
   for (int64_t f = 0; f < n_fixed; ++f) {
-    if (fixed[f] < 0 || fixed[f] >= n_v || (penalty && s->pen[fixed[f]] >= 0)) {
-      g_err = "fixed index out of range (or repeated, with a penalty)";
+    if (fixed[f] < 0 || fixed[f] >= n_v || (penalty ? s->pen[fixed[f]] >= 0 : s->fixed[fixed[f]] != 0)) {
+      g_err = "fixed index out of range or repeated";
       delete s;
       return nullptr;
     }
