@@ -4,8 +4,9 @@ configuration (mixed precision, the scene's own stream and tile tables).
 Twisting beam 20x20x80 (171,114 tets): every stage against the FP64 oracle on
 the whole mesh (element values, gradient, energy, assembled BSR, selection)
 and one PPN time step against the oracle's; the PCG on the assembled system
-against the oracle's FP64 PCG (iterations) and through its true residual.  Press 4x40^3 (1,423,656 tets, contact): the oracle
-evaluates the gradient and energy of the whole scene at a state with the
+against the oracle's FP64 PCG (iterations) and through its true residual.
+Press 4x40^3 (1,423,656 tets, contact): the oracle evaluates the gradient and
+energy of the whole scene at a state with the
 bottom layer inside the barrier's range; one GPU step is checked for the
 properties the method guarantees at any size (feasibility, descent,
 convergence).  Bounds as in the stage tests: relative 2e-5 of the largest entry
