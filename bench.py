@@ -336,7 +336,7 @@ def profile_pcg(iters, repeats=4, workload="beam"):
     print(json.dumps({"profile_pcg": out, "source_sha256_16": pcg_source_hash(), "nnzb": nnzb}))
 
 
-def run_batched(n_scenes=64, steps=3, warmup=1, seed=0, tol=1e-4):
+def run_batched(n_scenes=64, steps=10, warmup=1, seed=0, tol=1e-4):
     """Batched workload: n independent cube/beam scenes (tet counts log-uniform in
     1k-50k, E log-uniform 1e4-1e7, nu in 0.3-0.48, dt in {1/30, 1/60, 1/120})
     advancing together, one launch per phase over all of them (ppn_step_batch).
@@ -370,11 +370,17 @@ def run_batched(n_scenes=64, steps=3, warmup=1, seed=0, tol=1e-4):
     return out
 
 
-def run_serving(n_scenes=32, n_req=600, rate_hz=500.0, seed=1, tol=1e-4, max_batch=64):
+def run_serving(n_scenes=200, n_req=21000, warm=1000, rate_hz=500.0, seed=1, tol=1e-4, max_batch=64):
     """Request-stream workload: resident scenes of 2k-200k tets (log-uniform),
-    Poisson arrivals at rate_hz, each request one time step of a uniformly
-    random scene, served with continuous batching (ppn_server_*).  Reports
-    completed steps/s and p50/p99 latency (submit to result) per mode."""
+    admitted up to the server's HBM budget (80 % of the device), Poisson arrivals
+    at rate_hz, each request one time step of a uniformly random scene, served
+    with continuous batching (ppn_server_*).  A thread collects results in
+    submission order while requests arrive.  Reports completed steps/s and
+    p50/p99 latency (submit to result) over the requests after the first `warm`,
+    per mode."""
+    import queue
+    import threading
+
     import numpy as np
 
     import paper_2505_21013_gb300 as P
@@ -384,35 +390,54 @@ def run_serving(n_scenes=32, n_req=600, rate_hz=500.0, seed=1, tol=1e-4, max_bat
     arrivals = poisson_arrivals(rate_hz, n_req, seed=seed)
     which = np.random.default_rng(seed).integers(0, n_scenes, size=n_req)
     out = {"n_scenes": n_scenes, "tets_total": int(sum(s.n_tets for s in specs)), "requests": n_req,
-           "rate_hz": rate_hz}
+           "warmup_requests": warm, "rate_hz": rate_hz}
     for name, mode in (("ppn", P.MODE_PPN), ("pn", P.MODE_PN)):
         srv = P.Server(precision=P.PREC_MIXED, max_batch=max_batch)
         ids = [srv.add_scene(s) for s in specs]
         step_no = [0] * n_scenes
-        tickets = []
+        pending = queue.Queue()
+        results, errors = [], []
+
+        def collect():
+            while True:
+                item = pending.get()
+                if item is None:
+                    return
+                sid, t = item
+                done, rc, _, stt, tm = srv.poll(t, sid)
+                if rc not in (0, P.ppn.PPN_ERR_NEWTON_MAXITER):
+                    errors.append(rc)
+                results.append((sid, rc, stt, tm))
+
+        th = threading.Thread(target=collect, daemon=True)
+        th.start()
         t0 = time.perf_counter()
         for a, k in zip(arrivals, which):
             now = time.perf_counter() - t0
             if a > now:
                 time.sleep(a - now)
             k = int(k)
-            tickets.append((ids[k], srv.submit(ids[k], mode, tol, specs[k].targets_at(step_no[k]))))
+            pending.put((ids[k], srv.submit(ids[k], mode, tol, specs[k].targets_at(step_no[k]))))
             step_no[k] += 1
-        batch, capped = [], {}
-        for sid, t in tickets:
-            done, rc, _, stt, tm = srv.poll(t, sid)
-            if rc not in (0, P.ppn.PPN_ERR_NEWTON_MAXITER):
-                raise RuntimeError(f"serving request failed with status {rc}")
+        pending.put(None)
+        th.join()
+        if errors:
+            raise RuntimeError(f"serving requests failed with status {errors[:5]}")
+        meas = results[warm:]
+        lat = [tm["t_done_ms"] - tm["t_submit_ms"] for _, _, _, tm in meas]
+        span = max(tm["t_done_ms"] for _, _, _, tm in meas) - min(tm["t_submit_ms"] for _, _, _, tm in meas)
+        capped = {}
+        for sid, rc, stt, _ in results:
             if rc:
                 k = ids.index(sid)
                 capped[specs[k].name] = {"tets": specs[k].n_tets, "E": specs[k].E, "nu": specs[k].nu,
                                          "dt": specs[k].dt, "grad_norm2": stt["final_grad_norm2"]}
-            batch.append(tm["batch_max"])
         st = srv.stats()
         srv.close()
-        out[name] = {"steps_per_s": st["steps_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                     "mean_batch_max": float(np.mean(batch)), "resident_gb": st["resident_bytes"] / 1e9,
-                     "requests_at_newton_cap": capped}
+        out[name] = {"steps_per_s": 1e3 * len(meas) / span, "p50_ms": percentile(lat, 0.5),
+                     "p99_ms": percentile(lat, 0.99), "mean_batch_max": float(np.mean([tm["batch_max"] for *_, tm in meas])),
+                     "resident_scenes": st["resident_scenes"], "resident_gb": st["resident_bytes"] / 1e9,
+                     "budget_gb": st["budget_bytes"] / 1e9, "requests_at_newton_cap": capped}
     out["speedup_ppn_vs_pn"] = out["ppn"]["steps_per_s"] / out["pn"]["steps_per_s"]
     return out
 
@@ -529,6 +554,71 @@ def run_contact(steps=10, warmup=3, n=40, tol=1e-4):
     return out
 
 
+def run_seeds(seeds=(0, 1, 2, 3, 4), steps=10, warmup=3, tol=1e-4):
+    """The beam workload (20x20x80) for each jitter seed: PPN and PN device time of
+    `steps` steps after `warmup`, per seed and summarised (the L2 is flushed
+    between steps, as in the headline run)."""
+    import torch
+
+    import paper_2505_21013_gb300 as P
+    from ppn_inputs import twisting_beam_scene
+
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    for seed in seeds:
+        spec = twisting_beam_scene(20, 20, 80, h=0.01, E=1e6, nu=0.45, omega=2.0, dt=1.0 / 30.0, seed=seed)
+        row = {"seed": seed}
+        for name, mode in (("ppn", P.MODE_PPN), ("pn", P.MODE_PN)):
+            sc = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
+            sc.set_stream(stream.cuda_stream)
+            lat, newton, cg, proj = [], 0, 0, 0
+            for n in range(warmup + steps):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                sc.set_targets(spec.targets_at(n))
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                rc, _, st = sc.step(mode, tol, want_x=False)
+                ev1.record(stream)
+                if rc != 0:
+                    raise RuntimeError(f"seed {seed} step {n} returned status {rc}")
+                ev1.synchronize()
+                if n >= warmup:
+                    lat.append(ev0.elapsed_time(ev1))
+                    newton += st["newton_iters"]
+                    cg += st["total_cg_iters"]
+                    proj += st["total_projections"]
+            sc.close()
+            row[name] = {"steps_per_s": steps / (sum(lat) / 1e3), "p99_ms": percentile(lat, 0.99),
+                         "newton_iters": newton, "cg_iters": cg, "projections": proj}
+        row["speedup_ppn_vs_pn"] = row["ppn"]["steps_per_s"] / row["pn"]["steps_per_s"]
+        rows.append(row)
+    sp = [r["speedup_ppn_vs_pn"] for r in rows]
+    v = [r["ppn"]["steps_per_s"] for r in rows]
+    return {"workload": "twisting_beam_20x20x80 per seed", "steps": steps, "warmup": warmup, "seeds": rows,
+            "ppn_steps_per_s": {"mean": statistics.mean(v), "min": min(v), "max": max(v)},
+            "speedup_ppn_vs_pn": {"mean": statistics.mean(sp), "min": min(sp), "max": max(sp)}}
+
+
+def host_cpu():
+    """The host's logical CPU count and model name (for the oracle's timing)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
 def oracle_sample(max_seconds=25.0):
     """Time the FP64 oracle on the first PPN steps of the same beam (bounded)."""
     from oracle import oracle as O
@@ -545,7 +635,7 @@ def oracle_sample(max_seconds=25.0):
             break
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n} PPN time steps of the 20x20x80 twisting beam, single-threaded FP64"}
+            "sample": f"first {n} PPN time steps of the 20x20x80 twisting beam, single-threaded FP64", **host_cpu()}
 
 
 def main():
@@ -556,9 +646,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppn-only", action="store_true", help="skip the PN comparison run")
-    ap.add_argument("--workload", default="beam", choices=["beam", "batched", "serving", "ablation", "contact"],
+    ap.add_argument("--workload", default="beam",
+                    choices=["beam", "batched", "serving", "ablation", "contact", "seeds"],
                     help="beam: the headline line; batched / serving: the multi-scene workloads; "
-                         "ablation: the alpha/beta sweep; contact: boxes under a press in a cylinder")
+                         "ablation: the alpha/beta sweep; contact: boxes under a press in a cylinder; "
+                         "seeds: the beam for jitter seeds 0-4")
     ap.add_argument("--profile-pcg", type=int, default=0, metavar="ITERS",
                     help="run fixed-length PCG solves for an ncu capture instead of the benchmark")
     args = ap.parse_args()
@@ -572,7 +664,8 @@ def main():
         if args.workload == "contact":
             r = run_contact(steps=args.steps, warmup=args.warmup)
         else:
-            r = {"batched": run_batched, "serving": run_serving, "ablation": run_ablation}[args.workload]()
+            r = {"batched": run_batched, "serving": run_serving, "ablation": run_ablation,
+                 "seeds": run_seeds}[args.workload]()
         if int(os.environ.get("RANK", 0)) == 0:
             print(json.dumps({"workload": args.workload, **r}))
         return
@@ -609,7 +702,7 @@ def main():
         line = dict(base, impl="reference", value=v, ms_per_step=1e3 * sum(per_step) / k,
                     steps=k, p50_ms=1e3 * percentile(per_step, 0.5), p99_ms=1e3 * percentile(per_step, 0.99),
                     cpu_baseline={"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                                  "sample": f"first {k} PPN steps of the beam (bounded to ~150 s)"},
+                                  "sample": f"first {k} PPN steps of the beam (bounded to ~150 s)", **host_cpu()},
                     e2e={"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
         print(json.dumps(line))
         return
