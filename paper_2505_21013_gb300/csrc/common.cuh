@@ -130,6 +130,7 @@ struct SceneDev {
   int* cproj_stamp;        // nv: Newton-iteration id at which the contact element was projected
   int* cround_stamp;       // nv: selection round of that projection
   T* dHc;                  // nv x 9: clamping update of the contact element
+  T* Hc;                   // nv x 9: Hessian of the vertex's contact potential at the iterate of the last gradient
   // Dirichlet by penalty (pen_k > 0): constrained vertices are free and carry pen_k m / (2 dt^2) |u - t|^2
   double pen_k;
   const uint8_t* con;      // nv: 1 for a constrained vertex

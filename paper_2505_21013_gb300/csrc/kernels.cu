@@ -179,9 +179,11 @@ __global__ void __launch_bounds__(TILE) k_gradient(const SceneDev<T>* scenes, co
       if (S.obs->n > 0) {  // barrier potentials of the analytic obstacles
         const double4 X = ld_d4(S.X + v);
         const double x[3] = {X.x + uv.x, X.y + uv.y, X.z + uv.z};
-        double gc[3];
+        double gc[3], hc[9];
         bool act = false;
-        vertex_contact(S, x, nullptr, gc, nullptr, &act);
+        vertex_contact(S, x, nullptr, gc, hc, &act);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) S.Hc[(size_t)9 * v + k] = (T)hc[k];  // for the assembly's diagonal
         for (int k = 0; k < 3; ++k) {
           g[k] += gc[k];
           a[k] += fabs(gc[k]);
@@ -223,21 +225,6 @@ __device__ __forceinline__ void add_elem_block(const T* rec, int a, int b, T* ac
 #pragma unroll
       for (int k = 0; k < 3; ++k) acc[3 * i + k] += p[3 * k + i];
   }
-}
-
-// contact element of vertex i (and its clamping, if projected before assembly),
-// added to its diagonal block; out of line, off the assembly's main path
-template <typename T>
-__device__ __noinline__ void add_contact_block(const SceneDev<T>& S, int i, int use_probe, int it, T* acc) {
-  const double4 X = ld_d4(S.X + i), u = ld_d4((use_probe ? S.u_probe : S.u) + i);
-  const double x[3] = {X.x + u.x, X.y + u.y, X.z + u.z};
-  double Hc[9];
-  vertex_contact(S, x, nullptr, nullptr, Hc, nullptr);
-#pragma unroll
-  for (int q = 0; q < 9; ++q) acc[q] += (T)Hc[q];
-  if (S.cproj_stamp[i] == it)
-#pragma unroll
-    for (int q = 0; q < 9; ++q) acc[q] += S.dHc[(size_t)9 * i + q];
 }
 
 // A warp assembles 32 consecutive blocks from their contribution list (the
@@ -317,7 +304,13 @@ __global__ void __launch_bounds__(TILE, 4) k_assemble(const SceneDev<T>* scenes,
       acc[0] += m;
       acc[4] += m;
       acc[8] += m;
-      if (S.obs->n > 0) add_contact_block(S, i, use_probe, it, acc);
+      if (S.obs->n > 0) {  // the contact element of vertex i (Hessian from k_gradient at this iterate), and
+#pragma unroll             // its clamping if projected before assembly
+        for (int q = 0; q < 9; ++q) acc[q] += S.Hc[(size_t)9 * i + q];
+        if (S.cproj_stamp[i] == it)
+#pragma unroll
+          for (int q = 0; q < 9; ++q) acc[q] += S.dHc[(size_t)9 * i + q];
+      }
     }
   }
 #pragma unroll

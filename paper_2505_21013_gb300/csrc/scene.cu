@@ -375,6 +375,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   s.obs = d_obs;
   s.cround_stamp = alloc<int>(nv);
   s.dHc = alloc<T>((size_t)9 * nv);
+  s.Hc = alloc<T>((size_t)9 * nv);
   s.round_stamp = alloc<int>(nt);
   s.sel_list = alloc<int>(nt);
   s.dx = alloc<V4>(nv);
@@ -409,7 +410,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   if (!d_tets || !d_tetc || !d_mass || !d_fixed || !d_con || !s.tgt || !d_X || !d_vt_ptr || !d_vt_src || !d_row_ptr ||
       !d_col || !d_blk_row || !d_blk_ptr || !d_blk_src || !d_diag || !s.u || !s.u_n || !s.vel ||
       !s.uhat || !s.u_probe || !s.ge || !s.He || !s.dH || !s.g || !s.gmax || !s.val ||
-      !s.proj_stamp || !s.round_stamp || !s.cproj_stamp || !d_obs || !s.cround_stamp || !s.dHc || !s.sel_list || !s.dx || !s.r || !s.z || !s.q || !s.d0 ||
+      !s.proj_stamp || !s.round_stamp || !s.cproj_stamp || !d_obs || !s.cround_stamp || !s.dHc || !s.Hc || !s.sel_list || !s.dx || !s.r || !s.z || !s.q || !s.d0 ||
       !s.d1 || !s.Pinv || !s.vpart || !s.tpart || !s.ppart || !s.pword || (sizeof(T) == 4 && !s.zrec) || !s.ctl || !d_desc || !d_ids ||
       !d_bar || !d_fixed_list || !d_targets || !d_xyz || !d_ttiles || !d_vtiles || !d_btiles ||
       !d_ptiles || !d_etiles || !d_projtiles) {
@@ -729,6 +730,8 @@ static ppn_status probe_assemble(SceneImpl<T>& s, const double* x, const uint8_t
       }
   PPN_CU(cudaMemcpyAsync(s.d.proj_stamp, stamp.data(), sizeof(int) * s.nt, cudaMemcpyHostToDevice, s.stream));
   if ((rc = probe_clamp_list(s, p, sel))) return rc;
+  // the contact Hessians come from the gradient pass at the same positions
+  if (s.n_obst > 0) launch_gradient<T>(p.G->d_desc, p.G->d_vtiles, p.G->n_vtiles, 1, s.stream);
   launch_assemble<T>(p.G->d_desc, p.G->d_btiles, p.G->n_btiles, s.stream, 1);
   PPN_CU(cudaGetLastError());
   PPN_CU(cudaStreamSynchronize(s.stream));
