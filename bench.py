@@ -217,6 +217,7 @@ def run_ours(args, rank, world, dist):
             dist.barrier()
         kt = sc.kernel_times() if profile else None
         cg = sum(it["cg_iters"] for its in iters for it in its)
+        info = sc.info()  # with the layout of the last solve
         sc.close()
         return lat, stats, kt, info, cg
 
@@ -264,6 +265,7 @@ def run_ours(args, rank, world, dist):
         peak = peaks["hbm_gbs"] if peaks else 6800.0
         prof = pcg_profile_traffic()
         roof = {"bound": "hbm", "kernel": "k_pcg_sr (resident single-reduction block-Jacobi PCG)",
+                "layout": P.PCG_LAYOUTS.get(info.get("pcg_layout", -1), "unknown"),
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": round(prof["bytes"]) if prof else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",

@@ -145,6 +145,10 @@ typedef struct {
   int64_t n_verts, n_tets, n_fixed, nnzb, n_map;
   int64_t device_bytes;  /* device memory owned by the scene */
   int precision;
+  /* layout of the scene's last linear solve: -1 none yet; FP32 single-reduction
+   * kernel 0 resident, 1 blocks streamed, 2 global vectors, 3 resident with the
+   * halo replicated; 4 the standard resident kernel; 5 the global-memory kernel */
+  int pcg_layout;
 } ppn_scene_info;
 
 /* Per kernel family: launches and summed device time (CUDA events on the scene

@@ -5,8 +5,8 @@ C ABI (``include/ppn.h``).  ``ppn`` is the ctypes binding; ``build`` compiles
 """
 
 from . import ppn  # noqa: F401
-from .ppn import (MODE_NEWTON, MODE_PDN, MODE_PN, MODE_PPN, PREC_FP64, PREC_MIXED, PROJ_CLAMP,  # noqa: F401
-                  PROJ_MIRROR, PPNError, Scene, Server, ppn_default_params, ppn_step_batch)
+from .ppn import (MODE_NEWTON, MODE_PDN, MODE_PN, MODE_PPN, PCG_LAYOUTS, PREC_FP64, PREC_MIXED,  # noqa: F401
+                  PROJ_CLAMP, PROJ_MIRROR, PPNError, Scene, Server, ppn_default_params, ppn_step_batch)
 
 __all__ = ["ppn", "Scene", "Server", "PPNError", "ppn_default_params", "ppn_step_batch", "MODE_NEWTON", "MODE_PN",
-           "MODE_PPN", "MODE_PDN", "PROJ_CLAMP", "PROJ_MIRROR", "PREC_FP64", "PREC_MIXED"]
+           "MODE_PPN", "MODE_PDN", "PCG_LAYOUTS", "PROJ_CLAMP", "PROJ_MIRROR", "PREC_FP64", "PREC_MIXED"]

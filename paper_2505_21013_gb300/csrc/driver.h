@@ -98,6 +98,11 @@ struct Group {
   int tune_choice = 0;
   std::vector<int> tune_slots;
   unsigned long long* d_flags = nullptr;  // its per-CTA publication flags
+  // SR_HALO tables of that tile table (PcgLaunch): offsets, local columns, halo rows
+  int* d_halo = nullptr;
+  size_t cap_halo = 0;
+  const int *halo_off = nullptr, *halo_col = nullptr, *halo_ref = nullptr;
+  int halo_cap = 0;
   GridBar* d_bar = nullptr;
   cudaStream_t st = nullptr;
   Staging staging;
@@ -120,6 +125,8 @@ struct Group {
     if (h_bar) cudaFreeHost(h_bar);
     h_ctl = nullptr;
     h_bar = nullptr;
+    d_halo = nullptr;
+    cap_halo = 0;
     cap_n = cap_tt = cap_vt = cap_bt = cap_pt = cap_et = cap_proj = 0;
   }
   template <typename X>
@@ -351,6 +358,14 @@ struct Driver {
       L.smem_bytes = G.pcg_smem_bytes;
       L.smem_blocks = G.pcg_smem_blocks;
       L.sr_mode = G.pcg_sr_mode;
+      L.halo_off = G.halo_off;
+      L.halo_col = G.halo_col;
+      L.halo_ref = G.halo_ref;
+      L.halo_cap = G.halo_cap;
+      for (size_t k = 0; k < sl.size() && k < (size_t)HALO_MAX_SCENES; ++k) {
+        L.zrec[k] = G.h_desc[sl[k]].zrec;
+        L.zrec_bytes[k] = sizeof(T) * 16 * (size_t)G.S[sl[k]]->nv;
+      }
       const bool tune = G.pcg_sr && G.pcg_tune && ids.size() <= (size_t)PCG_MAX_SCENES;
       if (tune) {
         G.tune_choice = pcg_tuner().choose(G.tune_key);
@@ -363,6 +378,7 @@ struct Driver {
           }
         PPN_CU(cudaEventRecord(G.tune_ev[0], G.st));
       }
+      for (int k : sl) G.S[k]->last_pcg_layout = G.pcg_sr ? L.sr_mode : L.smem_bytes ? 4 : 5;
       L.launch_seq = ++G.pcg_launch_seq;
       L.flags = G.d_flags;
       L.n_pword = (int)sl.size();
@@ -394,15 +410,82 @@ struct Driver {
     return PPN_OK;
   }
 
+  // SR_HALO tables for `grid` CTAs over the tile table (the layout of
+  // PcgLaunch::halo_*): per CTA, the rows of other CTAs that its rows' columns
+  // refer to, in launch order, and each of its blocks' local column.  Returns
+  // the most halo rows of one CTA, or -1 when a scene is too large to refer to.
+  int build_halo(const std::vector<int>& sl, const std::vector<TileRef>& tt, int grid, std::vector<int>& tab) {
+    const int n_tiles = (int)tt.size();
+    const size_t ns = sl.size();
+    std::vector<int> toff(ns + 1, 0);
+    for (size_t k = 0; k < ns; ++k) {
+      if (G.S[sl[k]]->nv >= (1 << HALO_ROW_BITS)) return -1;
+      toff[k + 1] = toff[k] + G.S[sl[k]]->n_ptiles;
+    }
+    std::vector<std::vector<int>> mark(ns), hidx(ns);
+    for (size_t k = 0; k < ns; ++k) {
+      mark[k].assign(G.S[sl[k]]->nv, -1);
+      hidx[k].assign(G.S[sl[k]]->nv, 0);
+    }
+    std::vector<int> off(2 * (grid + 1), 0), col, ref;
+    std::vector<long long> hs;
+    int maxh = 0;
+    // every block of CTA b's rows, in the kernel's order (tiles, rows, blocks ascending)
+    auto blocks = [&](int t0, int t1, auto&& f) {
+      for (int t = t0; t < t1; ++t) {
+        const int k = tt[t].scene;
+        const SceneImpl<T>& sc = *G.S[sl[k]];
+        const int r0 = tt[t].tile * PCG_TILE, r1 = std::min(sc.nv, r0 + PCG_TILE);
+        for (int r = r0; r < r1; ++r)
+          for (int64_t q = sc.h_row_ptr[r]; q < sc.h_row_ptr[r + 1]; ++q) {
+            const int j = sc.h_col[q];
+            f(k, j, toff[k] + j / PCG_TILE);
+          }
+      }
+    };
+    for (int b = 0; b < grid; ++b) {
+      const int t0 = (int)(((long long)b * n_tiles) / grid), t1 = (int)(((long long)(b + 1) * n_tiles) / grid);
+      const int n_items = (t1 - t0) * PCG_TILE;
+      off[2 * b] = (int)col.size();
+      off[2 * b + 1] = (int)ref.size();
+      hs.clear();
+      blocks(t0, t1, [&](int k, int j, int gt) {
+        if ((gt < t0 || gt >= t1) && mark[k][j] != b) {
+          mark[k][j] = b;
+          hs.push_back(((long long)k << 32) | j);
+        }
+      });
+      std::sort(hs.begin(), hs.end());
+      for (size_t h = 0; h < hs.size(); ++h) {
+        const int k = (int)(hs[h] >> 32), j = (int)(hs[h] & 0xffffffffll);
+        hidx[k][j] = (int)h;
+        ref.push_back((k << HALO_ROW_BITS) | j);
+      }
+      blocks(t0, t1, [&](int k, int j, int gt) {
+        col.push_back(gt >= t0 && gt < t1 ? (gt - t0) * PCG_TILE + j % PCG_TILE : n_items + hidx[k][j]);
+      });
+      maxh = std::max(maxh, (int)hs.size());
+    }
+    off[2 * grid] = (int)col.size();
+    off[2 * grid + 1] = (int)ref.size();
+    tab = off;
+    tab.insert(tab.end(), col.begin(), col.end());
+    tab.insert(tab.end(), ref.begin(), ref.end());
+    return maxh;
+  }
+
   // Choose the PCG kernel for the launch's tile table.  FP32 (unless
   // PPN_PCG_STD is set): the single-reduction kernel, with the rows' BSR blocks
-  // and vectors resident in shared memory when they fit, else the vectors
+  // and vectors resident in shared memory and the halo replicated when they fit
+  // (unless PPN_PCG_NO_HALO is set), else without the halo, else the vectors
   // alone, else neither.  Otherwise the standard resident kernel when its
   // layout fits, else the global-memory kernel.
   void plan_smem(const std::vector<int>& sl, const std::vector<TileRef>& tt) {
     G.pcg_smem_bytes = 0;
     G.pcg_sr = false;
     G.pcg_tune = false;
+    G.halo_off = G.halo_col = G.halo_ref = nullptr;
+    G.halo_cap = 0;
     if (std::getenv("PPN_PCG_GLOBAL")) return;
     const int n_tiles = (int)tt.size();
     // largest rows / blocks of one CTA when n_tiles are split over `grid` CTAs
@@ -435,9 +518,36 @@ struct Driver {
       bool fits[3] = {false, false, false};
       size_t bytes[3];
       for (int mode = first; mode <= SR_GLOBAL; ++mode) {
-        bytes[mode] = pcg_sr_smem_bytes(max_items, mode == SR_RES ? max_blocks : 0, mode);
+        bytes[mode] = pcg_sr_smem_bytes(max_items, mode == SR_RES ? max_blocks : 0, 0, mode);
         fits[mode] = bytes[mode] <= (size_t)212 * 1024 && pcg_sr_max_grid(dev, bytes[mode], mode) >= grid;
         if (fits[mode] && (mode == SR_RES || f_str || f_gl)) break;
+      }
+      if (first == SR_RES && fits[SR_RES] && sl.size() <= (size_t)HALO_MAX_SCENES && !std::getenv("PPN_PCG_NO_HALO")) {
+        std::vector<int> tab;
+        const int nh = build_halo(sl, tt, grid, tab);
+        const size_t hb = nh < 0 ? 0 : pcg_sr_smem_bytes(max_items, max_blocks, nh, SR_HALO);
+        if (nh >= 0 && hb <= (size_t)227 * 1024 && pcg_sr_max_grid(dev, hb, SR_HALO) >= grid) {
+          if (tab.size() > G.cap_halo) {
+            if (G.d_halo) {  // (cudaFree waits for launches that may still read it)
+              G.allocs.erase(std::find(G.allocs.begin(), G.allocs.end(), (void*)G.d_halo));
+              cudaFree(G.d_halo);
+            }
+            G.d_halo = G.template alloc<int>(tab.size());
+            G.cap_halo = G.d_halo ? tab.size() : 0;
+          }
+          if (G.d_halo && G.upload(G.d_halo, tab.data(), sizeof(int) * tab.size()) == PPN_OK) {
+            G.halo_off = G.d_halo;
+            G.halo_col = G.d_halo + 2 * (grid + 1);
+            G.halo_ref = G.halo_col + tab[2 * grid];
+            G.halo_cap = nh;
+            G.pcg_smem_bytes = hb;
+            G.pcg_smem_blocks = max_blocks;
+            G.pcg_smem_grid = grid;
+            G.pcg_sr = true;
+            G.pcg_sr_mode = SR_HALO;
+            return;
+          }
+        }
       }
       for (int mode = first; mode <= SR_GLOBAL; ++mode) {
         if (!fits[mode]) continue;

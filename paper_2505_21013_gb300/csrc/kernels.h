@@ -38,8 +38,10 @@ struct GridBar {
   int pad;
 };
 
-constexpr int PCG_MAX_SCENES = 64;
-constexpr int XCH_MAX_CTAS_HOST = 1024;  // CTAs of one resident PCG launch  // scenes per PCG launch (per-CTA scalar state in shared memory)
+constexpr int PCG_MAX_SCENES = 64;      // scenes per PCG launch (per-CTA scalar state in shared memory)
+constexpr int XCH_MAX_CTAS_HOST = 1024;  // CTAs of one resident PCG launch
+constexpr int HALO_MAX_SCENES = 8;       // scenes per launch of the halo layout (SR_HALO)
+constexpr int HALO_ROW_BITS = 26;        // halo reference: slot << HALO_ROW_BITS | row
 
 struct PcgLaunch {
   int n_tiles;           // PCG row tiles in the launch's tile table (TileRef.scene = slot)
@@ -52,7 +54,18 @@ struct PcgLaunch {
   int use_b_from_g;      // 1: b = -g of the scene; 0: b given in r (probe)
   size_t smem_bytes;     // > 0: shared-memory-resident kernel with this dynamic size
   int smem_blocks;       // block capacity of that layout (max blocks of one CTA)
-  int sr_mode;           // single-reduction kernel: SR_RES, SR_STREAM or SR_GLOBAL
+  int sr_mode;           // single-reduction kernel: SR_RES, SR_STREAM, SR_GLOBAL or SR_HALO
+  // SR_HALO tables, device (built by the host for this tile table and grid):
+  //   halo_off[2 b], halo_off[2 b + 1]: first block and first halo row of CTA b (b <= grid)
+  //   halo_col[k]: local column of the launch's k-th block (CTA order, rows ascending):
+  //                own row item, or n_items + the column's index in the CTA's halo list
+  //   halo_ref[h]: halo rows, slot << HALO_ROW_BITS | row, ascending per CTA
+  const int* halo_off;
+  const int* halo_col;
+  const int* halo_ref;
+  int halo_cap;          // most halo rows of one CTA
+  void* zrec[HALO_MAX_SCENES];  // SR_HALO: exchange records of the slots (zeroed before the launch)
+  size_t zrec_bytes[HALO_MAX_SCENES];
   unsigned launch_seq;
   unsigned long long* flags;  // single-reduction kernel: per-CTA publication flags (grid words)
   int n_pword;           // stamped partial arrays to clear before the launch
@@ -66,10 +79,11 @@ size_t pcg_smem_bytes(int ni, int nb, int fsize);
 int pcg_smem_max_grid(int group, int device, size_t smem, int fsize);
 // single-reduction FP32 PCG (pcg_sr.cu).  Layouts: BSR blocks and vectors in
 // shared memory (SR_RES); vectors in shared memory, blocks streamed (SR_STREAM);
-// both in global memory (SR_GLOBAL).  Shared memory for ni rows / nb blocks,
-// co-resident grid, launch.
-constexpr int SR_RES = 0, SR_STREAM = 1, SR_GLOBAL = 2;
-size_t pcg_sr_smem_bytes(int ni, int nb, int mode);
+// both in global memory (SR_GLOBAL); as SR_RES plus a replicated halo, which
+// removes the neighbour exchange (SR_HALO).  Shared memory for ni rows / nb
+// blocks / nh halo rows, co-resident grid, launch.
+constexpr int SR_RES = 0, SR_STREAM = 1, SR_GLOBAL = 2, SR_HALO = 3;
+size_t pcg_sr_smem_bytes(int ni, int nb, int nh, int mode);
 int pcg_sr_max_grid(int device, size_t smem, int mode);
 cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cudaStream_t st);
 // one warp waits (at most `limit` polling rounds) for n stamped words to reach `stamp`; *out = 1 if it ran out

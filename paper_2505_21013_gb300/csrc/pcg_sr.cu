@@ -23,16 +23,31 @@
 // read-only path.  SR_GLOBAL, for rows that do not fit, keeps the vectors in
 // the scene's global PCG arrays as well (x in dx, r in z, w in q, p in d0,
 // s in d1, the inverse in Pinv), each row touched only by its own CTA.  In
-// every layout only u crosses CTAs, through a global array.
+// these three layouts only u crosses CTAs, through a global array.  SR_HALO
+// keeps what SR_RES keeps and replicates the CTA's halo (the rows of other
+// CTAs that columns of its rows refer to): for each halo row it holds r, s
+// and the block-Jacobi inverse and repeats the owner's update of them, so u
+// of the halo rows is formed in place and the SpMV reads shared memory only.
+// What crosses CTAs is then w of the halo rows, which the update needs.
 //
-// Synchronisation.  A CTA publishes its u values, then a flag with the
-// iteration's stamp; before its SpMV it waits only for the flags of the CTAs
-// that own the columns of its rows (a contiguous CTA range found at set-up).
-// The reduction's tile partials go out as stamped words after the SpMV, and
-// every CTA sums them in tile order.  One u array suffices: a CTA overwrites
-// it only after it has seen every CTA's partials of the previous iteration,
-// which each CTA posts after finishing the SpMV that read the old values.
-// All waits are bounded.
+// Synchronisation.  SR_RES, SR_STREAM, SR_GLOBAL: a CTA publishes its u
+// values, then a flag with the iteration's stamp; before its SpMV it waits
+// only for the flags of the CTAs that own the columns of its rows (a
+// contiguous CTA range found at set-up).  The reduction's tile partials go out
+// as stamped words after the SpMV, and every CTA sums them in tile order.  One
+// u array suffices: a CTA overwrites it only after it has seen every CTA's
+// partials of the previous iteration, which each CTA posts after finishing the
+// SpMV that read the old values.  SR_HALO: the SpMV stores w of each row as
+// three stamped 64-bit words (the partials' format) in one of two parity
+// buffers; while some warps wait for the reduction's words, the others read
+// the halo rows' w words, each valid once it carries the iteration's stamp.
+// A CTA overwrites a buffer two iterations later, after every CTA has posted
+// the partials that follow its reads.  This leaves one synchronisation per
+// iteration, the reduction.  All waits are bounded.
+//
+// Every layout evaluates the same expressions in the same order, through the
+// explicit fused multiply-adds of the helpers below: all four give the same
+// bits, and a replicated halo row the bits of its owner.
 #include "pcg_common.cuh"
 
 namespace ppn {
@@ -47,17 +62,20 @@ constexpr int NQ = 4;     // reduction slots: gamma, delta, rho, failed diagonal
 struct SrLayout {
   float* lws;    // [(ni / PCG_TILE + 1) * 16 * NQ] partial sums per 16-row group (8 per tile)
   TileRef* ltt;  // [ni / PCG_TILE + 1] the CTA's tiles
-  int* lrp;      // SR_RES: [ni + 1] local row pointers
-  int* lcol;     // SR_RES: [nb]
-  float* lval;   // SR_RES: [nb * 9]
-  float* lP;     // SR_RES, SR_STREAM: [ni * 9]
-  float *lx, *lr, *lu, *lw, *lp, *ls;  // SR_RES, SR_STREAM: [ni * 3] each
+  int* lrp;      // SR_RES, SR_HALO: [ni + 1] local row pointers
+  int* lcol;     // SR_RES: [nb] columns; SR_HALO: [nb] local columns (own item, or ni + halo index)
+  float* lval;   // SR_RES, SR_HALO: [nb * 9]
+  float* lP;     // SR_RES, SR_STREAM, SR_HALO: [ni * 6] inverse (00 01 02 11 12 22 of the symmetric block)
+  float *lx, *lr, *lu, *lw, *lp, *ls;  // SR_RES, SR_STREAM: [ni * 3] each; SR_HALO: all but lu
+  float4* lu4;   // SR_HALO: [ni + nh] u of the own rows, then of the halo rows (w while it arrives)
+  float *hr, *hs, *hP;  // SR_HALO: [nh * 3], [nh * 3], [nh * 6] r, s and inverse of the halo rows
+  int* href;     // SR_HALO: [nh] halo rows (slot << HALO_ROW_BITS | row)
 };
 
 __host__ __device__ inline size_t up16(size_t b) { return (b + 15) & ~size_t(15); }
 
 // the layout's pieces in carving order (nullptr base: sizes only)
-__host__ __device__ inline size_t carve_sr(char* base, int ni, int nb, int mode, SrLayout* L) {
+__host__ __device__ inline size_t carve_sr(char* base, int ni, int nb, int nh, int mode, SrLayout* L) {
   const int ntl = ni / PCG_TILE + 1;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -68,18 +86,65 @@ __host__ __device__ inline size_t carve_sr(char* base, int ni, int nb, int mode,
   SrLayout l{};
   l.lws = (float*)take(sizeof(float) * ntl * 16 * NQ);
   l.ltt = (TileRef*)take(sizeof(TileRef) * ntl);
-  if (mode == SR_RES) {
+  if (mode == SR_RES || mode == SR_HALO) {
     l.lrp = (int*)take(sizeof(int) * (ni + 1));
     l.lcol = (int*)take(sizeof(int) * nb);
     l.lval = (float*)take(sizeof(float) * 9 * nb);
   }
   if (mode != SR_GLOBAL) {
-    l.lP = (float*)take(sizeof(float) * 9 * ni);
+    l.lP = (float*)take(sizeof(float) * 6 * ni);
     float** v[6] = {&l.lx, &l.lr, &l.lu, &l.lw, &l.lp, &l.ls};
-    for (float** q : v) *q = (float*)take(sizeof(float) * 3 * ni);
+    for (float** q : v)
+      if (mode != SR_HALO || q != &l.lu) *q = (float*)take(sizeof(float) * 3 * ni);
+  }
+  if (mode == SR_HALO) {
+    l.lu4 = (float4*)take(sizeof(float4) * (ni + nh));
+    l.hr = (float*)take(sizeof(float) * 3 * nh);
+    l.hs = (float*)take(sizeof(float) * 3 * nh);
+    l.hP = (float*)take(sizeof(float) * 6 * nh);
+    l.href = (int*)take(sizeof(int) * nh);
   }
   if (L) *L = l;
   return off;
+}
+
+// ---- the arithmetic every layout shares (explicit rounding, so that all
+// layouts, and a halo row and its owner, give the same bits)
+// a BSR block times v, accumulated: ax += a[0:3].v, ay += a[3:6].v, az += a[6:9].v
+__device__ __forceinline__ void blk_mv(const float* a, float vx, float vy, float vz, float& ax, float& ay,
+                                       float& az) {
+  ax = __fmaf_rn(a[2], vz, __fmaf_rn(a[1], vy, __fmaf_rn(a[0], vx, ax)));
+  ay = __fmaf_rn(a[5], vz, __fmaf_rn(a[4], vy, __fmaf_rn(a[3], vx, ay)));
+  az = __fmaf_rn(a[8], vz, __fmaf_rn(a[7], vy, __fmaf_rn(a[6], vx, az)));
+}
+__device__ __forceinline__ float dot3(float a0, float a1, float a2, float b0, float b1, float b2) {
+  return __fmaf_rn(a2, b2, __fmaf_rn(a1, b1, __fmul_rn(a0, b0)));
+}
+// u = P r, P symmetric, q = its entries 00 01 02 11 12 22
+__device__ __forceinline__ void prec6(const float* q, const float* r, float* u) {
+  u[0] = dot3(q[0], q[1], q[2], r[0], r[1], r[2]);
+  u[1] = dot3(q[1], q[3], q[4], r[0], r[1], r[2]);
+  u[2] = dot3(q[2], q[4], q[5], r[0], r[1], r[2]);
+}
+__device__ __forceinline__ void sym6(const float* P, float* q) {
+  q[0] = P[0], q[1] = P[1], q[2] = P[2], q[3] = P[4], q[4] = P[5], q[5] = P[8];
+}
+// s = w + beta s, r -= alpha s (one component): the part a halo row repeats
+__device__ __forceinline__ void upd_sr(float a, float b, float w, float& sv, float& r) {
+  sv = __fmaf_rn(b, sv, w);
+  r = __fmaf_rn(-a, sv, r);
+}
+// p = u + beta p, x += alpha p (one component)
+__device__ __forceinline__ void upd_px(float a, float b, float u, float& p, float& x) {
+  p = __fmaf_rn(b, p, u);
+  x = __fmaf_rn(a, p, x);
+}
+__device__ __forceinline__ void st_relaxed_v2_u64(unsigned long long* p, unsigned long long a, unsigned long long b) {
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1,%2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ void ld_relaxed_v2_u64(const unsigned long long* p, unsigned long long& a,
+                                                  unsigned long long& b) {
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0,%1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
 
 // u of row i: the first four floats of the row's 32-byte record in zrec
@@ -159,25 +224,27 @@ __device__ __forceinline__ void sr_step(SState<float>& s, float gam, float del, 
 
 }  // namespace
 
-size_t pcg_sr_smem_bytes(int ni, int nb, int mode) { return carve_sr(nullptr, ni, nb, mode, nullptr); }
+size_t pcg_sr_smem_bytes(int ni, int nb, int nh, int mode) { return carve_sr(nullptr, ni, nb, nh, mode, nullptr); }
 
 template <int MODE>
 __global__ void __launch_bounds__(NTP, 1)
     k_pcg_sr(const SceneDev<float>* scenes, const TileRef* tiles, int n_tiles, const int* scene_ids,
-               int n_scenes, GridBar* bar, int b_from_g, int nb_cap, unsigned long long* flags) {
+               int n_scenes, GridBar* bar, int b_from_g, int nb_cap, unsigned long long* flags,
+               const int* halo_off, const int* halo_col, const int* halo_ref, int nh_cap) {
   using W = Words<float>;
-  constexpr bool RES = MODE == SR_RES, GV = MODE == SR_GLOBAL;
+  constexpr bool HALO = MODE == SR_HALO, RES = MODE == SR_RES || HALO, GV = MODE == SR_GLOBAL;
+  constexpr int MS = HALO ? HALO_MAX_SCENES : PCG_MAX_SCENES;  // scenes of one launch
   constexpr int GP = 2;                 // lanes per BSR row in the SpMV
   constexpr int RPP = NTP / GP;         // rows per SpMV pass
   constexpr int U = 16 / GP;            // blocks per lane per gather round
   constexpr int NW = NTP / 32;          // warps
   static_assert(RPP % PCG_TILE == 0 && NTP % PCG_TILE == 0, "passes cover whole tiles");
-  static_assert(PCG_MAX_SCENES <= NTP, "one thread per scene in the scalar step");
+  static_assert(MS <= NTP, "one thread per scene in the scalar step");
   extern __shared__ __align__(16) char dyn[];
-  __shared__ SState<float> st[PCG_MAX_SCENES];
-  __shared__ SceneLite<float> sl[PCG_MAX_SCENES];
-  __shared__ float s_sum[PCG_MAX_SCENES][NQ];
-  __shared__ int s_toff[PCG_MAX_SCENES];
+  __shared__ SState<float> st[MS];
+  __shared__ SceneLite<float> sl[MS];
+  __shared__ float s_sum[MS][NQ];
+  __shared__ int s_toff[MS];
   __shared__ int s_to, s_lo, s_hi;
   __shared__ int s_scan[NW];
 
@@ -188,7 +255,11 @@ __global__ void __launch_bounds__(NTP, 1)
   const int ntl = t1 - t0;
   const int n_items = ntl * PCG_TILE;
   SrLayout L;
-  carve_sr(dyn, n_items, nb_cap, MODE, &L);
+  carve_sr(dyn, n_items, nb_cap, nh_cap, MODE, &L);
+  // SR_HALO: this CTA's first block in halo_col, its halo rows in halo_ref
+  const int blk0 = HALO ? halo_off[2 * blockIdx.x] : 0;
+  const int h0 = HALO ? halo_off[2 * blockIdx.x + 1] : 0;
+  const int nh = HALO ? halo_off[2 * blockIdx.x + 3] - h0 : 0;
   if (tid == 0) {
     s_to = 0;
     s_lo = grid;
@@ -264,17 +335,18 @@ __global__ void __launch_bounds__(NTP, 1)
       const int kb = S.row_ptr[i], ke = S.row_ptr[i + 1];
       const size_t nb = (size_t)S.nnzb;
       for (int k = kb + lane32; k < ke; k += 32) {
-        const int j = S.col[k];
         if constexpr (RES) {
           const int b = L.lrp[item] + (k - kb);
-          L.lcol[b] = j;
+          L.lcol[b] = HALO ? halo_col[blk0 + b] : S.col[k];
 #pragma unroll
           for (int c = 0; c < 9; ++c) L.lval[9 * b + c] = S.val[c * nb + k];
         }
-        const long long gt = s_toff[slot] + j / PCG_TILE;  // tile in the launch's table
-        const int owner = (int)(((gt + 1) * grid + n_tiles - 1) / n_tiles) - 1;
-        lo = min(lo, owner);
-        hi = max(hi, owner);
+        if constexpr (!HALO) {
+          const long long gt = s_toff[slot] + S.col[k] / PCG_TILE;  // tile in the launch's table
+          const int owner = (int)(((gt + 1) * grid + n_tiles - 1) / n_tiles) - 1;
+          lo = min(lo, owner);
+          hi = max(hi, owner);
+        }
       }
     }
     atomicMin(&s_lo, lo);
@@ -290,8 +362,10 @@ __global__ void __launch_bounds__(NTP, 1)
     W::split(v, s, w);
     st_relaxed_u64(S.pword + (size_t)k * S.n_ptiles + tr.tile, w[0]);
   };
-  // every CTA sums the tile words of quantities [0, nq) of every live scene in tile order
-  auto reduce = [&](int nq, unsigned s) -> bool {
+  // every CTA sums the tile words of quantities [0, nq) of every live scene in tile order;
+  // SR_HALO: meanwhile the other warps read w of the halo rows (stamp s, buffer par) into
+  // their u slots, which the SpMV has finished reading
+  auto reduce = [&](int nq, unsigned s, int par) -> bool {
     for (int x = warp; x < n_scenes * nq; x += NW) {
       const int si = x / nq, q = x % nq;
       if (st[si].done) continue;  // warp-uniform
@@ -326,6 +400,31 @@ __global__ void __launch_bounds__(NTP, 1)
       acc = warp_sum(acc);
       if (lane32 == 0) s_sum[si][q] = acc;
     }
+    if constexpr (HALO) {
+      // the warps without tile words; all warps, after theirs, when every warp has some
+      const int fw = n_scenes * nq < NW ? n_scenes * nq : 0;
+      if (warp >= fw) {
+        for (int h = (warp - fw) * 32 + lane32; h < nh; h += (NW - fw) * 32) {
+          const int ref = L.href[h];
+          const int slot = ref >> HALO_ROW_BITS, row = ref & ((1 << HALO_ROW_BITS) - 1);
+          if (st[slot].done) continue;
+          const unsigned long long* wr =
+              reinterpret_cast<const unsigned long long*>(sl[slot].zrec) + ((size_t)par * sl[slot].nv + row) * 4;
+          unsigned long long w[3];
+          ld_relaxed_v2_u64(wr, w[0], w[1]);
+          w[2] = ld_relaxed_u64(wr + 2);
+          for (unsigned spins = 0; !(W::has(w[0], s) && W::has(w[1], s) && W::has(w[2], s)); ++spins) {
+            if (spins > kWaitSpins || *(volatile int*)&s_to) {
+              s_to = 1;
+              break;
+            }
+            ld_relaxed_v2_u64(wr, w[0], w[1]);
+            w[2] = ld_relaxed_u64(wr + 2);
+          }
+          L.lu4[n_items + h] = make_float4(W::join(w), W::join(w + 1), W::join(w + 2), 0.0f);
+        }
+      }
+    }
     __syncthreads();
     return !s_to;
   };
@@ -346,9 +445,10 @@ __global__ void __launch_bounds__(NTP, 1)
     __syncthreads();
     return !s_to;
   };
-  // w = A u over this CTA's rows, u gathered from the global array (GP lanes per row)
+  // w = A u over this CTA's rows (GP lanes per row), u gathered from the global array or, in
+  // SR_HALO, from shared memory; SR_HALO also stores w as stamped words (stamp s, buffer par)
   const unsigned long long pol = RES ? 0ull : l2_evict_first();
-  auto spmv = [&]() {
+  auto spmv = [&](unsigned s, int par) {
     for (int base = 0; base < n_items; base += RPP) {
       const int row = tid / GP, lane = tid % GP;
       const int item = base + row;
@@ -365,17 +465,12 @@ __global__ void __launch_bounds__(NTP, 1)
 #pragma unroll
             for (int u = 0; u < U; ++u) {
               const int b = b0 + GP * u;
-              if (b < le) vj[u] = ld_f4_cg(vb + (size_t)8 * L.lcol[b]);
+              if (b < le) vj[u] = HALO ? L.lu4[L.lcol[b]] : ld_f4_cg(vb + (size_t)8 * L.lcol[b]);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
               const int b = b0 + GP * u;
-              if (b < le) {
-                const float* a = L.lval + 9 * b;
-                ax += a[0] * vj[u].x + a[1] * vj[u].y + a[2] * vj[u].z;
-                ay += a[3] * vj[u].x + a[4] * vj[u].y + a[5] * vj[u].z;
-                az += a[6] * vj[u].x + a[7] * vj[u].y + a[8] * vj[u].z;
-              }
+              if (b < le) blk_mv(L.lval + 9 * b, vj[u].x, vj[u].y, vj[u].z, ax, ay, az);
             }
           }
         } else {
@@ -396,9 +491,7 @@ __global__ void __launch_bounds__(NTP, 1)
                 float a[9];
 #pragma unroll
                 for (int c = 0; c < 9; ++c) a[c] = ld_stream(S.val + c * nb + b, pol);
-                ax += a[0] * vj[u].x + a[1] * vj[u].y + a[2] * vj[u].z;
-                ay += a[3] * vj[u].x + a[4] * vj[u].y + a[5] * vj[u].z;
-                az += a[6] * vj[u].x + a[7] * vj[u].y + a[8] * vj[u].z;
+                blk_mv(a, vj[u].x, vj[u].y, vj[u].z, ax, ay, az);
               }
             }
           }
@@ -427,6 +520,19 @@ __global__ void __launch_bounds__(NTP, 1)
             const float4 uv = ld_f4_cg(u_ptr(sl[slot].zrec, i));
             r[0] = rv.x, r[1] = rv.y, r[2] = rv.z;
             u[0] = uv.x, u[1] = uv.y, u[2] = uv.z;
+          } else if constexpr (HALO) {
+            unsigned long long w[3];
+            W::split(ax, s, w);
+            W::split(ay, s, w + 1);
+            W::split(az, s, w + 2);
+            unsigned long long* wr =
+                reinterpret_cast<unsigned long long*>(sl[slot].zrec) + ((size_t)par * sl[slot].nv + i) * 4;
+            st_relaxed_v2_u64(wr, w[0], w[1]);
+            st_relaxed_u64(wr + 2, w[2]);
+            const float4 uv = L.lu4[item];
+            u[0] = uv.x, u[1] = uv.y, u[2] = uv.z;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r[c] = L.lr[3 * item + c];
           } else {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -434,9 +540,9 @@ __global__ void __launch_bounds__(NTP, 1)
               u[c] = L.lu[3 * item + c];
             }
           }
-          g = r[0] * u[0] + r[1] * u[1] + r[2] * u[2];
-          d = ax * u[0] + ay * u[1] + az * u[2];
-          rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+          g = dot3(r[0], r[1], r[2], u[0], u[1], u[2]);
+          d = dot3(ax, ay, az, u[0], u[1], u[2]);
+          rr = dot3(r[0], r[1], r[2], r[0], r[1], r[2]);
         }
       }
       // per group of 16 rows (one warp of the pass), in a fixed order
@@ -472,6 +578,20 @@ __global__ void __launch_bounds__(NTP, 1)
   };
 
   // ---------------- set-up: P = block-Jacobi inverse, x = 0, r = b, u = P r
+  // right-hand side b of row i: -g (FP64 gradient) or the given r
+  auto rhs = [&](const SceneLite<float>& S, int i, float* r) {
+    if (b_from_g) {
+      const double4 g = ld_d4(S.g + i);
+      r[0] = (float)(-g.x);
+      r[1] = (float)(-g.y);
+      r[2] = (float)(-g.z);
+    } else {
+      const float4 rv = ld_f4_cg(reinterpret_cast<const float*>(S.r + i));
+      r[0] = rv.x;
+      r[1] = rv.y;
+      r[2] = rv.z;
+    }
+  };
   for (int base = 0; base < n_items; base += NTP) {
     const int item = base + tid;
     float fail = 0.0f;
@@ -488,43 +608,43 @@ __global__ void __launch_bounds__(NTP, 1)
 #pragma unroll
         for (int c = 0; c < 9; ++c) D[c] = S.val[(size_t)c * S.nnzb + S.diag_idx[i]];
       }
-      float Pm[9];
+      float Pm[9], q[6];
       const bool ok = spd_inv3(D, Pm);
+      sym6(Pm, q);
       float* P = S.Pinv + (size_t)9 * i;
 #pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        P[c] = Pm[c];
-        if constexpr (!GV) L.lP[9 * item + c] = Pm[c];
+      for (int c = 0; c < 9; ++c) P[c] = Pm[c];
+      if constexpr (!GV) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) L.lP[6 * item + c] = q[c];
       }
-      float r0, r1, r2;
-      if (b_from_g) {
-        const double4 g = ld_d4(S.g + i);
-        r0 = (float)(-g.x);
-        r1 = (float)(-g.y);
-        r2 = (float)(-g.z);
-      } else {
-        const float4 rv = ld_f4_cg(reinterpret_cast<const float*>(S.r + i));
-        r0 = rv.x;
-        r1 = rv.y;
-        r2 = rv.z;
-      }
-      const float u0 = Pm[0] * r0 + Pm[1] * r1 + Pm[2] * r2;
-      const float u1 = Pm[3] * r0 + Pm[4] * r1 + Pm[5] * r2;
-      const float u2 = Pm[6] * r0 + Pm[7] * r1 + Pm[8] * r2;
-      st_f4(u_ptr(S.zrec, i), u0, u1, u2);
+      float r[3], u[3];
+      rhs(S, i, r);
+      prec6(q, r, u);
       if constexpr (GV) {
-        st_f4(reinterpret_cast<float*>(S.z + i), r0, r1, r2);
+        st_f4(u_ptr(S.zrec, i), u[0], u[1], u[2]);
+        st_f4(reinterpret_cast<float*>(S.z + i), r[0], r[1], r[2]);
         st_f4(reinterpret_cast<float*>(S.dx + i), 0.f, 0.f, 0.f);
         st_f4(reinterpret_cast<float*>(S.d0 + i), 0.f, 0.f, 0.f);
         st_f4(reinterpret_cast<float*>(S.d1 + i), 0.f, 0.f, 0.f);
       } else {
         const int k = 3 * item;
-        L.lr[k] = r0, L.lr[k + 1] = r1, L.lr[k + 2] = r2;
-        L.lu[k] = u0, L.lu[k + 1] = u1, L.lu[k + 2] = u2;
+        if constexpr (HALO) {
+          L.lu4[item] = make_float4(u[0], u[1], u[2], 0.0f);
+        } else {
+          st_f4(u_ptr(S.zrec, i), u[0], u[1], u[2]);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) L.lx[k + c] = L.lp[k + c] = L.ls[k + c] = 0.0f;
+          for (int c = 0; c < 3; ++c) L.lu[k + c] = u[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          L.lr[k + c] = r[c];
+          L.lx[k + c] = L.lp[k + c] = L.ls[k + c] = 0.0f;
+        }
       }
       fail = ok ? 0.0f : 1.0f;
+    } else if (HALO && item < n_items) {
+      L.lu4[item] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     fail = warp_sum(fail);  // the warp's 32 rows: its first 16-row group takes the count
     if (lane32 == 0) {
@@ -532,16 +652,43 @@ __global__ void __launch_bounds__(NTP, 1)
       L.lws[NQ * ((base >> 4) + 2 * warp + 1) + 3] = 0.0f;
     }
   }
+  // SR_HALO: the halo rows' state, as their owners set it up (same inputs, same operations)
+  if constexpr (HALO) {
+    for (int h = tid; h < nh; h += NTP) {
+      const int ref = halo_ref[h0 + h];
+      L.href[h] = ref;
+      const SceneLite<float>& S = sl[ref >> HALO_ROW_BITS];
+      const int i = ref & ((1 << HALO_ROW_BITS) - 1);
+      float D[9], Pm[9], r[3], u[3];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) D[c] = S.val[(size_t)c * S.nnzb + S.diag_idx[i]];
+      spd_inv3(D, Pm);
+      float* q = L.hP + 6 * h;
+      sym6(Pm, q);
+      rhs(S, i, r);
+      prec6(q, r, u);
+      L.lu4[n_items + h] = make_float4(u[0], u[1], u[2], 0.0f);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        L.hr[3 * h + c] = r[c];
+        L.hs[3 * h + c] = 0.0f;
+      }
+    }
+  }
 
   for (int it = 0;; ++it) {
-    // ---- u released to the neighbours (set-up wrote u_0; later iterations below)
-    publish_flag((unsigned long long)it + 1);
-    if (!wait_flags((unsigned long long)it + 1)) return fail_out();
-    spmv();  // w = A u
     const unsigned s = W::stamp((unsigned)it + 1);
+    if constexpr (HALO) {
+      __syncthreads();  // set-up, or the previous update, before the SpMV
+    } else {
+      // ---- u released to the neighbours (set-up wrote u_0; later iterations below)
+      publish_flag((unsigned long long)it + 1);
+      if (!wait_flags((unsigned long long)it + 1)) return fail_out();
+    }
+    spmv(s, it & 1);  // w = A u
     post_partials(s, it == 0);
-    if (!reduce(it == 0 ? NQ : 3, s)) return fail_out();
-    // one thread per scene (n_scenes <= PCG_MAX_SCENES < NTP); the barrier also finds whether all are done
+    if (!reduce(it == 0 ? NQ : 3, s, it & 1)) return fail_out();
+    // one thread per scene (n_scenes <= MS < NTP); the barrier also finds whether all are done
     int done = 1;
     if (tid < n_scenes) {
       if (!st[tid].done)
@@ -557,52 +704,81 @@ __global__ void __launch_bounds__(NTP, 1)
       if (i < 0 || st[slot].done) continue;
       const float a = st[slot].alpha, b = st[slot].beta;
       const SceneLite<float>& S = sl[slot];
-      float r[3], P[9];
+      float r[3], q[6], u[3];
       if constexpr (GV) {
         const float4 uv = ld_f4_cg(u_ptr(S.zrec, i));
-        const float4 pv = ld_f4_cg(reinterpret_cast<const float*>(S.d0 + i));
+        float4 pv = ld_f4_cg(reinterpret_cast<const float*>(S.d0 + i));
         const float4 wv = ld_f4_cg(reinterpret_cast<const float*>(S.q + i));
-        const float4 sv = ld_f4_cg(reinterpret_cast<const float*>(S.d1 + i));
-        const float4 xv = ld_f4_cg(reinterpret_cast<const float*>(S.dx + i));
+        float4 sv = ld_f4_cg(reinterpret_cast<const float*>(S.d1 + i));
+        float4 xv = ld_f4_cg(reinterpret_cast<const float*>(S.dx + i));
         const float4 rv = ld_f4_cg(reinterpret_cast<const float*>(S.z + i));
-        const float p0 = uv.x + b * pv.x, p1 = uv.y + b * pv.y, p2 = uv.z + b * pv.z;
-        const float s0 = wv.x + b * sv.x, s1 = wv.y + b * sv.y, s2 = wv.z + b * sv.z;
-        st_f4(reinterpret_cast<float*>(S.d0 + i), p0, p1, p2);
-        st_f4(reinterpret_cast<float*>(S.d1 + i), s0, s1, s2);
-        st_f4(reinterpret_cast<float*>(S.dx + i), xv.x + a * p0, xv.y + a * p1, xv.z + a * p2);
-        r[0] = rv.x - a * s0;
-        r[1] = rv.y - a * s1;
-        r[2] = rv.z - a * s2;
+        r[0] = rv.x, r[1] = rv.y, r[2] = rv.z;
+        upd_px(a, b, uv.x, pv.x, xv.x);
+        upd_px(a, b, uv.y, pv.y, xv.y);
+        upd_px(a, b, uv.z, pv.z, xv.z);
+        upd_sr(a, b, wv.x, sv.x, r[0]);
+        upd_sr(a, b, wv.y, sv.y, r[1]);
+        upd_sr(a, b, wv.z, sv.z, r[2]);
+        st_f4(reinterpret_cast<float*>(S.d0 + i), pv.x, pv.y, pv.z);
+        st_f4(reinterpret_cast<float*>(S.d1 + i), sv.x, sv.y, sv.z);
+        st_f4(reinterpret_cast<float*>(S.dx + i), xv.x, xv.y, xv.z);
         st_f4(reinterpret_cast<float*>(S.z + i), r[0], r[1], r[2]);
-#pragma unroll
-        for (int c = 0; c < 9; ++c) P[c] = __ldcg(S.Pinv + (size_t)9 * i + c);
+        const float* P = S.Pinv + (size_t)9 * i;
+        q[0] = __ldcg(P), q[1] = __ldcg(P + 1), q[2] = __ldcg(P + 2);
+        q[3] = __ldcg(P + 4), q[4] = __ldcg(P + 5), q[5] = __ldcg(P + 8);
       } else {
         const int k = 3 * item;
+        float uo[3];
+        if constexpr (HALO) {
+          const float4 uv = L.lu4[item];
+          uo[0] = uv.x, uo[1] = uv.y, uo[2] = uv.z;
+        } else {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) uo[c] = L.lu[k + c];
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float p = L.lu[k + c] + b * L.lp[k + c];
-          const float sv = L.lw[k + c] + b * L.ls[k + c];
-          L.lp[k + c] = p;
-          L.ls[k + c] = sv;
-          L.lx[k + c] += a * p;
-          r[c] = L.lr[k + c] - a * sv;
+          upd_px(a, b, uo[c], L.lp[k + c], L.lx[k + c]);
+          r[c] = L.lr[k + c];
+          upd_sr(a, b, L.lw[k + c], L.ls[k + c], r[c]);
           L.lr[k + c] = r[c];
         }
 #pragma unroll
-        for (int c = 0; c < 9; ++c) P[c] = L.lP[9 * item + c];
+        for (int c = 0; c < 6; ++c) q[c] = L.lP[6 * item + c];
       }
-      const float u0 = P[0] * r[0] + P[1] * r[1] + P[2] * r[2];
-      const float u1 = P[3] * r[0] + P[4] * r[1] + P[5] * r[2];
-      const float u2 = P[6] * r[0] + P[7] * r[1] + P[8] * r[2];
-      if constexpr (!GV) {
-        const int k = 3 * item;
-        L.lu[k] = u0, L.lu[k + 1] = u1, L.lu[k + 2] = u2;
+      prec6(q, r, u);
+      if constexpr (HALO) {
+        L.lu4[item] = make_float4(u[0], u[1], u[2], 0.0f);
+      } else {
+        if constexpr (!GV) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) L.lu[3 * item + c] = u[c];
+        }
+        st_f4(u_ptr(S.zrec, i), u[0], u[1], u[2]);
       }
-      st_f4(u_ptr(S.zrec, i), u0, u1, u2);
+    }
+    // SR_HALO: the halo rows repeat their owners' s, r and u updates with the owners' w
+    if constexpr (HALO) {
+      for (int h = tid; h < nh; h += NTP) {
+        const int slot = L.href[h] >> HALO_ROW_BITS;
+        if (st[slot].done) continue;
+        const float a = st[slot].alpha, b = st[slot].beta;
+        const float4 wv = L.lu4[n_items + h];
+        float r[3], u[3];
+        float* hs = L.hs + 3 * h;
+        float* hr = L.hr + 3 * h;
+        r[0] = hr[0], r[1] = hr[1], r[2] = hr[2];
+        upd_sr(a, b, wv.x, hs[0], r[0]);
+        upd_sr(a, b, wv.y, hs[1], r[1]);
+        upd_sr(a, b, wv.z, hs[2], r[2]);
+        hr[0] = r[0], hr[1] = r[1], hr[2] = r[2];
+        prec6(L.hP + 6 * h, r, u);
+        L.lu4[n_items + h] = make_float4(u[0], u[1], u[2], 0.0f);
+      }
     }
     for (int si = tid; si < n_scenes; si += NTP)
       if (!st[si].done) st[si].iters += 1;
-    // (the barrier of the next publish_flag orders these updates)
+    // (the barrier at the top of the next iteration orders these updates)
   }
 
   // x of this CTA's rows to global memory (SR_GLOBAL: already there); CTA 0 publishes the scalars
@@ -640,8 +816,12 @@ cudaError_t launch_wait_probe(const unsigned long long* w, int n, unsigned long 
 }
 
 static const void* sr_kernel(int mode) {
-  return mode == SR_RES ? (const void*)k_pcg_sr<SR_RES>
-                        : mode == SR_STREAM ? (const void*)k_pcg_sr<SR_STREAM> : (const void*)k_pcg_sr<SR_GLOBAL>;
+  switch (mode) {
+    case SR_RES: return (const void*)k_pcg_sr<SR_RES>;
+    case SR_STREAM: return (const void*)k_pcg_sr<SR_STREAM>;
+    case SR_GLOBAL: return (const void*)k_pcg_sr<SR_GLOBAL>;
+    default: return (const void*)k_pcg_sr<SR_HALO>;
+  }
 }
 
 int pcg_sr_max_grid(int device, size_t smem, int mode) {
@@ -661,8 +841,10 @@ int pcg_sr_max_grid(int device, size_t smem, int mode) {
 }
 
 cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cudaStream_t st) {
+  const bool halo = L.sr_mode == SR_HALO;
   if (L.n_scenes <= 0 || L.n_scenes > PCG_MAX_SCENES || L.n_tiles <= 0 || L.grid > XCH_MAX_CTAS || !L.flags ||
-      L.sr_mode < SR_RES || L.sr_mode > SR_GLOBAL || (L.sr_mode == SR_RES) != (L.smem_blocks > 0))
+      L.sr_mode < SR_RES || L.sr_mode > SR_HALO || (L.sr_mode == SR_RES || halo) != (L.smem_blocks > 0) ||
+      (halo && (L.n_scenes > HALO_MAX_SCENES || !L.halo_off || !L.halo_col || !L.halo_ref || L.halo_cap < 0)))
     return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(L.bar, 0, sizeof(GridBar), st);
   if (e != cudaSuccess) return e;
@@ -673,6 +855,11 @@ cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cud
     e = cudaMemsetAsync(L.pword[k], 0, L.pword_bytes[k], st);
     if (e != cudaSuccess) return e;
   }
+  for (int k = 0; halo && k < L.n_scenes; ++k) {
+    if (!L.zrec[k]) return cudaErrorInvalidValue;
+    e = cudaMemsetAsync(L.zrec[k], 0, L.zrec_bytes[k], st);
+    if (e != cudaSuccess) return e;
+  }
   const TileRef* tiles = L.tiles;
   int n_tiles = L.n_tiles;
   const int* ids = L.scene_ids;
@@ -681,8 +868,13 @@ cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cud
   int bg = L.use_b_from_g;
   int nb_cap = L.smem_blocks;
   unsigned long long* flags = L.flags;
-  void* args[] = {(void*)&scenes, (void*)&tiles, (void*)&n_tiles, (void*)&ids,  (void*)&n_scenes,
-                  (void*)&bar,    (void*)&bg,    (void*)&nb_cap,  (void*)&flags};
+  const int* h_off = halo ? L.halo_off : nullptr;
+  const int* h_col = halo ? L.halo_col : nullptr;
+  const int* h_ref = halo ? L.halo_ref : nullptr;
+  int nh_cap = halo ? L.halo_cap : 0;
+  void* args[] = {(void*)&scenes, (void*)&tiles, (void*)&n_tiles, (void*)&ids,   (void*)&n_scenes,
+                  (void*)&bar,    (void*)&bg,    (void*)&nb_cap,  (void*)&flags, (void*)&h_off,
+                  (void*)&h_col,  (void*)&h_ref, (void*)&nh_cap};
   const void* k = sr_kernel(L.sr_mode);
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
   if (e != cudaSuccess) return e;

@@ -960,6 +960,7 @@ ppn_status ppn_scene_get_info(const ppn_scene* s, ppn_scene_info* out) {
     out->n_map = x.nmap;
     out->device_bytes = (int64_t)x.dev_bytes;
     out->precision = s->precision;
+    out->pcg_layout = x.last_pcg_layout;
     return PPN_OK;
   });
 }

@@ -92,6 +92,7 @@ struct SceneImpl {
   Staging staging;
   KernelTimer timer;
   int pcg_group = 8, pcg_grid = 0;
+  int last_pcg_layout = -1;  // ppn_scene_info::pcg_layout
   // counters and per-step records
   int it_counter = 0, round_counter = 0;
   std::vector<ppn_iter_stats> iters;

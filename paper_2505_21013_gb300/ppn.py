@@ -96,7 +96,10 @@ class ppn_server_stats(C.Structure):
 class ppn_scene_info(C.Structure):
     _fields_ = [("n_verts", C.c_int64), ("n_tets", C.c_int64), ("n_fixed", C.c_int64),
                 ("nnzb", C.c_int64), ("n_map", C.c_int64), ("device_bytes", C.c_int64),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("pcg_layout", C.c_int)]
+
+
+PCG_LAYOUTS = {-1: "none", 0: "resident", 1: "streamed", 2: "global", 3: "halo", 4: "standard", 5: "standard_global"}
 
 
 class ppn_kernel_time(C.Structure):

@@ -98,6 +98,27 @@ def test_beam_full_size_pcg_residual(beam_after_one_step):
     assert np.linalg.norm(r) <= 3e-4 * np.linalg.norm(b)
 
 
+def test_beam_full_size_halo_layout_equals_resident(beam_after_one_step, monkeypatch):
+    # the benchmark's layout (152 CTAs, the halo replicated) against the layout that
+    # gathers the neighbours' u: the same bits after ~770 iterations
+    spec, g, o, _, (_, xo, _) = beam_after_one_step
+    vals = o.assemble(xo)
+    b = np.random.default_rng(13).standard_normal((spec.n_verts, 3))
+    b[spec.fixed] = 0
+    out = []
+    for env in (None, "PPN_PCG_NO_HALO"):
+        monkeypatch.delenv("PPN_PCG_NO_HALO", raising=False)
+        if env:
+            monkeypatch.setenv(env, "1")
+        sc = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
+        x, info = sc.probe_pcg(vals, b, rel_tol=1e-4)
+        out.append((x, info, P.PCG_LAYOUTS[sc.info()["pcg_layout"]]))
+        sc.close()
+    (xh, ih, lh), (xr, ir, lr) = out
+    assert (lh, lr) == ("halo", "resident")
+    assert ih == ir and ih["iters"] > 300 and np.array_equal(xh, xr)
+
+
 def test_press_full_size_contact_gradient_energy_and_step():
     spec = press_scene(n=40, boxes=4, press_speed=0.05, dt=1.0 / 60.0, seed=0)
     g = P.Scene.from_spec(spec, precision=P.PREC_MIXED)

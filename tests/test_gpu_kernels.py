@@ -198,28 +198,60 @@ def test_tiny_meshes_and_ragged_sizes():
         assert np.abs(v - o.assemble(x)).max() <= 1e-10 * np.abs(v).max()
 
 
+def _probe_layout(spec, vals, b, env, monkeypatch, rel_tol=1e-6):
+    for k in ("PPN_PCG_STREAM", "PPN_PCG_SR_GLOBAL", "PPN_PCG_NO_HALO"):
+        monkeypatch.delenv(k, raising=False)
+    if env:
+        monkeypatch.setenv(env, "1")
+    sc = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
+    x, info = sc.probe_pcg(vals, b, rel_tol=rel_tol)
+    layout = P.PCG_LAYOUTS[sc.info()["pcg_layout"]]
+    sc.close()
+    return x, info, layout
+
+
 def test_single_reduction_pcg_layouts(monkeypatch):
-    # the FP32 kernel with the BSR blocks streamed from global memory, and with the
-    # vectors in global memory too (the layouts for rows that do not fit in shared
-    # memory), performs the same operations in the same order as the resident one
-    spec = medium_spec(19)
+    # the FP32 kernel with the halo replicated (the default where it fits), with the
+    # neighbours' u gathered instead, with the BSR blocks streamed from global memory,
+    # and with the vectors in global memory too, performs the same operations in the
+    # same order: the same bits
+    spec = medium_spec(19)  # 546 rows: 5 CTAs of one tile, the last one ragged
     o = O.Scene.from_spec(spec)
     vals = o.assemble(spec.rest)  # K + M / dt^2 at rest: SPD
     rp, col = o.pattern()
     b = np.random.default_rng(21).standard_normal((spec.n_verts, 3))
     b[spec.fixed] = 0
-    res = P.Scene.from_spec(spec, precision=P.PREC_MIXED).probe_pcg(vals, b, rel_tol=1e-6)
-    monkeypatch.setenv("PPN_PCG_STREAM", "1")
-    st = P.Scene.from_spec(spec, precision=P.PREC_MIXED).probe_pcg(vals, b, rel_tol=1e-6)
-    monkeypatch.delenv("PPN_PCG_STREAM")
-    monkeypatch.setenv("PPN_PCG_SR_GLOBAL", "1")
-    gl = P.Scene.from_spec(spec, precision=P.PREC_MIXED).probe_pcg(vals, b, rel_tol=1e-6)
-    assert res[1] == st[1] == gl[1]
-    assert np.array_equal(res[0], st[0]) and np.array_equal(res[0], gl[0])
+    runs = {env: _probe_layout(spec, vals, b, env, monkeypatch)
+            for env in (None, "PPN_PCG_NO_HALO", "PPN_PCG_STREAM", "PPN_PCG_SR_GLOBAL")}
+    assert [r[2] for r in runs.values()] == ["halo", "resident", "streamed", "global"]
+    ref = runs[None]
+    for x, info, _ in runs.values():
+        assert info == ref[1] and np.array_equal(x, ref[0])
     # solved to 1e-6 in FP32: the true residual well within 1e-4
-    assert not res[1]["ind"] and not res[1]["hit_max"]
-    r = b.reshape(-1) - np.add.reduceat(np.einsum("kij,kj->ki", vals, res[0][col]), rp[:-1]).reshape(-1)
+    assert not ref[1]["ind"] and not ref[1]["hit_max"] and ref[1]["iters"] > 20
+    r = b.reshape(-1) - np.add.reduceat(np.einsum("kij,kj->ki", vals, ref[0][col]), rp[:-1]).reshape(-1)
     assert np.linalg.norm(r) <= 1e-4 * np.linalg.norm(b)
+
+
+def test_halo_layout_exits_like_the_resident_one(monkeypatch):
+    # negative curvature (an indefinite system) and a failed diagonal block end the
+    # halo layout's solve at the same iteration, with the same iterate
+    spec = medium_spec(23)
+    o = O.Scene.from_spec(spec)
+    vi = o.assemble(deformed(spec, 17, amp=3.0))
+    b = np.random.default_rng(5).standard_normal((spec.n_verts, 3))
+    b[spec.fixed] = 0
+    h = _probe_layout(spec, vi, b, None, monkeypatch, rel_tol=1e-8)
+    r = _probe_layout(spec, vi, b, "PPN_PCG_NO_HALO", monkeypatch, rel_tol=1e-8)
+    assert h[2] == "halo" and r[2] == "resident"
+    assert h[1]["ind"] and h[1] == r[1] and np.array_equal(h[0], r[0])
+    rp, col = o.pattern()
+    v2 = o.assemble(spec.rest)
+    free = np.setdiff1d(np.arange(spec.n_verts), spec.fixed)[-1]
+    k = rp[free] + np.nonzero(col[rp[free]:rp[free + 1]] == free)[0][0]
+    v2[k] = np.diag([-9.0, 5.0, 1.0])
+    h = _probe_layout(spec, v2, b, None, monkeypatch)
+    assert h[2] == "halo" and h[1]["precond_fail"] and h[1]["ind"] and h[1]["iters"] == 0
 
 
 def test_tuned_streamed_layouts_give_identical_steps(monkeypatch):

@@ -128,6 +128,8 @@ def test_batch_results_equal_alone_results():
         for i, sc in enumerate(scs):
             x, _ = sc.get_state()
             assert np.array_equal(x, alone[i][n])
+    # the three scenes shared the halo layout's launches (CTAs holding rows of two scenes)
+    assert all(P.PCG_LAYOUTS[sc.info()["pcg_layout"]] == "halo" for sc in scs)
 
 
 def test_checkpoint_resume_bitwise():
