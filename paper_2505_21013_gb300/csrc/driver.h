@@ -1060,7 +1060,11 @@ struct Driver {
       }
     }
     if (G.h_bar->timeout) {
-      set_error("PCG grid barrier timed out");
+      const GridBar& b = *G.h_bar;
+      set_error("PCG grid wait timed out (wait " + std::to_string(b.to_site) + " at CG iteration " +
+                std::to_string(b.to_iter) + " in CTA " + std::to_string(b.to_cta) + ": word " +
+                std::to_string(b.to_slot) + "/" + std::to_string(b.to_index) + " last seen with stamp " +
+                std::to_string(b.to_seen) + ")");
       return PPN_ERR_TIMEOUT;
     }
     return PPN_OK;

@@ -34,8 +34,12 @@ template <typename T> void launch_fallback(const SceneDev<T>*, const TileRef*, i
 struct GridBar {
   unsigned count;      // arrivals, monotonic within a launch
   int timeout;
-  unsigned stamp;      // last exchange whose broadcast is complete
-  int pad;
+  unsigned to_iter;    // first timeout: the CG iteration and the wait that ran out
+  int to_site;         // (1 neighbour flags, 2 reduction words, 3 halo w words; 0 not recorded)
+  unsigned to_seen;    // the stamp the wait last saw, on the word it waited for
+  int to_slot;         // that word's scene slot and tile (site 2) or row (site 3)
+  int to_index;
+  int to_cta;
 };
 
 constexpr int PCG_MAX_SCENES = 64;      // scenes per PCG launch (per-CTA scalar state in shared memory)

@@ -205,16 +205,18 @@ __global__ void __launch_bounds__(NTS, 1)
 #pragma unroll
     for (int j = 0; j < NWD; ++j) st_relaxed_u64(p + j, w[j]);
   };
-  // Every CTA sums quantities ks[0..nq) of every live scene from the tile words
-  // in the same fixed order (so all CTAs hold bitwise-equal scalars), then
-  // applies `update` to each live scene.  One warp per (scene, quantity); each
+  // Every CTA sums quantities ks[0..nq) of every scene from the tile words in
+  // the same fixed order (so all CTAs hold bitwise-equal scalars), then applies
+  // `update` to each live scene.  Tiles of scenes whose solve has ended are
+  // still posted and read, so every CTA waits for every other one at every
+  // exchange: a word is rewritten two exchanges later, after every CTA has read
+  // it.  One warp per (scene, quantity); each
   // lane polls all of its pending words in one round per L2 round trip.
   // `acquire`: the phase that follows gathers vector values of other CTAs.
   auto exchange = [&](const int* ks, int nq, bool acquire, auto&& update) -> bool {
     const unsigned s = W::stamp(epoch);
     for (int x = warp; x < n_scenes * nq; x += NW) {
       const int si = x / nq, q = x % nq;
-      if (st[si].done) continue;  // warp-uniform
       const SceneLite<T>& S = sl[si];
       const int n = S.n_ptiles;
       const unsigned long long* base = S.pword + NWD * (size_t)ks[q] * n;
@@ -451,7 +453,6 @@ __global__ void __launch_bounds__(NTS, 1)
     __syncthreads();
     ++epoch;
     for (int lt = tid; lt < ntl; lt += NTS) {
-      if (st[L.it_slot[lt * PCG_TILE]].done) continue;
       // tile lt was covered by pass lt / TPP, warps [WPT * (lt % TPP), + WPT)
       const T* w = L.lws + 3 * ((lt / TPP) * NW + WPT * (lt % TPP));
       T s = (T)0;
@@ -512,7 +513,6 @@ __global__ void __launch_bounds__(NTS, 1)
     __syncthreads();
     ++epoch;
     for (int lt = tid; lt < ntl; lt += NTS) {
-      if (st[L.it_slot[lt * PCG_TILE]].done) continue;
       const T* w = L.lws + 3 * 4 * lt;
       __threadfence();  // release this CTA's z and d stores before the partials
       post_tile(lt, 0, ((w[0] + w[3]) + w[6]) + w[9], W::stamp(epoch));

@@ -34,10 +34,14 @@
 // values, then a flag with the iteration's stamp; before its SpMV it waits
 // only for the flags of the CTAs that own the columns of its rows (a
 // contiguous CTA range found at set-up).  The reduction's tile partials go out
-// as stamped words after the SpMV, and every CTA sums them in tile order.  One
-// u array suffices: a CTA overwrites it only after it has seen every CTA's
-// partials of the previous iteration, which each CTA posts after finishing the
-// SpMV that read the old values.  SR_HALO: the SpMV stores w of each row as
+// as stamped words after the SpMV, into one of two parity buffers, and every
+// CTA sums them in tile order.  Every CTA posts all of its tiles every
+// iteration, also those of scenes whose solve has ended, so every CTA waits
+// for every other one each iteration: a buffer is overwritten two iterations
+// later, after every CTA has finished reading it.  One u array suffices: a CTA
+// overwrites it only after it has seen every CTA's partials of the previous
+// iteration, which each CTA posts after finishing the SpMV that read the old
+// values.  SR_HALO: the SpMV stores w of each row as
 // three stamped 64-bit words (the partials' format) in one of two parity
 // buffers; while some warps wait for the reduction's words, the others read
 // the halo rows' w words, each valid once it carries the iteration's stamp.
@@ -246,6 +250,8 @@ __global__ void __launch_bounds__(NTP, 1)
   __shared__ float s_sum[MS][NQ];
   __shared__ int s_toff[MS];
   __shared__ int s_to, s_lo, s_hi;
+  __shared__ unsigned s_seen;
+  __shared__ int s_wslot, s_widx;
   __shared__ int s_scan[NW];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane32 = tid & 31;
@@ -264,6 +270,8 @@ __global__ void __launch_bounds__(NTP, 1)
     s_to = 0;
     s_lo = grid;
     s_hi = -1;
+    s_seen = 0;
+    s_wslot = s_widx = -1;
   }
   for (int si = tid; si < n_scenes; si += NTP) {
     load_lite(sl[si], scenes[scene_ids[si]]);
@@ -355,23 +363,55 @@ __global__ void __launch_bounds__(NTP, 1)
   __syncthreads();
 
   // ---------------- exchange helpers
-  auto post_tile = [&](int lt, int k, float v, unsigned s) {
+  // tile word of quantity k of a tile in parity buffer par: pword[(par * NQ + k) * n_ptiles + tile]
+  auto post_tile = [&](int lt, int k, float v, unsigned s, int par) {
     const TileRef tr = L.ltt[lt];
     const SceneLite<float>& S = sl[tr.scene];
     unsigned long long w[1];
     W::split(v, s, w);
-    st_relaxed_u64(S.pword + (size_t)k * S.n_ptiles + tr.tile, w[0]);
+    st_relaxed_u64(S.pword + (size_t)(par * NQ + k) * S.n_ptiles + tr.tile, w[0]);
   };
-  // every CTA sums the tile words of quantities [0, nq) of every live scene in tile order;
-  // SR_HALO: meanwhile the other warps read w of the halo rows (stamp s, buffer par) into
-  // their u slots, which the SpMV has finished reading
+  // SR_HALO: w of the halo rows h0, h0 + dh, ... (stamp s, buffer par) into their u slots,
+  // which the SpMV has finished reading
+  auto halo_w = [&](int hb, int dh, unsigned s, int par) {
+    for (int h = hb; h < nh; h += dh) {
+      const int ref = L.href[h];
+      const int slot = ref >> HALO_ROW_BITS, row = ref & ((1 << HALO_ROW_BITS) - 1);
+      if (st[slot].done) continue;
+      const unsigned long long* wr =
+          reinterpret_cast<const unsigned long long*>(sl[slot].zrec) + ((size_t)par * sl[slot].nv + row) * 4;
+      unsigned long long w[3];
+      ld_relaxed_v2_u64(wr, w[0], w[1]);
+      w[2] = ld_relaxed_u64(wr + 2);
+      for (unsigned spins = 0; !(W::has(w[0], s) && W::has(w[1], s) && W::has(w[2], s)); ++spins) {
+        if (spins > kWaitSpins || *(volatile int*)&s_to) {
+          if (!s_to) {
+            s_to = 3;
+            s_seen = (unsigned)((W::has(w[0], s) ? (W::has(w[1], s) ? w[2] : w[1]) : w[0]) >> 32);
+            s_wslot = slot;
+            s_widx = row;
+          }
+          break;
+        }
+        ld_relaxed_v2_u64(wr, w[0], w[1]);
+        w[2] = ld_relaxed_u64(wr + 2);
+      }
+      L.lu4[n_items + h] = make_float4(W::join(w), W::join(w + 1), W::join(w + 2), 0.0f);
+    }
+  };
+  // every CTA sums the tile words (buffer par) of quantities [0, nq) of every scene of the
+  // launch in tile order; SR_HALO: the halo's w words are read meanwhile, by the warps
+  // without tile words when they are at least half of the CTA, else by every warp first
   auto reduce = [&](int nq, unsigned s, int par) -> bool {
-    for (int x = warp; x < n_scenes * nq; x += NW) {
+    const int npw = n_scenes * nq;  // warps with tile words to sum
+    if constexpr (HALO) {
+      if (npw > NW / 2) halo_w(tid, NTP, s, par);
+    }
+    for (int x = warp; x < npw; x += NW) {
       const int si = x / nq, q = x % nq;
-      if (st[si].done) continue;  // warp-uniform
       const SceneLite<float>& S = sl[si];
       const int n = S.n_ptiles;
-      const unsigned long long* base = S.pword + (size_t)q * n;
+      const unsigned long long* base = S.pword + (size_t)(par * NQ + q) * n;
       float acc = 0.0f;
       for (int tw = lane32; tw < n; tw += 32 * 8) {
         unsigned long long w[8];
@@ -386,7 +426,16 @@ __global__ void __launch_bounds__(NTP, 1)
           for (int u = 0; u < 8; ++u) ready &= W::has(w[u], s);
           if (ready) break;
           if (spins > kWaitSpins || *(volatile int*)&s_to) {
-            s_to = 1;
+            if (!s_to) {
+              s_to = 2;
+              for (int u = 0; u < 8; ++u)
+                if (!W::has(w[u], s)) {
+                  s_seen = (unsigned)(w[u] >> 32);
+                  s_wslot = si * 4 + q;
+                  s_widx = tw + 32 * u;
+                  break;
+                }
+            }
             break;
           }
 #pragma unroll
@@ -401,29 +450,7 @@ __global__ void __launch_bounds__(NTP, 1)
       if (lane32 == 0) s_sum[si][q] = acc;
     }
     if constexpr (HALO) {
-      // the warps without tile words; all warps, after theirs, when every warp has some
-      const int fw = n_scenes * nq < NW ? n_scenes * nq : 0;
-      if (warp >= fw) {
-        for (int h = (warp - fw) * 32 + lane32; h < nh; h += (NW - fw) * 32) {
-          const int ref = L.href[h];
-          const int slot = ref >> HALO_ROW_BITS, row = ref & ((1 << HALO_ROW_BITS) - 1);
-          if (st[slot].done) continue;
-          const unsigned long long* wr =
-              reinterpret_cast<const unsigned long long*>(sl[slot].zrec) + ((size_t)par * sl[slot].nv + row) * 4;
-          unsigned long long w[3];
-          ld_relaxed_v2_u64(wr, w[0], w[1]);
-          w[2] = ld_relaxed_u64(wr + 2);
-          for (unsigned spins = 0; !(W::has(w[0], s) && W::has(w[1], s) && W::has(w[2], s)); ++spins) {
-            if (spins > kWaitSpins || *(volatile int*)&s_to) {
-              s_to = 1;
-              break;
-            }
-            ld_relaxed_v2_u64(wr, w[0], w[1]);
-            w[2] = ld_relaxed_u64(wr + 2);
-          }
-          L.lu4[n_items + h] = make_float4(W::join(w), W::join(w + 1), W::join(w + 2), 0.0f);
-        }
-      }
+      if (npw <= NW / 2 && warp >= npw) halo_w((warp - npw) * 32 + lane32, (NW - npw) * 32, s, par);
     }
     __syncthreads();
     return !s_to;
@@ -439,7 +466,8 @@ __global__ void __launch_bounds__(NTP, 1)
   // wait until every CTA of the neighbour range has published `stamp`
   auto wait_flags = [&](unsigned long long stamp) -> bool {
     if (warp == 0) {
-      PPN_WARP_WAIT_STAMPS(flags, s_lo, s_hi, stamp, kWaitSpins, lane32, *(volatile int*)&s_to, s_to = 1);
+      PPN_WARP_WAIT_STAMPS(flags, s_lo, s_hi, stamp, kWaitSpins, lane32, *(volatile int*)&s_to,
+                           s_to = s_to ? s_to : 1);
       fence_acq_rel();  // acquire: the neighbours' values before this CTA's gathers
     }
     __syncthreads();
@@ -561,20 +589,31 @@ __global__ void __launch_bounds__(NTP, 1)
 
   // tile sums of gamma = r.u, delta = w.u, rho = r.r (and failed blocks) from the SpMV's
   // 16-row group sums (8 groups per tile, a fixed tree), posted
-  auto post_partials = [&](unsigned stamp, bool with_fail) {
+  // (every tile, also of scenes whose solve has ended: no CTA ever runs more than one
+  // iteration ahead of another, which the two parity buffers rely on)
+  auto post_partials = [&](unsigned stamp, bool with_fail, int par) {
     for (int lt = tid; lt < ntl; lt += NTP) {
-      if (st[L.ltt[lt].scene].done) continue;
       const float* w = L.lws + NQ * 8 * lt;
       const int nq = with_fail ? NQ : 3;
       for (int q = 0; q < nq; ++q) {
         const float a = (w[q] + w[NQ + q]) + (w[2 * NQ + q] + w[3 * NQ + q]);
         const float b = (w[4 * NQ + q] + w[5 * NQ + q]) + (w[6 * NQ + q] + w[7 * NQ + q]);
-        post_tile(lt, q, a + b, stamp);
+        post_tile(lt, q, a + b, stamp, par);
       }
     }
   };
-  auto fail_out = [&]() {
-    if (tid == 0) atomicExch(&bar->timeout, 1);
+  // a wait ran out: record the first one (iteration, wait) and flag the timeout
+  auto fail_out = [&](int it) {
+    if (tid == 0) {
+      if (atomicCAS(&bar->to_site, 0, s_to) == 0) {
+        bar->to_iter = (unsigned)it;
+        bar->to_seen = s_seen;
+        bar->to_slot = s_wslot;
+        bar->to_index = s_widx;
+        bar->to_cta = blockIdx.x;
+      }
+      atomicExch(&bar->timeout, 1);
+    }
   };
 
   // ---------------- set-up: P = block-Jacobi inverse, x = 0, r = b, u = P r
@@ -683,11 +722,11 @@ __global__ void __launch_bounds__(NTP, 1)
     } else {
       // ---- u released to the neighbours (set-up wrote u_0; later iterations below)
       publish_flag((unsigned long long)it + 1);
-      if (!wait_flags((unsigned long long)it + 1)) return fail_out();
+      if (!wait_flags((unsigned long long)it + 1)) return fail_out(it);
     }
     spmv(s, it & 1);  // w = A u
-    post_partials(s, it == 0);
-    if (!reduce(it == 0 ? NQ : 3, s, it & 1)) return fail_out();
+    post_partials(s, it == 0, it & 1);
+    if (!reduce(it == 0 ? NQ : 3, s, it & 1)) return fail_out(it);
     // one thread per scene (n_scenes <= MS < NTP); the barrier also finds whether all are done
     int done = 1;
     if (tid < n_scenes) {

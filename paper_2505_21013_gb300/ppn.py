@@ -179,6 +179,11 @@ def lib():
     return L
 
 
+def last_error() -> str:
+    """The calling thread's last error message from the library."""
+    return lib().ppn_last_error().decode(errors="replace")
+
+
 class PPNError(RuntimeError):
     def __init__(self, status: int, where: str):
         msg = lib().ppn_last_error().decode(errors="replace")

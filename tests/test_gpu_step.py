@@ -132,6 +132,37 @@ def test_batch_results_equal_alone_results():
     assert all(P.PCG_LAYOUTS[sc.info()["pcg_layout"]] == "halo" for sc in scs)
 
 
+def test_batch_of_mixed_scenes_with_ctas_spanning_scenes():
+    # five scenes of the request-stream mix (3k-56k tets): 192 PCG tiles over 152 CTAs,
+    # so 40 CTAs hold two tiles, some of them of two scenes, each with its own halo;
+    # the batch's steps equal the scenes' own steps, bit for bit
+    from ppn_inputs import serving_scenes
+
+    pool = serving_scenes(200, seed=1)
+    specs = [pool[i] for i in (108, 118, 125, 144, 191)]
+    alone = []
+    for sp in specs:
+        sc = P.Scene.from_spec(sp, precision=P.PREC_MIXED)
+        xs = []
+        for n in range(2):
+            sc.set_targets(sp.targets_at(n))
+            rc, x, _ = sc.step(P.MODE_PPN, 1e-4)
+            assert rc == 0, P.ppn.last_error()
+            xs.append(x)
+        sc.close()
+        alone.append(xs)
+    scs = [P.Scene.from_spec(sp, precision=P.PREC_MIXED) for sp in specs]
+    for n in range(2):
+        for sc, sp in zip(scs, specs):
+            sc.set_targets(sp.targets_at(n))
+        rc, st = P.ppn_step_batch(scs, [P.MODE_PPN] * len(scs), 1e-4)
+        assert rc == 0, P.ppn.last_error()
+        for i, sc in enumerate(scs):
+            x, _ = sc.get_state()
+            assert np.array_equal(x, alone[i][n])
+    assert all(P.PCG_LAYOUTS[sc.info()["pcg_layout"]] == "halo" for sc in scs)
+
+
 def test_checkpoint_resume_bitwise():
     spec = twisting_beam_scene(4, 4, 10, h=0.02, E=1e5, nu=0.45, omega=40.0, dt=0.1, seed=8)
     a = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
