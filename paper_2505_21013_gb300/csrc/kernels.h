@@ -35,7 +35,7 @@ struct GridBar {
   unsigned count;      // arrivals, monotonic within a launch
   int timeout;
   unsigned to_iter;    // first timeout: the CG iteration and the wait that ran out
-  int to_site;         // (1 neighbour flags, 2 reduction words, 3 halo w words; 0 not recorded)
+  int to_site;         // (1 neighbour flags, 2 reduction words, 3 halo w words, 4 progress flags; 0 not recorded)
   unsigned to_seen;    // the stamp the wait last saw, on the word it waited for
   int to_slot;         // that word's scene slot and tile (site 2) or row (site 3)
   int to_index;
@@ -71,7 +71,7 @@ struct PcgLaunch {
   void* zrec[HALO_MAX_SCENES];  // SR_HALO: exchange records of the slots (zeroed before the launch)
   size_t zrec_bytes[HALO_MAX_SCENES];
   unsigned launch_seq;
-  unsigned long long* flags;  // single-reduction kernel: per-CTA publication flags (grid words)
+  unsigned long long* flags;  // single-reduction kernel: per-CTA publication and progress flags (grid words)
   int n_pword;           // stamped partial arrays to clear before the launch
   void* pword[PCG_MAX_SCENES];
   size_t pword_bytes[PCG_MAX_SCENES];

@@ -35,19 +35,20 @@
 // only for the flags of the CTAs that own the columns of its rows (a
 // contiguous CTA range found at set-up).  The reduction's tile partials go out
 // as stamped words after the SpMV, into one of two parity buffers, and every
-// CTA sums them in tile order.  Every CTA posts all of its tiles every
-// iteration, also those of scenes whose solve has ended, so every CTA waits
-// for every other one each iteration: a buffer is overwritten two iterations
-// later, after every CTA has finished reading it.  One u array suffices: a CTA
+// CTA sums them in tile order.  Each CTA also raises a progress flag as it
+// starts an iteration; once a scene of the launch has finished (so that a CTA
+// may have no live tile to post), the reduction also waits for every CTA's
+// flag.  A buffer is overwritten two iterations later, after every CTA has
+// finished reading it.  One u array suffices: a CTA
 // overwrites it only after it has seen every CTA's partials of the previous
 // iteration, which each CTA posts after finishing the SpMV that read the old
 // values.  SR_HALO: the SpMV stores w of each row as
 // three stamped 64-bit words (the partials' format) in one of two parity
 // buffers; while some warps wait for the reduction's words, the others read
 // the halo rows' w words, each valid once it carries the iteration's stamp.
-// A CTA overwrites a buffer two iterations later, after every CTA has posted
-// the partials that follow its reads.  This leaves one synchronisation per
-// iteration, the reduction.  All waits are bounded.
+// A CTA overwrites a buffer two iterations later, after every CTA has raised
+// the progress flag that follows its reads.  This leaves one synchronisation
+// per iteration, the reduction.  All waits are bounded.
 //
 // Every layout evaluates the same expressions in the same order, through the
 // explicit fused multiply-adds of the helpers below: all four give the same
@@ -399,16 +400,30 @@ __global__ void __launch_bounds__(NTP, 1)
       L.lu4[n_items + h] = make_float4(W::join(w), W::join(w + 1), W::join(w + 2), 0.0f);
     }
   };
-  // every CTA sums the tile words (buffer par) of quantities [0, nq) of every scene of the
-  // launch in tile order; SR_HALO: the halo's w words are read meanwhile, by the warps
-  // without tile words when they are at least half of the CTA, else by every warp first
+  // every CTA sums the tile words (buffer par) of quantities [0, nq) of every live scene
+  // in tile order.  Once a scene of the launch has finished, a CTA may have no live tile
+  // left and post nothing; one warp then also waits until every CTA has started this
+  // iteration (progress flag >= s), so that no CTA is ever a whole iteration behind
+  // another, which the parity buffers rely on.  (While every scene is live, every CTA
+  // posts every iteration and the tile words alone ensure it.)  SR_HALO: the
+  // halo's w words are read meanwhile, by the warps without other work when they are at
+  // least half of the CTA, else by every warp first.
   auto reduce = [&](int nq, unsigned s, int par) -> bool {
-    const int npw = n_scenes * nq;  // warps with tile words to sum
+    const int npw = n_scenes * nq + 1;  // warps with words to wait for (the last: the flags)
     if constexpr (HALO) {
       if (npw > NW / 2) halo_w(tid, NTP, s, par);
     }
     for (int x = warp; x < npw; x += NW) {
+      if (x == npw - 1) {
+        bool any_done = false;
+        for (int si = 0; si < n_scenes; ++si) any_done |= st[si].done != 0;
+        if (any_done)
+          PPN_WARP_WAIT_STAMPS(flags, 0, grid - 1, (unsigned long long)s, kWaitSpins, lane32,
+                               *(volatile int*)&s_to, s_to = s_to ? s_to : 4);
+        continue;
+      }
       const int si = x / nq, q = x % nq;
+      if (st[si].done) continue;  // warp-uniform
       const SceneLite<float>& S = sl[si];
       const int n = S.n_ptiles;
       const unsigned long long* base = S.pword + (size_t)(par * NQ + q) * n;
@@ -589,10 +604,9 @@ __global__ void __launch_bounds__(NTP, 1)
 
   // tile sums of gamma = r.u, delta = w.u, rho = r.r (and failed blocks) from the SpMV's
   // 16-row group sums (8 groups per tile, a fixed tree), posted
-  // (every tile, also of scenes whose solve has ended: no CTA ever runs more than one
-  // iteration ahead of another, which the two parity buffers rely on)
   auto post_partials = [&](unsigned stamp, bool with_fail, int par) {
     for (int lt = tid; lt < ntl; lt += NTP) {
+      if (st[L.ltt[lt].scene].done) continue;
       const float* w = L.lws + NQ * 8 * lt;
       const int nq = with_fail ? NQ : 3;
       for (int q = 0; q < nq; ++q) {
@@ -719,6 +733,7 @@ __global__ void __launch_bounds__(NTP, 1)
     const unsigned s = W::stamp((unsigned)it + 1);
     if constexpr (HALO) {
       __syncthreads();  // set-up, or the previous update, before the SpMV
+      if (tid == 0) st_relaxed_u64(flags + blockIdx.x, (unsigned long long)it + 1);  // progress
     } else {
       // ---- u released to the neighbours (set-up wrote u_0; later iterations below)
       publish_flag((unsigned long long)it + 1);
