@@ -372,18 +372,18 @@ __global__ void __launch_bounds__(NTP, 1)
     W::split(v, s, w);
     st_relaxed_u64(S.pword + (size_t)(par * NQ + k) * S.n_ptiles + tr.tile, w[0]);
   };
-  // SR_HALO: w of the halo rows h0, h0 + dh, ... (stamp s, buffer par) into their u slots,
-  // which the SpMV has finished reading
+  // SR_HALO: w of the halo rows hb, hb + dh, ... (stamp s, buffer par) into their u slots,
+  // which the SpMV has finished reading; two rows at a time, both rows' loads in flight
+  // before the first is waited for
   auto halo_w = [&](int hb, int dh, unsigned s, int par) {
-    for (int h = hb; h < nh; h += dh) {
+    auto rec = [&](int h, int& slot, int& row) -> const unsigned long long* {
       const int ref = L.href[h];
-      const int slot = ref >> HALO_ROW_BITS, row = ref & ((1 << HALO_ROW_BITS) - 1);
-      if (st[slot].done) continue;
-      const unsigned long long* wr =
-          reinterpret_cast<const unsigned long long*>(sl[slot].zrec) + ((size_t)par * sl[slot].nv + row) * 4;
-      unsigned long long w[3];
-      ld_relaxed_v2_u64(wr, w[0], w[1]);
-      w[2] = ld_relaxed_u64(wr + 2);
+      slot = ref >> HALO_ROW_BITS;
+      row = ref & ((1 << HALO_ROW_BITS) - 1);
+      if (st[slot].done) return nullptr;
+      return reinterpret_cast<const unsigned long long*>(sl[slot].zrec) + ((size_t)par * sl[slot].nv + row) * 4;
+    };
+    auto wait = [&](const unsigned long long* wr, unsigned long long* w, int slot, int row) {
       for (unsigned spins = 0; !(W::has(w[0], s) && W::has(w[1], s) && W::has(w[2], s)); ++spins) {
         if (spins > kWaitSpins || *(volatile int*)&s_to) {
           if (!s_to) {
@@ -397,7 +397,29 @@ __global__ void __launch_bounds__(NTP, 1)
         ld_relaxed_v2_u64(wr, w[0], w[1]);
         w[2] = ld_relaxed_u64(wr + 2);
       }
-      L.lu4[n_items + h] = make_float4(W::join(w), W::join(w + 1), W::join(w + 2), 0.0f);
+    };
+    for (int h = hb; h < nh; h += 2 * dh) {
+      const int h2 = h + dh;
+      int sa, ra, sb = 0, rb = 0;
+      const unsigned long long* wa = rec(h, sa, ra);
+      const unsigned long long* wb = h2 < nh ? rec(h2, sb, rb) : nullptr;
+      unsigned long long a[3], b[3];
+      if (wa) {
+        ld_relaxed_v2_u64(wa, a[0], a[1]);
+        a[2] = ld_relaxed_u64(wa + 2);
+      }
+      if (wb) {
+        ld_relaxed_v2_u64(wb, b[0], b[1]);
+        b[2] = ld_relaxed_u64(wb + 2);
+      }
+      if (wa) {
+        wait(wa, a, sa, ra);
+        L.lu4[n_items + h] = make_float4(W::join(a), W::join(a + 1), W::join(a + 2), 0.0f);
+      }
+      if (wb) {
+        wait(wb, b, sb, rb);
+        L.lu4[n_items + h2] = make_float4(W::join(b), W::join(b + 1), W::join(b + 2), 0.0f);
+      }
     }
   };
   // every CTA sums the tile words (buffer par) of quantities [0, nq) of every live scene
