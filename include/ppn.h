@@ -246,6 +246,27 @@ PPN_API ppn_status ppn_probe_project(ppn_scene* s, const double* x, const int32_
  * words on the current device. */
 PPN_API ppn_status ppn_probe_bounded_wait(int n_words, int spin_limit, int preset);
 
+/* Host-side tables of the linear solver's halo layout (Sec. 4.1's block-Jacobi
+ * PCG, one CTA per SM; no GPU needed): for each CTA, the rows of other CTAs that
+ * columns of its rows refer to, and each block's column in the CTA's local
+ * numbering.  n_scenes (1..8) BSR patterns in launch order: row_ptr[k]
+ * (n_verts[k] + 1 int64) and col[k] (row_ptr[k][n_verts[k]] int32, ascending
+ * per row).  Rows are split into 128-row tiles, every tile of scene 0 first;
+ * CTA b of `grid` owns tiles [b T / grid, (b + 1) T / grid) of the T tiles.
+ * out (int32, caller-owned, out_cap words) receives, one after the other:
+ *   2 (grid + 1) words: first block and first halo row of each CTA, then the totals;
+ *   one word per block (the CTA's tiles, their rows, each row's blocks in order):
+ *     the column's local index, (tile - first tile of the CTA) * 128 + row % 128
+ *     for a row the CTA owns, else the CTA's row count + its index in the halo list;
+ *   one word per halo row: scene << 26 | row, ascending within each CTA.
+ * *out_len: the words written (or needed), *max_halo: the most halo rows of one
+ * CTA.  INVALID_ARG for null pointers, n_scenes outside 1..8, a scene with no
+ * rows or 2^26 rows or more, grid outside 1..T, or out_cap < *out_len (then
+ * nothing is written but *out_len). */
+PPN_API ppn_status ppn_probe_halo_tables(int n_scenes, const int64_t* const* row_ptr, const int32_t* const* col,
+                                         const int64_t* n_verts, int grid, int32_t* out, int64_t out_cap,
+                                         int64_t* out_len, int32_t* max_halo);
+
 PPN_API ppn_status ppn_probe_pcg(ppn_scene* s, const double* vals, const double* b, double rel_tol,
                          int max_iter, double* x, int* info);
 

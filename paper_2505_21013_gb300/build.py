@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libppn.so")
 SOURCES = ["kernels.cu", "pcg.cu", "pcg_smem.cu", "pcg_sr.cu", "pcg_static.cu", "scene.cu", "server.cu"]
-HEADERS = ["common.cuh", "tetmath.cuh", "eigclamp.cuh", "contact.cuh", "kernels.h", "scene.h", "driver.h", "pcg_common.cuh"]
+HEADERS = ["common.cuh", "tetmath.cuh", "eigclamp.cuh", "contact.cuh", "kernels.h", "scene.h", "driver.h", "pcg_common.cuh", "halo.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

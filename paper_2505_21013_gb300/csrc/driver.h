@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "halo.h"
 #include "scene.h"
 
 namespace ppn {
@@ -410,68 +411,15 @@ struct Driver {
     return PPN_OK;
   }
 
-  // SR_HALO tables for `grid` CTAs over the tile table (the layout of
-  // PcgLaunch::halo_*): per CTA, the rows of other CTAs that its rows' columns
-  // refer to, in launch order, and each of its blocks' local column.  Returns
-  // the most halo rows of one CTA, or -1 when a scene is too large to refer to.
-  int build_halo(const std::vector<int>& sl, const std::vector<TileRef>& tt, int grid, std::vector<int>& tab) {
-    const int n_tiles = (int)tt.size();
-    const size_t ns = sl.size();
-    std::vector<int> toff(ns + 1, 0);
-    for (size_t k = 0; k < ns; ++k) {
-      if (G.S[sl[k]]->nv >= (1 << HALO_ROW_BITS)) return -1;
-      toff[k + 1] = toff[k] + G.S[sl[k]]->n_ptiles;
+  // SR_HALO tables for `grid` CTAs over the launch's tile table (every PCG tile
+  // of each slot, slot after slot, as solve() builds it): build_halo_tables.
+  int build_halo(const std::vector<int>& sl, int grid, std::vector<int>& tab) {
+    std::vector<HaloPattern> pats;
+    for (int k : sl) {
+      const SceneImpl<T>& sc = *G.S[k];
+      pats.push_back({sc.nv, sc.h_row_ptr.data(), sc.h_col.data()});
     }
-    std::vector<std::vector<int>> mark(ns), hidx(ns);
-    for (size_t k = 0; k < ns; ++k) {
-      mark[k].assign(G.S[sl[k]]->nv, -1);
-      hidx[k].assign(G.S[sl[k]]->nv, 0);
-    }
-    std::vector<int> off(2 * (grid + 1), 0), col, ref;
-    std::vector<long long> hs;
-    int maxh = 0;
-    // every block of CTA b's rows, in the kernel's order (tiles, rows, blocks ascending)
-    auto blocks = [&](int t0, int t1, auto&& f) {
-      for (int t = t0; t < t1; ++t) {
-        const int k = tt[t].scene;
-        const SceneImpl<T>& sc = *G.S[sl[k]];
-        const int r0 = tt[t].tile * PCG_TILE, r1 = std::min(sc.nv, r0 + PCG_TILE);
-        for (int r = r0; r < r1; ++r)
-          for (int64_t q = sc.h_row_ptr[r]; q < sc.h_row_ptr[r + 1]; ++q) {
-            const int j = sc.h_col[q];
-            f(k, j, toff[k] + j / PCG_TILE);
-          }
-      }
-    };
-    for (int b = 0; b < grid; ++b) {
-      const int t0 = (int)(((long long)b * n_tiles) / grid), t1 = (int)(((long long)(b + 1) * n_tiles) / grid);
-      const int n_items = (t1 - t0) * PCG_TILE;
-      off[2 * b] = (int)col.size();
-      off[2 * b + 1] = (int)ref.size();
-      hs.clear();
-      blocks(t0, t1, [&](int k, int j, int gt) {
-        if ((gt < t0 || gt >= t1) && mark[k][j] != b) {
-          mark[k][j] = b;
-          hs.push_back(((long long)k << 32) | j);
-        }
-      });
-      std::sort(hs.begin(), hs.end());
-      for (size_t h = 0; h < hs.size(); ++h) {
-        const int k = (int)(hs[h] >> 32), j = (int)(hs[h] & 0xffffffffll);
-        hidx[k][j] = (int)h;
-        ref.push_back((k << HALO_ROW_BITS) | j);
-      }
-      blocks(t0, t1, [&](int k, int j, int gt) {
-        col.push_back(gt >= t0 && gt < t1 ? (gt - t0) * PCG_TILE + j % PCG_TILE : n_items + hidx[k][j]);
-      });
-      maxh = std::max(maxh, (int)hs.size());
-    }
-    off[2 * grid] = (int)col.size();
-    off[2 * grid + 1] = (int)ref.size();
-    tab = off;
-    tab.insert(tab.end(), col.begin(), col.end());
-    tab.insert(tab.end(), ref.begin(), ref.end());
-    return maxh;
+    return build_halo_tables(pats, grid, tab);
   }
 
   // Choose the PCG kernel for the launch's tile table.  FP32 (unless
@@ -524,7 +472,7 @@ struct Driver {
       }
       if (first == SR_RES && fits[SR_RES] && sl.size() <= (size_t)HALO_MAX_SCENES && !std::getenv("PPN_PCG_NO_HALO")) {
         std::vector<int> tab;
-        const int nh = build_halo(sl, tt, grid, tab);
+        const int nh = build_halo(sl, grid, tab);
         const size_t hb = nh < 0 ? 0 : pcg_sr_smem_bytes(max_items, max_blocks, nh, SR_HALO);
         if (nh >= 0 && hb <= (size_t)227 * 1024 && pcg_sr_max_grid(dev, hb, SR_HALO) >= grid) {
           if (tab.size() > G.cap_halo) {

@@ -1222,6 +1222,32 @@ ppn_status ppn_probe_elements(ppn_scene* s, const double* x, double* psi_e, doub
   return dispatch(s, [&](auto& sc) { return probe_elements(sc, x, psi_e, ge, He); });
 }
 
+ppn_status ppn_probe_halo_tables(int n_scenes, const int64_t* const* row_ptr, const int32_t* const* col,
+                                 const int64_t* n_verts, int grid, int32_t* out, int64_t out_cap,
+                                 int64_t* out_len, int32_t* max_halo) {
+  if (!row_ptr || !col || !n_verts || !out_len || !max_halo || n_scenes < 1 || n_scenes > HALO_MAX_SCENES)
+    return PPN_ERR_INVALID_ARG;
+  std::vector<HaloPattern> pats;
+  for (int k = 0; k < n_scenes; ++k) {
+    if (!row_ptr[k] || !col[k] || n_verts[k] < 1 || n_verts[k] >= (1 << HALO_ROW_BITS)) return PPN_ERR_INVALID_ARG;
+    pats.push_back({(int)n_verts[k], row_ptr[k], col[k]});
+  }
+  std::vector<int> tab;
+  const int mh = build_halo_tables(pats, grid, tab);
+  if (mh < 0) {
+    set_error("ppn_probe_halo_tables: grid outside 1..tiles");
+    return PPN_ERR_INVALID_ARG;
+  }
+  *out_len = (int64_t)tab.size();
+  *max_halo = mh;
+  if (!out || out_cap < (int64_t)tab.size()) {
+    set_error("ppn_probe_halo_tables: output buffer too small");
+    return PPN_ERR_INVALID_ARG;
+  }
+  std::memcpy(out, tab.data(), sizeof(int32_t) * tab.size());
+  return PPN_OK;
+}
+
 ppn_status ppn_probe_pattern(const ppn_scene* s, int64_t* row_ptr, int32_t* col) {
   return dispatch_c(s, [&](auto& x) {
     if (row_ptr) std::memcpy(row_ptr, x.h_row_ptr.data(), sizeof(int64_t) * x.h_row_ptr.size());

@@ -144,6 +144,8 @@ SIGNATURES = {
     "ppn_probe_project": (_st, [_P, _pd, _pi, C.c_int64, _pd]),
     "ppn_probe_pcg": (_st, [_P, _pd, _pd, C.c_double, C.c_int, _pd, C.POINTER(C.c_int)]),
     "ppn_probe_bounded_wait": (_st, [C.c_int, C.c_int, C.c_int]),
+    "ppn_probe_halo_tables": (_st, [C.c_int, C.POINTER(_pl), C.POINTER(_pi), _pl, C.c_int, _pi, C.c_int64, _pl,
+                                    _pi]),
     "ppn_server_default_config": (ppn_server_config, []),
     "ppn_server_create": (_st, [C.POINTER(ppn_server_config), C.POINTER(_P)]),
     "ppn_server_destroy": (None, [_P]),
@@ -406,6 +408,30 @@ class Scene:
 def probe_bounded_wait(n_words: int, spin_limit: int, preset: bool) -> int:
     """``ppn_probe_bounded_wait``: the status (PPN_OK, or 9 = PPN_ERR_TIMEOUT when the wait ran out)."""
     return int(lib().ppn_probe_bounded_wait(int(n_words), int(spin_limit), 1 if preset else 0))
+
+
+def probe_halo_tables(patterns, grid: int):
+    """``ppn_probe_halo_tables`` for [(row_ptr, col), ...]: (off [grid + 1, 2], local columns,
+    halo references, most halo rows of one CTA)."""
+    rps = [np.ascontiguousarray(rp, dtype=np.int64) for rp, _ in patterns]
+    cols = [np.ascontiguousarray(c, dtype=np.int32) for _, c in patterns]
+    n = len(patterns)
+    rp_arr = (_pl * n)(*[a.ctypes.data_as(_pl) for a in rps])
+    col_arr = (_pi * n)(*[a.ctypes.data_as(_pi) for a in cols])
+    nv = np.array([len(a) - 1 for a in rps], dtype=np.int64)
+    need, mh = C.c_int64(0), C.c_int32(0)
+    L = lib()
+    rc = L.ppn_probe_halo_tables(n, rp_arr, col_arr, nv.ctypes.data_as(_pl), int(grid), None, 0, C.byref(need),
+                                 C.byref(mh))
+    if rc != PPN_OK and need.value == 0:
+        _check(rc, "ppn_probe_halo_tables")
+    out = np.zeros(need.value, dtype=np.int32)
+    _check(L.ppn_probe_halo_tables(n, rp_arr, col_arr, nv.ctypes.data_as(_pl), int(grid), out.ctypes.data_as(_pi),
+                                   out.size, C.byref(need), C.byref(mh)), "ppn_probe_halo_tables")
+    no = 2 * (grid + 1)
+    off = out[:no].reshape(grid + 1, 2)
+    nb = int(off[grid, 0])
+    return off, out[no:no + nb], out[no + nb:], int(mh.value)
 
 
 def ppn_step_batch(scenes, modes, tol):
