@@ -1,7 +1,6 @@
 // Single-reduction block-Jacobi PCG (the linear solve of Algorithm 1; Sec. 4.1
-// "Linear Solvers", Sec. 5.1) for the FP32 path: one grid-wide reduction and
-// one neighbour-only synchronisation per iteration, instead of the two
-// grid-wide reductions of the textbook recurrences.
+// "Linear Solvers", Sec. 5.1) for the FP32 path: one grid-wide reduction per
+// iteration, instead of the two of the textbook recurrences.
 //
 // Method.  The recurrences of Chronopoulos & Gear (1989) for preconditioned
 // CG.  With u = M r, w = A u, s = A p, iteration i (i >= 1) computes
@@ -16,43 +15,44 @@
 // recurrence (w is recomputed by the SpMV every iteration), which keeps the
 // FP32 iteration counts and attained residuals those of the standard kernel.
 //
-// Data.  Three layouts (SR_RES, SR_STREAM, SR_GLOBAL).  SR_RES and SR_STREAM
-// keep each CTA's rows' block-Jacobi inverse and vectors x, r, u, w, p, s in
-// shared memory; SR_RES also keeps the rows' BSR blocks there, SR_STREAM
-// streams them from global memory (L2 / HBM) every iteration through the
-// read-only path.  SR_GLOBAL, for rows that do not fit, keeps the vectors in
-// the scene's global PCG arrays as well (x in dx, r in z, w in q, p in d0,
-// s in d1, the inverse in Pinv), each row touched only by its own CTA.  In
-// these three layouts only u crosses CTAs, through a global array.  SR_HALO
-// keeps what SR_RES keeps and replicates the CTA's halo (the rows of other
-// CTAs that columns of its rows refer to): for each halo row it holds r, s
-// and the block-Jacobi inverse and repeats the owner's update of them, so u
-// of the halo rows is formed in place and the SpMV reads shared memory only.
+// Data.  Four layouts.  SR_RES and SR_STREAM keep each CTA's rows'
+// block-Jacobi inverse and vectors x, r, u, w, p, s in shared memory; SR_RES
+// also keeps the rows' BSR blocks there, SR_STREAM streams them from global
+// memory (L2 / HBM) every iteration through the read-only path.  SR_GLOBAL,
+// for rows that do not fit, keeps the vectors in the scene's global PCG arrays
+// as well (x in dx, r in z, w in q, p in d0, s in d1, the inverse in Pinv),
+// each row touched only by its own CTA.  In these three layouts only u crosses
+// CTAs, through a global array.  SR_HALO keeps what SR_RES keeps and
+// replicates the CTA's halo (the rows of other CTAs that columns of its rows
+// refer to; tables from build_halo_tables): for each halo row it holds r, s
+// and the block-Jacobi inverse and repeats the owner's update of them, so u of
+// the halo rows is formed in place and the SpMV reads shared memory only.
 // What crosses CTAs is then w of the halo rows, which the update needs.
 //
-// Synchronisation.  SR_RES, SR_STREAM, SR_GLOBAL: a CTA publishes its u
-// values, then a flag with the iteration's stamp; before its SpMV it waits
-// only for the flags of the CTAs that own the columns of its rows (a
-// contiguous CTA range found at set-up).  The reduction's tile partials go out
-// as stamped words after the SpMV, into one of two parity buffers, and every
-// CTA sums them in tile order.  Each CTA also raises a progress flag as it
-// starts an iteration; once a scene of the launch has finished (so that a CTA
-// may have no live tile to post), the reduction also waits for every CTA's
-// flag.  A buffer is overwritten two iterations later, after every CTA has
-// finished reading it.  One u array suffices: a CTA
-// overwrites it only after it has seen every CTA's partials of the previous
-// iteration, which each CTA posts after finishing the SpMV that read the old
-// values.  SR_HALO: the SpMV stores w of each row as
-// three stamped 64-bit words (the partials' format) in one of two parity
-// buffers; while some warps wait for the reduction's words, the others read
-// the halo rows' w words, each valid once it carries the iteration's stamp.
-// A CTA overwrites a buffer two iterations later, after every CTA has raised
-// the progress flag that follows its reads.  This leaves one synchronisation
-// per iteration, the reduction.  All waits are bounded.
+// Synchronisation.  The reduction's tile partials go out as stamped words
+// after the SpMV, into one of two parity buffers, and every CTA sums them in
+// tile order.  Each CTA raises a progress flag with the iteration's stamp as
+// it starts an iteration.  Once a scene of the launch has finished, so that a
+// CTA may have no live tile left to post, the reduction also waits for every
+// CTA's flag.  Either way a buffer is overwritten two iterations later, after
+// every CTA has finished reading it.
+//   SR_RES, SR_STREAM, SR_GLOBAL: the progress flag also publishes the CTA's
+// u (released by a fence); before its SpMV a CTA waits only for the flags of
+// the CTAs that own the columns of its rows (a contiguous CTA range found at
+// set-up).  One u array suffices: a CTA overwrites it only after it has seen
+// every CTA's partials of the previous iteration, which each CTA posts after
+// finishing the SpMV that read the old values.
+//   SR_HALO: the SpMV stores w of each row as three stamped 64-bit words (the
+// partials' format) in one of two parity buffers; while some warps wait for
+// the reduction's words, the others read the halo rows' w words, each valid
+// once it carries the iteration's stamp.  A buffer is overwritten two
+// iterations later, after every CTA has raised the progress flag that follows
+// its reads.  This leaves one synchronisation per iteration, the reduction.
 //
-// Every layout evaluates the same expressions in the same order, through the
-// explicit fused multiply-adds of the helpers below: all four give the same
-// bits, and a replicated halo row the bits of its owner.
+// All waits are bounded.  Every layout evaluates the same expressions in the
+// same order, through the explicit fused multiply-adds of the helpers below:
+// all four give the same bits, and a replicated halo row the bits of its
+// owner.
 #include "pcg_common.cuh"
 
 namespace ppn {
@@ -333,7 +333,8 @@ __global__ void __launch_bounds__(NTP, 1)
     if (tid == 0) L.lrp[n_items] = carry;
     __syncthreads();
   }
-  // copy this CTA's blocks (RES); the CTAs owning their columns bound the neighbour range
+  // copy this CTA's blocks (SR_RES; SR_HALO with the local columns); without the halo, the
+  // CTAs owning their columns bound the neighbour range of the u flags
   {
     int lo = grid, hi = -1;
     for (int item = warp; item < n_items; item += NW) {
@@ -358,8 +359,10 @@ __global__ void __launch_bounds__(NTP, 1)
         }
       }
     }
-    atomicMin(&s_lo, lo);
-    atomicMax(&s_hi, hi);
+    if constexpr (!HALO) {
+      atomicMin(&s_lo, lo);
+      atomicMax(&s_hi, hi);
+    }
   }
   __syncthreads();
 
