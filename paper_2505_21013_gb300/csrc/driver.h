@@ -477,7 +477,8 @@ struct Driver {
         if (nh >= 0 && hb <= (size_t)227 * 1024 && pcg_sr_max_grid(dev, hb, SR_HALO) >= grid) {
           if (tab.size() > G.cap_halo) {
             if (G.d_halo) {  // (cudaFree waits for launches that may still read it)
-              G.allocs.erase(std::find(G.allocs.begin(), G.allocs.end(), (void*)G.d_halo));
+              const auto old = std::find(G.allocs.begin(), G.allocs.end(), (void*)G.d_halo);
+              if (old != G.allocs.end()) G.allocs.erase(old);
               cudaFree(G.d_halo);
             }
             G.d_halo = G.template alloc<int>(tab.size());
