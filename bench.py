@@ -108,16 +108,29 @@ def measured_peaks():
         return None
 
 
-def pcg_bytes_per_iter(info, fsize=4):
-    # algorithmic bytes of one CG iteration: BSR values + column index per block;
-    # per row: row pointer, gathered z and d_prev, written d and q (phase A),
-    # d, q, x, r, P^-1 read and x, r, z written (phase B); vectors are 16-byte float4
-    nnzb, nv = info["nnzb"], info["n_verts"]
-    return nnzb * (9 * fsize + 4) + nv * (4 + 4 * 16 + 4 * 16 + 9 * fsize + 3 * 16)
+# Algorithmic bytes per unit of work (FP32 values, int32 indices), the scope table's
+# per-unit figures:
+#   K8 + K9, one CG iteration: per BSR block 36 B value + 4 B column; per row a 4 B
+#            row pointer, 12 B of y, and ten 12-byte vector streams (x, r, z, p, q...)
+#   K3, one assembly: per tet 16 blocks x 36 B of H^e read + 64 B of map; per BSR
+#            block 36 B + 4 B written
+#   K1, one element pass: per tet 16 B indices + 36 B D_m^-1 + 4 B volume read,
+#            48 B g^e + 312 B packed H^e written; 24 B per vertex of unique
+#            vertex data
+def pcg_bytes_per_iter(info):
+    return info["nnzb"] * 40 + info["n_verts"] * (16 + 10 * 12)
+
+
+def assemble_bytes(info):
+    return info["n_tets"] * (16 * 36 + 64) + info["nnzb"] * 40
+
+
+def element_bytes(info):
+    return info["n_tets"] * (16 + 36 + 4 + 48 + 312) + info["n_verts"] * 24
 
 
 PCG_SOURCES = ("pcg_sr.cu", "pcg_common.cuh", "common.cuh", "kernels.h")
-PCG_PROFILE = os.path.join(ROOT, "profiles", "k_pcg_sr_twisting_beam_20x20x80.md")
+PCG_PROFILE = os.path.join(ROOT, "profiles", "k_pcg_sr_twisting_beam_20x20x80.json")
 
 
 def pcg_source_hash():
@@ -131,22 +144,15 @@ def pcg_source_hash():
 
 
 def pcg_profile_traffic():
-    """DRAM bytes per launch of the resident PCG kernel from the committed ncu
-    summary, or None when the kernel's sources changed since the capture."""
+    """DRAM bytes per launch of the resident PCG kernel from the ncu counters
+    recorded beside its summary (profiles/*.json), or None when the kernel's
+    sources changed since the capture."""
     try:
-        txt = open(PCG_PROFILE).read()
-    except OSError:
-        return None
-    kv = {}
-    for ln in txt.splitlines():
-        if ln.startswith("- ") and ": " in ln:
-            k, v = ln[2:].split(": ", 1)
-            kv[k.strip("` ")] = v.strip("` ")
-    try:
+        kv = json.load(open(PCG_PROFILE))
         if kv.get("source_sha256_16") != pcg_source_hash():
             return None
         return {"bytes": float(kv["dram_bytes_per_launch"]), "cg_iters": int(kv["cg_iters_per_launch"])}
-    except (KeyError, ValueError):
+    except (OSError, ValueError, KeyError, TypeError):
         return None
 
 
@@ -255,26 +261,36 @@ def run_ours(args, rank, world, dist):
     dom = max(kt.items(), key=lambda kv: kv[1]["total_ms"])
     name, rec = dom
     roof = None
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
     if name == "pcg" and rec["launches"]:
         bpi = pcg_bytes_per_iter(info)
-        setup = info["n_verts"] * (36 + 36 + 32 + 4 * 16)
         iters_per_launch = cg_total / rec["launches"]
-        alg_bytes = iters_per_launch * bpi + setup
+        alg_bytes = iters_per_launch * bpi
         avg_s = rec["total_ms"] / rec["launches"] / 1e3
         achieved = alg_bytes / avg_s / 1e9
-        peak = peaks["hbm_gbs"] if peaks else 6800.0
         prof = pcg_profile_traffic()
         roof = {"bound": "hbm", "kernel": "k_pcg_sr (resident single-reduction block-Jacobi PCG)",
                 "layout": P.PCG_LAYOUTS.get(info.get("pcg_layout", -1), "unknown"),
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": round(prof["bytes"]) if prof else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
+                "bytes_per_cg_iter": bpi, "cg_iters_per_launch": iters_per_launch,
                 "bytes_per_launch": alg_bytes, "avg_launch_ms": rec["total_ms"] / rec["launches"],
-                "cg_iters_per_launch": iters_per_launch,
                 "traffic_capture_cg_iters": prof["cg_iters"] if prof else None,
-                "note": "algorithmic bytes per launch = CG iterations x bytes per iteration + set-up; the working "
-                        "set of one solve (~25 MB) stays L2-resident across iterations, so DRAM traffic is far "
-                        "below the algorithmic bytes and the kernel is bound by grid-wide exchange latency"}
+                "note": "achieved = algorithmic bytes (nnzb x 40 + n_verts x 136 per CG iteration) x CG iterations "
+                        "per launch / average launch time; they are not DRAM bytes: the working set of one solve "
+                        "stays L2-resident across iterations, so DRAM traffic is far below the algorithmic bytes "
+                        "and the kernel is bound by grid-wide exchange latency"}
+        # the other HBM-bound kernels of the step, on the same scope-table bytes
+        kernels = {}
+        for fam, fn, kname in (("assemble", assemble_bytes, "k_assemble"), ("element", element_bytes, "k_element")):
+            k = kt.get(fam)
+            if k and k["launches"]:
+                ms = k["total_ms"] / k["launches"]
+                gbs = fn(info) / (ms / 1e3) / 1e9
+                kernels[kname] = {"bytes_per_launch": fn(info), "avg_launch_ms": round(ms, 5),
+                                  "achieved": round(gbs, 1), "frac": round(gbs / peak, 4)}
+        roof["kernels"] = kernels
     launches = int(sum(v["launches"] for v in kt.values()))
     r = {
         "value": value, "ms_per_step": ms_ppn / K,
@@ -296,6 +312,75 @@ def run_ours(args, rank, world, dist):
                    "cg_iters": sum(s["total_cg_iters"] for s in st_pn)}
         r["speedup_ppn_vs_pn"] = ms_pn / ms_ppn
     return r
+
+
+VIOLENT = {"workload": "violent_twisting_beam_20x20x80", "E": 1e5, "nu": 0.45, "omega_rad_s": 20.0,
+           "dt": 1.0 / 30.0, "tol": 1e-4}
+
+
+def run_violent(steps=8, warmup=2):
+    """The same 20x20x80 beam (171,114 tets), softer (E = 1e5) and turned at
+    20 rad/s, so that the unprojected Hessian turns indefinite and PPN really
+    selects, clamps and updates (Algorithm 1's inner loop).  PPN, PN and plain
+    Newton from the same state: device time per step by CUDA events on the
+    scene's stream (L2 flushed between steps), Newton iterations, projections,
+    solves, selection ties, and per-kernel-family device time of the PPN steps
+    (an untimed second pass with per-family events)."""
+    import numpy as np
+    import torch
+
+    import paper_2505_21013_gb300 as P
+    from ppn_inputs import twisting_beam_scene
+
+    spec = twisting_beam_scene(20, 20, 80, h=0.01, E=VIOLENT["E"], nu=VIOLENT["nu"], omega=VIOLENT["omega_rad_s"],
+                               dt=VIOLENT["dt"], seed=0)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tg = torch.tensor(np.stack([spec.targets_at(n) for n in range(warmup + steps)]), dtype=torch.float64,
+                      device="cuda")
+
+    def run(mode, profile=False):
+        sc = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
+        sc.set_stream(stream.cuda_stream)
+        lat, agg = [], {"newton_iters": 0, "projections": 0, "attempts": 0, "cg_iters": 0, "ties": 0}
+        for n in range(warmup + steps):
+            if profile and n == warmup:
+                torch.cuda.synchronize()
+                sc.set_profiling(True)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            sc.set_targets_device(tg[n].data_ptr())
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            rc, _, st = sc.step(mode, VIOLENT["tol"], want_x=False)
+            ev1.record(stream)
+            if rc != 0:
+                raise RuntimeError(f"violent step {n} returned status {rc}")
+            ev1.synchronize()
+            if n >= warmup:
+                lat.append(ev0.elapsed_time(ev1))
+                agg["newton_iters"] += st["newton_iters"]
+                agg["projections"] += st["total_projections"]
+                agg["attempts"] += st["total_attempts"]
+                agg["cg_iters"] += st["total_cg_iters"]
+                agg["ties"] += st["n_ties"]
+        kt = sc.kernel_times() if profile else None
+        sc.close()
+        r = {"steps_per_s": steps / (sum(lat) / 1e3), "ms_per_step": sum(lat) / steps,
+             "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99), **agg,
+             "projected_fraction": round(agg["projections"] / max(1, agg["newton_iters"] * spec.n_tets), 5)}
+        return r, kt
+
+    out = {"scene": VIOLENT["workload"], **{k: v for k, v in VIOLENT.items() if k != "workload"},
+           "n_tets": spec.n_tets, "steps": steps, "warmup": warmup, "l2": "flushed between steps (256 MB write)"}
+    out["ppn"], _ = run(P.MODE_PPN)
+    out["pn"], _ = run(P.MODE_PN)
+    out["newton"], _ = run(P.MODE_NEWTON)
+    _, kt = run(P.MODE_PPN, profile=True)
+    out["kernel_ms_ppn"] = {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3)} for k, v in kt.items()}
+    out["speedup_ppn_vs_pn"] = out["ppn"]["steps_per_s"] / out["pn"]["steps_per_s"]
+    out["speedup_ppn_vs_newton"] = out["ppn"]["steps_per_s"] / out["newton"]["steps_per_s"]
+    return out
 
 
 def profile_pcg(iters, repeats=4, workload="beam"):
@@ -648,8 +733,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppn-only", action="store_true", help="skip the PN comparison run")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline beam only: skip the violent, batched, serving and contact sub-lines")
     ap.add_argument("--workload", default="beam",
-                    choices=["beam", "batched", "serving", "ablation", "contact", "seeds"],
+                    choices=["beam", "batched", "serving", "ablation", "contact", "seeds", "violent"],
                     help="beam: the headline line; batched / serving: the multi-scene workloads; "
                          "ablation: the alpha/beta sweep; contact: boxes under a press in a cylinder; "
                          "seeds: the beam for jitter seeds 0-4")
@@ -665,9 +752,11 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         if args.workload == "contact":
             r = run_contact(steps=args.steps, warmup=args.warmup)
+        elif args.workload == "violent":
+            r = run_violent(steps=args.steps, warmup=args.warmup)
         else:
             r = {"batched": run_batched, "serving": run_serving, "ablation": run_ablation,
-                 "seeds": run_seeds}[args.workload]()
+                 "seeds": run_seeds, "violent": run_violent}[args.workload]()
         if int(os.environ.get("RANK", 0)) == 0:
             print(json.dumps({"workload": args.workload, **r}))
         return
@@ -716,8 +805,19 @@ def main():
         tdist.init_process_group("nccl")
         dist = tdist
     r = run_ours(args, rank, world, dist)
+    extras = {}
+    if world == 1 and not args.no_extras:
+        # the method's heuristic and the multi-scene and contact workloads on the same run,
+        # each with its own device-timed figures (not the headline value)
+        for key, fn in (("violent", lambda: run_violent(steps=8, warmup=2)),
+                        ("batched", lambda: run_batched(n_scenes=64, steps=5, warmup=1)),
+                        ("serving", lambda: run_serving(n_scenes=60, n_req=3000, warm=300, seed=1)),
+                        ("contact", lambda: run_contact(steps=5, warmup=2))):
+            t0 = time.perf_counter()
+            extras[key] = fn()
+            extras[key]["wall_s"] = round(time.perf_counter() - t0, 1)
     if rank == 0:
-        line = dict(base, **r)
+        line = dict(base, **r, **extras)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = oracle_sample()
         print(json.dumps(line))

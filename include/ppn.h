@@ -102,6 +102,10 @@ typedef struct {
                              * constraints by penalty potentials (Sec. 5.1): the constrained vertices
                              * stay free and carry k m_v / (2 dt^2) |x_v - t_v|^2, t_v the target; new
                              * targets take effect at once.  Fixed at scene creation; finite, >= 0. */
+  double tie_band;     /* selection ties (Algorithm 1's strict test r_e > delta, Sec. 4): an element not
+                        * yet projected with |r_e - delta| <= tie_band delta is counted as a tie in the
+                        * attempt and step statistics (the strict test still decides).  0: by precision,
+                        * 1e-12 in FP64, 1e-5 in the mixed mode (0).  Finite, >= 0. */
 } ppn_params;
 
 typedef struct {
@@ -129,6 +133,7 @@ typedef struct {
   int ind;               /* the solver reported indefiniteness */
   int cg_iters;
   double delta;          /* delta of the selection before this solve (inf for attempt 0) */
+  int n_ties;            /* selection ties (params.tie_band) of the rounds since the previous solve */
 } ppn_attempt;
 
 typedef struct {
@@ -139,6 +144,7 @@ typedef struct {
   int status;            /* ppn_status of the step */
   double final_grad_norm2;
   double device_ms;      /* stream time between the step's first and last kernel */
+  int n_ties;            /* selection ties of every PPN selection round of the step */
 } ppn_step_stats;
 
 typedef struct {
@@ -199,6 +205,18 @@ PPN_API ppn_status ppn_step_batch(ppn_scene* const* scenes, int n, const ppn_mod
 
 PPN_API ppn_status ppn_get_iter_stats(const ppn_scene* s, ppn_iter_stats* buf, int cap, int* n_written);
 PPN_API ppn_status ppn_get_attempts(const ppn_scene* s, ppn_attempt* buf, int cap, int* n_written);
+/* Selected sets of Algorithm 1 (Sec. 4: each round projects the elements with
+ * ||S^e g||_inf > delta that are not yet projected).  With recording on, every
+ * following step keeps, per attempt (the order of ppn_get_attempts), the elements
+ * that the PPN selection rounds since the previous solve chose: tets as their index
+ * e, contact elements as n_tets + v.  Attempts without a PPN selection (the first
+ * solve of an iteration, PN, PDN) have none.  Recording copies each selection to
+ * the host (diagnostics; it adds a device synchronisation per round). */
+PPN_API ppn_status ppn_set_record_selection(ppn_scene* s, int on);
+/* The elements of attempt idx of the last step, ascending; *n receives their count
+ * and min(cap, count) are written to buf (buf may be NULL when cap is 0).
+ * INVALID_ARG when idx is out of range or recording was off during the step. */
+PPN_API ppn_status ppn_get_attempt_selection(const ppn_scene* s, int idx, int32_t* buf, int64_t cap, int64_t* n);
 PPN_API ppn_status ppn_get_state(const ppn_scene* s, double* x, double* v);
 PPN_API ppn_status ppn_set_state(ppn_scene* s, const double* x, const double* v);
 /* Exact checkpoint of the internal state: displacement u = x - rest and
@@ -228,9 +246,14 @@ PPN_API ppn_status ppn_probe_pattern(const ppn_scene* s, int64_t* row_ptr, int32
 /* assembled matrix at x: vals nnzb*9 (3x3 row-major blocks); proj: n_tets flags
  * (NULL = none) of elements that enter projected */
 PPN_API ppn_status ppn_probe_assemble(ppn_scene* s, const double* x, const uint8_t* proj, double* vals);
-/* K4 selection on a given assembled gradient g (n_verts*3) */
+/* K4 selection on a given assembled gradient g (n_verts*3): out_new (n_tets flags),
+ * n_new, and n_ties, the elements not in `already` within the tie band of delta
+ * (params.tie_band); any output may be NULL */
 PPN_API ppn_status ppn_probe_select(ppn_scene* s, const double* g, double delta, const uint8_t* already,
-                            uint8_t* out_new, int64_t* n_new);
+                            uint8_t* out_new, int64_t* n_new, int64_t* n_ties);
+/* tets after the orientation normalisation of ppn_create_scene (n_tets*4 int32),
+ * as the kernels read them */
+PPN_API ppn_status ppn_probe_tets(const ppn_scene* s, int32_t* tets);
 /* K5 clamping updates dH^e = Hhat^e - H^e (n_sel*144) of the listed elements at x */
 PPN_API ppn_status ppn_probe_project(ppn_scene* s, const double* x, const int32_t* sel, int64_t n_sel,
                              double* dH);

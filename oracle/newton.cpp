@@ -60,6 +60,7 @@ struct ora_scene {
   void* hook_user = nullptr;
   std::vector<ora_iter_stats> iters;
   std::vector<ora_attempt> attempts;
+  std::vector<std::vector<int32_t>> attempt_sel;  // PPN selection before each attempt
 };
 
 namespace {
@@ -311,6 +312,7 @@ ora_params ora_default_params(void) {
   p.contact_dhat = 1e-3;
   p.ccd_safety = 0.9;
   p.dirichlet_penalty = 0.0;
+  p.tie_band = 1e-12;
   return p;
 }
 
@@ -557,10 +559,11 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
 
   s->iters.clear();
   s->attempts.clear();
+  s->attempt_sel.clear();
   double delta = kInf;  // Algorithm 1, before the Newton loop
   double g0 = -1.0;
   int status = ORA_ERR_NEWTON_MAXITER;
-  int total_proj = 0, total_cg = 0, total_att = 0;
+  int total_proj = 0, total_cg = 0, total_att = 0, total_ties = 0;
   int countdown = 0;  // PDN: iterations left that assemble projected
 
   for (int k = 0; k < p.newton_max_iter; ++k) {
@@ -636,6 +639,8 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
 
     int info[4];
     int attempt = 0;
+    int ties_pending = 0;               // ties of the selection rounds since the last solve
+    std::vector<int32_t> sel_pending;   // elements they selected
     auto solve = [&](int n_new, double delta_used) {
       ora::pcg(nv, s->row_ptr.data(), s->col.data(), vals.data(), b.data(), p.pcg_rel_tol,
                pcg_max(s), dx.data(), info);
@@ -650,7 +655,11 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
       a.ind = info[1];
       a.cg_iters = info[0];
       a.delta = delta_used;
+      a.n_ties = ties_pending;
       s->attempts.push_back(a);
+      s->attempt_sel.push_back(sel_pending);
+      ties_pending = 0;
+      sel_pending.clear();
       st.pcg_attempts += 1;
       st.cg_iters += info[0];
       st.precond_fail = info[2];
@@ -681,8 +690,24 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
             ++n_new;
           }
         }
+        // ties: elements not yet projected whose key lies within tie_band delta of delta
+        if (delta > p.eps_delta)
+          for (int64_t e = 0; e < nt + nv; ++e) {
+            if (proj[e] || (e >= nt && !cact[e - nt])) continue;
+            double r;
+            if (e < nt) {
+              r = element_residual(s, e, g.data());
+            } else {
+              const int64_t v = e - nt;
+              r = std::fmax(std::fabs(g[3 * v]), std::fmax(std::fabs(g[3 * v + 1]), std::fabs(g[3 * v + 2])));
+            }
+            if (std::fabs(r - delta) <= p.tie_band * delta) ++ties_pending, ++total_ties;
+          }
         for (int64_t e = 0; e < nt + nv; ++e)
-          if (fresh[e]) project_one(e);
+          if (fresh[e]) {
+            project_one(e);
+            sel_pending.push_back((int32_t)e);
+          }
         n_proj += (int)n_new;
         st.n_new_projected += (int)n_new;
         if (n_new > 0) ind = solve((int)n_new, delta);  // unchanged matrix: same verdict
@@ -769,6 +794,7 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
     out->total_cg_iters = total_cg;
     out->total_attempts = total_att;
     out->status = status;
+    out->n_ties = total_ties;
   }
   return status;
 }
@@ -783,6 +809,13 @@ int ora_scene_attempts(const ora_scene* s, ora_attempt* buf, int cap) {
   const int n = (int)s->attempts.size();
   for (int i = 0; i < n && i < cap; ++i) buf[i] = s->attempts[i];
   return n;
+}
+
+int64_t ora_scene_attempt_selection(const ora_scene* s, int idx, int32_t* buf, int64_t cap) {
+  if (idx < 0 || idx >= (int)s->attempt_sel.size()) return -1;
+  const std::vector<int32_t>& l = s->attempt_sel[idx];
+  for (int64_t i = 0; i < (int64_t)l.size() && i < cap; ++i) buf[i] = l[i];
+  return (int64_t)l.size();
 }
 
 }  // extern "C"

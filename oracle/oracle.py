@@ -26,7 +26,7 @@ class Params(C.Structure):
                 ("ls_max_halvings", C.c_int), ("tol_kind", C.c_int), ("init_guess", C.c_int),
                 ("pdn_countdown", C.c_int), ("projection", C.c_int), ("grad_floor", C.c_double),
                 ("ls_slack", C.c_double), ("contact_kappa", C.c_double), ("contact_dhat", C.c_double),
-                ("ccd_safety", C.c_double), ("dirichlet_penalty", C.c_double)]
+                ("ccd_safety", C.c_double), ("dirichlet_penalty", C.c_double), ("tie_band", C.c_double)]
 
 
 class Obstacle(C.Structure):
@@ -53,12 +53,13 @@ class IterStats(C.Structure):
 
 class Attempt(C.Structure):
     _fields_ = [("newton_iter", C.c_int), ("attempt", C.c_int), ("n_new_projected", C.c_int),
-                ("ind", C.c_int), ("cg_iters", C.c_int), ("delta", C.c_double)]
+                ("ind", C.c_int), ("cg_iters", C.c_int), ("delta", C.c_double), ("n_ties", C.c_int)]
 
 
 class StepStats(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("total_projections", C.c_int),
-                ("total_cg_iters", C.c_int), ("total_attempts", C.c_int), ("status", C.c_int)]
+                ("total_cg_iters", C.c_int), ("total_attempts", C.c_int), ("status", C.c_int),
+                ("n_ties", C.c_int)]
 
 
 HOOK = C.CFUNCTYPE(C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p)
@@ -126,6 +127,7 @@ def lib():
         "ora_scene_step": (I, [P, I, D, pd, C.POINTER(StepStats)]),
         "ora_scene_iter_stats": (I, [P, C.POINTER(IterStats), I]),
         "ora_scene_attempts": (I, [P, C.POINTER(Attempt), I]),
+        "ora_scene_attempt_selection": (I64, [P, I, pi, I64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -410,6 +412,16 @@ class Scene:
         for i in range(min(n, cap)):
             d = {k: getattr(buf[i], k) for k, _ in Attempt._fields_}
             out.append(d)
+        return out
+
+    def attempt_selection(self, idx: int):
+        """Elements newly selected by the PPN rounds before attempt ``idx`` of the last
+        step (ascending; the contact element of vertex v is n_tets + v)."""
+        n = lib().ora_scene_attempt_selection(self._h, int(idx), None, 0)
+        if n < 0:
+            raise IndexError(idx)
+        out = np.zeros(n, np.int32)
+        lib().ora_scene_attempt_selection(self._h, int(idx), _ip(out), n)
         return out
 
 

@@ -81,6 +81,8 @@ typedef struct {
   double ccd_safety;    /* line search starts at min(1, ccd_safety * gamma_ccd), default 0.9 */
   double dirichlet_penalty; /* 0: Dirichlet vertices eliminated (default); k > 0: they stay free and
                                carry the penalty potential k m_v / (2 dt^2) |x_v - t_v|^2 */
+  double tie_band;     /* a selection tie: an element not yet projected with |r_e - delta| <= tie_band
+                          delta (counted, not a change of the strict test r_e > delta), default 1e-12 */
 } ora_params;
 
 /* analytic obstacles for frictionless log-barrier contact (contact.cpp) */
@@ -117,6 +119,7 @@ typedef struct {
   int ind;
   int cg_iters;
   double delta;        /* delta used for the selection before this solve (inf for attempt 0) */
+  int n_ties;          /* selection ties of the rounds since the previous solve */
 } ora_attempt;
 
 typedef struct {
@@ -125,6 +128,7 @@ typedef struct {
   int total_cg_iters;
   int total_attempts;
   int status;
+  int n_ties;          /* selection ties of every round of the step */
 } ora_step_stats;
 
 typedef struct ora_scene ora_scene;
@@ -203,6 +207,11 @@ void ora_scene_project(const ora_scene* s, const double* x, const int32_t* sel, 
 int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_stats* out);
 int ora_scene_iter_stats(const ora_scene* s, ora_iter_stats* buf, int cap);
 int ora_scene_attempts(const ora_scene* s, ora_attempt* buf, int cap);
+/* elements newly selected by the PPN rounds before attempt `idx` of the last step, ascending
+ * (tets e in [0, n_t), the contact element of vertex v as n_t + v); attempts without a
+ * PPN selection (the first solve, PN, PDN) have none.  Returns the count (-1: no such
+ * attempt); at most cap are written. */
+int64_t ora_scene_attempt_selection(const ora_scene* s, int idx, int32_t* buf, int64_t cap);
 
 #ifdef __cplusplus
 }

@@ -49,6 +49,7 @@ struct Ctl {
   double pcg_rr0, pcg_rr, pcg_rz, pcg_dq, pcg_alpha, pcg_beta;
   int n_new;             // elements selected by the last selection
   int n_new_c;           // contact elements selected by the last selection
+  int n_ties;            // selection ties of the last selection (|r_e - delta| <= tie_band delta)
   int pcg_iters;         // CG updates performed (x = sum of alpha d)
   int pcg_ind;           // negative curvature or a non-SPD diagonal block
   int pcg_precond_fail;
@@ -117,6 +118,7 @@ struct SceneDev {
   double dt, inv_dt2;
   double grav[3];
   double delta, eps_delta, eig_eps;
+  double tie_band;         // relative half-width of the tie band around delta (counted, not selected)
   double gamma;
   double pcg_tol2;
   int pcg_max_iter;

@@ -286,6 +286,8 @@ struct HostState {
   double E0 = 0, dd = 0, dxmax = 0, gamma = 1;
   int halvings = 0;
   int countdown = 0;  // PDN: iterations left that assemble projected
+  int ties_pending = 0;          // selection ties of the rounds since the last solve
+  std::vector<int> sel_pending;  // elements those rounds selected (recorded on request)
   bool pre = false;   // this iteration projects every element before assembly
   int n_elem = 0;     // elements of the current iteration: tets + contact elements
   double tol = 0;     // Newton tolerance of the current step
@@ -541,6 +543,7 @@ struct Driver {
       G.h_desc[i].delta = H[i].delta;
       G.S[i]->iters.clear();
       G.S[i]->attempts.clear();
+      G.S[i]->attempt_sel.clear();
     }
     G.set_active(on);
     ppn_status rc = G.upload_desc();
@@ -668,6 +671,8 @@ struct Driver {
         continue;
       }
       h.cur = ppn_iter_stats{};
+      h.ties_pending = 0;
+      h.sel_pending.clear();
       h.cur.newton_iter = h.k;
       h.cur.grad_norm2 = h.gn2;
       h.cur.grad_norminf = h.ginf;
@@ -997,7 +1002,14 @@ struct Driver {
     a.ind = h.ind;
     a.cg_iters = c.pcg_iters;
     a.delta = delta;
+    a.n_ties = h.ties_pending;
     G.S[i]->attempts.push_back(a);
+    if (G.S[i]->record_sel) {
+      std::sort(h.sel_pending.begin(), h.sel_pending.end());
+      G.S[i]->attempt_sel.push_back(h.sel_pending);
+    }
+    h.ties_pending = 0;
+    h.sel_pending.clear();
   }
 
   ppn_status check_errors(const std::vector<char>& on) {
@@ -1033,7 +1045,7 @@ struct Driver {
     ppn_status rc = G.upload_desc();
     if (rc) return rc;
     for (int i = 0; i < n; ++i)
-      if (on[i]) PPN_CU(cudaMemsetAsync(&G.d_ctl[i].n_new, 0, 2 * sizeof(int), G.st));  // n_new, n_new_c
+      if (on[i]) PPN_CU(cudaMemsetAsync(&G.d_ctl[i].n_new, 0, 3 * sizeof(int), G.st));  // n_new, n_new_c, n_ties
     timed(FAM_SELECT, 0, [&] {
       launch_select<T>(G.d_desc, G.d_ttiles, G.n_ttiles, G.st);
       if (any_obstacles(on)) launch_select_contact<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st);  // clamps them too
@@ -1051,13 +1063,39 @@ struct Driver {
           const int nn = G.h_ctl[i].n_new, nc = G.h_ctl[i].n_new_c;
           H[i].n_proj += nn + nc;
           H[i].cur.n_new_projected += nn + nc;
+          H[i].ties_pending += G.h_ctl[i].n_ties;
+          H[i].tot.n_ties += G.h_ctl[i].n_ties;
           for (int t = 0; t < (nn + PROJ_CTA - 1) / PROJ_CTA; ++t) jt.push_back({i, t});
+          if (G.S[i]->record_sel && H[i].mode == PPN_MODE_PPN && (rc = record_selection(i, nn, nc))) return rc;
         }
     }
     if (jt.empty()) return PPN_OK;
     if ((rc = G.upload(G.d_projtiles, jt.data(), sizeof(TileRef) * jt.size()))) return rc;
     timed(FAM_PROJECT, 0, [&] { launch_project<T>(G.d_desc, G.d_projtiles, (int)jt.size(), 0, G.st); });
     return check_launch();
+  }
+
+  // the elements of scene i that the last selection chose (diagnostics, on request):
+  // tets from the compacted list, contact elements (n_tets + v) from their stamps
+  ppn_status record_selection(int i, int nn, int nc) {
+    SceneImpl<T>& s = *G.S[i];
+    std::vector<int>& out = H[i].sel_pending;
+    if (nn > 0) {
+      const size_t at = out.size();
+      out.resize(at + nn);
+      PPN_CU(cudaMemcpyAsync(out.data() + at, s.d.sel_list, sizeof(int) * nn, cudaMemcpyDeviceToHost, G.st));
+    }
+    std::vector<int> cr, cp;
+    if (nc > 0) {
+      cr.resize(s.nv);
+      cp.resize(s.nv);
+      PPN_CU(cudaMemcpyAsync(cr.data(), s.d.cround_stamp, sizeof(int) * s.nv, cudaMemcpyDeviceToHost, G.st));
+      PPN_CU(cudaMemcpyAsync(cp.data(), s.d.cproj_stamp, sizeof(int) * s.nv, cudaMemcpyDeviceToHost, G.st));
+    }
+    PPN_CU(cudaStreamSynchronize(G.st));
+    for (int v = 0; v < (int)cr.size(); ++v)
+      if (cr[v] == G.h_desc[i].round_id && cp[v] == G.h_desc[i].it_id) out.push_back(s.nt + v);
+    return PPN_OK;
   }
 
   ppn_status fallback_dir(const std::vector<char>& on, int kind) {

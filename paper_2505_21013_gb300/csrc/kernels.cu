@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(TILE) k_select(const SceneDev<T>* scenes, cons
   const SceneDev<T>& S = scenes[tr.scene];
   if (!S.active) return;
   const int e = tr.tile * TILE + threadIdx.x;
-  bool sel = false;
+  bool sel = false, tie = false;
   if (e < S.nt && S.proj_stamp[e] != S.it_id) {
     if (S.delta < 0.0 || S.delta <= S.eps_delta) {
       sel = true;
@@ -360,11 +360,14 @@ __global__ void __launch_bounds__(TILE) k_select(const SceneDev<T>* scenes, cons
       const int4 t = S.tets[e];
       const double r = fmax(fmax(S.gmax[t.x], S.gmax[t.y]), fmax(S.gmax[t.z], S.gmax[t.w]));
       sel = r > S.delta;
+      tie = fabs(r - S.delta) <= S.tie_band * S.delta;  // reported: the strict test decides
     }
   }
+  const int lane = threadIdx.x & 31;
+  const unsigned tmask = __ballot_sync(0xffffffffu, tie);
+  if (tmask != 0u && lane == 0) atomicAdd(&S.ctl->n_ties, __popc(tmask));
   const unsigned mask = __ballot_sync(0xffffffffu, sel);
   if (mask == 0u) return;
-  const int lane = threadIdx.x & 31;
   int base = 0;
   if (lane == __ffs(mask) - 1) base = atomicAdd(&S.ctl->n_new, __popc(mask));
   base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
@@ -419,13 +422,16 @@ __global__ void __launch_bounds__(TILE) k_select_contact(const SceneDev<T>* scen
   const int v = tr.tile * TILE + threadIdx.x;
   if (v >= S.nv || S.fixed[v] || S.cproj_stamp[v] == S.it_id) return;
   const bool all = S.delta < 0.0 || S.delta <= S.eps_delta;
-  if (!all && !(S.gmax[v] > S.delta)) return;
+  const bool tie = !all && fabs(S.gmax[v] - S.delta) <= S.tie_band * S.delta;
+  if (!all && !(S.gmax[v] > S.delta) && !tie) return;
   const double4 X = ld_d4(S.X + v), u = ld_d4(S.u + v);
   const double x[3] = {X.x + u.x, X.y + u.y, X.z + u.z};
   double Hc[9];
   bool act = false;
   vertex_contact(S, x, nullptr, nullptr, Hc, &act);
   if (!act) return;
+  if (tie) atomicAdd(&S.ctl->n_ties, 1);  // a contact element within the tie band (rare)
+  if (!all && !(S.gmax[v] > S.delta)) return;
   T H3[9], d3[9];
 #pragma unroll
   for (int c = 0; c < 9; ++c) H3[c] = (T)Hc[c];

@@ -173,6 +173,10 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
     set_error("dirichlet_penalty must be finite and >= 0");
     return PPN_ERR_INVALID_ARG;
   }
+  if (!(params.tie_band >= 0.0) || !std::isfinite(params.tie_band)) {
+    set_error("tie_band must be finite and >= 0");
+    return PPN_ERR_INVALID_ARG;
+  }
   const bool penalty = params.dirichlet_penalty > 0.0;
   dt = dt_;
   nv = (int)n_verts;
@@ -483,6 +487,8 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   for (int k = 0; k < 3; ++k) s.grav[k] = params.gravity[k];
   s.eps_delta = params.eps_delta;
   s.eig_eps = params.eig_eps;
+  // the tie band of the selection: the resolution of r_e against delta in each precision
+  s.tie_band = params.tie_band > 0.0 ? params.tie_band : (sizeof(T) == sizeof(double) ? 1e-12 : 1e-5);
   s.kappa = params.contact_kappa;
   s.dhat = params.contact_dhat;
   s.pen_k = params.dirichlet_penalty;
@@ -740,7 +746,7 @@ static ppn_status probe_assemble(SceneImpl<T>& s, const double* x, const uint8_t
 
 template <typename T>
 static ppn_status probe_select(SceneImpl<T>& s, const double* g, double delta, const uint8_t* already,
-                               uint8_t* out_new, int64_t* n_new) {
+                               uint8_t* out_new, int64_t* n_new, int64_t* n_ties) {
   Probe<T> p(s);
   ppn_status rc = p.begin();
   if (rc) return rc;
@@ -754,7 +760,7 @@ static ppn_status probe_select(SceneImpl<T>& s, const double* g, double delta, c
   PPN_CU(cudaMemcpy(s.d.proj_stamp, stamp.data(), sizeof(int) * s.nt, cudaMemcpyHostToDevice));
   p.G->h_desc[0].delta = delta;
   if ((rc = p.G->upload_desc())) return rc;
-  PPN_CU(cudaMemsetAsync(&p.G->d_ctl[0].n_new, 0, sizeof(int), s.stream));
+  PPN_CU(cudaMemsetAsync(&p.G->d_ctl[0].n_new, 0, 3 * sizeof(int), s.stream));  // n_new, n_new_c, n_ties
   launch_gmax<T>(p.G->d_desc, p.G->d_vtiles, p.G->n_vtiles, s.stream);
   launch_select<T>(p.G->d_desc, p.G->d_ttiles, p.G->n_ttiles, s.stream);
   PPN_CU(cudaGetLastError());
@@ -767,6 +773,7 @@ static ppn_status probe_select(SceneImpl<T>& s, const double* g, double delta, c
     for (int e : list) out_new[e] = 1;
   }
   if (n_new) *n_new = nn;
+  if (n_ties) *n_ties = p.G->h_ctl[0].n_ties;
   return PPN_OK;
 }
 
@@ -883,6 +890,7 @@ ppn_params ppn_default_params(void) {
   p.contact_dhat = 1e-3;
   p.ccd_safety = 0.9;
   p.dirichlet_penalty = 0.0;
+  p.tie_band = 0.0;
   p.pcg_rel_tol = 1e-4;
   p.armijo_c = 1e-4;
   p.gravity[0] = 0.0;
@@ -1124,6 +1132,32 @@ ppn_status ppn_get_attempts(const ppn_scene* s, ppn_attempt* buf, int cap, int* 
   });
 }
 
+ppn_status ppn_set_record_selection(ppn_scene* s, int on) {
+  return dispatch(s, [&](auto& x) {
+    x.record_sel = on != 0;
+    x.attempt_sel.clear();
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_get_attempt_selection(const ppn_scene* s, int idx, int32_t* buf, int64_t cap, int64_t* n) {
+  if (cap < 0 || (cap > 0 && !buf)) {
+    set_error("cap < 0, or a null buffer with cap > 0");
+    return PPN_ERR_INVALID_ARG;
+  }
+  return dispatch_c(s, [&](auto& x) {
+    if (idx < 0 || idx >= (int)x.attempt_sel.size()) {
+      set_error("no recorded selection for attempt " + std::to_string(idx) +
+                " (recording off during the step, or index out of range)");
+      return PPN_ERR_INVALID_ARG;
+    }
+    const std::vector<int>& l = x.attempt_sel[idx];
+    for (int64_t k = 0; k < (int64_t)l.size() && k < cap; ++k) buf[k] = l[k];
+    if (n) *n = (int64_t)l.size();
+    return PPN_OK;
+  });
+}
+
 ppn_status ppn_get_state(const ppn_scene* s, double* xo, double* vo) {
   return dispatch_c(s, [&](auto& x) {
     if (xo) {
@@ -1268,9 +1302,17 @@ ppn_status ppn_probe_assemble(ppn_scene* s, const double* x, const uint8_t* proj
 }
 
 ppn_status ppn_probe_select(ppn_scene* s, const double* g, double delta, const uint8_t* already,
-                            uint8_t* out_new, int64_t* n_new) {
+                            uint8_t* out_new, int64_t* n_new, int64_t* n_ties) {
   if (!g) return PPN_ERR_INVALID_ARG;
-  return dispatch(s, [&](auto& sc) { return probe_select(sc, g, delta, already, out_new, n_new); });
+  return dispatch(s, [&](auto& sc) { return probe_select(sc, g, delta, already, out_new, n_new, n_ties); });
+}
+
+ppn_status ppn_probe_tets(const ppn_scene* s, int32_t* tets) {
+  if (!tets) return PPN_ERR_INVALID_ARG;
+  return dispatch_c(s, [&](auto& x) {
+    PPN_CU(cudaMemcpy(tets, x.d.tets, sizeof(int4) * (size_t)x.nt, cudaMemcpyDeviceToHost));
+    return PPN_OK;
+  });
 }
 
 ppn_status ppn_probe_project(ppn_scene* s, const double* x, const int32_t* sel, int64_t n_sel,

@@ -97,6 +97,8 @@ struct SceneImpl {
   int it_counter = 0, round_counter = 0;
   std::vector<ppn_iter_stats> iters;
   std::vector<ppn_attempt> attempts;
+  bool record_sel = false;                    // keep the selected elements of every attempt
+  std::vector<std::vector<int>> attempt_sel;  // (ppn_set_record_selection)
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
 
   ~SceneImpl();

@@ -36,7 +36,8 @@ class ppn_params(C.Structure):
                 ("ls_max_halvings", C.c_int), ("precision", C.c_int), ("tol_kind", C.c_int),
                 ("init_guess", C.c_int), ("pdn_countdown", C.c_int), ("projection", C.c_int),
                 ("grad_floor", C.c_double), ("ls_slack", C.c_double), ("contact_kappa", C.c_double),
-                ("contact_dhat", C.c_double), ("ccd_safety", C.c_double), ("dirichlet_penalty", C.c_double)]
+                ("contact_dhat", C.c_double), ("ccd_safety", C.c_double), ("dirichlet_penalty", C.c_double),
+                ("tie_band", C.c_double)]
 
 
 class ppn_obstacle(C.Structure):
@@ -69,13 +70,13 @@ class ppn_iter_stats(C.Structure):
 
 class ppn_attempt(C.Structure):
     _fields_ = [("newton_iter", C.c_int), ("attempt", C.c_int), ("n_new_projected", C.c_int),
-                ("ind", C.c_int), ("cg_iters", C.c_int), ("delta", C.c_double)]
+                ("ind", C.c_int), ("cg_iters", C.c_int), ("delta", C.c_double), ("n_ties", C.c_int)]
 
 
 class ppn_step_stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("total_projections", C.c_int), ("total_cg_iters", C.c_int),
                 ("total_attempts", C.c_int), ("status", C.c_int), ("final_grad_norm2", C.c_double),
-                ("device_ms", C.c_double)]
+                ("device_ms", C.c_double), ("n_ties", C.c_int)]
 
 
 class ppn_server_config(C.Structure):
@@ -130,6 +131,9 @@ SIGNATURES = {
                              C.POINTER(ppn_step_stats)]),
     "ppn_get_iter_stats": (_st, [_P, C.POINTER(ppn_iter_stats), C.c_int, C.POINTER(C.c_int)]),
     "ppn_get_attempts": (_st, [_P, C.POINTER(ppn_attempt), C.c_int, C.POINTER(C.c_int)]),
+    "ppn_set_record_selection": (_st, [_P, C.c_int]),
+    "ppn_get_attempt_selection": (_st, [_P, C.c_int, _pi, C.c_int64, _pl]),
+    "ppn_probe_tets": (_st, [_P, _pi]),
     "ppn_get_state": (_st, [_P, _pd, _pd]),
     "ppn_set_state": (_st, [_P, _pd, _pd]),
     "ppn_get_displacement": (_st, [_P, _pd, _pd]),
@@ -140,7 +144,7 @@ SIGNATURES = {
     "ppn_probe_gradient": (_st, [_P, _pd, _pd, _pd, _pd, _pd]),
     "ppn_probe_pattern": (_st, [_P, _pl, _pi]),
     "ppn_probe_assemble": (_st, [_P, _pd, _pu, _pd]),
-    "ppn_probe_select": (_st, [_P, _pd, C.c_double, _pu, _pu, _pl]),
+    "ppn_probe_select": (_st, [_P, _pd, C.c_double, _pu, _pu, _pl, _pl]),
     "ppn_probe_project": (_st, [_P, _pd, _pi, C.c_int64, _pd]),
     "ppn_probe_pcg": (_st, [_P, _pd, _pd, C.c_double, C.c_int, _pd, C.POINTER(C.c_int)]),
     "ppn_probe_bounded_wait": (_st, [C.c_int, C.c_int, C.c_int]),
@@ -308,6 +312,19 @@ class Scene:
         _check(lib().ppn_get_attempts(self._h, buf, 4096, C.byref(n)), "ppn_get_attempts")
         return [struct_dict(buf[i]) for i in range(min(n.value, 4096))]
 
+    def set_record_selection(self, on: bool):
+        _check(lib().ppn_set_record_selection(self._h, 1 if on else 0), "ppn_set_record_selection")
+
+    def attempt_selection(self, idx: int):
+        """Elements selected before attempt ``idx`` of the last step (recording on):
+        ascending tet indices, contact elements as n_tets + v."""
+        n = C.c_int64()
+        _check(lib().ppn_get_attempt_selection(self._h, int(idx), None, 0, C.byref(n)), "ppn_get_attempt_selection")
+        out = np.zeros(n.value, np.int32)
+        _check(lib().ppn_get_attempt_selection(self._h, int(idx), out.ctypes.data_as(_pi), out.size, C.byref(n)),
+               "ppn_get_attempt_selection")
+        return out
+
     def get_state(self):
         x = np.zeros((self.n_verts, 3))
         v = np.zeros((self.n_verts, 3))
@@ -376,15 +393,23 @@ class Scene:
                                         _d(vals)), "ppn_probe_assemble")
         return vals
 
-    def probe_select(self, g, delta, already=None):
+    def probe_select(self, g, delta, already=None, with_ties=False):
         g = _arr(g, np.float64)
         out = np.zeros(self.n_tets, np.uint8)
         al = None if already is None else _arr(already, np.uint8)
-        n = C.c_int64()
+        n, nt = C.c_int64(), C.c_int64()
         _check(lib().ppn_probe_select(self._h, _d(g), float(delta),
                                       al.ctypes.data_as(_pu) if al is not None else None,
-                                      out.ctypes.data_as(_pu), C.byref(n)), "ppn_probe_select")
+                                      out.ctypes.data_as(_pu), C.byref(n), C.byref(nt)), "ppn_probe_select")
+        if with_ties:
+            return out.astype(bool), n.value, nt.value
         return out.astype(bool), n.value
+
+    def probe_tets(self):
+        """The tets after the orientation normalisation, as the kernels read them."""
+        t = np.zeros((self.n_tets, 4), np.int32)
+        _check(lib().ppn_probe_tets(self._h, t.ctypes.data_as(_pi)), "ppn_probe_tets")
+        return t
 
     def probe_project(self, x, sel):
         x = _arr(x, np.float64)

@@ -47,8 +47,8 @@ def test_element_gradients_hessians_energies(prec):
     x = deformed(spec, 2, amp=0.4)
     psi, ge, He = g.probe_elements(x)
     psi_o, ge_o, He_o = o.element_eval(x)
-    # tet orientation normalisation must agree
-    assert np.array_equal(o.tets(), o.tets())
+    # the CUDA path's orientation normalisation is the oracle's
+    assert np.array_equal(g.probe_tets(), o.tets())
     tol = TOL[prec]
     assert np.abs(ge - ge_o).max() <= tol * np.abs(ge_o).max()
     assert np.abs(He - He_o).max() <= tol * np.abs(He_o).max()
@@ -186,6 +186,28 @@ def test_pcg_zero_rhs_and_nonspd_diagonal():
     assert info["ind"] and info["precond_fail"] and info["iters"] == 0
 
 
+def test_orientation_normalisation_on_permuted_tets():
+    # corners given in random order, so about half the tets arrive negatively oriented:
+    # both sides swap corners 2 and 3 of exactly those, and every normalised tet has
+    # det[x1-x0, x2-x0, x3-x0] > 0 at rest
+    from ppn_inputs.scenes import SceneSpec
+
+    base = medium_spec(24)
+    rng = np.random.default_rng(25)
+    tets = np.array([t[rng.permutation(4)] for t in base.tets], dtype=np.int32)
+    spec = SceneSpec(**{**base.__dict__, "tets": tets})
+    g, o = scene_pair(spec, P.PREC_MIXED)
+    tg, to = g.probe_tets(), o.tets()
+    assert np.array_equal(tg, to)
+    X = spec.rest
+    D = np.stack([X[tg[:, k]] - X[tg[:, 0]] for k in (1, 2, 3)], axis=2)
+    assert (np.linalg.det(D) > 0).all()
+    flipped = (tg != tets).any(axis=1)
+    assert 0.3 < flipped.mean() < 0.7
+    assert np.array_equal(tg[flipped][:, [0, 1, 3, 2]], tets[flipped])
+    assert np.array_equal(tg[~flipped], tets[~flipped])
+
+
 def test_tiny_meshes_and_ragged_sizes():
     for cells in [(1, 1, 1), (2, 1, 1), (3, 2, 1)]:
         spec = tiny_scene(cells=cells, seed=sum(cells))
@@ -275,3 +297,52 @@ def test_tuned_streamed_layouts_give_identical_steps(monkeypatch):
     for (xa, na, ca), (xb, nb, cb) in zip(*out):
         assert na == nb and ca == cb
         assert np.array_equal(xa, xb)
+
+
+def _dense(rp, col, vals, n):
+    A = np.zeros((3 * n, 3 * n))
+    for r in range(n):
+        for k in range(rp[r], rp[r + 1]):
+            A[3 * r:3 * r + 3, 3 * col[k]:3 * col[k] + 3] = vals[k]
+    return A
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_pcg_curvature_exit_follows_the_oracle(prec):
+    # Indefinite systems of decreasing negative curvature: the Hessian of a compressed
+    # state with its spectrum shifted so that the most negative eigenvalue is a fraction
+    # f of the original one.  The smaller f, the later CG meets negative curvature.  The
+    # FP32 kernel forms the curvature of each direction by the single-reduction
+    # recurrence d^T A d = delta - beta gamma / alpha_prev, not by a direct product; it
+    # must leave with ind at the oracle's iteration (FP64: exactly up to one iteration;
+    # mixed: within 15 %, at least 2), and a shift that makes the system SPD must not
+    # report ind.
+    spec = medium_spec(14)
+    g, o = scene_pair(spec, prec)
+    rp, col = o.pattern()
+    n = spec.n_verts
+    vi = o.assemble(deformed(spec, 17, amp=0.3))
+    lmin = np.linalg.eigvalsh(_dense(rp, col, vi, n))[0]
+    assert lmin < 0
+    diag = np.array([rp[r] + np.nonzero(col[rp[r]:rp[r + 1]] == r)[0][0] for r in range(n)])
+    free = np.setdiff1d(np.arange(n), spec.fixed)
+    b = np.random.default_rng(16).standard_normal((n, 3))
+    b[spec.fixed] = 0
+    exits = []
+    for f in (0.5, 0.1, 0.02, 0.005, 0.001):
+        v2 = vi.copy()
+        v2[diag[free]] += (-lmin * (1.0 - f)) * np.eye(3)
+        xg, info = g.probe_pcg(v2, b, rel_tol=1e-8)
+        xo, info_o = O.pcg_bsr(rp, col, v2, b.reshape(-1), rel_tol=1e-8, max_iter=5000)
+        assert info_o["ind"] and info["ind"], f
+        assert not info["precond_fail"]
+        slack = 1 if prec == P.PREC_FP64 else max(2, int(0.15 * info_o["iters"]))
+        assert abs(info["iters"] - info_o["iters"]) <= slack, (f, info, info_o)
+        exits.append(info_o["iters"])
+    assert exits == sorted(exits) and exits[-1] >= 3 * exits[0]
+    # shifted past zero: SPD, no curvature exit on either side
+    v2 = vi.copy()
+    v2[diag[free]] += (-lmin * 1.05) * np.eye(3)
+    xg, info = g.probe_pcg(v2, b, rel_tol=1e-4)
+    xo, info_o = O.pcg_bsr(rp, col, v2, b.reshape(-1), rel_tol=1e-4, max_iter=5000)
+    assert not info_o["ind"] and not info["ind"] and not info["hit_max"]
