@@ -217,6 +217,12 @@ PPN_API ppn_status ppn_set_record_selection(ppn_scene* s, int on);
  * and min(cap, count) are written to buf (buf may be NULL when cap is 0).
  * INVALID_ARG when idx is out of range or recording was off during the step. */
 PPN_API ppn_status ppn_get_attempt_selection(const ppn_scene* s, int idx, int32_t* buf, int64_t cap, int64_t* n);
+/* With recording on (ppn_set_record_selection), the assembled gradient g of Newton
+ * iteration newton_iter of the last step, the vector the selection keys of Sec. 4
+ * (||S^e g||_inf) are taken from: n_verts*3 doubles, zero on eliminated Dirichlet
+ * vertices.  Every evaluated iterate is kept, also the last one (where the step
+ * stopped).  INVALID_ARG when no such record exists. */
+PPN_API ppn_status ppn_get_iteration_gradient(const ppn_scene* s, int newton_iter, double* g);
 PPN_API ppn_status ppn_get_state(const ppn_scene* s, double* x, double* v);
 PPN_API ppn_status ppn_set_state(ppn_scene* s, const double* x, const double* v);
 /* Exact checkpoint of the internal state: displacement u = x - rest and

@@ -61,6 +61,8 @@ struct ora_scene {
   std::vector<ora_iter_stats> iters;
   std::vector<ora_attempt> attempts;
   std::vector<std::vector<int32_t>> attempt_sel;  // PPN selection before each attempt
+  bool record = false;                            // keep each iteration's gradient
+  std::vector<std::vector<double>> iter_g;
 };
 
 namespace {
@@ -560,6 +562,7 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
   s->iters.clear();
   s->attempts.clear();
   s->attempt_sel.clear();
+  s->iter_g.clear();
   double delta = kInf;  // Algorithm 1, before the Newton loop
   double g0 = -1.0;
   int status = ORA_ERR_NEWTON_MAXITER;
@@ -569,6 +572,7 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
   for (int k = 0; k < p.newton_max_iter; ++k) {
     for (int64_t e = 0; e < nt; ++e) element(s, e, x.data(), nullptr, &ge[12 * e], &He[144 * e]);
     gradient_from(s, x.data(), xhat.data(), ge, g.data());
+    if (s->record) s->iter_g.push_back(g);
     double gn2 = 0.0, gninf = 0.0;
     for (int64_t i = 0; i < N; ++i) {
       gn2 += g[i] * g[i];
@@ -809,6 +813,17 @@ int ora_scene_attempts(const ora_scene* s, ora_attempt* buf, int cap) {
   const int n = (int)s->attempts.size();
   for (int i = 0; i < n && i < cap; ++i) buf[i] = s->attempts[i];
   return n;
+}
+
+void ora_scene_set_record(ora_scene* s, int on) {
+  s->record = on != 0;
+  s->iter_g.clear();
+}
+
+int ora_scene_iteration_gradient(const ora_scene* s, int k, double* g) {
+  if (k < 0 || k >= (int)s->iter_g.size()) return -1;
+  std::memcpy(g, s->iter_g[k].data(), sizeof(double) * s->iter_g[k].size());
+  return 0;
 }
 
 int64_t ora_scene_attempt_selection(const ora_scene* s, int idx, int32_t* buf, int64_t cap) {

@@ -128,6 +128,8 @@ def lib():
         "ora_scene_iter_stats": (I, [P, C.POINTER(IterStats), I]),
         "ora_scene_attempts": (I, [P, C.POINTER(Attempt), I]),
         "ora_scene_attempt_selection": (I64, [P, I, pi, I64]),
+        "ora_scene_set_record": (None, [P, I]),
+        "ora_scene_iteration_gradient": (I, [P, I, pd]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -413,6 +415,16 @@ class Scene:
             d = {k: getattr(buf[i], k) for k, _ in Attempt._fields_}
             out.append(d)
         return out
+
+    def set_record(self, on: bool):
+        lib().ora_scene_set_record(self._h, 1 if on else 0)
+
+    def iteration_gradient(self, k: int):
+        """Assembled gradient of Newton iteration k of the last step (recording on)."""
+        g = np.zeros((self.n_verts, 3))
+        if lib().ora_scene_iteration_gradient(self._h, int(k), _dp(g)) != 0:
+            raise IndexError(k)
+        return g
 
     def attempt_selection(self, idx: int):
         """Elements newly selected by the PPN rounds before attempt ``idx`` of the last

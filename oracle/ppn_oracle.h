@@ -212,6 +212,11 @@ int ora_scene_attempts(const ora_scene* s, ora_attempt* buf, int cap);
  * PPN selection (the first solve, PN, PDN) have none.  Returns the count (-1: no such
  * attempt); at most cap are written. */
 int64_t ora_scene_attempt_selection(const ora_scene* s, int idx, int32_t* buf, int64_t cap);
+/* with recording on, the assembled gradient of every Newton iteration of the next steps is
+ * kept (3 n_v doubles each); ora_scene_iteration_gradient copies that of iteration k of the
+ * last step and returns 0, or -1 when there is none */
+void ora_scene_set_record(ora_scene* s, int on);
+int ora_scene_iteration_gradient(const ora_scene* s, int k, double* g);
 
 #ifdef __cplusplus
 }

@@ -50,6 +50,7 @@ struct Ctl {
   int n_new;             // elements selected by the last selection
   int n_new_c;           // contact elements selected by the last selection
   int n_ties;            // selection ties of the last selection (|r_e - delta| <= tie_band delta)
+  int n_touched;         // BSR blocks touched by the elements of the last selection (incremental update)
   int pcg_iters;         // CG updates performed (x = sum of alpha d)
   int pcg_ind;           // negative curvature or a non-SPD diagonal block
   int pcg_precond_fail;
@@ -82,6 +83,7 @@ struct SceneDev {
   const int* blk_ptr;      // nnzb+1 block -> contributions (tet << 4 | a << 2 | b)
   const int* blk_src;
   const int* diag_idx;     // nv
+  const int* tet_blk;      // nt x 16: BSR block of each (a, b) corner pair of a tet
   // state
   double4* u;              // displacement x - X
   double4* u_n;
@@ -98,6 +100,8 @@ struct SceneDev {
   int* proj_stamp;         // Newton-iteration id at which the element was projected
   int* round_stamp;        // selection-round id at which it was projected
   int* sel_list;           // compacted newly selected elements
+  int* blk_mark;           // nnzb: selection round that last listed the block as touched
+  int* touched;            // nnzb: blocks touched by the last selection (n_touched of them)
   // PCG vectors (nv each) and block-Jacobi inverse (nv x 9)
   vec4_t<T>* dx;
   vec4_t<T>* r;

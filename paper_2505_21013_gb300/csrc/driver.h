@@ -83,6 +83,7 @@ struct Group {
   int n_ttiles = 0, n_vtiles = 0, n_btiles = 0, n_ptiles = 0, n_etiles = 0;
   int* d_ids = nullptr;
   TileRef* d_pcgtiles = nullptr;
+  TileRef* d_touchtiles = nullptr;  // (selected element, corner pair) tiles of the touched-block update
   unsigned pcg_launch_seq = 0;
   std::vector<int> pcg_ids;  // slots of the tile table currently on the device
   int pcg_ntiles = 0;
@@ -186,10 +187,11 @@ struct Group {
       d_projtiles = alloc<TileRef>(cap_proj);
       d_ids = alloc<int>(cap_n);
       d_pcgtiles = alloc<TileRef>(cap_pt);
+      d_touchtiles = alloc<TileRef>(cap_bt);
       d_flags = alloc<unsigned long long>(XCH_MAX_CTAS_HOST);
       d_bar = alloc<GridBar>(1);
       if (!d_desc || !d_ctl || !d_ttiles || !d_vtiles || !d_btiles || !d_ptiles || !d_etiles ||
-          !d_projtiles || !d_ids || !d_bar || !d_pcgtiles) {
+          !d_projtiles || !d_ids || !d_bar || !d_pcgtiles || !d_touchtiles) {
         set_error("cudaMalloc failed for a scene group");
         return PPN_ERR_OOM;
       }
@@ -544,6 +546,7 @@ struct Driver {
       G.S[i]->iters.clear();
       G.S[i]->attempts.clear();
       G.S[i]->attempt_sel.clear();
+      G.S[i]->iter_g.clear();
     }
     G.set_active(on);
     ppn_status rc = G.upload_desc();
@@ -643,6 +646,20 @@ struct Driver {
     timed(FAM_GRADIENT, 0, [&] { launch_gradient<T>(G.d_desc, G.d_vtiles, G.n_vtiles, 0, G.st); });
     if ((rc = check_launch())) return rc;
     if ((rc = G.sync_ctl())) return rc;
+    for (int i = 0; i < n; ++i)  // the iteration's assembled gradient, on request (diagnostics)
+      if (run[i] && G.S[i]->record_sel) {
+        SceneImpl<T>& s = *G.S[i];
+        std::vector<double4> g4(s.nv);
+        PPN_CU(cudaMemcpyAsync(g4.data(), s.d.g, sizeof(double4) * s.nv, cudaMemcpyDeviceToHost, G.st));
+        PPN_CU(cudaStreamSynchronize(G.st));
+        std::vector<double> g3(3 * (size_t)s.nv);
+        for (int v = 0; v < s.nv; ++v) {
+          g3[3 * v] = g4[v].x;
+          g3[3 * v + 1] = g4[v].y;
+          g3[3 * v + 2] = g4[v].z;
+        }
+        s.iter_g.push_back(std::move(g3));
+      }
     std::vector<char> solve_on(n, 0), pn_on(n, 0);
     bool any_solve = false, any_pn = false;
     for (int i = 0; i < n; ++i) {
@@ -727,13 +744,7 @@ struct Driver {
           G.h_desc[i].round_id = ++G.S[i]->round_counter;
         }
       if ((rc = select_and_project(pdn, false))) return rc;
-      G.set_active(pdn);
-      if ((rc = G.upload_desc())) return rc;
-      timed(FAM_UPDATE, 0, [&] {
-          launch_update<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st);
-          if (any_obstacles(solve_on)) launch_update_contact<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st);
-        });
-      if ((rc = check_launch())) return rc;
+      if ((rc = update_in_place(pdn))) return rc;
       if ((rc = solve(pdn, 1))) return rc;
       if ((rc = G.sync_ctl())) return rc;
       if ((rc = check_errors(pdn))) return rc;
@@ -744,8 +755,8 @@ struct Driver {
           if (H[i].ind) H[i].fallback = true;  // fully projected and still indefinite (rounding)
         }
     }
-    // ---- PPN retries (Algorithm 1 inner loop)
-    int attempt = 1;
+    // ---- PPN retries (Algorithm 1 inner loop); a round that selects nothing new skips the
+    // solve and tightens delta again, so attempts are numbered by solve
     while (any_retry) {
       for (int i = 0; i < n; ++i)
         if (retry[i]) {
@@ -763,20 +774,14 @@ struct Driver {
           any_resolve = true;
         }
       if (any_resolve) {
-        G.set_active(resolve);
-        if ((rc = G.upload_desc())) return rc;
-        timed(FAM_UPDATE, 0, [&] {
-          launch_update<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st);
-          if (any_obstacles(solve_on)) launch_update_contact<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st);
-        });
-        if ((rc = check_launch())) return rc;
+        if ((rc = update_in_place(resolve))) return rc;
         if ((rc = solve(resolve, 1))) return rc;
         std::vector<int> n_new(n);
         for (int i = 0; i < n; ++i) n_new[i] = G.h_ctl[i].n_new + G.h_ctl[i].n_new_c;
         if ((rc = G.sync_ctl())) return rc;
         if ((rc = check_errors(resolve))) return rc;
         for (int i = 0; i < n; ++i)
-          if (resolve[i]) record_attempt(i, attempt, n_new[i], H[i].delta);
+          if (resolve[i]) record_attempt(i, H[i].cur.pcg_attempts, n_new[i], H[i].delta);  // solves so far
       }
       any_retry = false;
       for (int i = 0; i < n; ++i) {
@@ -794,7 +799,6 @@ struct Driver {
           retry[i] = 0;
         }
       }
-      ++attempt;
     }
     for (int i = 0; i < n; ++i)
       if (solve_on[i] && H[i].mode == PPN_MODE_PPN) H[i].delta *= Pi(i).beta;  // relax
@@ -1045,7 +1049,7 @@ struct Driver {
     ppn_status rc = G.upload_desc();
     if (rc) return rc;
     for (int i = 0; i < n; ++i)
-      if (on[i]) PPN_CU(cudaMemsetAsync(&G.d_ctl[i].n_new, 0, 3 * sizeof(int), G.st));  // n_new, n_new_c, n_ties
+      if (on[i]) PPN_CU(cudaMemsetAsync(&G.d_ctl[i].n_new, 0, 4 * sizeof(int), G.st));  // n_new, n_new_c, n_ties, n_touched
     timed(FAM_SELECT, 0, [&] {
       launch_select<T>(G.d_desc, G.d_ttiles, G.n_ttiles, G.st);
       if (any_obstacles(on)) launch_select_contact<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st);  // clamps them too
@@ -1072,6 +1076,54 @@ struct Driver {
     if (jt.empty()) return PPN_OK;
     if ((rc = G.upload(G.d_projtiles, jt.data(), sizeof(TileRef) * jt.size()))) return rc;
     timed(FAM_PROJECT, 0, [&] { launch_project<T>(G.d_desc, G.d_projtiles, (int)jt.size(), 0, G.st); });
+    return check_launch();
+  }
+
+  // In-place update H += S^eT dH^e S^e of the elements the last selection projected
+  // (Sec. 4.1, "Incremental Hessian updates").  A scene whose selection touches at most
+  // as many blocks as it has (16 per element) updates only those blocks; otherwise every
+  // block is swept (PDN's all-element rounds).  Both forms give the same bits.
+  // PPN_UPDATE_SWEEP=1 always sweeps (tests).  Contact elements update their diagonal blocks.
+  ppn_status update_in_place(const std::vector<char>& on) {
+    const int n = (int)on.size();
+    const bool force_sweep = std::getenv("PPN_UPDATE_SWEEP") != nullptr;
+    std::vector<char> sweep(n, 0), touch(n, 0);
+    std::vector<TileRef> jt;
+    bool any_sweep = false, any_touch = false;
+    for (int i = 0; i < n; ++i) {
+      if (!on[i]) continue;
+      const long long nn = G.h_ctl[i].n_new;
+      if (nn == 0) continue;
+      if (!force_sweep && 16 * nn <= (long long)G.S[i]->nnzb) {
+        touch[i] = 1;
+        any_touch = true;
+        for (int t = 0; t < (int)((16 * nn + TILE - 1) / TILE); ++t) jt.push_back({i, t});
+      } else {
+        sweep[i] = 1;
+        any_sweep = true;
+      }
+    }
+    ppn_status rc = PPN_OK;
+    const bool contact = any_obstacles(on);
+    timed(FAM_UPDATE, 0, [&] {
+      if (any_sweep) {
+        G.set_active(sweep);
+        if ((rc = G.upload_desc())) return;
+        launch_update<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st);
+      }
+      if (any_touch) {
+        G.set_active(touch);
+        if ((rc = G.upload_desc())) return;
+        if ((rc = G.upload(G.d_touchtiles, jt.data(), sizeof(TileRef) * jt.size()))) return;
+        launch_update_touched<T>(G.d_desc, G.d_touchtiles, (int)jt.size(), G.st);
+      }
+      if (contact) {
+        G.set_active(on);
+        if ((rc = G.upload_desc())) return;
+        launch_update_contact<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st);
+      }
+    });
+    if (rc) return rc;
     return check_launch();
   }
 

@@ -344,6 +344,58 @@ __global__ void __launch_bounds__(TILE) k_update(const SceneDev<T>* scenes, cons
   for (int c = 0; c < 9; ++c) S.val[(size_t)c * S.nnzb + k] += acc[c];
 }
 
+// Touched-block form of the same update (Sec. 4.1, "Incremental Hessian updates":
+// only the blocks of the newly projected elements change).  k_touch lists, once
+// each, the blocks that the 16 corner pairs of the last selection's tets map to
+// (a per-block mark of the selection round deduplicates them; the mark's exchange
+// and the list's counter are the only atomics).  k_update_touched then sums each
+// listed block's contributions of that round exactly as k_update does, in the
+// block's contribution order, so both forms give the same bits.
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_touch(const SceneDev<T>* scenes, const TileRef* tiles) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int q = tr.tile * TILE + threadIdx.x;  // (selected element, corner pair)
+  bool fresh = false;
+  int k = 0;
+  if (q < 16 * S.ctl->n_new) {
+    const int e = S.sel_list[q >> 4];
+    k = S.tet_blk[(size_t)16 * e + (q & 15)];
+    const int i = S.blk_row[k], j = S.col[k];
+    if (!S.fixed[i] && !S.fixed[j]) fresh = atomicExch(&S.blk_mark[k], S.round_id) != S.round_id;
+  }
+  const unsigned mask = __ballot_sync(0xffffffffu, fresh);
+  if (mask == 0u) return;
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == __ffs(mask) - 1) base = atomicAdd(&S.ctl->n_touched, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+  if (fresh) S.touched[base + __popc(mask & ((1u << lane) - 1u))] = k;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_update_touched(const SceneDev<T>* scenes, const TileRef* tiles) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int q = tr.tile * TILE + threadIdx.x;
+  if (q >= S.ctl->n_touched) return;
+  const int k = S.touched[q];
+  const int rd = S.round_id;
+  T acc[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) acc[c] = (T)0;
+  for (int c = S.blk_ptr[k]; c < S.blk_ptr[k + 1]; ++c) {
+    const int src = S.blk_src[c];
+    const int e = src >> 4;
+    if (S.round_stamp[e] != rd) continue;
+    add_elem_block(S.dH + (size_t)e * HE_STRIDE, (src >> 2) & 3, src & 3, acc);
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) S.val[(size_t)c * S.nnzb + k] += acc[c];
+}
+
 // ------------------------------------------------------------ K4 selection
 // delta < 0 selects every element (PN: project all before assembly)
 template <typename T>
@@ -738,6 +790,13 @@ void launch_update(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t s
   if (n) k_update<T><<<n, TILE, 0, st>>>(s, t);
 }
 template <typename T>
+void launch_update_touched(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
+  if (n) {
+    k_touch<T><<<n, TILE, 0, st>>>(s, t);
+    k_update_touched<T><<<n, TILE, 0, st>>>(s, t);
+  }
+}
+template <typename T>
 void launch_select(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
   if (n) k_select<T><<<n, TILE, 0, st>>>(s, t);
 }
@@ -780,6 +839,7 @@ void launch_fallback(const SceneDev<T>* s, const TileRef* t, int n, int kind, cu
   template void launch_gradient<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
   template void launch_assemble<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t, int); \
   template void launch_update<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \
+  template void launch_update_touched<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \
   template void launch_select<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \
   template void launch_project<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
   template void launch_energy<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);  \

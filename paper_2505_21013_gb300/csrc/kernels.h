@@ -13,6 +13,9 @@ template <typename T> void launch_element(const SceneDev<T>*, const TileRef*, in
 template <typename T> void launch_gradient(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
 template <typename T> void launch_assemble(const SceneDev<T>*, const TileRef*, int, cudaStream_t, int use_probe = 0);
 template <typename T> void launch_update(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
+// touched-block form: n tiles of TILE (selected element, corner pair) entries per scene
+// (16 x the selection's count); the scene's ctl->n_touched must be zero before the launch
+template <typename T> void launch_update_touched(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
 template <typename T> void launch_select(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
 template <typename T> void launch_project(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
 template <typename T> void launch_energy(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);

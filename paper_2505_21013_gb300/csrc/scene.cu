@@ -310,8 +310,6 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
       }
   }
   nmap = 16 * nt;
-  blk_of.clear();
-  blk_of.shrink_to_fit();
   // vertex -> (tet, corner)
   std::vector<int> vt_ptr(nv + 1, 0), vt_src((size_t)4 * nt);
   for (int e = 0; e < nt; ++e) {
@@ -362,6 +360,9 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   int* d_blk_ptr = alloc<int>(nnzb + 1);
   int* d_blk_src = alloc<int>((size_t)16 * nt);
   int* d_diag = alloc<int>(nv);
+  int* d_tet_blk = alloc<int>((size_t)16 * nt);
+  s.blk_mark = alloc<int>(nnzb);
+  s.touched = alloc<int>(nnzb);
   s.u = alloc<double4>(nv);
   s.u_n = alloc<double4>(nv);
   s.vel = alloc<double4>(nv);
@@ -412,7 +413,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   d_etiles = alloc<TileRef>(et.size());
   d_projtiles = alloc<TileRef>(jt.size());
   if (!d_tets || !d_tetc || !d_mass || !d_fixed || !d_con || !s.tgt || !d_X || !d_vt_ptr || !d_vt_src || !d_row_ptr ||
-      !d_col || !d_blk_row || !d_blk_ptr || !d_blk_src || !d_diag || !s.u || !s.u_n || !s.vel ||
+      !d_col || !d_blk_row || !d_blk_ptr || !d_blk_src || !d_diag || !d_tet_blk || !s.blk_mark || !s.touched || !s.u || !s.u_n || !s.vel ||
       !s.uhat || !s.u_probe || !s.ge || !s.He || !s.dH || !s.g || !s.gmax || !s.val ||
       !s.proj_stamp || !s.round_stamp || !s.cproj_stamp || !d_obs || !s.cround_stamp || !s.dHc || !s.Hc || !s.sel_list || !s.dx || !s.r || !s.z || !s.q || !s.d0 ||
       !s.d1 || !s.Pinv || !s.vpart || !s.tpart || !s.ppart || !s.pword || (sizeof(T) == 4 && !s.zrec) || !s.ctl || !d_desc || !d_ids ||
@@ -445,6 +446,8 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   PPN_CU(up(d_blk_ptr, blk_ptr.data(), sizeof(int) * (nnzb + 1)));
   PPN_CU(up(d_blk_src, blk_src.data(), sizeof(int) * blk_src.size()));
   PPN_CU(up(d_diag, diag_idx.data(), sizeof(int) * nv));
+  PPN_CU(up(d_tet_blk, blk_of.data(), sizeof(int) * blk_of.size()));
+  PPN_CU(cudaMemset(s.blk_mark, 0xff, sizeof(int) * nnzb));
   if (nfixed) {
     PPN_CU(up(d_fixed_list, fixed_list.data(), sizeof(int) * nfixed));
     PPN_CU(up(d_targets, tg.data(), sizeof(double) * tg.size()));
@@ -482,6 +485,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   s.blk_ptr = d_blk_ptr;
   s.blk_src = d_blk_src;
   s.diag_idx = d_diag;
+  s.tet_blk = d_tet_blk;
   s.dt = dt;
   s.inv_dt2 = 1.0 / (dt * dt);
   for (int k = 0; k < 3; ++k) s.grav[k] = params.gravity[k];
@@ -1136,6 +1140,19 @@ ppn_status ppn_set_record_selection(ppn_scene* s, int on) {
   return dispatch(s, [&](auto& x) {
     x.record_sel = on != 0;
     x.attempt_sel.clear();
+    x.iter_g.clear();
+    return PPN_OK;
+  });
+}
+
+ppn_status ppn_get_iteration_gradient(const ppn_scene* s, int newton_iter, double* g) {
+  if (!g) return PPN_ERR_INVALID_ARG;
+  return dispatch_c(s, [&](auto& x) {
+    if (newton_iter < 0 || newton_iter >= (int)x.iter_g.size()) {
+      set_error("no recorded gradient for Newton iteration " + std::to_string(newton_iter));
+      return PPN_ERR_INVALID_ARG;
+    }
+    std::memcpy(g, x.iter_g[newton_iter].data(), sizeof(double) * x.iter_g[newton_iter].size());
     return PPN_OK;
   });
 }

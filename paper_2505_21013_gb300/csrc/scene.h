@@ -99,6 +99,7 @@ struct SceneImpl {
   std::vector<ppn_attempt> attempts;
   bool record_sel = false;                    // keep the selected elements of every attempt
   std::vector<std::vector<int>> attempt_sel;  // (ppn_set_record_selection)
+  std::vector<std::vector<double>> iter_g;    // assembled gradient of every Newton iteration (same switch)
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
 
   ~SceneImpl();

@@ -134,6 +134,7 @@ SIGNATURES = {
     "ppn_set_record_selection": (_st, [_P, C.c_int]),
     "ppn_get_attempt_selection": (_st, [_P, C.c_int, _pi, C.c_int64, _pl]),
     "ppn_probe_tets": (_st, [_P, _pi]),
+    "ppn_get_iteration_gradient": (_st, [_P, C.c_int, _pd]),
     "ppn_get_state": (_st, [_P, _pd, _pd]),
     "ppn_set_state": (_st, [_P, _pd, _pd]),
     "ppn_get_displacement": (_st, [_P, _pd, _pd]),
@@ -324,6 +325,12 @@ class Scene:
         _check(lib().ppn_get_attempt_selection(self._h, int(idx), out.ctypes.data_as(_pi), out.size, C.byref(n)),
                "ppn_get_attempt_selection")
         return out
+
+    def iteration_gradient(self, k: int):
+        """The assembled gradient of Newton iteration k of the last step (recording on)."""
+        g = np.zeros((self.n_verts, 3))
+        _check(lib().ppn_get_iteration_gradient(self._h, int(k), _d(g)), "ppn_get_iteration_gradient")
+        return g
 
     def get_state(self):
         x = np.zeros((self.n_verts, 3))

@@ -36,6 +36,7 @@ def run_recorded(spec, steps, tol, prec, pg=None, po=None):
     g = P.Scene.from_spec(spec, params=pg, precision=prec)
     g.set_record_selection(True)
     o = O.Scene.from_spec(spec, po)
+    o.set_record(True)
     rec = []
     for n in range(steps):
         tg = spec.targets_at(n)
@@ -45,40 +46,94 @@ def run_recorded(spec, steps, tol, prec, pg=None, po=None):
         rco, xo, sto = o.step(O.PPN, tol)
         ag, ao = g.attempts(), o.attempts()
         rec.append(dict(rc=rc, x=x, st=st, ag=ag, selg=[g.attempt_selection(i) for i in range(len(ag))],
-                        rco=rco, xo=xo, sto=sto, ao=ao, selo=[o.attempt_selection(i) for i in range(len(ao))]))
+                        gg=[g.iteration_gradient(k) for k in range(st["newton_iters"] + 1)],
+                        rco=rco, xo=xo, sto=sto, ao=ao, selo=[o.attempt_selection(i) for i in range(len(ao))],
+                        go=[o.iteration_gradient(k) for k in range(sto["newton_iters"] + 1)]))
     g.close()
     return rec
 
 
-@pytest.mark.parametrize("seed,omega,alpha,beta", [(1, 40.0, 0.5, 2.0), (3, 40.0, 0.5, 2.0), (4, 20.0, 0.5, 2.0),
-                                                   (1, 40.0, 0.25, 1.0), (3, 40.0, 0.9, 16.0)])
-def test_selected_sets_match_the_oracle_at_every_retry(seed, omega, alpha, beta):
+def keys(tets, grad):
+    """r_e = ||S^e g||_inf of every tet."""
+    return np.abs(grad[tets]).max(axis=(1, 2))
+
+
+CASES = [(1, 40.0, 0.5, 2.0), (3, 40.0, 0.5, 2.0), (4, 20.0, 0.5, 2.0), (1, 40.0, 0.25, 1.0), (3, 40.0, 0.9, 16.0)]
+
+
+@pytest.mark.parametrize("seed,omega,alpha,beta", CASES)
+def test_every_retry_selects_exactly_on_the_gpu_iterate(seed, omega, alpha, beta):
+    # Every PPN retry of every Newton iteration of four violent FP64 steps: the oracle's
+    # selection applied to the GPU's own gradient of that iteration, at the GPU's delta,
+    # with the GPU's earlier selections of the iteration as the projected set, gives the
+    # GPU's selected set bit for bit (the decisions are FP64 comparisons of the same
+    # values on both sides).  Ties at that delta are reported.
     spec = violent(seed, omega)
     pg, po = params_pair(alpha, beta)
+    o = O.Scene.from_spec(spec, po)
+    tets = o.tets()
     rec = run_recorded(spec, 4, 1e-6, P.PREC_FP64, pg, po)
     retries = 0
+    for n, r in enumerate(rec):
+        assert r["rc"] == 0
+        already, it_prev = np.zeros(spec.n_tets, np.uint8), -1
+        for a, sg in zip(r["ag"], r["selg"]):
+            if a["newton_iter"] != it_prev:
+                already[:] = 0
+                it_prev = a["newton_iter"]
+            if a["attempt"] == 0:
+                assert len(sg) == 0
+                continue
+            retries += 1
+            grad = r["gg"][a["newton_iter"]]
+            sel_o, n_o = o.select(grad, a["delta"], already)
+            assert np.array_equal(np.nonzero(sel_o)[0], sg), f"step {n} iteration {a['newton_iter']}"
+            assert a["n_new_projected"] == n_o == len(sg)
+            rk = keys(tets, grad)
+            ties = int(((np.abs(rk - a["delta"]) <= 1e-12 * a["delta"]) & (already == 0)).sum())
+            assert a["n_ties"] >= ties
+            already[sg] = 1
+    assert retries >= 5
+
+
+@pytest.mark.parametrize("seed,omega,alpha,beta", CASES)
+def test_selected_sets_follow_the_oracle_run(seed, omega, alpha, beta):
+    # The GPU run against the oracle's own run of the same steps.  Attempt by attempt
+    # (the same Newton iteration, solve number and verdict), delta agrees to rounding and
+    # the selected sets are equal.  The two FP64 trajectories differ by rounding (about
+    # 1e-10 of the displacement after a few iterations), so an element whose key lies
+    # within 1e-6 delta of delta on the oracle's iterate may flip; after such a flip the
+    # runs may take different retries, and the step is compared by its result only.
+    spec = violent(seed, omega)
+    pg, po = params_pair(alpha, beta)
+    tets = O.Scene.from_spec(spec, po).tets()
+    rec = run_recorded(spec, 4, 1e-6, P.PREC_FP64, pg, po)
+    exact = 0
     for n, r in enumerate(rec):
         assert r["rc"] == r["rco"] == 0
         disp = np.abs(r["xo"] - spec.rest).max()
         assert np.abs(r["x"] - r["xo"]).max() <= 1e-5 * disp
-        # the same solves in the same order: Newton iterations, retries and verdicts
-        assert [(a["newton_iter"], a["attempt"], a["ind"]) for a in r["ag"]] == \
-               [(a["newton_iter"], a["attempt"], a["ind"]) for a in r["ao"]], f"step {n}"
+        assert abs(r["st"]["newton_iters"] - r["sto"]["newton_iters"]) <= 1
+        flipped = False
         for a, b, sg, so in zip(r["ag"], r["ao"], r["selg"], r["selo"]):
-            assert a["n_ties"] == b["n_ties"]
+            assert (a["newton_iter"], a["attempt"], a["ind"]) == (b["newton_iter"], b["attempt"], b["ind"]), \
+                f"step {n}: the runs took different solves before any selection differed"
             if a["attempt"] == 0:
-                assert len(sg) == len(so) == 0
                 continue
-            retries += 1
             assert a["delta"] == pytest.approx(b["delta"], rel=1e-8)
-            assert a["n_new_projected"] == len(sg)
-            if a["n_ties"] == 0:
-                assert np.array_equal(sg, so), f"step {n} iteration {a['newton_iter']} attempt {a['attempt']}"
-            else:  # only tie elements may differ
-                assert len(np.setxor1d(sg, so)) <= a["n_ties"]
-        assert r["st"]["n_ties"] == r["sto"]["n_ties"]
-        assert r["st"]["newton_iters"] == r["sto"]["newton_iters"]
-    assert retries > 0
+            if np.array_equal(sg, so):
+                exact += 1
+                assert a["n_ties"] == b["n_ties"]
+                continue
+            near = np.abs(keys(tets, r["go"][b["newton_iter"]]) - b["delta"]) <= 1e-6 * b["delta"]
+            diff = np.setxor1d(sg, so)
+            assert near[diff].all(), f"step {n} iteration {a['newton_iter']}: {diff} not near delta"
+            flipped = True
+            break
+        if not flipped:
+            assert len(r["ag"]) == len(r["ao"])
+            assert r["st"]["n_ties"] == r["sto"]["n_ties"]
+    assert exact >= 5
 
 
 def test_mixed_first_retry_selects_the_oracle_set():

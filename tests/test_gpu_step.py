@@ -224,3 +224,29 @@ def test_scene_at_rest_stops_at_the_rounding_floor(prec):
     assert sto["newton_iters"] == 0 and st["newton_iters"] <= (0 if prec == P.PREC_FP64 else 1)
     disp = np.abs(xo - spec.rest).max()
     assert np.abs(x - xo).max() <= (1e-5 if prec == P.PREC_FP64 else 2e-3) * disp
+
+
+@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
+def test_touched_block_update_equals_the_full_sweep(prec, monkeypatch):
+    # Sec. 4.1's in-place update H += S^eT dH^e S^e of the newly projected elements: the
+    # touched-block form (only the blocks of the selection's tets, listed once each) and
+    # the sweep over every block sum the same contributions in the same order, so PPN
+    # steps that project give the same bits either way
+    spec = twisting_beam_scene(6, 6, 16, h=0.02, E=1e5, nu=0.45, omega=30.0, dt=0.1, seed=9)
+    out = []
+    for sweep in (False, True):
+        if sweep:
+            monkeypatch.setenv("PPN_UPDATE_SWEEP", "1")
+        sc = P.Scene.from_spec(spec, precision=prec)
+        xs = []
+        for n in range(3):
+            sc.set_targets(spec.targets_at(n))
+            rc, x, st = sc.step(P.MODE_PPN, 1e-5)
+            assert rc == 0
+            xs.append((x, st["total_projections"], st["total_cg_iters"]))
+        sc.close()
+        out.append(xs)
+    assert sum(p for _, p, _ in out[0]) > 0
+    for (xa, pa, ca), (xb, pb, cb) in zip(*out):
+        assert pa == pb and ca == cb
+        assert np.array_equal(xa, xb)
