@@ -149,6 +149,16 @@ struct TileRef {
   int tile;
 };
 
+// Spacing, in 64-bit words, of the stamped tile partials of the single-reduction PCG.
+// Every CTA polls every tile's word once per CG iteration; packed 16 to a 128-byte L2
+// line, the words of a few hundred tiles sit in a few dozen lines that all 152 SMs poll
+// at once, and the requests queue at those lines' L2 slices.  One word per line spreads
+// them over the slices (a 250-tile reduction fell from 4.2 to 1.4 us per iteration in
+// a same-box A/B); past a few hundred tiles the extra lines cost more than the queueing,
+// and two words per 16 bytes measured best (2000 tiles).  The partials' array holds
+// 8 x n_ptiles x pword_stride(n_ptiles) words.
+__host__ __device__ inline int pword_stride(int n_ptiles) { return n_ptiles <= 512 ? 16 : 2; }
+
 // ---- small helpers ----
 __device__ __forceinline__ double4 ld_d4(const double4* p) {
   const double2* q = reinterpret_cast<const double2*>(p);

@@ -389,7 +389,7 @@ struct Driver {
       L.n_pword = (int)sl.size();
       for (size_t k = 0; k < sl.size(); ++k) {
         L.pword[k] = G.h_desc[sl[k]].pword;
-        L.pword_bytes[k] = sizeof(unsigned long long) * 8 * G.S[sl[k]]->n_ptiles;
+        L.pword_bytes[k] = sizeof(unsigned long long) * 8 * G.S[sl[k]]->n_ptiles * pword_stride(G.S[sl[k]]->n_ptiles);
       }
       double bytes = 0.0;
       cudaError_t err = cudaSuccess;

@@ -367,13 +367,14 @@ __global__ void __launch_bounds__(NTP, 1)
   __syncthreads();
 
   // ---------------- exchange helpers
-  // tile word of quantity k of a tile in parity buffer par: pword[(par * NQ + k) * n_ptiles + tile]
+  // tile word of quantity k of a tile in parity buffer par:
+  // pword[((par * NQ + k) * n_ptiles + tile) * pword_stride(n_ptiles)]
   auto post_tile = [&](int lt, int k, float v, unsigned s, int par) {
     const TileRef tr = L.ltt[lt];
     const SceneLite<float>& S = sl[tr.scene];
     unsigned long long w[1];
     W::split(v, s, w);
-    st_relaxed_u64(S.pword + (size_t)(par * NQ + k) * S.n_ptiles + tr.tile, w[0]);
+    st_relaxed_u64(S.pword + ((size_t)(par * NQ + k) * S.n_ptiles + tr.tile) * pword_stride(S.n_ptiles), w[0]);
   };
   // SR_HALO: w of the halo rows hb, hb + dh, ... (stamp s, buffer par) into their u slots,
   // which the SpMV has finished reading; two rows at a time, both rows' loads in flight
@@ -451,14 +452,15 @@ __global__ void __launch_bounds__(NTP, 1)
       if (st[si].done) continue;  // warp-uniform
       const SceneLite<float>& S = sl[si];
       const int n = S.n_ptiles;
-      const unsigned long long* base = S.pword + (size_t)(par * NQ + q) * n;
+      const size_t ws = (size_t)pword_stride(n);
+      const unsigned long long* base = S.pword + (size_t)(par * NQ + q) * n * ws;
       float acc = 0.0f;
       for (int tw = lane32; tw < n; tw += 32 * 8) {
         unsigned long long w[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int t = tw + 32 * u;
-          w[u] = t < n ? ld_relaxed_u64(base + t) : W::filler(s);
+          w[u] = t < n ? ld_relaxed_u64(base + t * ws) : W::filler(s);
         }
         for (unsigned spins = 0;; ++spins) {
           bool ready = true;
@@ -480,7 +482,7 @@ __global__ void __launch_bounds__(NTP, 1)
           }
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            if (!W::has(w[u], s)) w[u] = ld_relaxed_u64(base + tw + 32 * u);
+            if (!W::has(w[u], s)) w[u] = ld_relaxed_u64(base + (tw + 32 * u) * ws);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u)

@@ -393,7 +393,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   s.vpart = alloc<double>((size_t)4 * n_vtiles);
   s.tpart = alloc<double>((size_t)4 * (n_vtiles + n_ttiles));
   s.ppart = alloc<double>((size_t)4 * n_ptiles);
-  s.pword = alloc<unsigned long long>((size_t)8 * n_ptiles);
+  s.pword = alloc<unsigned long long>((size_t)8 * n_ptiles * pword_stride(n_ptiles));
   s.zrec = sizeof(T) == 4 ? alloc<T>((size_t)16 * nv) : nullptr;
   s.ctl = alloc<Ctl>(1);
   d_desc = alloc<SceneDev<T>>(1);
