@@ -474,7 +474,8 @@ struct Driver {
         fits[mode] = bytes[mode] <= (size_t)212 * 1024 && pcg_sr_max_grid(dev, bytes[mode], mode) >= grid;
         if (fits[mode] && (mode == SR_RES || f_str || f_gl)) break;
       }
-      if (first == SR_RES && fits[SR_RES] && sl.size() <= (size_t)HALO_MAX_SCENES && !std::getenv("PPN_PCG_NO_HALO")) {
+      if (first == SR_RES && fits[SR_RES] && sl.size() <= (size_t)HALO_MAX_SCENES && max_items <= SR_HALO_MAX_ROWS &&
+          !std::getenv("PPN_PCG_NO_HALO")) {
         std::vector<int> tab;
         const int nh = build_halo(sl, grid, tab);
         const size_t hb = nh < 0 ? 0 : pcg_sr_smem_bytes(max_items, max_blocks, nh, SR_HALO);

@@ -90,6 +90,9 @@ int pcg_smem_max_grid(int group, int device, size_t smem, int fsize);
 // removes the neighbour exchange (SR_HALO).  Shared memory for ni rows / nb
 // blocks / nh halo rows, co-resident grid, launch.
 constexpr int SR_RES = 0, SR_STREAM = 1, SR_GLOBAL = 2, SR_HALO = 3;
+// SR_HALO keeps each row's CG state in the registers of one thread: a CTA holds at
+// most one SpMV pass of rows (512 threads, two lanes per row)
+constexpr int SR_HALO_MAX_ROWS = 256;
 size_t pcg_sr_smem_bytes(int ni, int nb, int nh, int mode);
 int pcg_sr_max_grid(int device, size_t smem, int mode);
 cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cudaStream_t st);

@@ -70,8 +70,8 @@ struct SrLayout {
   int* lrp;      // SR_RES, SR_HALO: [ni + 1] local row pointers
   int* lcol;     // SR_RES: [nb] columns; SR_HALO: [nb] local columns (own item, or ni + halo index)
   float* lval;   // SR_RES, SR_HALO: [nb * 9]
-  float* lP;     // SR_RES, SR_STREAM, SR_HALO: [ni * 6] inverse (00 01 02 11 12 22 of the symmetric block)
-  float *lx, *lr, *lu, *lw, *lp, *ls;  // SR_RES, SR_STREAM: [ni * 3] each; SR_HALO: all but lu
+  float* lP;     // SR_RES, SR_STREAM: [ni * 6] inverse (00 01 02 11 12 22 of the symmetric block)
+  float *lx, *lr, *lu, *lw, *lp, *ls;  // SR_RES, SR_STREAM: [ni * 3] each (SR_HALO: in registers)
   float4* lu4;   // SR_HALO: [ni + nh] u of the own rows, then of the halo rows (w while it arrives)
   float *hr, *hs, *hP;  // SR_HALO: [nh * 3], [nh * 3], [nh * 6] r, s and inverse of the halo rows
   int* href;     // SR_HALO: [nh] halo rows (slot << HALO_ROW_BITS | row)
@@ -96,11 +96,10 @@ __host__ __device__ inline size_t carve_sr(char* base, int ni, int nb, int nh, i
     l.lcol = (int*)take(sizeof(int) * nb);
     l.lval = (float*)take(sizeof(float) * 9 * nb);
   }
-  if (mode != SR_GLOBAL) {
+  if (mode == SR_RES || mode == SR_STREAM) {
     l.lP = (float*)take(sizeof(float) * 6 * ni);
     float** v[6] = {&l.lx, &l.lr, &l.lu, &l.lw, &l.lp, &l.ls};
-    for (float** q : v)
-      if (mode != SR_HALO || q != &l.lu) *q = (float*)take(sizeof(float) * 3 * ni);
+    for (float** q : v) *q = (float*)take(sizeof(float) * 3 * ni);
   }
   if (mode == SR_HALO) {
     l.lu4 = (float4*)take(sizeof(float4) * (ni + nh));
@@ -295,6 +294,21 @@ __global__ void __launch_bounds__(NTP, 1)
     return i < sl[slot].nv ? i : -1;
   };
   __syncthreads();
+  // SR_HALO: the CTA's rows fit one SpMV pass, and the lane that forms w of a row in the
+  // SpMV (the first of its GP lanes) owns the row: its x, r, p, s, u, w and block-Jacobi
+  // inverse stay in that thread's registers for the whole solve (the same values, by the
+  // same operations, as the other layouts keep in shared or global memory)
+  const int o_item = tid / GP;
+  const bool owner = HALO && tid % GP == 0 && o_item < n_items;
+  int o_slot = 0, o_row = -1;
+  if (owner) o_row = row_of(o_item, o_slot);
+  float ox[3] = {0.f, 0.f, 0.f}, orr[3] = {0.f, 0.f, 0.f}, op[3] = {0.f, 0.f, 0.f}, os[3] = {0.f, 0.f, 0.f};
+  float ou[3] = {0.f, 0.f, 0.f}, ow[3] = {0.f, 0.f, 0.f}, oq[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  static_assert(SR_HALO_MAX_ROWS == RPP, "the halo layout's rows fit one SpMV pass");
+  if (HALO && n_items > RPP) {  // the planner never builds such a table; refuse it without touching memory
+    if (tid == 0) atomicExch(&bar->timeout, 1);
+    return;
+  }
   // local row pointers (exclusive scan of the row lengths), resident blocks only
   if constexpr (RES) {
     int carry = 0;
@@ -367,15 +381,8 @@ __global__ void __launch_bounds__(NTP, 1)
   __syncthreads();
 
   // ---------------- exchange helpers
-  // tile word of quantity k of a tile in parity buffer par:
+  // tile words: quantity k of a tile in parity buffer par is
   // pword[((par * NQ + k) * n_ptiles + tile) * pword_stride(n_ptiles)]
-  auto post_tile = [&](int lt, int k, float v, unsigned s, int par) {
-    const TileRef tr = L.ltt[lt];
-    const SceneLite<float>& S = sl[tr.scene];
-    unsigned long long w[1];
-    W::split(v, s, w);
-    st_relaxed_u64(S.pword + ((size_t)(par * NQ + k) * S.n_ptiles + tr.tile) * pword_stride(S.n_ptiles), w[0]);
-  };
   // SR_HALO: w of the halo rows hb, hb + dh, ... (stamp s, buffer par) into their u slots,
   // which the SpMV has finished reading; two rows at a time, both rows' loads in flight
   // before the first is waited for
@@ -398,6 +405,7 @@ __global__ void __launch_bounds__(NTP, 1)
           }
           break;
         }
+        if (spins > 0) __nanosleep(32);  // a row not ready at the second look: back off a little
         ld_relaxed_v2_u64(wr, w[0], w[1]);
         w[2] = ld_relaxed_u64(wr + 2);
       }
@@ -578,6 +586,8 @@ __global__ void __launch_bounds__(NTP, 1)
       if (lane == 0 && item < n_items) {
         if constexpr (GV) {
           if (i >= 0) st_f4(reinterpret_cast<float*>(sl[slot].q + i), ax, ay, az);
+        } else if constexpr (HALO) {
+          ow[0] = ax, ow[1] = ay, ow[2] = az;
         } else {
           L.lw[3 * item] = ax;
           L.lw[3 * item + 1] = ay;
@@ -599,10 +609,11 @@ __global__ void __launch_bounds__(NTP, 1)
                 reinterpret_cast<unsigned long long*>(sl[slot].zrec) + ((size_t)par * sl[slot].nv + i) * 4;
             st_relaxed_v2_u64(wr, w[0], w[1]);
             st_relaxed_u64(wr + 2, w[2]);
-            const float4 uv = L.lu4[item];
-            u[0] = uv.x, u[1] = uv.y, u[2] = uv.z;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) r[c] = L.lr[3 * item + c];
+            for (int c = 0; c < 3; ++c) {
+              u[c] = ou[c];
+              r[c] = orr[c];
+            }
           } else {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -633,13 +644,19 @@ __global__ void __launch_bounds__(NTP, 1)
   // 16-row group sums (8 groups per tile, a fixed tree), posted
   auto post_partials = [&](unsigned stamp, bool with_fail, int par) {
     for (int lt = tid; lt < ntl; lt += NTP) {
-      if (st[L.ltt[lt].scene].done) continue;
+      const TileRef tr = L.ltt[lt];
+      const SceneLite<float>& S = sl[tr.scene];
+      if (st[tr.scene].done) continue;
       const float* w = L.lws + NQ * 8 * lt;
+      const size_t ws = (size_t)pword_stride(S.n_ptiles);
+      unsigned long long* base = S.pword + ((size_t)par * NQ * S.n_ptiles + tr.tile) * ws;
       const int nq = with_fail ? NQ : 3;
       for (int q = 0; q < nq; ++q) {
         const float a = (w[q] + w[NQ + q]) + (w[2 * NQ + q] + w[3 * NQ + q]);
         const float b = (w[4 * NQ + q] + w[5 * NQ + q]) + (w[6 * NQ + q] + w[7 * NQ + q]);
-        post_tile(lt, q, a + b, stamp, par);
+        unsigned long long wd[1];
+        W::split(a + b, stamp, wd);
+        st_relaxed_u64(base + (size_t)q * S.n_ptiles * ws, wd[0]);
       }
     }
   };
@@ -672,7 +689,33 @@ __global__ void __launch_bounds__(NTP, 1)
       r[2] = rv.z;
     }
   };
-  for (int base = 0; base < n_items; base += NTP) {
+  if constexpr (HALO) {
+    // each owner sets up its row; the failed-block count of a 16-row group (one warp's
+    // owners) goes to the group's slot
+    float fail = 0.0f;
+    if (owner && o_row >= 0) {
+      const SceneLite<float>& S = sl[o_slot];
+      const int i = o_row;
+      float D[9], Pm[9];
+      const int bd = L.lrp[o_item] + (S.diag_idx[i] - S.row_ptr[i]);
+#pragma unroll
+      for (int c = 0; c < 9; ++c) D[c] = L.lval[9 * bd + c];
+      const bool ok = spd_inv3(D, Pm);
+      sym6(Pm, oq);
+      float* P = S.Pinv + (size_t)9 * i;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) P[c] = Pm[c];
+      rhs(S, i, orr);
+      prec6(oq, orr, ou);
+      L.lu4[o_item] = make_float4(ou[0], ou[1], ou[2], 0.0f);
+      fail = ok ? 0.0f : 1.0f;
+    } else if (owner) {
+      L.lu4[o_item] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    fail = warp_sum(fail);
+    if (lane32 == 0) L.lws[NQ * warp + 3] = fail;
+  }
+  for (int base = 0; !HALO && base < n_items; base += NTP) {
     const int item = base + tid;
     float fail = 0.0f;
     int slot = 0;
@@ -768,6 +811,9 @@ __global__ void __launch_bounds__(NTP, 1)
     }
     spmv(s, it & 1);  // w = A u
     post_partials(s, it == 0, it & 1);
+    // the posts leave before any warp starts polling: polling warps fill the load/store
+    // queue with L2 reads, and the posting lanes' shared-memory reads would wait behind them
+    __syncthreads();
     if (!reduce(it == 0 ? NQ : 3, s, it & 1)) return fail_out(it);
     // one thread per scene (n_scenes <= MS < NTP); the barrier also finds whether all are done
     int done = 1;
@@ -779,7 +825,19 @@ __global__ void __launch_bounds__(NTP, 1)
     }
     if (__syncthreads_and(done)) break;
     // ---- p = u + beta p, s = w + beta s; x += alpha p, r -= alpha s, u = M r (published)
-    for (int item = tid; item < n_items; item += NTP) {
+    if constexpr (HALO) {
+      if (o_row >= 0 && !st[o_slot].done) {
+        const float a = st[o_slot].alpha, b = st[o_slot].beta;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          upd_px(a, b, ou[c], op[c], ox[c]);
+          upd_sr(a, b, ow[c], os[c], orr[c]);
+        }
+        prec6(oq, orr, ou);
+        L.lu4[o_item] = make_float4(ou[0], ou[1], ou[2], 0.0f);
+      }
+    }
+    for (int item = tid; !HALO && item < n_items; item += NTP) {
       int slot;
       const int i = row_of(item, slot);
       if (i < 0 || st[slot].done) continue;
@@ -840,20 +898,29 @@ __global__ void __launch_bounds__(NTP, 1)
     }
     // SR_HALO: the halo rows repeat their owners' s, r and u updates with the owners' w
     if constexpr (HALO) {
+      // every load of a row issued before its arithmetic (the arrays do not alias)
       for (int h = tid; h < nh; h += NTP) {
         const int slot = L.href[h] >> HALO_ROW_BITS;
         if (st[slot].done) continue;
         const float a = st[slot].alpha, b = st[slot].beta;
         const float4 wv = L.lu4[n_items + h];
-        float r[3], u[3];
-        float* hs = L.hs + 3 * h;
-        float* hr = L.hr + 3 * h;
-        r[0] = hr[0], r[1] = hr[1], r[2] = hr[2];
-        upd_sr(a, b, wv.x, hs[0], r[0]);
-        upd_sr(a, b, wv.y, hs[1], r[1]);
-        upd_sr(a, b, wv.z, hs[2], r[2]);
-        hr[0] = r[0], hr[1] = r[1], hr[2] = r[2];
-        prec6(L.hP + 6 * h, r, u);
+        float r[3], sv[3], q[6], u[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          r[c] = L.hr[3 * h + c];
+          sv[c] = L.hs[3 * h + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) q[c] = L.hP[6 * h + c];
+        upd_sr(a, b, wv.x, sv[0], r[0]);
+        upd_sr(a, b, wv.y, sv[1], r[1]);
+        upd_sr(a, b, wv.z, sv[2], r[2]);
+        prec6(q, r, u);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          L.hr[3 * h + c] = r[c];
+          L.hs[3 * h + c] = sv[c];
+        }
         L.lu4[n_items + h] = make_float4(u[0], u[1], u[2], 0.0f);
       }
     }
@@ -863,7 +930,9 @@ __global__ void __launch_bounds__(NTP, 1)
   }
 
   // x of this CTA's rows to global memory (SR_GLOBAL: already there); CTA 0 publishes the scalars
-  if constexpr (!GV) {
+  if constexpr (HALO) {
+    if (o_row >= 0) st_v(sl[o_slot].dx + o_row, mk<float4, float>(ox[0], ox[1], ox[2]));
+  } else if constexpr (!GV) {
     for (int item = tid; item < n_items; item += NTP) {
       int slot;
       const int i = row_of(item, slot);
@@ -925,7 +994,8 @@ cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cud
   const bool halo = L.sr_mode == SR_HALO;
   if (L.n_scenes <= 0 || L.n_scenes > PCG_MAX_SCENES || L.n_tiles <= 0 || L.grid > XCH_MAX_CTAS || !L.flags ||
       L.sr_mode < SR_RES || L.sr_mode > SR_HALO || (L.sr_mode == SR_RES || halo) != (L.smem_blocks > 0) ||
-      (halo && (L.n_scenes > HALO_MAX_SCENES || !L.halo_off || !L.halo_col || !L.halo_ref || L.halo_cap < 0)))
+      (halo && (L.n_scenes > HALO_MAX_SCENES || !L.halo_off || !L.halo_col || !L.halo_ref || L.halo_cap < 0 ||
+                (L.n_tiles + L.grid - 1) / L.grid * PCG_TILE > SR_HALO_MAX_ROWS)))
     return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(L.bar, 0, sizeof(GridBar), st);
   if (e != cudaSuccess) return e;
