@@ -410,14 +410,22 @@ PPN_API ppn_status ppn_server_get_stats(ppn_server* srv, ppn_server_stats* out);
  *   b        n_rows 16-byte records {b_x, b_y, b_z, ignored} (16-byte aligned)
  *   x        n_rows 16-byte records, written with the solution (16-byte aligned)
  * rel_tol: stop at ||r|| <= rel_tol ||b||; max_iter <= 0: max(1000, 3 n_rows).
- * info (host, may be NULL): [iterations, ind, precond_fail, hit_max].
- * stream: a cudaStream_t or NULL; the call waits for it before returning.
+ * info (host, may be NULL): [iterations, ind, precond_fail, hit_max].  A solve that
+ * meets negative curvature (ind) or a diagonal block without a Cholesky factor
+ * (precond_fail, then also ind) is a valid outcome and returns PPN_OK: x holds the
+ * last iterate before the offending direction (zero when that is the first one, or
+ * when the preconditioner failed).  Pass info to tell such a solve from a
+ * converged one; with info NULL nothing distinguishes them.
+ * stream: a cudaStream_t on the current device, or NULL; the call waits for it
+ * before returning (a stream of another device: PPN_ERR_INVALID_ARG).
  *
  * Errors: PPN_ERR_INVALID_ARG for null pointers, n_rows > PPN_PCG_STATIC_MAX_ROWS,
- * or a malformed pattern (checked on the device before the solve);
+ * or a malformed pattern (checked on the device before the solve: row pointers,
+ * column range, exactly one diagonal block per row);
  * PPN_ERR_TIMEOUT when a grid-wide wait runs out; PPN_ERR_NONFINITE; PPN_ERR_CUDA.
- * The first call on a device looks up the arena's address and the solver's
- * occupancy; make it once at start-up.  The arena is shared per device: calls
+ * The first call on a device (and the first after cudaDeviceReset, in the new
+ * context) looks up the arena's address and the solver's occupancy; make it once at
+ * start-up, before any stream capture.  The arena is shared per device: calls
  * on the same device must not overlap, and the library serialises its host
  * threads with a lock.  The barrier and status words that must start at zero
  * are cleared by every call. */

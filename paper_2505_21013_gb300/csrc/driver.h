@@ -1088,43 +1088,60 @@ struct Driver {
   ppn_status update_in_place(const std::vector<char>& on) {
     const int n = (int)on.size();
     const bool force_sweep = std::getenv("PPN_UPDATE_SWEEP") != nullptr;
-    std::vector<char> sweep(n, 0), touch(n, 0);
-    std::vector<TileRef> jt;
-    bool any_sweep = false, any_touch = false;
+    std::vector<char> sweep(n, 0);
+    std::vector<int> touch;  // scenes updated block by block, with their tile counts
+    std::vector<int> touch_tiles;
+    bool any_sweep = false;
     for (int i = 0; i < n; ++i) {
       if (!on[i]) continue;
       const long long nn = G.h_ctl[i].n_new;
       if (nn == 0) continue;
       if (!force_sweep && 16 * nn <= (long long)G.S[i]->nnzb) {
-        touch[i] = 1;
-        any_touch = true;
-        for (int t = 0; t < (int)((16 * nn + TILE - 1) / TILE); ++t) jt.push_back({i, t});
+        touch.push_back(i);
+        touch_tiles.push_back((int)((16 * nn + TILE - 1) / TILE));
       } else {
         sweep[i] = 1;
         any_sweep = true;
       }
     }
+    // the descriptors on the device mark the scenes of the last selection active; a
+    // sweep runs over every block tile of the group, so it needs its own active set
     ppn_status rc = PPN_OK;
-    const bool contact = any_obstacles(on);
-    timed(FAM_UPDATE, 0, [&] {
-      if (any_sweep) {
-        G.set_active(sweep);
-        if ((rc = G.upload_desc())) return;
-        launch_update<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st);
+    if (any_sweep) {
+      G.set_active(sweep);
+      if ((rc = G.upload_desc())) return rc;
+      timed(FAM_UPDATE, 0, [&] { launch_update<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st); });
+      if (!touch.empty()) {
+        std::vector<char> t(n, 0);
+        for (int i : touch) t[i] = 1;
+        G.set_active(t);
+        if ((rc = G.upload_desc())) return rc;
       }
-      if (any_touch) {
-        G.set_active(touch);
-        if ((rc = G.upload_desc())) return;
-        if ((rc = G.upload(G.d_touchtiles, jt.data(), sizeof(TileRef) * jt.size()))) return;
-        launch_update_touched<T>(G.d_desc, G.d_touchtiles, (int)jt.size(), G.st);
+    }
+    if (!touch.empty()) {
+      // a scene's first block tiles in the group's table are (scene, 0), (scene, 1), ...: a
+      // touched-block launch takes that range directly, so nothing is uploaded for up to
+      // two scenes; more scenes share one launch over an uploaded table
+      if (touch.size() <= 2) {
+        for (size_t k = 0; k < touch.size(); ++k) {
+          int off = 0;
+          for (int j = 0; j < touch[k]; ++j) off += G.S[j]->n_btiles;
+          timed(FAM_UPDATE, 0,
+                [&] { launch_update_touched<T>(G.d_desc, G.d_btiles + off, touch_tiles[k], G.st); });
+        }
+      } else {
+        std::vector<TileRef> jt;
+        for (size_t k = 0; k < touch.size(); ++k)
+          for (int t = 0; t < touch_tiles[k]; ++t) jt.push_back({touch[k], t});
+        if ((rc = G.upload(G.d_touchtiles, jt.data(), sizeof(TileRef) * jt.size()))) return rc;
+        timed(FAM_UPDATE, 0, [&] { launch_update_touched<T>(G.d_desc, G.d_touchtiles, (int)jt.size(), G.st); });
       }
-      if (contact) {
-        G.set_active(on);
-        if ((rc = G.upload_desc())) return;
-        launch_update_contact<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st);
-      }
-    });
-    if (rc) return rc;
+    }
+    if (any_obstacles(on)) {
+      G.set_active(on);
+      if ((rc = G.upload_desc())) return rc;
+      timed(FAM_UPDATE, 0, [&] { launch_update_contact<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st); });
+    }
     return check_launch();
   }
 

@@ -13,8 +13,10 @@
 // Scratch.  `g_pcg_static` holds the solver descriptor, the status words, the
 // grid barrier, the tile table, the diagonal-block index and the PCG vectors
 // for at most PPN_PCG_STATIC_MAX_ROWS block rows (the layout is carved per
-// call from the row count).  Its device address is looked up once per device,
-// at the first call, and cached.  Larger systems are rejected with
+// call from the row count).  Its device address is looked up once per device
+// context, at the first call in it, and cached with the context's id: a call
+// after cudaDeviceReset (a new primary context, in which the array may sit
+// elsewhere) looks it up again.  Larger systems are rejected with
 // PPN_ERR_INVALID_ARG.
 //
 // Start values.  The barrier counter and the status word must be zero when the
@@ -31,6 +33,8 @@
 // The solver is the global-memory cooperative kernel of pcg.cu (group of four
 // lanes per row), so the arithmetic is the one a scene's solve performs with
 // that kernel.  Nothing here changes the scene path.
+#include <cuda.h>
+
 #include <algorithm>
 #include <mutex>
 #include <string>
@@ -98,9 +102,38 @@ Arena carve(unsigned char* base, int n, int t) {
 struct DeviceSetup {
   unsigned char* base = nullptr;  // device address of g_pcg_static
   int grid = 0;                   // co-resident CTAs of the solver
+  unsigned long long ctx = 0;     // id of the context the address belongs to (0: unknown)
 };
 std::mutex g_lock;
 DeviceSetup g_dev[kMaxDevices];
+
+// id of the calling thread's current context, through the driver's entry points
+// (found once; 0 when the driver does not offer them, then the first lookup is kept)
+unsigned long long current_context_id() {
+  using GetCur = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCur get_cur = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked = false;
+  if (!looked) {  // (under g_lock)
+    looked = true;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_cur, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess ||
+        q2 != cudaDriverEntryPointSuccess) {
+      get_cur = nullptr;
+      get_id = nullptr;
+      cudaGetLastError();
+    }
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur && get_id && get_cur(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS) return id;
+  return 0;
+}
 
 // Tile table and diagonal index, with a check of the caller's pattern: row
 // pointers non-decreasing from 0 to nnzb, columns in range, one diagonal block
@@ -112,15 +145,20 @@ __global__ void k_static_prep(const int* __restrict__ row_ptr, const int* __rest
   if (i >= n) return;
   const int kb = row_ptr[i], ke = row_ptr[i + 1];
   bool bad = kb < 0 || ke < kb || ke > nnzb || (i == 0 && kb != 0) || (i == n - 1 && ke != nnzb);
-  int d = -1;
+  int d = -1, n_diag = 0;
   if (!bad)
     for (int k = kb; k < ke; ++k) {
       const int j = col[k];
       if (j < 0 || j >= n) bad = true;
-      if (j == i) d = k;
+      if (j == i) {
+        d = k;
+        ++n_diag;
+      }
     }
   diag[i] = bad ? 0 : d;
-  if (bad || d < 0) atomicOr(&ctl->error, kErrPattern);
+  // exactly one diagonal block: with two, the preconditioner would invert one of them
+  // while the SpMV sums both
+  if (bad || n_diag != 1) atomicOr(&ctl->error, kErrPattern);
 }
 
 ppn_status fail(ppn_status rc, const std::string& msg) {
@@ -153,8 +191,19 @@ PPN_API ppn_status ppn_pcg_solve_static(const int32_t* row_ptr, const int32_t* c
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail(PPN_ERR_CUDA, "ppn_pcg_solve_static: no usable current device");
+  if (st) {  // the arena and the occupancy are those of the current device: the stream must be on it
+    int sdev = -1;
+    if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PPN_ERR_INVALID_ARG, "ppn_pcg_solve_static: the stream is not a valid stream");
+    }
+    if (sdev != dev)
+      return fail(PPN_ERR_INVALID_ARG, "ppn_pcg_solve_static: the stream belongs to device " + std::to_string(sdev) +
+                                           ", the current device is " + std::to_string(dev));
+  }
   DeviceSetup& D = g_dev[dev];
-  if (!D.base) {  // first call on this device: symbol address and solver occupancy
+  const unsigned long long ctx = current_context_id();
+  if (!D.base || (ctx && ctx != D.ctx)) {  // first call in this context: symbol address and solver occupancy
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_static);
     if (e != cudaSuccess || !p)
@@ -163,6 +212,7 @@ PPN_API ppn_status ppn_pcg_solve_static(const int32_t* row_ptr, const int32_t* c
     if (grid <= 0) return fail(PPN_ERR_CUDA, "ppn_pcg_solve_static: solver occupancy query failed");
     D.grid = grid;
     D.base = (unsigned char*)p;
+    D.ctx = ctx;
   }
   const int n_tiles = (n_rows + PCG_TILE - 1) / PCG_TILE;
   const Arena A = carve(D.base, n_rows, n_tiles);

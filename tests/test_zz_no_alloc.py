@@ -68,3 +68,9 @@ def test_static_arena_rejects_oversize_and_bad_patterns():
     bx = torch.zeros((2, 4), dtype=torch.float32, device=dev)
     with pytest.raises(P.PPNError, match="malformed BSR pattern"):
         P.ppn.pcg_solve_static(rp.data_ptr(), col.data_ptr(), val.data_ptr(), 2, 2, bx.data_ptr(), bx.data_ptr())
+    # a row with two diagonal blocks is malformed too (the preconditioner would invert one of them)
+    rp2 = torch.tensor([0, 2, 3], dtype=torch.int32, device=dev)
+    col2 = torch.tensor([0, 0, 1], dtype=torch.int32, device=dev)
+    val2 = torch.ones(27, dtype=torch.float32, device=dev)
+    with pytest.raises(P.PPNError, match="malformed BSR pattern"):
+        P.ppn.pcg_solve_static(rp2.data_ptr(), col2.data_ptr(), val2.data_ptr(), 2, 3, bx.data_ptr(), bx.data_ptr())
