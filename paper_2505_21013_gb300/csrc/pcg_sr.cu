@@ -63,6 +63,16 @@ namespace {
 
 constexpr int NTP = 512;  // threads per CTA
 constexpr int NQ = 4;     // reduction slots: gamma, delta, rho, failed diagonal blocks
+constexpr int SP_GP = 2;  // lanes per BSR row in the SpMV
+
+// SpMV lanes: a warp works on 32 / SP_GP consecutive rows; its lanes 0..15 take the
+// first lane of each row, lanes 16..31 the second.  An 8-lane phase of a 16-byte
+// gather then reads u of 8 consecutive rows at the same column offset (128 contiguous
+// bytes, no bank conflict), where interleaving the two lanes of a row read two
+// overlapping runs.  The per-row sum (lane 0 + lane 1) and the warp's fixed tree over
+// its rows pair the same values in the same order either way.
+__device__ __forceinline__ int spmv_row(int tid) { return (tid >> 5) * (32 / SP_GP) + (tid & (32 / SP_GP - 1)); }
+__device__ __forceinline__ int spmv_lane(int tid) { return (tid & 31) / (32 / SP_GP); }
 
 struct SrLayout {
   float* lws;    // [(ni / PCG_TILE + 1) * 16 * NQ] partial sums per 16-row group (8 per tile)
@@ -238,7 +248,7 @@ __global__ void __launch_bounds__(NTP, 1)
   using W = Words<float>;
   constexpr bool HALO = MODE == SR_HALO, RES = MODE == SR_RES || HALO, GV = MODE == SR_GLOBAL;
   constexpr int MS = HALO ? HALO_MAX_SCENES : PCG_MAX_SCENES;  // scenes of one launch
-  constexpr int GP = 2;                 // lanes per BSR row in the SpMV
+  constexpr int GP = SP_GP;             // lanes per BSR row in the SpMV
   constexpr int RPP = NTP / GP;         // rows per SpMV pass
   constexpr int U = 16 / GP;            // blocks per lane per gather round
   constexpr int NW = NTP / 32;          // warps
@@ -298,8 +308,8 @@ __global__ void __launch_bounds__(NTP, 1)
   // SpMV (the first of its GP lanes) owns the row: its x, r, p, s, u, w and block-Jacobi
   // inverse stay in that thread's registers for the whole solve (the same values, by the
   // same operations, as the other layouts keep in shared or global memory)
-  const int o_item = tid / GP;
-  const bool owner = HALO && tid % GP == 0 && o_item < n_items;
+  const int o_item = spmv_row(tid);
+  const bool owner = HALO && spmv_lane(tid) == 0 && o_item < n_items;
   int o_slot = 0, o_row = -1;
   if (owner) o_row = row_of(o_item, o_slot);
   float ox[3] = {0.f, 0.f, 0.f}, orr[3] = {0.f, 0.f, 0.f}, op[3] = {0.f, 0.f, 0.f}, os[3] = {0.f, 0.f, 0.f};
@@ -528,7 +538,7 @@ __global__ void __launch_bounds__(NTP, 1)
   const unsigned long long pol = RES ? 0ull : l2_evict_first();
   auto spmv = [&](unsigned s, int par) {
     for (int base = 0; base < n_items; base += RPP) {
-      const int row = tid / GP, lane = tid % GP;
+      const int row = spmv_row(tid), lane = spmv_lane(tid);
       const int item = base + row;
       float ax = 0.f, ay = 0.f, az = 0.f;
       int slot = 0, i = -1;
@@ -576,10 +586,10 @@ __global__ void __launch_bounds__(NTP, 1)
         }
       }
 #pragma unroll
-      for (int o = GP / 2; o > 0; o >>= 1) {
-        ax += __shfl_down_sync(0xffffffffu, ax, o, GP);
-        ay += __shfl_down_sync(0xffffffffu, ay, o, GP);
-        az += __shfl_down_sync(0xffffffffu, az, o, GP);
+      for (int o = 16; o >= 32 / GP; o >>= 1) {  // the row's lanes, 32 / GP apart: lane 0 + lane 1
+        ax += __shfl_down_sync(0xffffffffu, ax, o);
+        ay += __shfl_down_sync(0xffffffffu, ay, o);
+        az += __shfl_down_sync(0xffffffffu, az, o);
       }
       // w of the row, and its terms of gamma = r.u, delta = w.u, rho = r.r
       float g = 0.f, d = 0.f, rr = 0.f;
