@@ -58,7 +58,7 @@ struct Ctl {
   int pcg_done;
   int error;             // bit flags, see kErr*
   int pad0;
-  unsigned tiles_done[4];  // last-tile counters of the reductions (gradient, energy, spare)
+  unsigned tiles_done[5];  // last-tile counters of the reductions (gradient, energy, ccd, gap, g^T dx)
 };
 
 constexpr int kErrTimeout = 1;

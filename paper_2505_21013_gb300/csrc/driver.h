@@ -286,6 +286,8 @@ struct HostState {
   bool ind = false, fallback = false;
   int precond_fail = 0, pcg_iters_last = 0;
   double E0 = 0, dd = 0, dxmax = 0, gamma = 1;
+  bool has_next = false;  // E_next holds the incremental potential at the current iterate
+  double E_next = 0;      // (the last accepted trial energy of this time step)
   int halvings = 0;
   int countdown = 0;  // PDN: iterations left that assemble projected
   int ties_pending = 0;          // selection ties of the rounds since the last solve
@@ -897,6 +899,8 @@ struct Driver {
         if (Et <= h.E0 + Pi(i).armijo_c * h.gamma * h.dd + Pi(i).ls_slack * std::fabs(h.E0)) {
           ls[i] = 0;
           accept[i] = 1;
+          h.has_next = true;  // k_axpy_u forms the accepted point with the trial's own operations
+          h.E_next = Et;
           h.cur.gamma = h.gamma;
           h.cur.energy_new = Et;
           h.cur.ls_halvings = h.halvings;
@@ -1176,22 +1180,44 @@ struct Driver {
     return check_launch();
   }
 
-  // energy at u + gamma dx for the flagged scenes; at_zero also records E0, g^T dx, max|dx|
+  // energy at u + gamma dx for the flagged scenes; at_zero also records E0, g^T dx, max|dx|.
+  // At gamma = 0 a scene whose current iterate came from an accepted line-search trial of
+  // this time step already has its energy (the same displacement bits, the same kernel):
+  // only g^T dx and max |dx| are reduced, over the vertices.
   ppn_status energy(const std::vector<char>& on, bool at_zero) {
     const int n = (int)on.size();
-    if (at_zero)
-      for (int i = 0; i < n; ++i)
-        if (on[i]) G.h_desc[i].gamma = 0.0;
-    G.set_active(on);
-    ppn_status rc = G.upload_desc();
-    if (rc) return rc;
-    timed(FAM_ENERGY, 0, [&] { launch_energy<T>(G.d_desc, G.d_etiles, G.n_etiles, 0, G.st); });
-    if ((rc = check_launch())) return rc;
+    std::vector<char> full(on), quick(n, 0);
+    bool any_full = false, any_quick = false;
+    const bool force_full = std::getenv("PPN_ENERGY_FULL") != nullptr;  // tests: always the full pass
+    for (int i = 0; i < n; ++i) {
+      if (!on[i]) continue;
+      if (at_zero) G.h_desc[i].gamma = 0.0;
+      if (at_zero && H[i].has_next && !force_full) {
+        full[i] = 0;
+        quick[i] = 1;
+        any_quick = true;
+      } else {
+        any_full = true;
+      }
+    }
+    ppn_status rc = PPN_OK;
+    if (any_full) {
+      G.set_active(full);
+      if ((rc = G.upload_desc())) return rc;
+      timed(FAM_ENERGY, 0, [&] { launch_energy<T>(G.d_desc, G.d_etiles, G.n_etiles, 0, G.st); });
+      if ((rc = check_launch())) return rc;
+    }
+    if (any_quick) {
+      G.set_active(quick);
+      if ((rc = G.upload_desc())) return rc;
+      timed(FAM_ENERGY, 0, [&] { launch_dirderiv<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st); });
+      if ((rc = check_launch())) return rc;
+    }
     if ((rc = G.sync_ctl())) return rc;
     if (at_zero)
       for (int i = 0; i < n; ++i)
         if (on[i]) {
-          H[i].E0 = G.h_ctl[i].energy[0];
+          H[i].E0 = quick[i] ? H[i].E_next : G.h_ctl[i].energy[0];
           H[i].dd = G.h_ctl[i].energy[1];
           H[i].dxmax = G.h_ctl[i].energy[2];
         }

@@ -603,40 +603,31 @@ __global__ void __launch_bounds__(TILE) k_energy(const SceneDev<T>* scenes, cons
     const int vt = tr.tile - S.n_ttiles;
     const int v = vt * TILE + threadIdx.x;
     if (v < S.nv && !S.fixed[v]) {
-      const double4 uv = ld_d4(U + v), uh = ld_d4(S.uhat + v);
-      double d0 = uv.x - uh.x, d1 = uv.y - uh.y, d2 = uv.z - uh.z;
+      // the trial displacement u + gamma dx first, formed as k_axpy_u forms the accepted
+      // update, so that the energy of an accepted trial is that of the new iterate bit for bit
+      double4 uv = ld_d4(U + v);
+      const double4 uh = ld_d4(S.uhat + v);
       if (!use_probe) {
         const vec4_t<T> d = S.dx[v];
         if (gam != 0.0) {
-          d0 += gam * (double)d.x;
-          d1 += gam * (double)d.y;
-          d2 += gam * (double)d.z;
+          uv.x = uv.x + gam * (double)d.x;
+          uv.y = uv.y + gam * (double)d.y;
+          uv.z = uv.z + gam * (double)d.z;
         }
         const double4 g = ld_d4(S.g + v);
         dd = g.x * (double)d.x + g.y * (double)d.y + g.z * (double)d.z;
         dmax = fmax(fabs((double)d.x), fmax(fabs((double)d.y), fabs((double)d.z)));
       }
+      const double d0 = uv.x - uh.x, d1 = uv.y - uh.y, d2 = uv.z - uh.z;
       en = 0.5 * S.mass[v] * S.inv_dt2 * (d0 * d0 + d1 * d1 + d2 * d2);
       if (S.pen_k > 0.0 && S.con[v]) {  // Dirichlet penalty potential at u + gamma dx
         const double4 t = ld_d4(S.tgt + v);
-        double p0 = uv.x - t.x, p1 = uv.y - t.y, p2 = uv.z - t.z;
-        if (!use_probe && gam != 0.0) {
-          const vec4_t<T> d = S.dx[v];
-          p0 += gam * (double)d.x;
-          p1 += gam * (double)d.y;
-          p2 += gam * (double)d.z;
-        }
+        const double p0 = uv.x - t.x, p1 = uv.y - t.y, p2 = uv.z - t.z;
         en += 0.5 * S.pen_k * S.mass[v] * S.inv_dt2 * (p0 * p0 + p1 * p1 + p2 * p2);
       }
       if (S.obs->n > 0) {  // barrier potentials; +inf where a surface is reached
         const double4 X = ld_d4(S.X + v);
-        double x[3] = {X.x + uv.x, X.y + uv.y, X.z + uv.z};
-        if (!use_probe && gam != 0.0) {
-          const vec4_t<T> d = S.dx[v];
-          x[0] += gam * (double)d.x;
-          x[1] += gam * (double)d.y;
-          x[2] += gam * (double)d.z;
-        }
+        const double x[3] = {X.x + uv.x, X.y + uv.y, X.z + uv.z};
         double Ec;
         en += vertex_contact(S, x, &Ec, nullptr, nullptr, nullptr) ? Ec : std::numeric_limits<double>::infinity();
       }
@@ -652,6 +643,32 @@ __global__ void __launch_bounds__(TILE) k_energy(const SceneDev<T>* scenes, cons
   }
   finish_reduction<TILE, 3>(S.tpart, &S.ctl->tiles_done[1], S.n_ttiles + S.n_vtiles, 2,
                             S.ctl->energy, sm);
+}
+
+// g^T dx and max |dx| over the free vertices into ctl->energy[1], [2] (the line search's
+// directional derivative when the energy at gamma = 0 is already known: the previous
+// iteration's accepted trial energy, computed at the same displacement bits)
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_dirderiv(const SceneDev<T>* scenes, const TileRef* tiles) {
+  __shared__ double sm[32];
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int v = tr.tile * TILE + threadIdx.x;
+  double dd = 0.0, dmax = 0.0;
+  if (v < S.nv && !S.fixed[v]) {
+    const vec4_t<T> d = S.dx[v];
+    const double4 g = ld_d4(S.g + v);
+    dd = g.x * (double)d.x + g.y * (double)d.y + g.z * (double)d.z;
+    dmax = fmax(fabs((double)d.x), fmax(fabs((double)d.y), fabs((double)d.z)));
+  }
+  const double s0 = block_sum<TILE>(dd, sm);
+  const double s1 = block_max<TILE>(dmax, sm);
+  if (threadIdx.x == 0) {
+    S.vpart[4 * tr.tile + 0] = s0;
+    S.vpart[4 * tr.tile + 1] = s1;
+  }
+  finish_reduction<TILE, 2>(S.vpart, &S.ctl->tiles_done[4], S.n_vtiles, 1, S.ctl->energy + 1, sm);
 }
 
 // per-vertex |g_v|_inf of a given assembled gradient (selection probe)
@@ -809,6 +826,10 @@ void launch_energy(const SceneDev<T>* s, const TileRef* t, int n, int probe, cud
   if (n) k_energy<T><<<n, TILE, 0, st>>>(s, t, probe);
 }
 template <typename T>
+void launch_dirderiv(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
+  if (n) k_dirderiv<T><<<n, TILE, 0, st>>>(s, t);
+}
+template <typename T>
 void launch_predict(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
   if (n) k_predict<T><<<n, TILE, 0, st>>>(s, t, nullptr, nullptr, 0);
 }
@@ -844,6 +865,7 @@ void launch_fallback(const SceneDev<T>* s, const TileRef* t, int n, int kind, cu
   template void launch_project<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
   template void launch_energy<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);  \
   template void launch_predict<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \
+  template void launch_dirderiv<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \
   template void launch_select_contact<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \
   template void launch_update_contact<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \
   template void launch_ccd<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \

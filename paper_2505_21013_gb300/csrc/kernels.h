@@ -20,6 +20,8 @@ template <typename T> void launch_select(const SceneDev<T>*, const TileRef*, int
 template <typename T> void launch_project(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
 template <typename T> void launch_energy(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
 template <typename T> void launch_predict(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
+// g^T dx and max |dx| over the free vertices (vertex tiles) into ctl->energy[1], [2]
+template <typename T> void launch_dirderiv(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
 // contact elements (vertex tiles): selection + clamping, in-place update, first contact time
 template <typename T> void launch_select_contact(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
 template <typename T> void launch_update_contact(const SceneDev<T>*, const TileRef*, int, cudaStream_t);

@@ -77,6 +77,7 @@ __device__ __forceinline__ int spmv_lane(int tid) { return (tid & 31) / (32 / SP
 struct SrLayout {
   float* lws;    // [(ni / PCG_TILE + 1) * 16 * NQ] partial sums per 16-row group (8 per tile)
   TileRef* ltt;  // [ni / PCG_TILE + 1] the CTA's tiles
+  int* ltc;      // [ni / PCG_TILE + 1] groups of each tile done in the current SpMV
   int* lrp;      // SR_RES, SR_HALO: [ni + 1] local row pointers
   int* lcol;     // SR_RES: [nb] columns; SR_HALO: [nb] local columns (own item, or ni + halo index)
   float* lval;   // SR_RES, SR_HALO: [nb * 9]
@@ -100,6 +101,7 @@ __host__ __device__ inline size_t carve_sr(char* base, int ni, int nb, int nh, i
   };
   SrLayout l{};
   l.lws = (float*)take(sizeof(float) * ntl * 16 * NQ);
+  l.ltc = (int*)take(sizeof(int) * ntl);
   l.ltt = (TileRef*)take(sizeof(TileRef) * ntl);
   if (mode == SR_RES || mode == SR_HALO) {
     l.lrp = (int*)take(sizeof(int) * (ni + 1));
@@ -194,7 +196,7 @@ __device__ __forceinline__ int ld_stream(const int* a, unsigned long long pol) {
 // scalar step after the reduction of iteration `it` (it updates done so far):
 // stopping tests, then alpha and beta of the next direction, or the exits
 __device__ __forceinline__ void sr_step(SState<float>& s, float gam, float del, float rho, float fail, int it,
-                                        double tol2, int max_iter) {
+                                        float tol2, int max_iter) {
   s.rr = rho;
   if (it == 0) {
     s.rr0 = rho;
@@ -213,7 +215,7 @@ __device__ __forceinline__ void sr_step(SState<float>& s, float gam, float del, 
     s.done = 1;
     return;
   }
-  if (it > 0 && rho <= (float)tol2 * s.rr0) {
+  if (it > 0 && rho <= tol2 * s.rr0) {
     s.done = 1;
     return;
   }
@@ -258,6 +260,7 @@ __global__ void __launch_bounds__(NTP, 1)
   __shared__ SState<float> st[MS];
   __shared__ SceneLite<float> sl[MS];
   __shared__ float s_sum[MS][NQ];
+  __shared__ float s_tol2[MS];  // the scenes' squared relative tolerances, converted once (FP64 -> FP32)
   __shared__ int s_toff[MS];
   __shared__ int s_to, s_lo, s_hi;
   __shared__ unsigned s_seen;
@@ -286,8 +289,12 @@ __global__ void __launch_bounds__(NTP, 1)
   for (int si = tid; si < n_scenes; si += NTP) {
     load_lite(sl[si], scenes[scene_ids[si]]);
     st[si].done = 0;
+    s_tol2[si] = (float)sl[si].tol2;
   }
-  for (int lt = tid; lt < ntl; lt += NTP) L.ltt[lt] = tiles[t0 + lt];
+  for (int lt = tid; lt < ntl; lt += NTP) {
+    L.ltt[lt] = tiles[t0 + lt];
+    L.ltc[lt] = 0;
+  }
   __syncthreads();
   if (tid == 0) {
     int o = 0;
@@ -536,7 +543,25 @@ __global__ void __launch_bounds__(NTP, 1)
   // w = A u over this CTA's rows (GP lanes per row), u gathered from the global array or, in
   // SR_HALO, from shared memory; SR_HALO also stores w as stamped words (stamp s, buffer par)
   const unsigned long long pol = RES ? 0ull : l2_evict_first();
-  auto spmv = [&](unsigned s, int par) {
+  // the tile partials of tile lt (stamp s, buffer par): the fixed tree over its eight
+  // 16-row group sums, posted as stamped words
+  auto post_tile = [&](int lt, unsigned s, int par, int nq) {
+    const TileRef tr = L.ltt[lt];
+    const SceneLite<float>& S = sl[tr.scene];
+    if (st[tr.scene].done) return;
+    const float* w = L.lws + NQ * 8 * lt;
+    const size_t ws = (size_t)pword_stride(S.n_ptiles);
+    unsigned long long* wbase = S.pword + ((size_t)par * NQ * S.n_ptiles + tr.tile) * ws;
+    for (int q = 0; q < nq; ++q) {
+      const float a = (w[q] + w[NQ + q]) + (w[2 * NQ + q] + w[3 * NQ + q]);
+      const float b = (w[4 * NQ + q] + w[5 * NQ + q]) + (w[6 * NQ + q] + w[7 * NQ + q]);
+      unsigned long long wd[1];
+      W::split(a + b, s, wd);
+      st_relaxed_u64(wbase + (size_t)q * S.n_ptiles * ws, wd[0]);
+    }
+  };
+  // w = A u; each tile's partials are posted by the warp that completes its last group
+  auto spmv = [&](unsigned s, int par, int nq) {
     for (int base = 0; base < n_items; base += RPP) {
       const int row = spmv_row(tid), lane = spmv_lane(tid);
       const int item = base + row;
@@ -641,35 +666,24 @@ __global__ void __launch_bounds__(NTP, 1)
       d = warp_sum(d);
       rr = warp_sum(rr);
       if (lane32 == 0) {
-        float* o = L.lws + NQ * ((base >> 4) + warp);
+        const int grp = (base >> 4) + warp, lt = grp >> 3;
+        float* o = L.lws + NQ * grp;
         o[0] = g;
         o[1] = d;
         o[2] = rr;
+        if (lt < ntl) {  // (the groups past the CTA's tiles of a one-tile CTA post nothing)
+          __threadfence_block();  // the group sums before the count
+          if (atomicAdd(&L.ltc[lt], 1) == 7) {
+            __threadfence_block();  // the other groups' sums after their counts
+            L.ltc[lt] = 0;
+            post_tile(lt, s, par, nq);
+          }
+        }
       }
     }
     __syncthreads();
   };
 
-  // tile sums of gamma = r.u, delta = w.u, rho = r.r (and failed blocks) from the SpMV's
-  // 16-row group sums (8 groups per tile, a fixed tree), posted
-  auto post_partials = [&](unsigned stamp, bool with_fail, int par) {
-    for (int lt = tid; lt < ntl; lt += NTP) {
-      const TileRef tr = L.ltt[lt];
-      const SceneLite<float>& S = sl[tr.scene];
-      if (st[tr.scene].done) continue;
-      const float* w = L.lws + NQ * 8 * lt;
-      const size_t ws = (size_t)pword_stride(S.n_ptiles);
-      unsigned long long* base = S.pword + ((size_t)par * NQ * S.n_ptiles + tr.tile) * ws;
-      const int nq = with_fail ? NQ : 3;
-      for (int q = 0; q < nq; ++q) {
-        const float a = (w[q] + w[NQ + q]) + (w[2 * NQ + q] + w[3 * NQ + q]);
-        const float b = (w[4 * NQ + q] + w[5 * NQ + q]) + (w[6 * NQ + q] + w[7 * NQ + q]);
-        unsigned long long wd[1];
-        W::split(a + b, stamp, wd);
-        st_relaxed_u64(base + (size_t)q * S.n_ptiles * ws, wd[0]);
-      }
-    }
-  };
   // a wait ran out: record the first one (iteration, wait) and flag the timeout
   auto fail_out = [&](int it) {
     if (tid == 0) {
@@ -819,18 +833,14 @@ __global__ void __launch_bounds__(NTP, 1)
       publish_flag((unsigned long long)it + 1);
       if (!wait_flags((unsigned long long)it + 1)) return fail_out(it);
     }
-    spmv(s, it & 1);  // w = A u
-    post_partials(s, it == 0, it & 1);
-    // the posts leave before any warp starts polling: polling warps fill the load/store
-    // queue with L2 reads, and the posting lanes' shared-memory reads would wait behind them
-    __syncthreads();
+    spmv(s, it & 1, it == 0 ? NQ : 3);  // w = A u, and the tile partials posted
     if (!reduce(it == 0 ? NQ : 3, s, it & 1)) return fail_out(it);
     // one thread per scene (n_scenes <= MS < NTP); the barrier also finds whether all are done
     int done = 1;
     if (tid < n_scenes) {
       if (!st[tid].done)
         sr_step(st[tid], s_sum[tid][0], s_sum[tid][1], s_sum[tid][2], it == 0 ? s_sum[tid][3] : 0.0f, it,
-                sl[tid].tol2, sl[tid].max_iter);
+                s_tol2[tid], sl[tid].max_iter);
       done = st[tid].done;
     }
     if (__syncthreads_and(done)) break;

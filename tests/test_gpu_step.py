@@ -250,3 +250,40 @@ def test_touched_block_update_equals_the_full_sweep(prec, monkeypatch):
     for (xa, pa, ca), (xb, pb, cb) in zip(*out):
         assert pa == pb and ca == cb
         assert np.array_equal(xa, xb)
+
+
+@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
+def test_reused_line_search_energy_equals_a_fresh_pass(prec, monkeypatch):
+    # From the second Newton iteration of a step on, the energy at gamma = 0 is the
+    # previous iteration's accepted trial energy (formed at the same displacement bits)
+    # and only g^T dx and max |dx| are reduced; a run that evaluates the energy afresh at
+    # every iterate takes the same steps, bit for bit
+    from ppn_inputs import drop_scene
+
+    specs = [twisting_beam_scene(6, 6, 16, h=0.02, E=1e5, nu=0.45, omega=30.0, dt=0.1, seed=10),
+             drop_scene(cells=(3, 3, 3), height=0.002, obstacle="sphere", seed=11)]
+    for spec in specs:
+        out = []
+        for full in (False, True):
+            if full:
+                monkeypatch.setenv("PPN_ENERGY_FULL", "1")
+            else:
+                monkeypatch.delenv("PPN_ENERGY_FULL", raising=False)
+            sc = P.Scene.from_spec(spec, precision=prec)
+            if spec.obstacles is not None:
+                sc.set_obstacles(spec.obstacles_at(0))
+            xs = []
+            for n in range(3):
+                sc.set_targets(spec.targets_at(n))
+                rc, x, st = sc.step(P.MODE_PPN, 1e-5)
+                assert rc == 0
+                its = sc.iter_stats()
+                xs.append((x, st["newton_iters"], [(it["energy"], it["energy_new"], it["ls_halvings"]) for it in its]))
+            sc.close()
+            out.append(xs)
+        assert any(s[1] > 1 for s in out[0])
+        for (xa, na, ea), (xb, nb, eb) in zip(*out):
+            assert na == nb and ea == eb
+            assert np.array_equal(xa, xb)
+            # the energy at the start of an iteration is the last one's accepted energy
+            assert all(ea[k][0] == ea[k - 1][1] for k in range(1, len(ea)))
