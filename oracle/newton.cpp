@@ -28,6 +28,10 @@
 
 #include "ppn_oracle.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 namespace ora {
 double det3x3(const double* M);
 void edge_matrix(const double* c, double* D);
@@ -292,6 +296,22 @@ int fallback_direction(const ora_scene* s, const std::vector<double>& vals, cons
 }  // namespace
 
 extern "C" {
+
+int ora_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void ora_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
 
 ora_params ora_default_params(void) {
   ora_params p;
@@ -570,6 +590,8 @@ int ora_scene_step(ora_scene* s, int mode, double tol, double* out_x, ora_step_s
   int countdown = 0;  // PDN: iterations left that assemble projected
 
   for (int k = 0; k < p.newton_max_iter; ++k) {
+    // elements are independent (each writes its own g^e, H^e): OpenMP shares them out
+#pragma omp parallel for schedule(static)
     for (int64_t e = 0; e < nt; ++e) element(s, e, x.data(), nullptr, &ge[12 * e], &He[144 * e]);
     gradient_from(s, x.data(), xhat.data(), ge, g.data());
     if (s->record) s->iter_g.push_back(g);

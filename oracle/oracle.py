@@ -92,6 +92,8 @@ def lib():
     pd, pi, pl, pu = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_uint8)
     sig = {
         "ora_default_params": (Params, []),
+        "ora_num_threads": (I, []),
+        "ora_set_num_threads": (None, [I]),
         "ora_last_error": (C.c_char_p, []),
         "ora_lame": (None, [D, D, pd, pd]),
         "ora_snh_psi": (D, [pd, D, D]),
@@ -141,6 +143,15 @@ def lib():
 
 def default_params() -> Params:
     return lib().ora_default_params()
+
+
+def num_threads() -> int:
+    """Threads of the oracle's parallel loops (OMP_NUM_THREADS)."""
+    return int(lib().ora_num_threads())
+
+
+def set_num_threads(n: int):
+    lib().ora_set_num_threads(int(n))
 
 
 def lame(E, nu):

@@ -143,6 +143,11 @@ typedef int (*ora_solve_hook)(int newton_iter, int attempt, int n_projected_tota
  * steps.  A set of another size, kind or normal replaces the old one at once. */
 void ora_scene_set_obstacles(ora_scene* s, const ora_obstacle* obs, int n);
 ora_params ora_default_params(void);
+/* threads the oracle's parallel loops use (OMP_NUM_THREADS; 1 without OpenMP).  Only
+ * loops over independent elements and SpMV rows run in parallel: the results do not
+ * depend on the thread count. */
+int ora_num_threads(void);
+void ora_set_num_threads(int n); /* n > 0; no effect without OpenMP */
 const char* ora_last_error(void);
 
 /* ---- material (Stable Neo-Hookean reading) ---- */

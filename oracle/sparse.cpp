@@ -20,6 +20,8 @@ namespace ora {
 // y = A x on a BSR matrix with 3x3 row-major blocks
 void bsr_spmv(int64_t n_rows, const int64_t* row_ptr, const int32_t* col, const double* vals,
               const double* x, double* y) {
+  // rows are independent: with OpenMP they are shared out over the host's cores (same results)
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n_rows; ++i) {
     double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
