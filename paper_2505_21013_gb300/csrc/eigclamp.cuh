@@ -17,8 +17,8 @@
 // so the twelve eigenpairs of H^e are the nine of M, lifted by q_a = sum_j S_aj z_j,
 // plus the three rigid translations with eigenvalue exactly 0 (T annihilates
 // them).  Clamping those adds eps/4 I to every 3x3 block.  The 9x9 problem is
-// solved with cyclic Jacobi sweeps (symmetric 2x2 Schur rotations); all index
-// arithmetic unrolls at compile time so the matrices live in registers.
+// solved with Jacobi sweeps of symmetric 2x2 Schur rotations in round-robin order;
+// all index arithmetic unrolls at compile time so the matrices live in registers.
 #pragma once
 
 #include "tetmath.cuh"
@@ -56,20 +56,37 @@ PPN_HD double rsqrt_t<double>(double x) {
   return 1.0 / sqrt(x);
 }
 
-// one Jacobi rotation zeroing A(p, q); V accumulates the eigenvectors (columns)
+// The symmetric Schur rotation zeroing A(p, q) (Golub & Van Loan, Sec. 8.5): t = tan of
+// the angle, c, s its cosine and sine; skip when A(p, q) is already zero.
+template <typename T>
+struct JRot {
+  T app, aqq, apq, t, c, s;
+  bool skip;
+};
 template <typename T, int P, int Q>
-PPN_HD void jrot(T* A, T* V) {
-  const T apq = A[s9(P, Q)];
-  if (apq == (T)0) return;
-  const T app = A[s9(P, P)], aqq = A[s9(Q, Q)];
-  const T tau = (aqq - app) / ((T)2 * apq);
+PPN_HD JRot<T> jrot_params(const T* A) {
+  JRot<T> r;
+  r.apq = A[s9(P, Q)];
+  r.app = A[s9(P, P)];
+  r.aqq = A[s9(Q, Q)];
+  r.skip = r.apq == (T)0;
+  const T apq = r.skip ? (T)1 : r.apq;
+  const T tau = (r.aqq - r.app) / ((T)2 * apq);
   const T at = tau < (T)0 ? -tau : tau;
   T t = at > JacobiCfg<T>::big_tau ? (T)0.5 / at : (T)1 / (at + sqrt((T)1 + at * at));
   if (tau < (T)0) t = -t;
-  const T c = rsqrt_t<T>((T)1 + t * t);
-  const T s = t * c;
-  A[s9(P, P)] = app - t * apq;
-  A[s9(Q, Q)] = aqq + t * apq;
+  r.t = t;
+  r.c = rsqrt_t<T>((T)1 + t * t);
+  r.s = t * r.c;
+  return r;
+}
+// A <- J^T A J and V <- V J for the rotation of (P, Q); V accumulates the eigenvectors (columns)
+template <typename T, int P, int Q>
+PPN_HD void jrot_apply(T* A, T* V, const JRot<T>& r) {
+  if (r.skip) return;
+  const T t = r.t, c = r.c, s = r.s;
+  A[s9(P, P)] = r.app - t * r.apq;
+  A[s9(Q, Q)] = r.aqq + t * r.apq;
   A[s9(P, Q)] = (T)0;
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
@@ -86,18 +103,47 @@ PPN_HD void jrot(T* A, T* V) {
   }
 }
 
-template <typename T, int P, int Q>
-struct SweepStep {
+// Round-robin ordering of the 36 index pairs of a sweep (the circle method for 9
+// indices): in round r index x meets (2r - x) mod 9 and index r sits out, so every
+// round holds 4 disjoint pairs and every pair meets once in the 9 rounds.  Disjoint
+// rotations commute, and a rotation's parameters read only the (p,p), (q,q), (p,q)
+// entries of its pair, which the round's other rotations leave unchanged: the four
+// parameter computations of a round are independent (four times the work in flight
+// of a cyclic-by-row sweep, whose rotations wait for one another).
+PPN_HD constexpr int rr_mate(int r, int x) { return ((2 * r - x) % 9 + 9) % 9; }
+PPN_HD constexpr int rr_p(int r, int i) {
+  int k = 0;
+  for (int x = 0; x < 9; ++x)
+    if (x != r && x < rr_mate(r, x)) {
+      if (k == i) return x;
+      ++k;
+    }
+  return -1;
+}
+PPN_HD constexpr int rr_q(int r, int i) { return rr_mate(r, rr_p(r, i)); }
+
+template <typename T, int R>
+PPN_HD void jround(T* A, T* V) {
+  constexpr int p0 = rr_p(R, 0), q0 = rr_q(R, 0), p1 = rr_p(R, 1), q1 = rr_q(R, 1);
+  constexpr int p2 = rr_p(R, 2), q2 = rr_q(R, 2), p3 = rr_p(R, 3), q3 = rr_q(R, 3);
+  static_assert(p3 >= 0 && q0 > p0 && q1 > p1 && q2 > p2 && q3 > p3, "four pairs per round");
+  const JRot<T> r0 = jrot_params<T, p0, q0>(A), r1 = jrot_params<T, p1, q1>(A);
+  const JRot<T> r2 = jrot_params<T, p2, q2>(A), r3 = jrot_params<T, p3, q3>(A);
+  jrot_apply<T, p0, q0>(A, V, r0);
+  jrot_apply<T, p1, q1>(A, V, r1);
+  jrot_apply<T, p2, q2>(A, V, r2);
+  jrot_apply<T, p3, q3>(A, V, r3);
+}
+
+template <typename T, int R>
+struct SweepRounds {
   PPN_HD static void run(T* A, T* V) {
-    jrot<T, P, Q>(A, V);
-    if constexpr (Q < 8)
-      SweepStep<T, P, Q + 1>::run(A, V);
-    else if constexpr (P < 7)
-      SweepStep<T, P + 1, P + 2>::run(A, V);
+    jround<T, R>(A, V);
+    if constexpr (R < 8) SweepRounds<T, R + 1>::run(A, V);
   }
 };
 
-// cyclic-by-row Jacobi on the packed symmetric 9x9 A; returns sweeps used
+// Jacobi on the packed symmetric 9x9 A with round-robin sweeps; returns sweeps used
 template <typename T>
 PPN_HD int jacobi9(T* A, T* V) {
 #pragma unroll
@@ -116,7 +162,7 @@ PPN_HD int jacobi9(T* A, T* V) {
 #pragma unroll
       for (int c = r + 1; c < 9; ++c) off2 += (T)2 * A[s9(r, c)] * A[s9(r, c)];
     if (!(off2 > tol2)) break;
-    SweepStep<T, 0, 1>::run(A, V);
+    SweepRounds<T, 0>::run(A, V);
   }
   return sweep;
 }
