@@ -454,6 +454,11 @@ def run_batched(n_scenes=64, steps=10, warmup=1, seed=0, tol=1e-4):
         out[name] = {"scene_steps_per_s": n_scenes * steps / (sum(lat) / 1e3), "ms_per_batched_step": sum(lat) / steps,
                      "newton_iters": newton, "projections": proj, "steps_at_newton_cap": capped}
     out["speedup_ppn_vs_pn"] = out["ppn"]["scene_steps_per_s"] / out["pn"]["scene_steps_per_s"]
+    # the linear solver's autotuner: per shape class the configuration it kept (layout x L2
+    # priority of the streamed blocks, all bitwise-equal) and each one's time per CG iteration
+    out["pcg_tuning"] = [{"tiles_per_cta": t["tiles_per_cta"], "blocks_per_row": t["blocks_per_row"],
+                          "log2_matrix_mb": t["log2_matrix_mb"], "kept": t["kept"],
+                          "us_per_iter": [round(x, 2) for x in t["us_per_iter"]]} for t in P.ppn.pcg_tuning()]
     return out
 
 

@@ -231,6 +231,24 @@ PPN_API ppn_status ppn_set_state(ppn_scene* s, const double* x, const double* v)
 PPN_API ppn_status ppn_get_displacement(const ppn_scene* s, double* u, double* v);
 PPN_API ppn_status ppn_set_displacement(ppn_scene* s, const double* u, const double* v);
 
+/* The FP32 linear solver's autotuner (process-wide).  Where several launch configurations of
+ * the single-reduction PCG give bitwise-identical results (the streamed layouts: vectors in
+ * shared memory with the blocks streamed, or everything in global memory; and the L2
+ * priority of the streamed blocks: evict-first, or normal, which lets a matrix smaller than
+ * L2 stay resident), the first launches of each shape class try each configuration, timed
+ * by CUDA events, and later launches keep the fastest per CG iteration.  One record per
+ * shape class seen so far; n_written receives the count, at most cap are written. */
+typedef struct {
+  int tiles_per_cta;     /* shape class: 128-row tiles of the busiest CTA, */
+  int blocks_per_row;    /* BSR blocks per row, */
+  int log2_matrix_mb;    /* and floor(log2(the launch's matrix in MB)) */
+  int choice;            /* kept configuration: layout (0 streamed blocks, 1 global vectors) + 2 x
+                          * L2 priority (0 evict-first, 1 normal); -1 while still exploring */
+  int launches[4];       /* timed launches of each configuration (0: untried or not allowed) */
+  double us_per_iter[4]; /* their mean device time per CG iteration */
+} ppn_pcg_tuning;
+PPN_API ppn_status ppn_get_pcg_tuning(ppn_pcg_tuning* buf, int cap, int* n_written);
+
 PPN_API ppn_status ppn_set_profiling(ppn_scene* s, int on);
 PPN_API ppn_status ppn_get_kernel_times(const ppn_scene* s, ppn_kernel_time* buf, int cap, int* n_written);
 

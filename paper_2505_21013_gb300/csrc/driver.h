@@ -12,6 +12,7 @@
 #pragma once
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -34,35 +35,58 @@ namespace ppn {
     }                                                                                     \
   } while (0)
 
-// Online choice between the two streamed layouts of the single-reduction FP32
-// PCG (vectors in shared memory with the blocks streamed, or everything in
-// global memory), which give bitwise-identical results.  Per shape class (CTA
-// tiles, blocks per row) the first launches alternate the layouts, each timed
-// by CUDA events on the launching stream; later launches take the layout with
-// the smaller time per CG iteration.  Shared by all groups of the process.
+// Online choice of the launch configuration of the single-reduction FP32 PCG among
+// configurations that give bitwise-identical results: the streamed layouts (vectors in
+// shared memory with the blocks streamed, or everything in global memory) and the L2
+// priority of the streamed blocks (evict-first, which keeps the vectors resident while a
+// matrix larger than L2 streams past, or normal, which lets a smaller matrix stay
+// resident across iterations).  A choice is layout (0 streamed, 1 global) + 2 x priority
+// (0 evict-first, 1 normal).  Per shape class (CTA tiles, blocks per row, log2 of the
+// launch's matrix in MB) the first launches try every allowed choice kExplore times,
+// each timed by CUDA events on the launching stream; later launches take the choice
+// with the smallest time per CG iteration.  Shared by all groups of the process.
 struct PcgTuner {
-  static constexpr int kExplore = 3;  // timed launches per layout before choosing
+  static constexpr int kExplore = 2, kChoices = 4;
+  using Key = std::array<int, 3>;
   struct Rec {
-    double ms[2] = {0.0, 0.0};
-    long long iters[2] = {0, 0};
-    int n[2] = {0, 0};
+    double ms[kChoices] = {0.0, 0.0, 0.0, 0.0};
+    long long iters[kChoices] = {0, 0, 0, 0};
+    int n[kChoices] = {0, 0, 0, 0};
+    unsigned allowed = 0;
   };
   std::mutex mu;
-  std::map<std::pair<int, int>, Rec> recs;
-  // 0: SR_STREAM, 1: SR_GLOBAL
-  int choose(std::pair<int, int> key) {
+  std::map<Key, Rec> recs;
+  int choose(const Key& key, unsigned allowed) {
     std::lock_guard<std::mutex> lk(mu);
-    const Rec& r = recs[key];
-    if (r.n[0] < kExplore || r.n[1] < kExplore) return r.n[0] <= r.n[1] ? 0 : 1;
-    return r.ms[0] / (double)r.iters[0] <= r.ms[1] / (double)r.iters[1] ? 0 : 1;
+    Rec& r = recs[key];
+    r.allowed = allowed;
+    int pick = -1;
+    for (int k = 0; k < kChoices; ++k)  // explore: the least-tried allowed choice
+      if ((allowed >> k) & 1u && r.n[k] < kExplore && (pick < 0 || r.n[k] < r.n[pick])) pick = k;
+    if (pick >= 0) return pick;
+    double best = 0.0;
+    for (int k = 0; k < kChoices; ++k) {
+      if (!((allowed >> k) & 1u)) continue;
+      const double t = r.ms[k] / (double)std::max(1ll, r.iters[k]);
+      if (pick < 0 || t < best) {
+        pick = k;
+        best = t;
+      }
+    }
+    return pick;
   }
-  void report(std::pair<int, int> key, int k, double ms, long long iters) {
+  void report(const Key& key, int k, double ms, long long iters) {
     if (iters <= 0 || !(ms > 0.0)) return;
     std::lock_guard<std::mutex> lk(mu);
     Rec& r = recs[key];
     r.ms[k] += ms;
     r.iters[k] += iters;
     r.n[k] += 1;
+  }
+  // the records, for ppn_get_pcg_tuning
+  std::vector<std::pair<Key, Rec>> snapshot() {
+    std::lock_guard<std::mutex> lk(mu);
+    return std::vector<std::pair<Key, Rec>>(recs.begin(), recs.end());
   }
 };
 inline PcgTuner& pcg_tuner() {
@@ -93,7 +117,8 @@ struct Group {
   int pcg_sr_mode = 0;          // its layout (SR_RES, SR_STREAM, SR_GLOBAL)
   // layout chosen per launch by the tuner (SR_STREAM and SR_GLOBAL both fit)
   bool pcg_tune = false;
-  std::pair<int, int> tune_key{0, 0};
+  PcgTuner::Key tune_key{0, 0, 0};
+  unsigned tune_allowed = 0;      // allowed tuner choices for that table
   size_t tune_bytes[2] = {0, 0};  // dynamic shared memory of SR_STREAM, SR_GLOBAL
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};
   bool tune_pending = false;      // a timed launch awaits its sync
@@ -374,10 +399,12 @@ struct Driver {
         L.zrec_bytes[k] = sizeof(T) * 16 * (size_t)G.S[sl[k]]->nv;
       }
       const bool tune = G.pcg_sr && G.pcg_tune && ids.size() <= (size_t)PCG_MAX_SCENES;
+      L.l2_keep = std::getenv("PPN_PCG_L2_KEEP") ? 1 : 0;
       if (tune) {
-        G.tune_choice = pcg_tuner().choose(G.tune_key);
-        L.sr_mode = G.tune_choice ? SR_GLOBAL : SR_STREAM;
-        L.smem_bytes = G.tune_bytes[G.tune_choice];
+        G.tune_choice = pcg_tuner().choose(G.tune_key, G.tune_allowed);
+        L.sr_mode = (G.tune_choice & 1) ? SR_GLOBAL : SR_STREAM;
+        L.l2_keep = G.tune_choice >> 1;
+        L.smem_bytes = G.tune_bytes[G.tune_choice & 1];
         for (cudaEvent_t& e : G.tune_ev)
           if (!e && cudaEventCreate(&e) != cudaSuccess) {
             set_error("cudaEventCreate failed");
@@ -512,9 +539,16 @@ struct Driver {
         G.pcg_smem_grid = grid;
         G.pcg_sr = true;
         G.pcg_sr_mode = mode;
-        G.pcg_tune = mode == SR_STREAM && fits[SR_GLOBAL];
+        // tuned: the streamed layouts that fit, each at both L2 priorities (not when a
+        // switch fixes the layout)
+        G.pcg_tune = (mode == SR_STREAM || mode == SR_GLOBAL) && !f_str && !f_gl;
         if (G.pcg_tune) {
-          G.tune_key = {(max_items + PCG_TILE - 1) / PCG_TILE, max_blocks / std::max(1, max_items)};
+          double mat = 0.0;
+          for (int k : sl) mat += (double)G.S[k]->nnzb * (9 * sizeof(float) + 4);
+          int lg = 0;
+          while (lg < 30 && (double)(1ll << (lg + 1)) <= mat / 1e6) ++lg;
+          G.tune_key = {(max_items + PCG_TILE - 1) / PCG_TILE, max_blocks / std::max(1, max_items), lg};
+          G.tune_allowed = (mode == SR_STREAM ? 0x5u : 0u) | (fits[SR_GLOBAL] ? 0xAu : 0u);
           G.tune_bytes[0] = bytes[SR_STREAM];
           G.tune_bytes[1] = bytes[SR_GLOBAL];
         }

@@ -318,6 +318,32 @@ __global__ void __launch_bounds__(TILE, 4) k_assemble(const SceneDev<T>* scenes,
 }
 
 // ----------------------------------------------------- K6 incremental update
+// dH contributions of block k from the elements selected in round rd, summed in the
+// block's contribution order; the map entries and the stamps are loaded eight at a
+// time so that a block's list is not one dependent load after another.  Returns
+// whether any contribution matched.
+template <typename T>
+__device__ __forceinline__ bool round_contributions(const SceneDev<T>& S, int k, int rd, T* acc) {
+#pragma unroll
+  for (int c = 0; c < 9; ++c) acc[c] = (T)0;
+  bool any = false;
+  const int cb = S.blk_ptr[k], ce = S.blk_ptr[k + 1];
+  for (int c0 = cb; c0 < ce; c0 += 8) {
+    int src[8], hit[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) src[u] = c0 + u < ce ? S.blk_src[c0 + u] : -1;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) hit[u] = src[u] >= 0 && S.round_stamp[src[u] >> 4] == rd;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (hit[u]) {
+        any = true;
+        add_elem_block(S.dH + (size_t)(src[u] >> 4) * HE_STRIDE, (src[u] >> 2) & 3, src[u] & 3, acc);
+      }
+  }
+  return any;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_update(const SceneDev<T>* scenes, const TileRef* tiles) {
   const TileRef tr = tiles[blockIdx.x];
@@ -327,19 +353,8 @@ __global__ void __launch_bounds__(TILE) k_update(const SceneDev<T>* scenes, cons
   if (k >= S.nnzb) return;
   const int i = S.blk_row[k], j = S.col[k];
   if (S.fixed[i] || S.fixed[j]) return;
-  const int rd = S.round_id;
   T acc[9];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) acc[c] = (T)0;
-  bool any = false;
-  for (int c = S.blk_ptr[k]; c < S.blk_ptr[k + 1]; ++c) {
-    const int src = S.blk_src[c];
-    const int e = src >> 4;
-    if (S.round_stamp[e] != rd) continue;
-    any = true;
-    add_elem_block(S.dH + (size_t)e * HE_STRIDE, (src >> 2) & 3, src & 3, acc);
-  }
-  if (!any) return;
+  if (!round_contributions(S, k, S.round_id, acc)) return;
 #pragma unroll
   for (int c = 0; c < 9; ++c) S.val[(size_t)c * S.nnzb + k] += acc[c];
 }
@@ -382,16 +397,8 @@ __global__ void __launch_bounds__(TILE) k_update_touched(const SceneDev<T>* scen
   const int q = tr.tile * TILE + threadIdx.x;
   if (q >= S.ctl->n_touched) return;
   const int k = S.touched[q];
-  const int rd = S.round_id;
   T acc[9];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) acc[c] = (T)0;
-  for (int c = S.blk_ptr[k]; c < S.blk_ptr[k + 1]; ++c) {
-    const int src = S.blk_src[c];
-    const int e = src >> 4;
-    if (S.round_stamp[e] != rd) continue;
-    add_elem_block(S.dH + (size_t)e * HE_STRIDE, (src >> 2) & 3, src & 3, acc);
-  }
+  round_contributions(S, k, S.round_id, acc);
 #pragma unroll
   for (int c = 0; c < 9; ++c) S.val[(size_t)c * S.nnzb + k] += acc[c];
 }

@@ -64,6 +64,7 @@ struct PcgLaunch {
   size_t smem_bytes;     // > 0: shared-memory-resident kernel with this dynamic size
   int smem_blocks;       // block capacity of that layout (max blocks of one CTA)
   int sr_mode;           // single-reduction kernel: SR_RES, SR_STREAM, SR_GLOBAL or SR_HALO
+  int l2_keep;           // SR_STREAM, SR_GLOBAL: 0 streamed blocks evict-first in L2, 1 at normal priority
   // SR_HALO tables, device (built by the host for this tile table and grid):
   //   halo_off[2 b], halo_off[2 b + 1]: first block and first halo row of CTA b (b <= grid)
   //   halo_col[k]: local column of the launch's k-th block (CTA order, rows ascending):

@@ -182,6 +182,13 @@ __device__ __forceinline__ unsigned long long l2_evict_first() {
   asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
+// the same loads at normal L2 priority: a matrix smaller than L2 can stay resident across
+// iterations (a batch of small scenes); the tuner chooses per shape class
+__device__ __forceinline__ unsigned long long l2_evict_normal() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ float ld_stream(const float* a, unsigned long long pol) {
   float v;
   asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
@@ -246,7 +253,7 @@ template <int MODE>
 __global__ void __launch_bounds__(NTP, 1)
     k_pcg_sr(const SceneDev<float>* scenes, const TileRef* tiles, int n_tiles, const int* scene_ids,
                int n_scenes, GridBar* bar, int b_from_g, int nb_cap, unsigned long long* flags,
-               const int* halo_off, const int* halo_col, const int* halo_ref, int nh_cap) {
+               const int* halo_off, const int* halo_col, const int* halo_ref, int nh_cap, int l2_keep) {
   using W = Words<float>;
   constexpr bool HALO = MODE == SR_HALO, RES = MODE == SR_RES || HALO, GV = MODE == SR_GLOBAL;
   constexpr int MS = HALO ? HALO_MAX_SCENES : PCG_MAX_SCENES;  // scenes of one launch
@@ -542,7 +549,7 @@ __global__ void __launch_bounds__(NTP, 1)
   };
   // w = A u over this CTA's rows (GP lanes per row), u gathered from the global array or, in
   // SR_HALO, from shared memory; SR_HALO also stores w as stamped words (stamp s, buffer par)
-  const unsigned long long pol = RES ? 0ull : l2_evict_first();
+  const unsigned long long pol = RES ? 0ull : l2_keep ? l2_evict_normal() : l2_evict_first();
   // the tile partials of tile lt (stamp s, buffer par): the fixed tree over its eight
   // 16-row group sums, posted as stamped words
   auto post_tile = [&](int lt, unsigned s, int par, int nq) {
@@ -1043,9 +1050,10 @@ cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cud
   const int* h_col = halo ? L.halo_col : nullptr;
   const int* h_ref = halo ? L.halo_ref : nullptr;
   int nh_cap = halo ? L.halo_cap : 0;
+  int l2_keep = L.l2_keep;
   void* args[] = {(void*)&scenes, (void*)&tiles, (void*)&n_tiles, (void*)&ids,   (void*)&n_scenes,
                   (void*)&bar,    (void*)&bg,    (void*)&nb_cap,  (void*)&flags, (void*)&h_off,
-                  (void*)&h_col,  (void*)&h_ref, (void*)&nh_cap};
+                  (void*)&h_col,  (void*)&h_ref, (void*)&nh_cap, (void*)&l2_keep};
   const void* k = sr_kernel(L.sr_mode);
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
   if (e != cudaSuccess) return e;

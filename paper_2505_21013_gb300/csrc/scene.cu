@@ -1136,6 +1136,41 @@ ppn_status ppn_get_attempts(const ppn_scene* s, ppn_attempt* buf, int cap, int* 
   });
 }
 
+ppn_status ppn_get_pcg_tuning(ppn_pcg_tuning* buf, int cap, int* n_written) {
+  if (cap < 0 || (cap > 0 && !buf)) {
+    set_error("cap < 0, or a null buffer with cap > 0");
+    return PPN_ERR_INVALID_ARG;
+  }
+  const auto recs = pcg_tuner().snapshot();
+  int i = 0;
+  for (const auto& kv : recs) {
+    if (i < cap) {
+      ppn_pcg_tuning& o = buf[i];
+      o.tiles_per_cta = kv.first[0];
+      o.blocks_per_row = kv.first[1];
+      o.log2_matrix_mb = kv.first[2];
+      const PcgTuner::Rec& r = kv.second;
+      bool done = true;
+      int best = -1;
+      double bt = 0.0;
+      for (int k = 0; k < PcgTuner::kChoices; ++k) {
+        o.launches[k] = r.n[k];
+        o.us_per_iter[k] = r.iters[k] > 0 ? 1e3 * r.ms[k] / (double)r.iters[k] : 0.0;
+        if (!((r.allowed >> k) & 1u)) continue;
+        if (r.n[k] < PcgTuner::kExplore) done = false;
+        if (r.iters[k] > 0 && (best < 0 || o.us_per_iter[k] < bt)) {
+          best = k;
+          bt = o.us_per_iter[k];
+        }
+      }
+      o.choice = done ? best : -1;
+    }
+    ++i;
+  }
+  if (n_written) *n_written = i;
+  return PPN_OK;
+}
+
 ppn_status ppn_set_record_selection(ppn_scene* s, int on) {
   return dispatch(s, [&](auto& x) {
     x.record_sel = on != 0;

@@ -79,6 +79,15 @@ class ppn_step_stats(C.Structure):
                 ("device_ms", C.c_double), ("n_ties", C.c_int)]
 
 
+class ppn_pcg_tuning(C.Structure):
+    _fields_ = [("tiles_per_cta", C.c_int), ("blocks_per_row", C.c_int), ("log2_matrix_mb", C.c_int),
+                ("choice", C.c_int), ("launches", C.c_int * 4), ("us_per_iter", C.c_double * 4)]
+
+
+PCG_TUNING_CHOICES = {0: "streamed, evict-first", 1: "global, evict-first", 2: "streamed, L2 normal",
+                      3: "global, L2 normal", -1: "exploring"}
+
+
 class ppn_server_config(C.Structure):
     _fields_ = [("hbm_fraction", C.c_double), ("max_batch", C.c_int), ("precision", C.c_int)]
 
@@ -134,6 +143,7 @@ SIGNATURES = {
     "ppn_set_record_selection": (_st, [_P, C.c_int]),
     "ppn_get_attempt_selection": (_st, [_P, C.c_int, _pi, C.c_int64, _pl]),
     "ppn_probe_tets": (_st, [_P, _pi]),
+    "ppn_get_pcg_tuning": (_st, [C.POINTER(ppn_pcg_tuning), C.c_int, C.POINTER(C.c_int)]),
     "ppn_get_iteration_gradient": (_st, [_P, C.c_int, _pd]),
     "ppn_get_state": (_st, [_P, _pd, _pd]),
     "ppn_set_state": (_st, [_P, _pd, _pd]),
@@ -464,6 +474,19 @@ def probe_halo_tables(patterns, grid: int):
     off = out[:no].reshape(grid + 1, 2)
     nb = int(off[grid, 0])
     return off, out[no:no + nb], out[no + nb:], int(mh.value)
+
+
+def pcg_tuning():
+    """``ppn_get_pcg_tuning``: the linear solver's autotuner records, one dict per shape class."""
+    buf = (ppn_pcg_tuning * 64)()
+    n = C.c_int()
+    _check(lib().ppn_get_pcg_tuning(buf, 64, C.byref(n)), "ppn_get_pcg_tuning")
+    out = []
+    for i in range(min(n.value, 64)):
+        d = struct_dict(buf[i])
+        d["kept"] = PCG_TUNING_CHOICES.get(d["choice"], "?")
+        out.append(d)
+    return out
 
 
 def ppn_step_batch(scenes, modes, tol):

@@ -346,3 +346,28 @@ def test_pcg_curvature_exit_follows_the_oracle(prec):
     xg, info = g.probe_pcg(v2, b, rel_tol=1e-4)
     xo, info_o = O.pcg_bsr(rp, col, v2, b.reshape(-1), rel_tol=1e-4, max_iter=5000)
     assert not info_o["ind"] and not info["ind"] and not info["hit_max"]
+
+
+def test_l2_priority_of_streamed_blocks_changes_no_bits(monkeypatch):
+    # the autotuner's L2 priority of the streamed BSR blocks (evict-first or normal) is a
+    # cache hint only: each streamed layout gives the same iterates at both priorities
+    spec = medium_spec(28)
+    o = O.Scene.from_spec(spec)
+    vals = o.assemble(spec.rest)
+    b = np.random.default_rng(29).standard_normal((spec.n_verts, 3))
+    b[spec.fixed] = 0
+    runs = []
+    for env in ("PPN_PCG_STREAM", "PPN_PCG_SR_GLOBAL"):
+        for keep in (False, True):
+            if keep:
+                monkeypatch.setenv("PPN_PCG_L2_KEEP", "1")
+            else:
+                monkeypatch.delenv("PPN_PCG_L2_KEEP", raising=False)
+            runs.append(_probe_layout(spec, vals, b, env, monkeypatch))
+    monkeypatch.delenv("PPN_PCG_L2_KEEP", raising=False)
+    assert [r[2] for r in runs] == ["streamed", "streamed", "global", "global"]
+    for x, info, _ in runs:
+        assert info == runs[0][1] and np.array_equal(x, runs[0][0])
+    # the tuner reports its shape classes through the C ABI
+    rec = P.ppn.pcg_tuning()
+    assert isinstance(rec, list)
