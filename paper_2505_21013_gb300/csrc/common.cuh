@@ -82,6 +82,7 @@ struct SceneDev {
   const int* blk_row;      // nnzb
   const int* blk_ptr;      // nnzb+1 block -> contributions (tet << 4 | a << 2 | b)
   const int* blk_src;
+  const unsigned char* blk_lane;  // nmap: the block of each contribution, modulo 32 (its lane in k_assemble)
   const int* diag_idx;     // nv
   const int* tet_blk;      // nt x 16: BSR block of each (a, b) corner pair of a tet
   // state

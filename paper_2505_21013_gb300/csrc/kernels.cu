@@ -212,8 +212,33 @@ __global__ void __launch_bounds__(TILE) k_gradient(const SceneDev<T>* scenes, co
 }
 
 // ------------------------------------------------------------- K3 assembly
+// FP32 records: block t (floats 9t..9t+8 of a 16-byte-aligned record) lies within the
+// three 16-byte words that start at float 9t - (t mod 4), since 9t mod 4 = t mod 4 <= 3:
+// three aligned vector loads instead of nine scalar ones, then the nine values by offset
+__device__ __forceinline__ void elem_block_f(const float* rec, int t, float* blk) {
+  const int o = t & 3;
+  const float4* p = reinterpret_cast<const float4*>(rec + 9 * t - o);
+  const float4 x = __ldg(p), y = __ldg(p + 1), z = __ldg(p + 2);
+  const float w[12] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, z.x, z.y, z.z, z.w};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) blk[k] = o == 0 ? w[k] : o == 1 ? w[k + 1] : o == 2 ? w[k + 2] : w[k + 3];
+}
 template <typename T>
 __device__ __forceinline__ void add_elem_block(const T* rec, int a, int b, T* acc) {
+  if constexpr (sizeof(T) == 4) {
+    float p[9];
+    elem_block_f(rec, a <= b ? tri4(a, b) : tri4(b, a), p);
+    if (a <= b) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc[k] += p[k];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc[3 * i + k] += p[3 * k + i];
+    }
+    return;
+  }
   if (a <= b) {
     const T* p = rec + 9 * tri4(a, b);
 #pragma unroll
@@ -229,17 +254,17 @@ __device__ __forceinline__ void add_elem_block(const T* rec, int a, int b, T* ac
 
 // A warp assembles 32 consecutive blocks from their contribution list (the
 // blocks' (tet, a, b) sources, contiguous in blk_src), 32 contributions at a time:
-// lane l loads contribution c0 + l, a segmented scan across the warp sums the
+// lane l loads contribution c0 + l and its block's place among the warp's 32 (a
+// byte per contribution, built at scene creation), a segmented scan across the warp sums the
 // contributions of each block in the chunk, and the last lane of each block's
 // run adds the run's sum to the block's total in shared memory (chunks in
 // order).  Work per warp follows the number of contributions, not the longest
 // block (a diagonal block has ~24, an off-diagonal one ~4-6).  Then lane l writes
 // block k0 + l, with the inertia (and contact) terms on the diagonal.
 template <typename T>
-__global__ void __launch_bounds__(TILE, 4) k_assemble(const SceneDev<T>* scenes, const TileRef* tiles, int use_probe) {
+__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 6 : 4) k_assemble(const SceneDev<T>* scenes, const TileRef* tiles, int use_probe) {
   constexpr int NWA = TILE / 32;
   __shared__ T s_acc[NWA][32][9];
-  __shared__ int s_end[NWA][32];
   const TileRef tr = tiles[blockIdx.x];
   const SceneDev<T>& S = scenes[tr.scene];
   if (!S.active) return;
@@ -250,30 +275,44 @@ __global__ void __launch_bounds__(TILE, 4) k_assemble(const SceneDev<T>* scenes,
   const int it = S.it_id;
 #pragma unroll
   for (int c = 0; c < 9; ++c) s_acc[warp][lane][c] = (T)0;
-  s_end[warp][lane] = S.blk_ptr[k0 + min(lane, nk - 1) + 1];  // end of each block's contributions
-  const int cb = S.blk_ptr[k0], ce = s_end[warp][nk - 1];
+  const int cb = S.blk_ptr[k0], ce = S.blk_ptr[k0 + nk];
   __syncwarp();
+  // the next chunk's sources are loaded one chunk ahead, so that a chunk's element
+  // blocks are one dependent load away from the loop's start
+  int src_n = 0, bl_n = nk;
+  if (cb + lane < ce) {
+    src_n = S.blk_src[cb + lane];
+    bl_n = S.blk_lane[cb + lane];
+  }
   for (int cbase = cb; cbase < ce; cbase += 32) {
     const int c = cbase + lane;
+    const int src = src_n;
+    int bl = bl_n;  // local block of contribution c (the warp's blocks start at a multiple of 32); nk: none
+    if (c + 32 < ce) {
+      src_n = S.blk_src[c + 32];
+      bl_n = S.blk_lane[c + 32];
+    } else {
+      bl_n = nk;
+    }
     T v[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) v[q] = (T)0;
-    int bl = nk;  // local block of contribution c: the number of block ends <= c
     if (c < ce) {
-      int lo = 0, hi = nk - 1;  // first block whose end is > c
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (s_end[warp][mid] > c) hi = mid; else lo = mid + 1;
-      }
-      bl = lo;
-      const int src = S.blk_src[c];
       const int e = src >> 4, a = (src >> 2) & 3, b = src & 3;
       add_elem_block(S.He + (size_t)e * HE_STRIDE, a, b, v);
       if (S.proj_stamp[e] == it) add_elem_block(S.dH + (size_t)e * HE_STRIDE, a, b, v);
     }
-    // inclusive sums over each run of equal bl (bl non-decreasing across lanes)
+    // inclusive sums over each run of equal bl (bl non-decreasing across lanes); a run of
+    // length L needs the offsets below L, so the rounds stop at the chunk's longest run
+    // (the rounds left out would add nothing: the same sums)
+    const int bp = __shfl_up_sync(0xffffffffu, bl, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || bp != bl);
+    const unsigned later = heads & ~((2u << lane) - 1u);  // heads above this lane (none for lane 31)
+    const int run = (later ? __ffs(later) - 1 : 32) - lane;  // a head's run length
+    const int longest = (int)__reduce_max_sync(0xffffffffu, (heads >> lane) & 1u ? (unsigned)run : 0u);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
+      if (o >= longest) break;  // warp-uniform
       const int bo = __shfl_up_sync(0xffffffffu, bl, o);
 #pragma unroll
       for (int q = 0; q < 9; ++q) {

@@ -359,6 +359,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   int* d_blk_row = alloc<int>(nnzb);
   int* d_blk_ptr = alloc<int>(nnzb + 1);
   int* d_blk_src = alloc<int>((size_t)16 * nt);
+  unsigned char* d_blk_lane = alloc<unsigned char>((size_t)16 * nt);
   int* d_diag = alloc<int>(nv);
   int* d_tet_blk = alloc<int>((size_t)16 * nt);
   s.blk_mark = alloc<int>(nnzb);
@@ -413,7 +414,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   d_etiles = alloc<TileRef>(et.size());
   d_projtiles = alloc<TileRef>(jt.size());
   if (!d_tets || !d_tetc || !d_mass || !d_fixed || !d_con || !s.tgt || !d_X || !d_vt_ptr || !d_vt_src || !d_row_ptr ||
-      !d_col || !d_blk_row || !d_blk_ptr || !d_blk_src || !d_diag || !d_tet_blk || !s.blk_mark || !s.touched || !s.u || !s.u_n || !s.vel ||
+      !d_col || !d_blk_row || !d_blk_ptr || !d_blk_src || !d_blk_lane || !d_diag || !d_tet_blk || !s.blk_mark || !s.touched || !s.u || !s.u_n || !s.vel ||
       !s.uhat || !s.u_probe || !s.ge || !s.He || !s.dH || !s.g || !s.gmax || !s.val ||
       !s.proj_stamp || !s.round_stamp || !s.cproj_stamp || !d_obs || !s.cround_stamp || !s.dHc || !s.Hc || !s.sel_list || !s.dx || !s.r || !s.z || !s.q || !s.d0 ||
       !s.d1 || !s.Pinv || !s.vpart || !s.tpart || !s.ppart || !s.pword || (sizeof(T) == 4 && !s.zrec) || !s.ctl || !d_desc || !d_ids ||
@@ -445,6 +446,12 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   PPN_CU(up(d_blk_row, blk_row.data(), sizeof(int) * nnzb));
   PPN_CU(up(d_blk_ptr, blk_ptr.data(), sizeof(int) * (nnzb + 1)));
   PPN_CU(up(d_blk_src, blk_src.data(), sizeof(int) * blk_src.size()));
+  {
+    std::vector<unsigned char> lane((size_t)16 * nt);
+    for (int k = 0; k < nnzb; ++k)
+      for (int cc = blk_ptr[k]; cc < blk_ptr[k + 1]; ++cc) lane[cc] = (unsigned char)(k & 31);
+    PPN_CU(up(d_blk_lane, lane.data(), lane.size()));
+  }
   PPN_CU(up(d_diag, diag_idx.data(), sizeof(int) * nv));
   PPN_CU(up(d_tet_blk, blk_of.data(), sizeof(int) * blk_of.size()));
   PPN_CU(cudaMemset(s.blk_mark, 0xff, sizeof(int) * nnzb));
@@ -484,6 +491,7 @@ ppn_status SceneImpl<T>::init(const double* rest_xyz, int64_t n_verts, const int
   s.blk_row = d_blk_row;
   s.blk_ptr = d_blk_ptr;
   s.blk_src = d_blk_src;
+  s.blk_lane = d_blk_lane;
   s.diag_idx = d_diag;
   s.tet_blk = d_tet_blk;
   s.dt = dt;
