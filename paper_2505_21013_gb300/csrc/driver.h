@@ -469,19 +469,28 @@ struct Driver {
     G.halo_cap = 0;
     if (std::getenv("PPN_PCG_GLOBAL")) return;
     const int n_tiles = (int)tt.size();
-    // largest rows / blocks of one CTA when n_tiles are split over `grid` CTAs
+    // largest rows / blocks of one CTA when n_tiles are split over `grid` CTAs, and the
+    // largest slot count of the single-reduction kernel's resident layouts (per 16-row
+    // group, 32 slots per step of ceil(longest row / 2))
+    int max_slots = 0;
     auto layout = [&](int grid, int& max_items, int& max_blocks) {
-      max_items = max_blocks = 0;
+      max_items = max_blocks = max_slots = 0;
       for (int b = 0; b < grid; ++b) {
         const int t0 = (int)(((long long)b * n_tiles) / grid), t1 = (int)(((long long)(b + 1) * n_tiles) / grid);
-        int blocks = 0;
+        int blocks = 0, slots = 0;
         for (int t = t0; t < t1; ++t) {
           const SceneImpl<T>& sc = *G.S[sl[tt[t].scene]];
           const int r0 = tt[t].tile * PCG_TILE, r1 = std::min(sc.nv, r0 + PCG_TILE);
           if (r1 > r0) blocks += (int)(sc.h_row_ptr[r1] - sc.h_row_ptr[r0]);
+          for (int g = r0; g < r1; g += 16) {
+            int m = 0;
+            for (int r = g; r < std::min(r1, g + 16); ++r) m = std::max(m, (int)(sc.h_row_ptr[r + 1] - sc.h_row_ptr[r]));
+            slots += 32 * ((m + 1) / 2);
+          }
         }
         max_items = std::max(max_items, (t1 - t0) * PCG_TILE);
         max_blocks = std::max(max_blocks, blocks);
+        max_slots = std::max(max_slots, slots);
       }
     };
     int dev = 0, n_sm = 0;
@@ -499,7 +508,7 @@ struct Driver {
       bool fits[3] = {false, false, false};
       size_t bytes[3];
       for (int mode = first; mode <= SR_GLOBAL; ++mode) {
-        bytes[mode] = pcg_sr_smem_bytes(max_items, mode == SR_RES ? max_blocks : 0, 0, mode);
+        bytes[mode] = pcg_sr_smem_bytes(max_items, mode == SR_RES ? max_slots : 0, 0, mode);
         fits[mode] = bytes[mode] <= (size_t)212 * 1024 && pcg_sr_max_grid(dev, bytes[mode], mode) >= grid;
         if (fits[mode] && (mode == SR_RES || f_str || f_gl)) break;
       }
@@ -507,7 +516,7 @@ struct Driver {
           !std::getenv("PPN_PCG_NO_HALO")) {
         std::vector<int> tab;
         const int nh = build_halo(sl, grid, tab);
-        const size_t hb = nh < 0 ? 0 : pcg_sr_smem_bytes(max_items, max_blocks, nh, SR_HALO);
+        const size_t hb = nh < 0 ? 0 : pcg_sr_smem_bytes(max_items, max_slots, nh, SR_HALO);
         if (nh >= 0 && hb <= (size_t)227 * 1024 && pcg_sr_max_grid(dev, hb, SR_HALO) >= grid) {
           if (tab.size() > G.cap_halo) {
             if (G.d_halo) {  // (cudaFree waits for launches that may still read it)
@@ -524,7 +533,7 @@ struct Driver {
             G.halo_ref = G.halo_col + tab[2 * grid];
             G.halo_cap = nh;
             G.pcg_smem_bytes = hb;
-            G.pcg_smem_blocks = max_blocks;
+            G.pcg_smem_blocks = max_slots;
             G.pcg_smem_grid = grid;
             G.pcg_sr = true;
             G.pcg_sr_mode = SR_HALO;
@@ -535,7 +544,7 @@ struct Driver {
       for (int mode = first; mode <= SR_GLOBAL; ++mode) {
         if (!fits[mode]) continue;
         G.pcg_smem_bytes = bytes[mode];
-        G.pcg_smem_blocks = mode == SR_RES ? max_blocks : 0;
+        G.pcg_smem_blocks = mode == SR_RES ? max_slots : 0;
         G.pcg_smem_grid = grid;
         G.pcg_sr = true;
         G.pcg_sr_mode = mode;

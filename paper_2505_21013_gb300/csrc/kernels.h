@@ -62,7 +62,7 @@ struct PcgLaunch {
   int group;             // lanes per BSR row (4 or 8)
   int use_b_from_g;      // 1: b = -g of the scene; 0: b given in r (probe)
   size_t smem_bytes;     // > 0: shared-memory-resident kernel with this dynamic size
-  int smem_blocks;       // block capacity of that layout (max blocks of one CTA)
+  int smem_blocks;       // block capacity of that layout (max blocks of one CTA; k_pcg_sr: max slots)
   int sr_mode;           // single-reduction kernel: SR_RES, SR_STREAM, SR_GLOBAL or SR_HALO
   int l2_keep;           // SR_STREAM, SR_GLOBAL: 0 streamed blocks evict-first in L2, 1 at normal priority
   // SR_HALO tables, device (built by the host for this tile table and grid):

@@ -64,6 +64,7 @@ namespace {
 constexpr int NTP = 512;  // threads per CTA
 constexpr int NQ = 4;     // reduction slots: gamma, delta, rho, failed diagonal blocks
 constexpr int SP_GP = 2;  // lanes per BSR row in the SpMV
+static_assert(SP_GP == 2, "the resident blocks' slots pair the two lanes of a row");
 
 // SpMV lanes: a warp works on 32 / SP_GP consecutive rows; its lanes 0..15 take the
 // first lane of each row, lanes 16..31 the second.  An 8-lane phase of a 16-byte
@@ -74,13 +75,25 @@ constexpr int SP_GP = 2;  // lanes per BSR row in the SpMV
 __device__ __forceinline__ int spmv_row(int tid) { return (tid >> 5) * (32 / SP_GP) + (tid & (32 / SP_GP - 1)); }
 __device__ __forceinline__ int spmv_lane(int tid) { return (tid & 31) / (32 / SP_GP); }
 
+// Resident blocks by slot.  The 16 rows of a warp's SpMV group (items 16 g .. 16 g + 15)
+// take their blocks in steps: step j holds block 2 j + h of row r in lane 16 h + r, the
+// lane that multiplies it, so that every shared-memory load of the SpMV (a column, one of
+// a block's nine values) reads 32 consecutive words, free of bank conflicts.  A group
+// has ceil(longest row / 2) steps; the slots past a shorter row's end stay unused.  Slot
+// q = 32 (lgb[g] + j) + lane; value c of the block in slot q is at lval[288 (q / 32) + 32 c + q % 32].
+__device__ __forceinline__ int blk_slot(const int* lgb, int item, int k) {
+  return (lgb[item >> 4] + (k >> 1)) * 32 + 16 * (k & 1) + (item & 15);
+}
+__device__ __forceinline__ int slot_val(int q, int c) { return (q >> 5) * 288 + 32 * c + (q & 31); }
+
 struct SrLayout {
   float* lws;    // [(ni / PCG_TILE + 1) * 16 * NQ] partial sums per 16-row group (8 per tile)
   TileRef* ltt;  // [ni / PCG_TILE + 1] the CTA's tiles
   int* ltc;      // [ni / PCG_TILE + 1] groups of each tile done in the current SpMV
-  int* lrp;      // SR_RES, SR_HALO: [ni + 1] local row pointers
-  int* lcol;     // SR_RES: [nb] columns; SR_HALO: [nb] local columns (own item, or ni + halo index)
-  float* lval;   // SR_RES, SR_HALO: [nb * 9]
+  int* lrp;      // SR_RES, SR_HALO: [ni + 1] local row pointers (blocks in CTA order)
+  int* lgb;      // SR_RES, SR_HALO: [ni / 16 + 1] first slot step of each 16-row group
+  int* lcol;     // SR_RES: [nb] columns; SR_HALO: [nb] local columns (own item, or ni + halo index); by slot
+  float* lval;   // SR_RES, SR_HALO: [nb * 9] by slot step: nine runs of 32 values
   float* lP;     // SR_RES, SR_STREAM: [ni * 6] inverse (00 01 02 11 12 22 of the symmetric block)
   float *lx, *lr, *lu, *lw, *lp, *ls;  // SR_RES, SR_STREAM: [ni * 3] each (SR_HALO: in registers)
   float4* lu4;   // SR_HALO: [ni + nh] u of the own rows, then of the halo rows (w while it arrives)
@@ -105,6 +118,7 @@ __host__ __device__ inline size_t carve_sr(char* base, int ni, int nb, int nh, i
   l.ltt = (TileRef*)take(sizeof(TileRef) * ntl);
   if (mode == SR_RES || mode == SR_HALO) {
     l.lrp = (int*)take(sizeof(int) * (ni + 1));
+    l.lgb = (int*)take(sizeof(int) * (ni / 16 + 1));
     l.lcol = (int*)take(sizeof(int) * nb);
     l.lval = (float*)take(sizeof(float) * 9 * nb);
   }
@@ -370,6 +384,25 @@ __global__ void __launch_bounds__(NTP, 1)
     }
     if (tid == 0) L.lrp[n_items] = carry;
     __syncthreads();
+    // the groups' slot steps (ceil(longest row / 2)), then their first steps; a table
+    // the planner sized too small is refused before any block is stored
+    const int ng = n_items / 16;
+    for (int g = tid; g < ng; g += NTP) {
+      int m = 0;
+      for (int r = 16 * g; r < 16 * g + 16; ++r) m = max(m, L.lrp[r + 1] - L.lrp[r]);
+      L.lgb[g + 1] = (m + 1) >> 1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      L.lgb[0] = 0;
+      for (int g = 0; g < ng; ++g) L.lgb[g + 1] += L.lgb[g];
+      if (32 * L.lgb[ng] > nb_cap) {
+        s_to = 5;
+        atomicExch(&bar->timeout, 1);
+      }
+    }
+    __syncthreads();
+    if (s_to) return;
   }
   // copy this CTA's blocks (SR_RES; SR_HALO with the local columns); without the halo, the
   // CTAs owning their columns bound the neighbour range of the u flags
@@ -384,10 +417,10 @@ __global__ void __launch_bounds__(NTP, 1)
       const size_t nb = (size_t)S.nnzb;
       for (int k = kb + lane32; k < ke; k += 32) {
         if constexpr (RES) {
-          const int b = L.lrp[item] + (k - kb);
-          L.lcol[b] = HALO ? halo_col[blk0 + b] : S.col[k];
+          const int q = blk_slot(L.lgb, item, k - kb);
+          L.lcol[q] = HALO ? halo_col[blk0 + L.lrp[item] + (k - kb)] : S.col[k];
 #pragma unroll
-          for (int c = 0; c < 9; ++c) L.lval[9 * b + c] = S.val[c * nb + k];
+          for (int c = 0; c < 9; ++c) L.lval[slot_val(q, c)] = S.val[c * nb + k];
         }
         if constexpr (!HALO) {
           const long long gt = s_toff[slot] + S.col[k] / PCG_TILE;  // tile in the launch's table
@@ -579,18 +612,29 @@ __global__ void __launch_bounds__(NTP, 1)
         const SceneLite<float>& S = sl[slot];
         const float* vb = u_ptr(S.zrec, 0);
         if constexpr (RES) {
-          const int lb = L.lrp[item], le = L.lrp[item + 1];
-          for (int b0 = lb + lane; b0 < le; b0 += GP * U) {
+          // this lane's blocks lane, lane + 2, ... of the row, in order, by slot step
+          const int len = L.lrp[item + 1] - L.lrp[item], g = item >> 4;
+          const int j0 = L.lgb[g], nj = L.lgb[g + 1] - j0;
+          for (int jb = 0; jb < nj; jb += U) {
             float4 vj[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-              const int b = b0 + GP * u;
-              if (b < le) vj[u] = HALO ? L.lu4[L.lcol[b]] : ld_f4_cg(vb + (size_t)8 * L.lcol[b]);
+              const int j = jb + u;
+              if (GP * j + lane < len) {
+                const int cl = L.lcol[(j0 + j) * 32 + lane32];
+                vj[u] = HALO ? L.lu4[cl] : ld_f4_cg(vb + (size_t)8 * cl);
+              }
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-              const int b = b0 + GP * u;
-              if (b < le) blk_mv(L.lval + 9 * b, vj[u].x, vj[u].y, vj[u].z, ax, ay, az);
+              const int j = jb + u;
+              if (GP * j + lane < len) {
+                const float* v = L.lval + (j0 + j) * 288 + lane32;
+                float a[9];
+#pragma unroll
+                for (int c = 0; c < 9; ++c) a[c] = v[32 * c];
+                blk_mv(a, vj[u].x, vj[u].y, vj[u].z, ax, ay, az);
+              }
             }
           }
         } else {
@@ -728,9 +772,9 @@ __global__ void __launch_bounds__(NTP, 1)
       const SceneLite<float>& S = sl[o_slot];
       const int i = o_row;
       float D[9], Pm[9];
-      const int bd = L.lrp[o_item] + (S.diag_idx[i] - S.row_ptr[i]);
+      const int bd = blk_slot(L.lgb, o_item, S.diag_idx[i] - S.row_ptr[i]);
 #pragma unroll
-      for (int c = 0; c < 9; ++c) D[c] = L.lval[9 * bd + c];
+      for (int c = 0; c < 9; ++c) D[c] = L.lval[slot_val(bd, c)];
       const bool ok = spd_inv3(D, Pm);
       sym6(Pm, oq);
       float* P = S.Pinv + (size_t)9 * i;
@@ -755,9 +799,9 @@ __global__ void __launch_bounds__(NTP, 1)
       const SceneLite<float>& S = sl[slot];
       float D[9];
       if constexpr (RES) {
-        const int bd = L.lrp[item] + (S.diag_idx[i] - S.row_ptr[i]);
+        const int bd = blk_slot(L.lgb, item, S.diag_idx[i] - S.row_ptr[i]);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) D[c] = L.lval[9 * bd + c];
+        for (int c = 0; c < 9; ++c) D[c] = L.lval[slot_val(bd, c)];
       } else {
 #pragma unroll
         for (int c = 0; c < 9; ++c) D[c] = S.val[(size_t)c * S.nnzb + S.diag_idx[i]];
