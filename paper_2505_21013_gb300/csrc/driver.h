@@ -183,7 +183,7 @@ struct Group {
       for (int t = 0; t < s.n_btiles; ++t) bt.push_back({i, t});
       for (int t = 0; t < s.n_ptiles; ++t) pt.push_back({i, t});
       for (int t = 0; t < s.n_ttiles + s.n_vtiles; ++t) et.push_back({i, t});
-      projcap += (s.nt + PROJ_CTA - 1) / PROJ_CTA;
+      projcap += (s.nt + PROJW_TETS - 1) / PROJW_TETS;  // (the warp form's tiles are the smaller)
     }
     n_ttiles = (int)tt.size();
     n_vtiles = (int)vt.size();
@@ -1103,11 +1103,16 @@ struct Driver {
       if (any_obstacles(on)) launch_select_contact<T>(G.d_desc, G.d_vtiles, G.n_vtiles, G.st);  // clamps them too
     });
     if ((rc = check_launch())) return rc;
+    // PN's passes over every element: one thread per tet (throughput); a PPN round's
+    // selection: the warp form (latency).  PPN_PROJECT_THREAD=1 / PPN_PROJECT_WARP=1
+    // force one form (tests, measurement)
+    const bool warp = project_warp_form(!pn);
+    const int per = warp ? PROJW_TETS : PROJ_CTA;
     std::vector<TileRef> jt;
     if (pn) {
       for (int i = 0; i < n; ++i)
         if (on[i])
-          for (int t = 0; t < (G.S[i]->nt + PROJ_CTA - 1) / PROJ_CTA; ++t) jt.push_back({i, t});
+          for (int t = 0; t < (G.S[i]->nt + per - 1) / per; ++t) jt.push_back({i, t});
     } else {
       if ((rc = G.sync_ctl())) return rc;
       for (int i = 0; i < n; ++i)
@@ -1117,13 +1122,13 @@ struct Driver {
           H[i].cur.n_new_projected += nn + nc;
           H[i].ties_pending += G.h_ctl[i].n_ties;
           H[i].tot.n_ties += G.h_ctl[i].n_ties;
-          for (int t = 0; t < (nn + PROJ_CTA - 1) / PROJ_CTA; ++t) jt.push_back({i, t});
+          for (int t = 0; t < (nn + per - 1) / per; ++t) jt.push_back({i, t});
           if (G.S[i]->record_sel && H[i].mode == PPN_MODE_PPN && (rc = record_selection(i, nn, nc))) return rc;
         }
     }
     if (jt.empty()) return PPN_OK;
     if ((rc = G.upload(G.d_projtiles, jt.data(), sizeof(TileRef) * jt.size()))) return rc;
-    timed(FAM_PROJECT, 0, [&] { launch_project<T>(G.d_desc, G.d_projtiles, (int)jt.size(), 0, G.st); });
+    timed(FAM_PROJECT, 0, [&] { launch_project<T>(G.d_desc, G.d_projtiles, (int)jt.size(), 0, G.st, warp); });
     return check_launch();
   }
 

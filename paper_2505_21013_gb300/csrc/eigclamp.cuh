@@ -167,11 +167,10 @@ PPN_HD int jacobi9(T* A, T* V) {
   return sweep;
 }
 
-// dH blocks (10 x 9, upper block triangle, tri4 order) of the clamped tet.
-// W = Dm^-1 (row a-1 = dN_a), V = rest volume.  Returns the number of clamped
-// eigenvalues of M (the three translation modes are always clamped as well).
+// The reduced problem of a tet: M (packed symmetric 9x9, s9 order) and the lift
+// S_aj = (L^-1 dN_a)_j.  W = Dm^-1 (row a-1 = dN_a), V = rest volume.
 template <typename T>
-PPN_HD int clamp_tet(const TetState<T>& st, const T* W, T Vol, T mu, T lam, T eps, bool mirror, T* out) {
+PPN_HD void reduce9(const TetState<T>& st, const T* W, T Vol, T mu, T lam, T* A, T S[4][3]) {
   T dN[4][3];
   shape_grads(W, dN);
   // G = sum_a dN_a dN_a^T and its Cholesky factor L
@@ -195,7 +194,6 @@ PPN_HD int clamp_tet(const TetState<T>& st, const T* W, T Vol, T mu, T lam, T ep
 #pragma unroll
   for (int j = 0; j < 3; ++j) matvec3(st.C, l[j], cl[j]);
 
-  T A[45];
 #pragma unroll
   for (int j = 0; j < 3; ++j)
 #pragma unroll
@@ -208,17 +206,24 @@ PPN_HD int clamp_tet(const TetState<T>& st, const T* W, T Vol, T mu, T lam, T ep
         for (int k = 0; k < 3; ++k)
           if (3 * j + i <= 3 * m + k) A[s9(3 * j + i, 3 * m + k)] = blk[3 * i + k];
     }
-  T Vec[81];
-  jacobi9(A, Vec);
-
   // S_aj = (L^-1 dN_a)_j by forward substitution
-  T S[4][3];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     S[a][0] = dN[a][0] / L00;
     S[a][1] = (dN[a][1] - L10 * S[a][0]) / L11;
     S[a][2] = (dN[a][2] - L20 * S[a][0] - L21 * S[a][1]) / L22;
   }
+}
+
+// dH blocks (10 x 9, upper block triangle, tri4 order) of the clamped tet.
+// Returns the number of clamped eigenvalues of M (the three translation modes are
+// always clamped as well).
+template <typename T>
+PPN_HD int clamp_tet(const TetState<T>& st, const T* W, T Vol, T mu, T lam, T eps, bool mirror, T* out) {
+  T A[45], S[4][3];
+  reduce9(st, W, Vol, mu, lam, A, S);
+  T Vec[81];
+  jacobi9(A, Vec);
   const T e4 = eps * (T)0.25;
 #pragma unroll
   for (int b = 0; b < 10; ++b)

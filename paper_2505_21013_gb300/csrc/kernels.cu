@@ -18,6 +18,8 @@
 //   k_energy    per tet and per vertex: incremental potential at u + gamma dx
 //               and g^T dx, FP64 sums (line search, Sec. 5.1)
 //   small vector kernels: predictor, position update, velocity, fallback direction
+#include <cstdlib>
+
 #include "common.cuh"
 #include "contact.cuh"
 #include "eigclamp.cuh"
@@ -507,6 +509,197 @@ __global__ void __launch_bounds__(PROJ_CTA) k_project(const SceneDev<T>* scenes,
   for (int k = 0; k < 90; ++k) dst[k] = out[k];
 }
 
+// K5, warp form, for the few hundred to few thousand tets of a PPN selection round,
+// where one thread per tet leaves the launch as long as one thread's serial Jacobi.
+// Three tets per warp, nine lanes per tet (lanes 27..31 idle): lane 9 g + i holds
+// row i of tet g's reduced matrix M and row i of its eigenvector matrix.  The four
+// rotations of a round-robin round (disjoint pairs) go at once: the lane of each
+// pair's first index forms its rotation as the one-thread form does, every lane
+// rotates the four column pairs of its rows of M and of the eigenvectors, each row of
+// a pair then combines with its partner row (fetched by shuffle), and the pair's 2x2
+// block is set as in the one-thread form (diagonal app - t apq and aqq + t apq,
+// off-diagonal 0).  Sweeps stop per tet at the one-thread form's test.  The clamped
+// update, the sum over clamped eigenpairs of w q q^T plus eps/4 I per block, is
+// formed by lane i for block i of the upper block triangle and entry i of block 9.
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ T wsel(const T* a, int idx) {  // a[idx] for a lane-varying idx, in registers
+  T x = a[0];
+#pragma unroll
+  for (int c = 1; c < 9; ++c) x = c == idx ? a[c] : x;
+  return x;
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void wround(T* a, T* v, int i, int base, bool done) {
+  constexpr int p0 = rr_p(R, 0), q0 = rr_q(R, 0), p1 = rr_p(R, 1), q1 = rr_q(R, 1);
+  constexpr int p2 = rr_p(R, 2), q2 = rr_q(R, 2), p3 = rr_p(R, 3), q3 = rr_q(R, 3);
+  const int mate = rr_mate(R, i);  // (index R meets itself: it sits the round out)
+  const bool first = i < mate;
+  const T dii = wsel(a, i), dim = wsel(a, mate);
+  const T dmm = __shfl_sync(kFull, dii, base + mate);
+  // the pair's rotation, formed by its first lane (jrot_params on (i, mate))
+  const bool skip = done || !first || dim == (T)0;
+  const T apq = skip ? (T)1 : dim;
+  const T tau = (dmm - dii) / ((T)2 * apq);
+  const T at = tau < (T)0 ? -tau : tau;
+  T t = at > JacobiCfg<T>::big_tau ? (T)0.5 / at : (T)1 / (at + sqrt((T)1 + at * at));
+  if (tau < (T)0) t = -t;
+  if (skip) t = (T)0;
+  const T cs = rsqrt_t<T>((T)1 + t * t);
+  const T c = skip ? (T)1 : cs, s = skip ? (T)0 : t * cs;
+  // the four rotations for the column pairs, from their first lanes
+  const T c0 = __shfl_sync(kFull, c, base + p0), s0 = __shfl_sync(kFull, s, base + p0);
+  const T c1 = __shfl_sync(kFull, c, base + p1), s1 = __shfl_sync(kFull, s, base + p1);
+  const T c2 = __shfl_sync(kFull, c, base + p2), s2 = __shfl_sync(kFull, s, base + p2);
+  const T c3 = __shfl_sync(kFull, c, base + p3), s3 = __shfl_sync(kFull, s, base + p3);
+  // this lane's own pair, from its first lane
+  const int src = base + (first ? i : mate);
+  const T tm = __shfl_sync(kFull, t, src), cm = __shfl_sync(kFull, c, src), sm = __shfl_sync(kFull, s, src);
+  const T apqm = __shfl_sync(kFull, dim, src);
+  const int rot = __shfl_sync(kFull, (int)!skip, src);
+  auto colrot = [&](T* m, int P, int Q, T cc, T ss) {
+    const T mp = m[P], mq = m[Q];
+    m[P] = cc * mp - ss * mq;
+    m[Q] = ss * mp + cc * mq;
+  };
+  colrot(a, p0, q0, c0, s0);
+  colrot(a, p1, q1, c1, s1);
+  colrot(a, p2, q2, c2, s2);
+  colrot(a, p3, q3, c3, s3);
+  colrot(v, p0, q0, c0, s0);
+  colrot(v, p1, q1, c1, s1);
+  colrot(v, p2, q2, c2, s2);
+  colrot(v, p3, q3, c3, s3);
+  T b[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) b[k] = __shfl_sync(kFull, a[k], base + mate);
+  const T nd = first ? dii - tm * apqm : dii + tm * apqm;
+  if (rot) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const T r = first ? cm * a[k] - sm * b[k] : sm * b[k] + cm * a[k];
+      a[k] = k == i ? nd : k == mate ? (T)0 : r;
+    }
+  }
+}
+
+template <typename T, int R>
+struct WRounds {
+  __device__ __forceinline__ static void run(T* a, T* v, int i, int base, bool done) {
+    wround<T, R>(a, v, i, base, done);
+    if constexpr (R < 8) WRounds<T, R + 1>::run(a, v, i, base, done);
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(PROJW_CTA) k_project_w(const SceneDev<T>* scenes, const TileRef* tiles,
+                                                         int use_probe) {
+  const TileRef tr = tiles[blockIdx.x];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  const int lane = threadIdx.x & 31;
+  const int wt = 3 * (tr.tile * (PROJW_CTA / 32) + (int)(threadIdx.x >> 5));  // the warp's first tet
+  const int n = S.ctl->n_new;
+  if (wt >= n) return;  // warp-uniform
+  const int grp = lane < 27 ? lane / 9 : 3;
+  const int i = lane < 27 ? lane - 9 * grp : 0;
+  const int base = lane < 27 ? 9 * grp : 0;  // (idle lanes read tet 0's lanes; their results are dropped)
+  const bool live = grp < 3 && wt + grp < n;
+  const int e = live ? S.sel_list[wt + grp] : 0;
+  T A[45], Sl[4][3];
+  {
+    const int4 tt = S.tets[e];
+    const double4* U = use_probe ? S.u_probe : S.u;
+    double u[4][3];
+    load_u(U, tt.x, u[0]);
+    load_u(U, tt.y, u[1]);
+    load_u(U, tt.z, u[2]);
+    load_u(U, tt.w, u[3]);
+    T W[9], V, mu, lam;
+    load_tetc(S.tetc, e, W, V, mu, lam);
+    T H[9];
+    disp_grad(u[0], u[1], u[2], u[3], W, H);
+    TetState<T> st;
+    tet_state(H, mu, lam, st);
+    reduce9(st, W, V, mu, lam, A, Sl);
+  }
+  T a[9], v[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    T x = A[s9(0, c)];
+#pragma unroll
+    for (int r = 1; r < 9; ++r) x = r == i ? A[s9(r, c)] : x;
+    a[c] = live ? x : (T)0;
+    v[c] = c == i ? (T)1 : (T)0;
+  }
+  // sums over a tet's nine lanes, in lane order (the same value on each)
+  auto gsum = [&](T x) {
+    T s = (T)0;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) s += __shfl_sync(kFull, x, base + r);
+    return s;
+  };
+  T f = (T)0, o = (T)0;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) f += a[c] * a[c];
+  const T tol2 = JacobiCfg<T>::rel_tol * JacobiCfg<T>::rel_tol * gsum(f);
+  bool done = !live;
+  for (int sweep = 0; sweep < JacobiCfg<T>::max_sweeps; ++sweep) {
+    o = (T)0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) o += c == i ? (T)0 : a[c] * a[c];
+    const T off2 = gsum(o);  // (every lane takes part in the shuffles, done or not)
+    done = done || !(off2 > tol2);
+    if (__all_sync(kFull, done)) break;
+    WRounds<T, 0>::run(a, v, i, base, done);
+  }
+  // clamping weights (lane i: eigenvalue i), and this lane's output entries
+  const T li = wsel(a, i), eps = (T)S.eig_eps;
+  const bool mirror = S.proj_kind == 1;
+  const T wi = li < eps ? (mirror ? (-li > eps ? -li : eps) : eps) - li : (T)0;
+  const T e4 = eps * (T)0.25;
+  const int ba = (i >= 4) + (i >= 7), bb = i < 4 ? i : i < 7 ? i - 3 : i - 5;  // block i = (ba, bb)
+  const int r9 = i / 3, c9 = i - 3 * r9;                                          // entry i of block 9 = (3, 3)
+  T acc[9], acc9 = r9 == c9 ? e4 : (T)0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = (k == 0 || k == 4 || k == 8) ? e4 : (T)0;
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const T wp = __shfl_sync(kFull, wi, base + p);
+    T col[9];  // eigenvector p: column p of the eigenvector matrix, one row per lane
+#pragma unroll
+    for (int r = 0; r < 9; ++r) col[r] = __shfl_sync(kFull, v[p], base + r);
+    if (wp != (T)0) {
+      T q[4][3];
+#pragma unroll
+      for (int aa = 0; aa < 4; ++aa)
+#pragma unroll
+        for (int ii = 0; ii < 3; ++ii)
+          q[aa][ii] = Sl[aa][0] * col[ii] + Sl[aa][1] * col[3 + ii] + Sl[aa][2] * col[6 + ii];
+      T qa[3], qb[3];
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii) {
+        qa[ii] = ba == 0 ? q[0][ii] : ba == 1 ? q[1][ii] : q[2][ii];
+        qb[ii] = bb == 0 ? q[0][ii] : bb == 1 ? q[1][ii] : bb == 2 ? q[2][ii] : q[3][ii];
+      }
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc[3 * ii + k] += wp * qa[ii] * qb[k];
+      const T q3r = r9 == 0 ? q[3][0] : r9 == 1 ? q[3][1] : q[3][2];
+      const T q3c = c9 == 0 ? q[3][0] : c9 == 1 ? q[3][1] : q[3][2];
+      acc9 += wp * q3r * q3c;
+    }
+  }
+  if (!live) return;
+  T* dst = S.dH + (size_t)e * HE_STRIDE;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) dst[9 * i + k] = acc[k];
+  dst[81 + i] = acc9;
+}
+
 // ------------------------------------------------------ contact elements
 // Selection and clamping of contact elements (one per free vertex within dhat
 // of an obstacle): key ||g_v||_inf > delta (or delta <= eps_delta; delta < 0:
@@ -863,9 +1056,15 @@ template <typename T>
 void launch_select(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
   if (n) k_select<T><<<n, TILE, 0, st>>>(s, t);
 }
+bool project_warp_form(bool selection_round) {
+  if (std::getenv("PPN_PROJECT_THREAD")) return false;
+  if (std::getenv("PPN_PROJECT_WARP")) return true;
+  return selection_round;
+}
 template <typename T>
-void launch_project(const SceneDev<T>* s, const TileRef* t, int n, int probe, cudaStream_t st) {
-  if (n) k_project<T><<<n, PROJ_CTA, 0, st>>>(s, t, probe);
+void launch_project(const SceneDev<T>* s, const TileRef* t, int n, int probe, cudaStream_t st, int warp) {
+  if (n && warp) k_project_w<T><<<n, PROJW_CTA, 0, st>>>(s, t, probe);
+  else if (n) k_project<T><<<n, PROJ_CTA, 0, st>>>(s, t, probe);
 }
 template <typename T>
 void launch_energy(const SceneDev<T>* s, const TileRef* t, int n, int probe, cudaStream_t st) {
@@ -908,7 +1107,7 @@ void launch_fallback(const SceneDev<T>* s, const TileRef* t, int n, int kind, cu
   template void launch_update<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \
   template void launch_update_touched<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \
   template void launch_select<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \
-  template void launch_project<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
+  template void launch_project<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t, int); \
   template void launch_energy<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);  \
   template void launch_predict<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \
   template void launch_dirderiv<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \

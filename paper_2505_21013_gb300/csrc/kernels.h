@@ -8,6 +8,8 @@
 namespace ppn {
 
 constexpr int PROJ_CTA = 128;  // threads per CTA of the projection kernel (register heavy)
+constexpr int PROJW_CTA = 128;  // threads per CTA of its warp form: 4 warps of 3 tets
+constexpr int PROJW_TETS = 3 * PROJW_CTA / 32;  // tets per CTA of the warp form
 
 template <typename T> void launch_element(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
 template <typename T> void launch_gradient(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
@@ -17,7 +19,11 @@ template <typename T> void launch_update(const SceneDev<T>*, const TileRef*, int
 // (16 x the selection's count); the scene's ctl->n_touched must be zero before the launch
 template <typename T> void launch_update_touched(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
 template <typename T> void launch_select(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
-template <typename T> void launch_project(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
+// warp != 0: the warp form (tiles of PROJW_TETS selected tets), else one thread per tet (tiles of PROJ_CTA)
+template <typename T> void launch_project(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t, int warp);
+// the projection form for a selection round (true) or a pass over every element (false),
+// unless PPN_PROJECT_THREAD=1 or PPN_PROJECT_WARP=1 fixes it
+bool project_warp_form(bool selection_round);
 template <typename T> void launch_energy(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
 template <typename T> void launch_predict(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
 // g^T dx and max |dx| over the free vertices (vertex tiles) into ctl->energy[1], [2]

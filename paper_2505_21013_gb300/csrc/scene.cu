@@ -721,11 +721,13 @@ static ppn_status probe_clamp_list(SceneImpl<T>& s, Probe<T>& p, const std::vect
   PPN_CU(cudaMemcpy(s.d.sel_list, sel.data(), sizeof(int) * sel.size(), cudaMemcpyHostToDevice));
   const int n = (int)sel.size();
   PPN_CU(cudaMemcpy(&p.G->d_ctl[0].n_new, &n, sizeof(int), cudaMemcpyHostToDevice));
+  const bool warp = project_warp_form(true);  // as a PPN selection round
+  const int per = warp ? PROJW_TETS : PROJ_CTA;
   std::vector<TileRef> jt;
-  for (int t = 0; t < (n + PROJ_CTA - 1) / PROJ_CTA; ++t) jt.push_back({0, t});
+  for (int t = 0; t < (n + per - 1) / per; ++t) jt.push_back({0, t});
   ppn_status rc = p.G->upload(p.G->d_projtiles, jt.data(), sizeof(TileRef) * jt.size());
   if (rc) return rc;
-  launch_project<T>(p.G->d_desc, p.G->d_projtiles, (int)jt.size(), 1, s.stream);
+  launch_project<T>(p.G->d_desc, p.G->d_projtiles, (int)jt.size(), 1, s.stream, warp);
   PPN_CU(cudaGetLastError());
   PPN_CU(cudaStreamSynchronize(s.stream));
   return PPN_OK;

@@ -118,9 +118,13 @@ def test_selection_is_exact_with_ties():
     assert not sel[5]
 
 
+@pytest.mark.parametrize("form", ["warp", "thread"])
 @pytest.mark.parametrize("mirror", [False, True])
 @pytest.mark.parametrize("prec", PRECS)
-def test_projection_updates(prec, mirror):
+def test_projection_updates(prec, mirror, form, monkeypatch):
+    # both forms of the clamping kernel: nine lanes per tet (PPN's selection rounds)
+    # and one thread per tet (PN's passes over every element)
+    monkeypatch.setenv("PPN_PROJECT_THREAD" if form == "thread" else "PPN_PROJECT_WARP", "1")
     spec = medium_spec(12)
     g, o = scene_pair(spec, prec, mirror)
     x = deformed(spec, 13, amp=1.0)
