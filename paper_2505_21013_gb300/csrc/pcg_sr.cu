@@ -662,13 +662,10 @@ __global__ void __launch_bounds__(NTP, 1)
         }
       }
 #pragma unroll
-      for (int o = 16; o >= 32 / GP; o >>= 1) {  // the row's lanes, 32 / GP apart: lane 0 + lane 1
-        ax += __shfl_down_sync(0xffffffffu, ax, o);
-        ay += __shfl_down_sync(0xffffffffu, ay, o);
-        az += __shfl_down_sync(0xffffffffu, az, o);
-      }
-      // w of the row, and its terms of gamma = r.u, delta = w.u, rho = r.r
-      float g = 0.f, d = 0.f, rr = 0.f;
+      // the row's w in both of its lanes (lane 0 + lane 1, and lane 1 + lane 0: the same bits)
+      ax += __shfl_xor_sync(0xffffffffu, ax, 16);
+      ay += __shfl_xor_sync(0xffffffffu, ay, 16);
+      az += __shfl_xor_sync(0xffffffffu, az, 16);
       if (lane == 0 && item < n_items) {
         if constexpr (GV) {
           if (i >= 0) st_f4(reinterpret_cast<float*>(sl[slot].q + i), ax, ay, az);
@@ -679,7 +676,11 @@ __global__ void __launch_bounds__(NTP, 1)
           L.lw[3 * item + 1] = ay;
           L.lw[3 * item + 2] = az;
         }
-        if (i >= 0 && !st[slot].done) {
+      }
+      // the row's terms: gamma = r.u and rho = r.r in its first lane, delta = w.u in its second
+      float x = 0.f, rr = 0.f;
+      if (item < n_items && i >= 0 && !st[slot].done) {
+        if (lane == 0) {
           float r[3], u[3];
           if constexpr (GV) {
             const float4 rv = ld_f4_cg(reinterpret_cast<const float*>(sl[slot].z + i));
@@ -707,21 +708,39 @@ __global__ void __launch_bounds__(NTP, 1)
               u[c] = L.lu[3 * item + c];
             }
           }
-          g = dot3(r[0], r[1], r[2], u[0], u[1], u[2]);
-          d = dot3(ax, ay, az, u[0], u[1], u[2]);
+          x = dot3(r[0], r[1], r[2], u[0], u[1], u[2]);
           rr = dot3(r[0], r[1], r[2], r[0], r[1], r[2]);
+        } else {
+          float u[3];
+          if constexpr (GV) {
+            const float4 uv = ld_f4_cg(u_ptr(sl[slot].zrec, i));
+            u[0] = uv.x, u[1] = uv.y, u[2] = uv.z;
+          } else if constexpr (HALO) {
+            const float4 uv = L.lu4[item];
+            u[0] = uv.x, u[1] = uv.y, u[2] = uv.z;
+          } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) u[c] = L.lu[3 * item + c];
+          }
+          x = dot3(ax, ay, az, u[0], u[1], u[2]);
         }
       }
-      // per group of 16 rows (one warp of the pass), in a fixed order
-      g = warp_sum(g);
-      d = warp_sum(d);
-      rr = warp_sum(rr);
+      // per group of 16 rows (one warp of the pass), in a fixed order: the tree over the 16
+      // rows of warp_sum, lanes 0-15 for gamma and rho, lanes 16-31 for delta
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        rr += __shfl_xor_sync(0xffffffffu, rr, o);
+      }
+      const int grp = (base >> 4) + warp, lt = grp >> 3;
+      float* og = L.lws + NQ * grp;
+      if (lane32 == 16) og[1] = x;
       if (lane32 == 0) {
-        const int grp = (base >> 4) + warp, lt = grp >> 3;
-        float* o = L.lws + NQ * grp;
-        o[0] = g;
-        o[1] = d;
-        o[2] = rr;
+        og[0] = x;
+        og[2] = rr;
+      }
+      __syncwarp();  // (delta's sum, stored by lane 16, before lane 0's count)
+      if (lane32 == 0) {
         if (lt < ntl) {  // (the groups past the CTA's tiles of a one-tile CTA post nothing)
           __threadfence_block();  // the group sums before the count
           if (atomicAdd(&L.ltc[lt], 1) == 7) {
