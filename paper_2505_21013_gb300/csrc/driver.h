@@ -762,7 +762,7 @@ struct Driver {
     // ---- assembly and first solve
     G.set_active(solve_on);
     if ((rc = G.upload_desc())) return rc;
-    timed(FAM_ASSEMBLE, 0, [&] { launch_assemble<T>(G.d_desc, G.d_btiles, G.n_btiles, G.st); });
+    timed(FAM_ASSEMBLE, 0, [&] { launch_assemble<T>(G.d_desc, G.d_btiles, G.n_btiles, G.d_vtiles, G.n_vtiles, G.st); });
     if ((rc = check_launch())) return rc;
     if ((rc = solve(solve_on, 1))) return rc;
     if ((rc = G.sync_ctl())) return rc;

@@ -358,6 +358,105 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 6 : 4) k_assemble(const
   for (int q = 0; q < 9; ++q) S.val[(size_t)q * S.nnzb + k] = acc[q];
 }
 
+// Off-diagonal blocks: a thread per block sums its contributions (the block's (tet, a,
+// b) sources, a != b, in element order) one after another, the next source loaded one
+// step ahead; a contribution is formed (He, plus dH if projected) before it is added.
+// The sums run in the order of the plain per-element scatter.
+template <typename T>
+__device__ __forceinline__ void assemble_offdiag(const SceneDev<T>& S, int tile) {
+  const int k = tile * TILE + (int)threadIdx.x;
+  if (k >= S.nnzb) return;
+  const int i = S.blk_row[k], j = S.col[k];
+  if (i == j) return;  // (the diagonal blocks: assemble_diag)
+  const int it = S.it_id;
+  T acc[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) acc[q] = (T)0;
+  if (!S.fixed[i] && !S.fixed[j]) {
+    const int c0 = S.blk_ptr[k], c1 = S.blk_ptr[k + 1];
+    int src_n = c0 < c1 ? S.blk_src[c0] : 0;
+    for (int c = c0; c < c1; ++c) {
+      const int src = src_n;
+      if (c + 1 < c1) src_n = S.blk_src[c + 1];
+      const int e = src >> 4, a = (src >> 2) & 3, b = src & 3;
+      T v[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) v[q] = (T)0;
+      add_elem_block(S.He + (size_t)e * HE_STRIDE, a, b, v);
+      if (S.proj_stamp[e] == it) add_elem_block(S.dH + (size_t)e * HE_STRIDE, a, b, v);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) acc[q] += v[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q) S.val[(size_t)q * S.nnzb + k] = acc[q];
+}
+
+// Diagonal blocks: a thread per vertex i sums the blocks (a, a) of the tets incident to
+// i (the vertex -> tet incidence, in its order; the next incidence loaded one step
+// ahead), then adds the inertia (and contact) terms.  Each contribution is formed as in
+// the off-diagonal form (He, plus dH if projected) before it is added.
+template <typename T>
+__device__ __forceinline__ void assemble_diag(const SceneDev<T>& S, int tile) {
+  const int i = tile * TILE + (int)threadIdx.x;
+  if (i >= S.nv) return;
+  const int it = S.it_id;
+  const int k = S.diag_idx[i];
+  T acc[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) acc[q] = (T)0;
+  if (S.fixed[i]) {
+    acc[0] = acc[4] = acc[8] = (T)1;
+  } else {
+    const int c0 = S.vt_ptr[i], c1 = S.vt_ptr[i + 1];
+    int src_n = c0 < c1 ? S.vt_src[c0] : 0;  // the next incidence, loaded one step ahead
+    for (int c = c0; c < c1; ++c) {
+      const int src = src_n;
+      if (c + 1 < c1) src_n = S.vt_src[c + 1];
+      const int e = src >> 2, a = src & 3;
+      T v[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) v[q] = (T)0;
+      add_elem_block(S.He + (size_t)e * HE_STRIDE, a, a, v);
+      if (S.proj_stamp[e] == it) add_elem_block(S.dH + (size_t)e * HE_STRIDE, a, a, v);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) acc[q] += v[q];
+    }
+    // inertia, and the Dirichlet penalty k m / dt^2 of a constrained vertex
+    const T m = (T)(S.mass[i] * S.inv_dt2 * (S.pen_k > 0.0 && S.con[i] ? 1.0 + S.pen_k : 1.0));
+    acc[0] += m;
+    acc[4] += m;
+    acc[8] += m;
+    if (S.obs->n > 0) {  // the contact element of vertex i (Hessian from k_gradient at this iterate), and
+#pragma unroll           // its clamping if projected before assembly
+      for (int q = 0; q < 9; ++q) acc[q] += S.Hc[(size_t)9 * i + q];
+      if (S.cproj_stamp[i] == it)
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] += S.dHc[(size_t)9 * i + q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q) S.val[(size_t)q * S.nnzb + k] = acc[q];
+}
+
+// K3, element-order form (the FP64 path): blocks [0, n_btiles) of the grid take
+// BSR-block tiles (a thread per off-diagonal block), the rest vertex tiles (a thread per
+// diagonal block).  Every block sums its contributions one after another in element
+// order, the order of a plain per-element scatter, so that the FP64 matrix follows that
+// reference's rounding; the warp form above is the faster FP32 path.
+template <typename T>
+__global__ void __launch_bounds__(TILE)
+    k_assemble_seq(const SceneDev<T>* scenes, const TileRef* btiles, int n_btiles, const TileRef* vtiles) {
+  const bool off = (int)blockIdx.x < n_btiles;
+  const TileRef tr = off ? btiles[blockIdx.x] : vtiles[blockIdx.x - n_btiles];
+  const SceneDev<T>& S = scenes[tr.scene];
+  if (!S.active) return;
+  if (off)
+    assemble_offdiag(S, tr.tile);
+  else
+    assemble_diag(S, tr.tile);
+}
+
 // ----------------------------------------------------- K6 incremental update
 // dH contributions of block k from the elements selected in round rd, summed in the
 // block's contribution order; the map entries and the stamps are loaded eight at a
@@ -1038,8 +1137,13 @@ void launch_gradient(const SceneDev<T>* s, const TileRef* t, int n, int probe, c
   if (n) k_gradient<T><<<n, TILE, 0, st>>>(s, t, probe);
 }
 template <typename T>
-void launch_assemble(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st, int use_probe) {
-  if (n) k_assemble<T><<<n, TILE, 0, st>>>(s, t, use_probe);
+void launch_assemble(const SceneDev<T>* s, const TileRef* bt, int nb, const TileRef* vt, int nv, cudaStream_t st,
+                     int use_probe) {
+  if constexpr (sizeof(T) == 8) {
+    if (nb + nv) k_assemble_seq<T><<<nb + nv, TILE, 0, st>>>(s, bt, nb, vt);
+  } else {
+    if (nb) k_assemble<T><<<nb, TILE, 0, st>>>(s, bt, use_probe);
+  }
 }
 template <typename T>
 void launch_update(const SceneDev<T>* s, const TileRef* t, int n, cudaStream_t st) {
@@ -1103,7 +1207,7 @@ void launch_fallback(const SceneDev<T>* s, const TileRef* t, int n, int kind, cu
 #define PPN_INST(T)                                                                            \
   template void launch_element<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
   template void launch_gradient<T>(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t); \
-  template void launch_assemble<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t, int); \
+  template void launch_assemble<T>(const SceneDev<T>*, const TileRef*, int, const TileRef*, int, cudaStream_t, int); \
   template void launch_update<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \
   template void launch_update_touched<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t); \
   template void launch_select<T>(const SceneDev<T>*, const TileRef*, int, cudaStream_t);       \

@@ -13,7 +13,11 @@ constexpr int PROJW_TETS = 3 * PROJW_CTA / 32;  // tets per CTA of the warp form
 
 template <typename T> void launch_element(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
 template <typename T> void launch_gradient(const SceneDev<T>*, const TileRef*, int, int, cudaStream_t);
-template <typename T> void launch_assemble(const SceneDev<T>*, const TileRef*, int, cudaStream_t, int use_probe = 0);
+// FP32: the warp form over n_btiles BSR-block tiles; FP64: the element-order form, off-diagonal
+// blocks over the block tiles and diagonal blocks over n_vtiles vertex tiles
+template <typename T>
+void launch_assemble(const SceneDev<T>*, const TileRef* btiles, int n_btiles, const TileRef* vtiles, int n_vtiles,
+                     cudaStream_t, int use_probe = 0);
 template <typename T> void launch_update(const SceneDev<T>*, const TileRef*, int, cudaStream_t);
 // touched-block form: n tiles of TILE (selected element, corner pair) entries per scene
 // (16 x the selection's count); the scene's ctl->n_touched must be zero before the launch

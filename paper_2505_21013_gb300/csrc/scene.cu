@@ -752,7 +752,7 @@ static ppn_status probe_assemble(SceneImpl<T>& s, const double* x, const uint8_t
   if ((rc = probe_clamp_list(s, p, sel))) return rc;
   // the contact Hessians come from the gradient pass at the same positions
   if (s.n_obst > 0) launch_gradient<T>(p.G->d_desc, p.G->d_vtiles, p.G->n_vtiles, 1, s.stream);
-  launch_assemble<T>(p.G->d_desc, p.G->d_btiles, p.G->n_btiles, s.stream, 1);
+  launch_assemble<T>(p.G->d_desc, p.G->d_btiles, p.G->n_btiles, p.G->d_vtiles, p.G->n_vtiles, s.stream, 1);
   PPN_CU(cudaGetLastError());
   PPN_CU(cudaStreamSynchronize(s.stream));
   return read_bsr(s, vals);
