@@ -398,6 +398,9 @@ ora_scene* ora_scene_create(const double* rest, int64_t n_v, const int32_t* tets
   }
   const bool penalty = s->p.dirichlet_penalty > 0.0;
   if (penalty) s->pen.assign(n_v, -1);
+  // The Dirichlet set is a set of vertices, each with one prescribed target (Sec. 5.1's
+  // boundary conditions): an index listed twice would give a vertex two targets, which
+  // the method does not define, so it is rejected like an index out of range.
   for (int64_t f = 0; f < n_fixed; ++f) {
     if (fixed[f] < 0 || fixed[f] >= n_v || (penalty ? s->pen[fixed[f]] >= 0 : s->fixed[fixed[f]] != 0)) {
       g_err = "fixed index out of range or repeated";
