@@ -20,8 +20,9 @@
  *   - Every call returns a ppn_status; the library never aborts.  On failure
  *     ppn_last_error() (thread-local) holds a one-line reason.  Device waits
  *     inside kernels are bounded and report PPN_ERR_TIMEOUT.
- *   - A scene owns its device memory (cudaMalloc at creation, cudaFree at
- *     destruction) and runs on its own stream unless ppn_set_stream is called.
+ *   - A scene owns its device memory (cudaMalloc at creation, or the allocator
+ *     installed with ppn_set_allocator; freed at destruction) and runs on its own
+ *     stream unless ppn_set_stream is called.
  *   - Not thread-safe per scene: calls on one scene must not overlap.
  */
 #ifndef PPN_H
@@ -185,6 +186,22 @@ PPN_API ppn_status ppn_scene_get_info(const ppn_scene* s, ppn_scene_info* out);
 
 /* Use a caller stream (a cudaStream_t passed as void*); NULL = the scene's own. */
 PPN_API ppn_status ppn_set_stream(ppn_scene* s, void* cuda_stream);
+
+/* Device memory from a caller's allocator (e.g. a framework's caching allocator).
+ * By default scenes, the scene groups that step them together and servers take their
+ * device buffers from cudaMalloc.  ppn_set_allocator installs alloc_fn / free_fn for
+ * the owners created after the call; each owner keeps the allocator it was created
+ * with until it is destroyed, so the caller keeps both functions and ctx valid that
+ * long.  alloc_fn(bytes, ctx) returns device memory of the current device, aligned to
+ * at least 256 bytes, or NULL: the creation then fails with PPN_ERR_OOM (a pointer
+ * that is not 256-byte aligned is handed back to free_fn and counts as a failure).
+ * free_fn(ptr, ctx) releases a pointer alloc_fn returned; the library synchronises the
+ * owner's stream first.  Both are called from the thread that creates, steps or
+ * destroys the owner.  Both NULL restores cudaMalloc / cudaFree; exactly one NULL is
+ * PPN_ERR_INVALID_ARG.  Pinned host staging buffers are not affected. */
+typedef void* (*ppn_device_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*ppn_device_free_fn)(void* ptr, void* ctx);
+PPN_API ppn_status ppn_set_allocator(ppn_device_alloc_fn alloc_fn, ppn_device_free_fn free_fn, void* ctx);
 
 /* Dirichlet targets for the next step, n_fixed*3 doubles in the order of `fixed`. */
 PPN_API ppn_status ppn_set_kinematic_targets(ppn_scene* s, const double* xyz_of_fixed);

@@ -135,6 +135,7 @@ struct Group {
   Staging staging;
   KernelTimer* timer = nullptr;
   int pcg_grid = 0, pcg_group = 8;
+  DevAllocator dalloc = current_allocator();
   std::vector<void*> allocs;
   // capacities of the device tables (a group can be rebuilt for new members)
   size_t cap_n = 0, cap_tt = 0, cap_vt = 0, cap_bt = 0, cap_pt = 0, cap_et = 0, cap_proj = 0;
@@ -146,7 +147,7 @@ struct Group {
   void release() {
     if (st) cudaStreamSynchronize(st);
     tune_pending = false;
-    for (void* p : allocs) cudaFree(p);
+    for (void* p : allocs) dev_free(dalloc, p);
     allocs.clear();
     if (h_ctl) cudaFreeHost(h_ctl);
     if (h_bar) cudaFreeHost(h_bar);
@@ -158,8 +159,8 @@ struct Group {
   }
   template <typename X>
   X* alloc(size_t n) {
-    void* p = nullptr;
-    if (cudaMalloc(&p, std::max<size_t>(1, n) * sizeof(X)) != cudaSuccess) return nullptr;
+    void* p = dev_alloc(dalloc, std::max<size_t>(1, n) * sizeof(X));
+    if (!p) return nullptr;
     allocs.push_back(p);
     return reinterpret_cast<X*>(p);
   }
@@ -522,7 +523,7 @@ struct Driver {
             if (G.d_halo) {  // (cudaFree waits for launches that may still read it)
               const auto old = std::find(G.allocs.begin(), G.allocs.end(), (void*)G.d_halo);
               if (old != G.allocs.end()) G.allocs.erase(old);
-              cudaFree(G.d_halo);
+              dev_free(G.dalloc, G.d_halo);
             }
             G.d_halo = G.template alloc<int>(tab.size());
             G.cap_halo = G.d_halo ? tab.size() : 0;

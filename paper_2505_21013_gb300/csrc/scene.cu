@@ -121,8 +121,8 @@ template <typename T>
 template <typename X>
 X* SceneImpl<T>::alloc(size_t n) {
   if (n == 0) n = 1;
-  void* p = nullptr;
-  if (cudaMalloc(&p, n * sizeof(X)) != cudaSuccess) return nullptr;
+  void* p = dev_alloc(dalloc, n * sizeof(X));
+  if (!p) return nullptr;
   allocs.push_back(p);
   dev_bytes += n * sizeof(X);
   return reinterpret_cast<X*>(p);
@@ -131,7 +131,7 @@ X* SceneImpl<T>::alloc(size_t n) {
 template <typename T>
 SceneImpl<T>::~SceneImpl() {
   if (stream) cudaStreamSynchronize(stream);
-  for (void* p : allocs) cudaFree(p);
+  for (void* p : allocs) dev_free(dalloc, p);
   if (h_ctl) cudaFreeHost(h_ctl);
   if (ev_a) cudaEventDestroy(ev_a);
   if (ev_b) cudaEventDestroy(ev_b);
@@ -888,6 +888,18 @@ static ppn_status dispatch_c(const ppn_scene* s, F&& f) {
   return dispatch(const_cast<ppn_scene*>(s), f);
 }
 
+// the allocator ppn_set_allocator installed (cudaMalloc when none)
+namespace ppn {
+namespace {
+std::mutex g_alloc_mu;
+DevAllocator g_alloc;
+}  // namespace
+DevAllocator current_allocator() {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  return g_alloc;
+}
+}  // namespace ppn
+
 extern "C" {
 
 ppn_params ppn_default_params(void) {
@@ -985,6 +997,16 @@ ppn_status ppn_scene_get_info(const ppn_scene* s, ppn_scene_info* out) {
     out->pcg_layout = x.last_pcg_layout;
     return PPN_OK;
   });
+}
+
+ppn_status ppn_set_allocator(ppn_device_alloc_fn alloc_fn, ppn_device_free_fn free_fn, void* ctx) {
+  if ((alloc_fn == nullptr) != (free_fn == nullptr)) {
+    ppn::set_error("ppn_set_allocator: give both functions or neither");
+    return PPN_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(ppn::g_alloc_mu);
+  ppn::g_alloc = ppn::DevAllocator{alloc_fn, free_fn, alloc_fn ? ctx : nullptr};
+  return PPN_OK;
 }
 
 ppn_status ppn_set_stream(ppn_scene* s, void* cuda_stream) {

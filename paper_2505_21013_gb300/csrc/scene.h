@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <memory>
 #include <string>
 #include <vector>
@@ -14,6 +15,34 @@
 namespace ppn {
 
 void set_error(const std::string& msg);
+
+// Device memory of a scene or a scene group: cudaMalloc / cudaFree, or the allocator a
+// caller installed with ppn_set_allocator, captured by the owner at its creation.
+struct DevAllocator {
+  ppn_device_alloc_fn alloc = nullptr;
+  ppn_device_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+DevAllocator current_allocator();
+inline void* dev_alloc(const DevAllocator& a, size_t bytes) {
+  if (!a.alloc) {
+    void* p = nullptr;
+    return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+  }
+  void* p = a.alloc(bytes, a.ctx);
+  if (p && (reinterpret_cast<uintptr_t>(p) & 255u)) {  // the alignment the kernels' vector loads rely on
+    a.free(p, a.ctx);
+    return nullptr;
+  }
+  return p;
+}
+inline void dev_free(const DevAllocator& a, void* p) {
+  if (!p) return;
+  if (a.free)
+    a.free(p, a.ctx);
+  else
+    cudaFree(p);
+}
 
 // Pinned staging arena for small host->device uploads (descriptor tables,
 // tile tables).  Slots are recycled after the owning stream has been synchronized.
@@ -71,6 +100,7 @@ struct SceneImpl {
   std::vector<int64_t> h_row_ptr; // pattern (host copy for probes)
   std::vector<int> h_col;
   // device memory
+  DevAllocator dalloc = current_allocator();
   std::vector<void*> allocs;
   size_t dev_bytes = 0;
   SceneDev<T> d{};                // host mirror of the device descriptor

@@ -133,6 +133,7 @@ SIGNATURES = {
     "ppn_destroy_scene": (None, [_P]),
     "ppn_scene_get_info": (_st, [_P, C.POINTER(ppn_scene_info)]),
     "ppn_set_stream": (_st, [_P, _P]),
+    "ppn_set_allocator": (_st, [_P, _P, _P]),
     "ppn_set_kinematic_targets": (_st, [_P, _pd]),
     "ppn_set_kinematic_targets_device": (_st, [_P, _P]),
     "ppn_step": (_st, [_P, C.c_int, C.c_double, _pd, C.POINTER(ppn_step_stats)]),
@@ -474,6 +475,28 @@ def probe_halo_tables(patterns, grid: int):
     off = out[:no].reshape(grid + 1, 2)
     nb = int(off[grid, 0])
     return off, out[no:no + nb], out[no + nb:], int(mh.value)
+
+
+# ppn_device_alloc_fn / ppn_device_free_fn
+DEVICE_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+DEVICE_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+_allocator_refs = []  # the installed callbacks, kept alive while scenes may use them
+
+
+def set_allocator(alloc=None, free=None):
+    """Install alloc(bytes) -> device pointer (int, 0 on failure) and free(ptr) as the
+    device allocator of scenes, scene groups and servers created afterwards; both None
+    restores cudaMalloc / cudaFree.  Owners created earlier keep the allocator they were
+    created with, so the callbacks stay referenced here."""
+    if (alloc is None) != (free is None):
+        raise ValueError("give both alloc and free, or neither")
+    if alloc is None:
+        _check(lib().ppn_set_allocator(None, None, None), "ppn_set_allocator")
+        return
+    fa = DEVICE_ALLOC_FN(lambda n, ctx: alloc(int(n)) or None)
+    ff = DEVICE_FREE_FN(lambda p, ctx: free(int(p)))
+    _allocator_refs.append((fa, ff))
+    _check(lib().ppn_set_allocator(C.cast(fa, C.c_void_p), C.cast(ff, C.c_void_p), None), "ppn_set_allocator")
 
 
 def pcg_tuning():

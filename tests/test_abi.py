@@ -63,3 +63,19 @@ def test_invalid_arguments_are_rejected_without_a_gpu(libpath):
     assert L.ppn_probe_bounded_wait(0, 10, 0) == 1
     assert L.ppn_probe_bounded_wait(8, 0, 0) == 1
     assert L.ppn_probe_bounded_wait(8, (1 << 20) + 1, 1) == 1
+
+
+def test_allocator_arguments_are_checked_without_a_gpu(libpath):
+    import ctypes as C
+
+    from paper_2505_21013_gb300 import ppn
+
+    L = ppn.lib()
+    fa = ppn.DEVICE_ALLOC_FN(lambda n, ctx: None)
+    ff = ppn.DEVICE_FREE_FN(lambda p, ctx: None)
+    # exactly one of the two functions is an error; both or neither is accepted
+    assert L.ppn_set_allocator(C.cast(fa, C.c_void_p), None, None) == 1
+    assert L.ppn_set_allocator(None, C.cast(ff, C.c_void_p), None) == 1
+    assert L.ppn_set_allocator(C.cast(fa, C.c_void_p), C.cast(ff, C.c_void_p), None) == 0
+    assert L.ppn_set_allocator(None, None, None) == 0
+
