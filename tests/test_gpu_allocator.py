@@ -75,3 +75,29 @@ def test_misaligned_allocator_memory_is_refused():
     # the library still works on cudaMalloc afterwards
     _, xs = steps(spec, 1, P.PREC_MIXED)
     assert np.isfinite(xs[0]).all()
+
+
+def test_server_scenes_on_a_caller_allocator_give_everything_back():
+    # the server's scenes and the groups its worker builds for batches take the caller's
+    # memory, from the worker thread as well; destroying the server returns all of it
+    specs = [twisting_beam_scene(4, 4, 10, h=0.02, E=1e5, nu=0.45, omega=20.0, dt=1 / 30, seed=s) for s in (1, 2)]
+    ref = []
+    for spec in specs:
+        sc, xs = steps(spec, 1, P.PREC_MIXED)
+        ref.append(xs[0])
+        sc.close()
+    blocks = TorchBlocks()
+    ppn.set_allocator(blocks.alloc, blocks.free)
+    try:
+        srv = P.Server(precision=P.PREC_MIXED, max_batch=2)
+        ids = [srv.add_scene(spec) for spec in specs]
+        tickets = [srv.submit(sid, P.MODE_PPN, 1e-4, spec.targets_at(0)) for sid, spec in zip(ids, specs)]
+        for sid, t, x_ref in zip(ids, tickets, ref):
+            done, rc, x, _, _ = srv.poll(t, sid)
+            assert done and rc == 0
+            disp = np.abs(x_ref - specs[ids.index(sid)].rest).max()
+            assert np.abs(x - x_ref).max() <= 1e-6 * disp  # (the serving tests' bound for a scene in a mix)
+        srv.close()
+    finally:
+        ppn.set_allocator(None, None)
+    assert blocks.n_alloc > 0 and not blocks.out and blocks.n_free == blocks.n_alloc
