@@ -273,7 +273,10 @@ __global__ void __launch_bounds__(NTP, 1)
   constexpr int MS = HALO ? HALO_MAX_SCENES : PCG_MAX_SCENES;  // scenes of one launch
   constexpr int GP = SP_GP;             // lanes per BSR row in the SpMV
   constexpr int RPP = NTP / GP;         // rows per SpMV pass
-  constexpr int U = 16 / GP;            // blocks per lane per gather round
+  // blocks per lane per gather round: from shared memory four (more in flight lengthen the
+  // register-bound loop: 4.73 against 4.58 us per CG iteration on the beam), from global
+  // memory eight (the streamed SpMV waits on memory latency)
+  constexpr int U = RES ? 8 / GP : 16 / GP;
   constexpr int NW = NTP / 32;          // warps
   static_assert(RPP % PCG_TILE == 0 && NTP % PCG_TILE == 0, "passes cover whole tiles");
   static_assert(MS <= NTP, "one thread per scene in the scalar step");
