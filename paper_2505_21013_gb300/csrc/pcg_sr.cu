@@ -444,8 +444,8 @@ __global__ void __launch_bounds__(NTP, 1)
   // tile words: quantity k of a tile in parity buffer par is
   // pword[((par * NQ + k) * n_ptiles + tile) * pword_stride(n_ptiles)]
   // SR_HALO: w of the halo rows hb, hb + dh, ... (stamp s, buffer par) into their u slots,
-  // which the SpMV has finished reading; two rows at a time, both rows' loads in flight
-  // before the first is waited for
+  // which the SpMV has finished reading; one row at a time (two rows' loads in flight
+  // measured slower in this register-bound kernel)
   auto halo_w = [&](int hb, int dh, unsigned s, int par) {
     auto rec = [&](int h, int& slot, int& row) -> const unsigned long long* {
       const int ref = L.href[h];
@@ -470,27 +470,15 @@ __global__ void __launch_bounds__(NTP, 1)
         w[2] = ld_relaxed_u64(wr + 2);
       }
     };
-    for (int h = hb; h < nh; h += 2 * dh) {
-      const int h2 = h + dh;
-      int sa, ra, sb = 0, rb = 0;
+    for (int h = hb; h < nh; h += dh) {
+      int sa, ra;
       const unsigned long long* wa = rec(h, sa, ra);
-      const unsigned long long* wb = h2 < nh ? rec(h2, sb, rb) : nullptr;
-      unsigned long long a[3], b[3];
+      unsigned long long a[3];
       if (wa) {
         ld_relaxed_v2_u64(wa, a[0], a[1]);
         a[2] = ld_relaxed_u64(wa + 2);
-      }
-      if (wb) {
-        ld_relaxed_v2_u64(wb, b[0], b[1]);
-        b[2] = ld_relaxed_u64(wb + 2);
-      }
-      if (wa) {
         wait(wa, a, sa, ra);
         L.lu4[n_items + h] = make_float4(W::join(a), W::join(a + 1), W::join(a + 2), 0.0f);
-      }
-      if (wb) {
-        wait(wb, b, sb, rb);
-        L.lu4[n_items + h2] = make_float4(W::join(b), W::join(b + 1), W::join(b + 2), 0.0f);
       }
     }
   };
