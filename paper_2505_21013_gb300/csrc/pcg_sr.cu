@@ -465,7 +465,6 @@ __global__ void __launch_bounds__(NTP, 1)
           }
           break;
         }
-        if (spins > 0) __nanosleep(32);  // a row not ready at the second look: back off a little
         ld_relaxed_v2_u64(wr, w[0], w[1]);
         w[2] = ld_relaxed_u64(wr + 2);
       }
