@@ -469,6 +469,7 @@ __global__ void __launch_bounds__(NTP, 1)
         w[2] = ld_relaxed_u64(wr + 2);
       }
     };
+#pragma unroll 1
     for (int h = hb; h < nh; h += dh) {
       int sa, ra;
       const unsigned long long* wa = rec(h, sa, ra);
@@ -978,7 +979,9 @@ __global__ void __launch_bounds__(NTP, 1)
     }
     // SR_HALO: the halo rows repeat their owners' s, r and u updates with the owners' w
     if constexpr (HALO) {
-      // every load of a row issued before its arithmetic (the arrays do not alias)
+      // every load of a row issued before its arithmetic (the arrays do not alias); the loop
+      // is kept rolled (unrolled it measured 1 % slower in this register-bound kernel)
+#pragma unroll 1
       for (int h = tid; h < nh; h += NTP) {
         const int slot = L.href[h] >> HALO_ROW_BITS;
         if (st[slot].done) continue;
