@@ -305,8 +305,16 @@ class Scene:
         _check(lib().ppn_set_kinematic_targets_device(self._h, C.c_void_p(ptr)),
                "ppn_set_kinematic_targets_device")
 
-    def step(self, mode: int, tol: float, want_x: bool = True, raise_on=(PPN_OK, 6, 5)):
-        out = np.zeros((self.n_verts, 3)) if want_x else None
+    def step(self, mode: int, tol: float, want_x: bool = True, raise_on=(PPN_OK, 6, 5), out=None):
+        """ppn_step.  The positions go into `out` when given (a C-contiguous float64
+        (n_verts, 3) array, for example in pinned host memory), else into a new array
+        when want_x."""
+        if out is not None:
+            if out.dtype != np.float64 or out.shape != (self.n_verts, 3) or not out.flags.c_contiguous:
+                raise ValueError("out must be a C-contiguous float64 array of shape (n_verts, 3)")
+            want_x = True
+        elif want_x:
+            out = np.zeros((self.n_verts, 3))
         st = ppn_step_stats()
         rc = lib().ppn_step(self._h, int(mode), float(tol), _d(out) if want_x else None, C.byref(st))
         _check(rc, "ppn_step", ok=raise_on)

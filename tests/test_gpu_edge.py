@@ -72,3 +72,27 @@ def test_fully_constrained_body_has_nothing_to_solve(prec):
     assert np.array_equal(xo, tg)
     assert np.abs(x - tg).max() <= 1e-14  # x = X + (t - X) on the GPU: within an ulp of t
     assert st["newton_iters"] == sto["newton_iters"] == 0
+
+
+def test_step_writes_positions_into_a_caller_buffer():
+    # Scene.step(out=...) fills a caller's C-contiguous float64 (n_verts, 3) buffer, here in
+    # pinned host memory as the benchmark's end-to-end loop uses it, with the same bits as the
+    # default path; a buffer of the wrong shape, type or layout is refused before the call
+    torch = pytest.importorskip("torch")
+    spec = tiny_scene(cells=(2, 2, 3), seed=7)
+    a = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
+    b = P.Scene.from_spec(spec, precision=P.PREC_MIXED)
+    pinned = torch.empty((spec.n_verts, 3), dtype=torch.float64).pin_memory()
+    out = pinned.numpy()
+    for n in range(2):
+        a.set_targets(spec.targets_at(n))
+        b.set_targets(spec.targets_at(n))
+        rca, xa, _ = a.step(P.MODE_PPN, 1e-6)
+        rcb, xb, _ = b.step(P.MODE_PPN, 1e-6, out=out)
+        assert rca == rcb == 0
+        assert xb is out
+        assert np.array_equal(xa, out)
+    for bad in (np.zeros((spec.n_verts, 3), np.float32), np.zeros((spec.n_verts + 1, 3)),
+                np.zeros((3, spec.n_verts)).T):
+        with pytest.raises(ValueError):
+            b.step(P.MODE_PPN, 1e-6, out=bad)
