@@ -263,12 +263,15 @@ __device__ __forceinline__ void sr_step(SState<float>& s, float gam, float del, 
 
 size_t pcg_sr_smem_bytes(int ni, int nb, int nh, int mode) { return carve_sr(nullptr, ni, nb, nh, mode, nullptr); }
 
-template <int MODE>
+template <int MODE, bool ONE>
 __global__ void __launch_bounds__(NTP, 1)
     k_pcg_sr(const SceneDev<float>* scenes, const TileRef* tiles, int n_tiles, const int* scene_ids,
-               int n_scenes, GridBar* bar, int b_from_g, int nb_cap, unsigned long long* flags,
+               int n_scenes_arg, GridBar* bar, int b_from_g, int nb_cap, unsigned long long* flags,
                const int* halo_off, const int* halo_col, const int* halo_ref, int nh_cap, int l2_keep) {
   using W = Words<float>;
+  // ONE: a launch of a single scene, whose slot is 0 and which never finishes while another
+  // scene runs on (no progress-flag wait); the same operations in the same order
+  const int n_scenes = ONE ? 1 : n_scenes_arg;
   constexpr bool HALO = MODE == SR_HALO, RES = MODE == SR_RES || HALO, GV = MODE == SR_GLOBAL;
   constexpr int MS = HALO ? HALO_MAX_SCENES : PCG_MAX_SCENES;  // scenes of one launch
   constexpr int GP = SP_GP;             // lanes per BSR row in the SpMV
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(NTP, 1)
   // row of a local item (-1: past the scene's last row) and its slot
   auto row_of = [&](int item, int& slot) -> int {
     const TileRef tr = L.ltt[item / PCG_TILE];
-    slot = tr.scene;
+    slot = ONE ? 0 : tr.scene;
     const int i = tr.tile * PCG_TILE + item % PCG_TILE;
     return i < sl[slot].nv ? i : -1;
   };
@@ -449,7 +452,7 @@ __global__ void __launch_bounds__(NTP, 1)
   auto halo_w = [&](int hb, int dh, unsigned s, int par) {
     auto rec = [&](int h, int& slot, int& row) -> const unsigned long long* {
       const int ref = L.href[h];
-      slot = ref >> HALO_ROW_BITS;
+      slot = ONE ? 0 : ref >> HALO_ROW_BITS;
       row = ref & ((1 << HALO_ROW_BITS) - 1);
       if (st[slot].done) return nullptr;
       return reinterpret_cast<const unsigned long long*>(sl[slot].zrec) + ((size_t)par * sl[slot].nv + row) * 4;
@@ -497,14 +500,16 @@ __global__ void __launch_bounds__(NTP, 1)
     }
     for (int x = warp; x < npw; x += NW) {
       if (x == npw - 1) {
-        bool any_done = false;
-        for (int si = 0; si < n_scenes; ++si) any_done |= st[si].done != 0;
-        if (any_done)
-          PPN_WARP_WAIT_STAMPS(flags, 0, grid - 1, (unsigned long long)s, kWaitSpins, lane32,
-                               *(volatile int*)&s_to, s_to = s_to ? s_to : 4);
+        if constexpr (!ONE) {
+          bool any_done = false;
+          for (int si = 0; si < n_scenes; ++si) any_done |= st[si].done != 0;
+          if (any_done)
+            PPN_WARP_WAIT_STAMPS(flags, 0, grid - 1, (unsigned long long)s, kWaitSpins, lane32,
+                                 *(volatile int*)&s_to, s_to = s_to ? s_to : 4);
+        }
         continue;
       }
-      const int si = x / nq, q = x % nq;
+      const int si = ONE ? 0 : x / nq, q = ONE ? x : x % nq;
       if (st[si].done) continue;  // warp-uniform
       const SceneLite<float>& S = sl[si];
       const int n = S.n_ptiles;
@@ -578,8 +583,9 @@ __global__ void __launch_bounds__(NTP, 1)
   // 16-row group sums, posted as stamped words
   auto post_tile = [&](int lt, unsigned s, int par, int nq) {
     const TileRef tr = L.ltt[lt];
-    const SceneLite<float>& S = sl[tr.scene];
-    if (st[tr.scene].done) return;
+    const int sc = ONE ? 0 : tr.scene;
+    const SceneLite<float>& S = sl[sc];
+    if (st[sc].done) return;
     const float* w = L.lws + NQ * 8 * lt;
     const size_t ws = (size_t)pword_stride(S.n_ptiles);
     unsigned long long* wbase = S.pword + ((size_t)par * NQ * S.n_ptiles + tr.tile) * ws;
@@ -865,7 +871,7 @@ __global__ void __launch_bounds__(NTP, 1)
     for (int h = tid; h < nh; h += NTP) {
       const int ref = halo_ref[h0 + h];
       L.href[h] = ref;
-      const SceneLite<float>& S = sl[ref >> HALO_ROW_BITS];
+      const SceneLite<float>& S = sl[ONE ? 0 : ref >> HALO_ROW_BITS];
       const int i = ref & ((1 << HALO_ROW_BITS) - 1);
       float D[9], Pm[9], r[3], u[3];
 #pragma unroll
@@ -983,7 +989,7 @@ __global__ void __launch_bounds__(NTP, 1)
       // is kept rolled (unrolled it measured 1 % slower in this register-bound kernel)
 #pragma unroll 1
       for (int h = tid; h < nh; h += NTP) {
-        const int slot = L.href[h] >> HALO_ROW_BITS;
+        const int slot = ONE ? 0 : L.href[h] >> HALO_ROW_BITS;
         if (st[slot].done) continue;
         const float a = st[slot].alpha, b = st[slot].beta;
         const float4 wv = L.lu4[n_items + h];
@@ -1048,17 +1054,24 @@ cudaError_t launch_wait_probe(const unsigned long long* w, int n, unsigned long 
   return cudaGetLastError();
 }
 
-static const void* sr_kernel(int mode) {
+// The kernel of a layout; `one`: a launch of a single scene.  The single-scene forms of
+// the layouts without the halo drop the per-scene indexing of their SpMV and update
+// (press, global layout, same-box A/B: 50.1 -> 45.5 us per CG iteration, the same bits).
+// The halo layout keeps one form: its single-scene form measured 4.48 -> 4.66 us on the
+// beam, where the compiler schedules the register-resident rows differently.
+static const void* sr_kernel(int mode, bool one) {
   switch (mode) {
-    case SR_RES: return (const void*)k_pcg_sr<SR_RES>;
-    case SR_STREAM: return (const void*)k_pcg_sr<SR_STREAM>;
-    case SR_GLOBAL: return (const void*)k_pcg_sr<SR_GLOBAL>;
-    default: return (const void*)k_pcg_sr<SR_HALO>;
+    case SR_RES: return one ? (const void*)k_pcg_sr<SR_RES, true> : (const void*)k_pcg_sr<SR_RES, false>;
+    case SR_STREAM: return one ? (const void*)k_pcg_sr<SR_STREAM, true> : (const void*)k_pcg_sr<SR_STREAM, false>;
+    case SR_GLOBAL: return one ? (const void*)k_pcg_sr<SR_GLOBAL, true> : (const void*)k_pcg_sr<SR_GLOBAL, false>;
+    default: return (const void*)k_pcg_sr<SR_HALO, false>;
   }
 }
 
 int pcg_sr_max_grid(int device, size_t smem, int mode) {
-  const void* k = sr_kernel(mode);
+  // (the multi-scene form; the single-scene forms use no more registers or shared memory, so the
+  // same one CTA per SM is co-resident, and the launch sets its own kernel's attribute)
+  const void* k = sr_kernel(mode, false);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -1110,7 +1123,7 @@ cudaError_t launch_pcg_sr(const SceneDev<float>* scenes, const PcgLaunch& L, cud
   void* args[] = {(void*)&scenes, (void*)&tiles, (void*)&n_tiles, (void*)&ids,   (void*)&n_scenes,
                   (void*)&bar,    (void*)&bg,    (void*)&nb_cap,  (void*)&flags, (void*)&h_off,
                   (void*)&h_col,  (void*)&h_ref, (void*)&nh_cap, (void*)&l2_keep};
-  const void* k = sr_kernel(L.sr_mode);
+  const void* k = sr_kernel(L.sr_mode, L.n_scenes == 1);
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(k, dim3(L.grid), dim3(NTP), args, L.smem_bytes, st);
